@@ -321,3 +321,88 @@ def test_batch_matches_single_calls():
             assert res[k][p] == r[k]
         assert oracle.decode_cigar(cg[p, : r["cigar_len"]]) == r["cigar"]
         assert (cm[cmoff[p]: cmoff[p] + tlen[p]] == r["colmax"]).all()
+
+
+def _all_strings(A, max_len):
+    out = [[]]
+    for L in range(1, max_len + 1):
+        for k in range(A ** L):
+            s, v = [], k
+            for _ in range(L):
+                s.append(v % A)
+                v //= A
+            out.append(s)
+    return out[1:]
+
+
+@pytest.mark.parametrize("match,mismatch,O,X", [(2, -3, 3, 1), (2, -1, 2, 1), (1, -1, 3, 1),
+                                                (3, -2, 4, 2)])
+def test_cigar_canonical_exhaustive_small(match, mismatch, O, X):
+    # every pair of strings of length <= 3 over three letters: all tie patterns
+    # between M, D and I, and between opening and extending a gap, occur here
+    W = dna_matrix(match, mismatch, 3)
+    strs = _all_strings(3, 3)
+    for qs in strs:
+        for ts in strs:
+            best, canon = canonical_global(qs, ts, W, O, X)
+            got, sc = oracle.cigar(np.array(qs, np.uint8), np.array(ts, np.uint8), W, O, X)
+            assert sc == best
+            assert got == runs(canon), (qs, ts)
+
+
+def test_d_preferred_over_i_on_tie():
+    # AC against CA: I M D and D M I both score -4; walking back from the end,
+    # the horizontal gap state (D) is preferred, giving 1I1M1D
+    W = dna_matrix(2, -3, 2)
+    got, sc = oracle.cigar(np.array([0, 1], np.uint8), np.array([1, 0], np.uint8), W, 3, 1)
+    assert sc == -4 and oracle.cigar_string(got) == "1I1M1D"
+
+
+def _two_copies(m1, m2, gap, rng):
+    """target = pad + Q[:m1] + spacer + Q[:m2] + pad over {A,C} vs query Q over {A,C}.
+
+    The spacer and pads are G/T only, so each copy scores 2 * its length.
+    """
+    m = max(m1, m2)
+    q = rng.integers(0, 2, m).astype(np.uint8)
+    pad = lambda k: rng.integers(2, 4, k).astype(np.uint8)
+    t = np.concatenate([pad(20), q[:m1], pad(gap), q[:m2], pad(20)])
+    return q, t, 20 + m1 - 1, 20 + m1 + gap + m2 - 1
+
+
+def test_secondary_mask_bounds_right_side():
+    rng = np.random.default_rng(31)
+    W = dna_matrix(2, -2)
+    q, t, e1, e2 = _two_copies(40, 40, 30, rng)
+    d = e2 - e1
+    r = oracle.align(q, t, W, 3, 1, mask_len=d)       # e2 = e1 + L: masked
+    assert r["ref_end1"] == e1 and r["score1"] == 80 and r["score2"] < 80
+    r = oracle.align(q, t, W, 3, 1, mask_len=d - 1)   # e2 = e1 + L + 1: visible
+    assert r["score2"] == 80 and r["ref_end2"] == e2
+
+
+def test_secondary_mask_bounds_left_side():
+    rng = np.random.default_rng(37)
+    W = dna_matrix(2, -2)
+    q, t, e1, e2 = _two_copies(25, 40, 30, rng)       # the right copy is primary
+    d = e2 - e1
+    r = oracle.align(q, t, W, 3, 1, mask_len=d)       # e1 = e2 - L: masked
+    assert r["ref_end1"] == e2 and r["score1"] == 80 and r["score2"] < 50
+    r = oracle.align(q, t, W, 3, 1, mask_len=d - 1)   # e1 = e2 - L - 1: visible
+    assert r["score2"] == 50 and r["ref_end2"] == e1
+
+
+def test_secondary_tie_takes_first_column():
+    rng = np.random.default_rng(41)
+    W = dna_matrix(2, -2)
+    m = 30
+    q = rng.integers(0, 2, m).astype(np.uint8)
+    pad = lambda k: rng.integers(2, 4, k).astype(np.uint8)
+    # primary: a full copy; two equal partial copies (20 letters) further right.
+    # The primary's trailing-gap tail in the max array (60 - 3 - (k - 1) at k
+    # columns past its end) must lie inside the mask, hence mask_len = 60 and
+    # the copies start 70 columns after the primary.
+    t = np.concatenate([pad(10), q, pad(70), q[:20], pad(40), q[:20], pad(10)])
+    r = oracle.align(q, t, W, 3, 1, mask_len=60)
+    assert r["score1"] == 60 and r["score2"] == 40
+    assert r["ref_end2"] == 10 + m + 70 + 20 - 1
