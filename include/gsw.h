@@ -1,0 +1,178 @@
+/*
+ * gsw.h -- C ABI of the GB300 (sm_103a) SSW alignment library.
+ *
+ * The library computes, for each (query, target) pair, what the SSW paper
+ * (Zhao, Lee, Garrison, Marth 2012) describes in "Algorithm and
+ * implementation" and "Results / Usage": the optimal local Smith-Waterman-Gotoh
+ * score, its end on target and query (found from the per-column "max" array
+ * and the column that holds the matrix maximum), the suboptimal score from the
+ * max array with the primary's neighbourhood masked, the begin by a reversed
+ * SW from the end, and the alignment (CIGAR) by a banded SW between begin and
+ * end.  All of it runs in this library's CUDA kernels; there is no CPU path.
+ *
+ * Conventions shared by every call:
+ *   - Sequences are letter codes, one byte per residue, in [0, alphabet).
+ *     A query of length m has rows i = 0..m-1; a target of length n has
+ *     columns j = 0..n-1.  Positions in results are 0-based and inclusive.
+ *   - matrix is alphabet x alphabet int8, row-major, matrix[a*alphabet + b] =
+ *     score of query letter a against target letter b (host memory, copied).
+ *   - gap_open O and gap_extend X are non-negative with O >= X; a gap of
+ *     length k costs O + (k-1)*X (the paper prints penalties, e.g. "gap open
+ *     -2 and extension -1" in the Fig. 1 caption, without fixing this
+ *     convention; this is the reading the library implements).
+ *   - Ties: the end is the first target column whose max equals the optimum,
+ *     then the first query row in that column with it; the begin is the
+ *     largest (target, query) begin among optimal alignments ending there; the
+ *     CIGAR is the one traced back from the end preferring a match/mismatch
+ *     column, then a target gap (D), then a query gap (I), and closing a gap as
+ *     early as possible.
+ *   - Errors: every call returns GSW_OK (0) or a negative GSW_E* code and
+ *     never throws; gsw_strerror() names the code, gsw_last_error() gives a
+ *     one-line detail for the calling thread.
+ */
+#ifndef GSW_H
+#define GSW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GSW_OK 0
+#define GSW_EINVAL (-1)       /* bad argument (sizes, codes, scoring, flags) */
+#define GSW_ENOMEM (-2)       /* device or pinned memory exhausted / over budget */
+#define GSW_ECUDA (-3)        /* a CUDA runtime call failed */
+#define GSW_ETIMEDOUT (-4)    /* a bounded wait gave up (serving loop) */
+#define GSW_ECIGAR_SPACE (-5) /* the caller's CIGAR buffer is too small */
+#define GSW_EOVERFLOW (-6)    /* a score does not fit in int32 arithmetic */
+#define GSW_ENOTFOUND (-7)    /* unknown request id */
+#define GSW_ESTATE (-8)       /* call not valid in the object's current state */
+
+/* flags for gsw_align_batch / gsw_align_profile */
+#define GSW_BEGIN 0x1u      /* also run the reversed SW: ref_begin1, read_begin1 */
+#define GSW_CIGAR 0x2u      /* also run the banded SW + traceback (implies GSW_BEGIN) */
+#define GSW_COLMAX 0x4u     /* write the per-column max array to `colmax` */
+#define GSW_HOST_IO 0x8u    /* every pointer argument is host memory; the call
+                               stages it through the context and returns when
+                               the results are back in host memory */
+#define GSW_FORCE_S32 0x10u /* skip the 16-bit lanes (32-bit fill for every pair) */
+#define GSW_PLAIN 0x20u     /* baseline: one fill/reverse/traceback launch
+                               sequence per pair, no batching */
+
+/* CIGAR words: (run_length << 4) | op, op 0 = M (match or mismatch column),
+ * 1 = I (query letter against a gap), 2 = D (target letter against a gap). */
+#define GSW_CIGAR_M 0u
+#define GSW_CIGAR_I 1u
+#define GSW_CIGAR_D 2u
+
+/* per-pair status bits in gsw_result.flags */
+#define GSW_RES_S32 0x1u          /* the fill ran in 32-bit lanes (16-bit overflowed or forced) */
+#define GSW_RES_CIGAR_SPACE 0x2u  /* no room for this pair's CIGAR: cigar_len = -needed */
+
+/*
+ * One pair's result (Results, "Usage": the SW score, alignment location and
+ * traceback of the optimal alignment, and the score and location of the
+ * suboptimal alignment).  Missing values are -1: with score1 = 0 there is no
+ * alignment and every position is -1; begins are -1 unless GSW_BEGIN or
+ * GSW_CIGAR was given; score2 = 0 gives ref_end2 = -1.
+ */
+typedef struct gsw_result {
+    int32_t score1;      /* optimal local score (>= 0) */
+    int32_t score2;      /* largest max-array entry outside [ref_end1-L, ref_end1+L] */
+    int32_t ref_begin1;  /* target begin of the optimal alignment */
+    int32_t ref_end1;    /* target end: first column whose max equals score1 */
+    int32_t read_begin1; /* query begin */
+    int32_t read_end1;   /* query end: first row of column ref_end1 holding score1 */
+    int32_t ref_end2;    /* first column holding score2 */
+    int32_t cigar_len;   /* number of CIGAR words; 0 if none; -needed on GSW_RES_CIGAR_SPACE */
+    int64_t cigar_off;   /* index of the first CIGAR word in the caller's buffer, -1 if none */
+    int32_t flags;       /* GSW_RES_* bits */
+    int32_t reserved;
+} gsw_result;
+
+typedef struct gsw_ctx gsw_ctx;
+typedef struct gsw_profile gsw_profile;
+
+/*
+ * Creates a context on CUDA device `device`.  The context owns the device
+ * scratch (work queues, per-slot column-max and strip-boundary buffers,
+ * traceback scratch) and pinned staging for GSW_HOST_IO; it never holds more
+ * than `mem_budget_bytes` of device memory (0 = 4 GiB).  Batches that need
+ * more scratch are processed in chunks.  One context may be used by one host
+ * thread at a time.  Errors: GSW_EINVAL (bad device), GSW_ECUDA, GSW_ENOMEM.
+ */
+int gsw_context_create(int device, size_t mem_budget_bytes, gsw_ctx **out);
+
+/* Releases everything the context owns.  Waits for its work to finish. */
+int gsw_context_destroy(gsw_ctx *ctx);
+
+/*
+ * Aligns npairs pairs: query p is q[q_off[p] .. q_off[p]+q_len[p]), target p
+ * is t[t_off[p] .. t_off[p]+t_len[p]).  Lengths may be 0 (score1 = 0).
+ *
+ * Memory: q, q_off, q_len, t, t_off, t_len, results, cigar, colmax and
+ * colmax_off are device pointers, unless flags has GSW_HOST_IO, in which case
+ * they are all host pointers.  The caller owns every buffer.  `results` has
+ * npairs records.  `cigar` has `cigar_capacity` uint32 words shared by the
+ * batch (may be NULL with capacity 0 when GSW_CIGAR is not set); pairs that
+ * do not fit are marked GSW_RES_CIGAR_SPACE and the call returns
+ * GSW_ECIGAR_SPACE after filling everything else.  With GSW_COLMAX, colmax
+ * receives t_len[p] int32 values at colmax[colmax_off[p]].
+ *
+ * mask_len is the half-width L of the window masked around ref_end1 before
+ * the suboptimal score is taken; negative means max(q_len/2, 15).
+ *
+ * Stream: work is queued on `stream` (a cudaStream_t; NULL = the legacy
+ * default stream) and the call returns without synchronizing, except with
+ * GSW_HOST_IO, where it returns when the host results are ready.
+ *
+ * Errors: GSW_EINVAL (alphabet not in [1, 32], matrix entries outside
+ * [-127, 127], O < X, O or X > 255 or negative, npairs < 0, mask_len too
+ * large), GSW_ENOMEM, GSW_ECUDA, GSW_ECIGAR_SPACE, GSW_EOVERFLOW (a pair whose
+ * score or intermediate value exceeds int32 range cannot happen for lengths
+ * below 2^24 and |W| <= 127; longer inputs are rejected with GSW_EINVAL).
+ */
+int gsw_align_batch(gsw_ctx *ctx, int32_t npairs,
+                    const uint8_t *q, const int64_t *q_off, const int32_t *q_len,
+                    const uint8_t *t, const int64_t *t_off, const int32_t *t_len,
+                    const int8_t *matrix, int32_t alphabet, int32_t gap_open,
+                    int32_t gap_extend, uint32_t flags, int32_t mask_len,
+                    gsw_result *results, uint32_t *cigar, int64_t cigar_capacity,
+                    int32_t *colmax, const int64_t *colmax_off, void *stream);
+
+/*
+ * ssw_init-style query profile: copies one query and its scoring onto the
+ * device, where it stays until gsw_profile_destroy.  query is host memory.
+ * Errors: as gsw_align_batch for the scoring arguments; GSW_ENOMEM.
+ */
+int gsw_profile_create(gsw_ctx *ctx, const uint8_t *query, int32_t qlen,
+                       const int8_t *matrix, int32_t alphabet, int32_t gap_open,
+                       int32_t gap_extend, gsw_profile **out);
+int gsw_profile_destroy(gsw_profile *prof);
+
+/*
+ * Aligns the profile's query against ntargets targets (layout and memory
+ * rules of gsw_align_batch's t, t_off, t_len, results, cigar, colmax).
+ */
+int gsw_align_profile(gsw_ctx *ctx, const gsw_profile *prof, int32_t ntargets,
+                      const uint8_t *t, const int64_t *t_off, const int32_t *t_len,
+                      uint32_t flags, int32_t mask_len, gsw_result *results,
+                      uint32_t *cigar, int64_t cigar_capacity, int32_t *colmax,
+                      const int64_t *colmax_off, void *stream);
+
+/* Name of an error code (static string). */
+const char *gsw_strerror(int code);
+
+/* Detail of the last error raised on the calling thread (static per thread). */
+const char *gsw_last_error(void);
+
+/* Library version string. */
+const char *gsw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSW_H */

@@ -1,0 +1,506 @@
+// Host runtime behind include/gsw.h: contexts, scratch management and the
+// stage chain of one batch (plan -> fill -> 32-bit refill of overflowed pairs
+// -> reversed fill -> banded traceback), all enqueued on the caller's stream.
+#include "gsw_impl.cuh"
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace gsw;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int set_err(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CUDA_TRY(x)                                                                            \
+    do {                                                                                       \
+        cudaError_t e__ = (x);                                                                 \
+        if (e__ != cudaSuccess) return set_err(GSW_ECUDA, "%s: %s", #x, cudaGetErrorString(e__)); \
+    } while (0)
+
+#define GSW_TRY(x)              \
+    do {                        \
+        int r__ = (x);          \
+        if (r__ != GSW_OK) return r__; \
+    } while (0)
+
+}  // namespace
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct gsw_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    int sms = 0;
+    DevBuf plan_keys, plan_order, plan_small;
+    DevBuf fill_cm, fill_bnd;
+    DevBuf trace_dirs, trace_ops;
+    DevBuf misc;  // counters: trace head, cigar cursor, trace need, max lengths
+    DevBuf io_q, io_t, io_qoff, io_toff, io_qlen, io_tlen, io_res, io_cigar, io_colmax, io_cmoff;
+    DevBuf prof_qoff, prof_qlen;
+    void *host_small = nullptr;  // pinned readback area
+};
+
+struct gsw_profile {
+    gsw_ctx *ctx;
+    uint8_t *query;  // device
+    int32_t qlen;
+    Scoring sc;
+};
+
+namespace {
+
+// Grows `b` to at least `need` bytes (never shrinks).  Synchronizes the device
+// before releasing an old allocation that queued work may still use.
+int ensure(gsw_ctx *ctx, DevBuf &b, size_t need) {
+    if (need <= b.bytes) return GSW_OK;
+    need = std::max<size_t>(need, 256);
+    if (b.p) {
+        CUDA_TRY(cudaDeviceSynchronize());
+        CUDA_TRY(cudaFree(b.p));
+        ctx->used -= b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (ctx->used + need > ctx->budget)
+        return set_err(GSW_ENOMEM, "scratch of %zu bytes exceeds the context budget (%zu used of %zu)", need,
+                       ctx->used, ctx->budget);
+    cudaError_t e = cudaMalloc(&b.p, need);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return set_err(GSW_ENOMEM, "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+    }
+    b.bytes = need;
+    ctx->used += need;
+    return GSW_OK;
+}
+
+void release(gsw_ctx *ctx, DevBuf &b) {
+    if (b.p) cudaFree(b.p);
+    ctx->used -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+int make_scoring(const int8_t *matrix, int32_t A, int32_t O, int32_t X, Scoring *sc) {
+    if (!matrix) return set_err(GSW_EINVAL, "matrix is NULL");
+    if (A < 1 || A > kMaxAlpha) return set_err(GSW_EINVAL, "alphabet %d not in [1, %d]", A, kMaxAlpha);
+    if (X < 0 || O < X || O > 255) return set_err(GSW_EINVAL, "need 0 <= gap_extend <= gap_open <= 255 (got %d, %d)", O, X);
+    std::memset(sc, 0, sizeof(*sc));
+    sc->A = A;
+    sc->O = O;
+    sc->X = X;
+    int wmax = -128, wmin = 127;
+    for (int i = 0; i < A * A; i++) {
+        if (matrix[i] < -127) return set_err(GSW_EINVAL, "matrix entry %d out of [-127, 127]", matrix[i]);
+        sc->W[i] = matrix[i];
+        wmax = std::max<int>(wmax, matrix[i]);
+        wmin = std::min<int>(wmin, matrix[i]);
+    }
+    sc->wmax = wmax;
+    sc->wmin = wmin;
+    sc->dna4 = A == 4;
+    return GSW_OK;
+}
+
+// device scratch layout of ctx->misc (64-bit words)
+enum MiscSlot { kMiscTraceHead = 0, kMiscCursor = 1, kMiscNeed = 2 /* 3 words */, kMiscMaxLen = 5, kMiscValid = 6, kMiscWords = 8 };
+
+int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st, int maxm, int maxn) {
+    const int npairs = bv.npairs;
+    unsigned long long *misc = reinterpret_cast<unsigned long long *>(ctx->misc.p);
+    // ---- plan buffers
+    GSW_TRY(ensure(ctx, ctx->plan_keys, sizeof(int32_t) * (size_t)std::max(npairs, 1)));
+    GSW_TRY(ensure(ctx, ctx->plan_order, sizeof(int32_t) * (size_t)std::max(npairs, 1)));
+    const size_t small_words = 3 * (size_t)kPlanBins + 3 * kNumVariants + 8;
+    GSW_TRY(ensure(ctx, ctx->plan_small, sizeof(int32_t) * small_words));
+    int32_t *ps = reinterpret_cast<int32_t *>(ctx->plan_small.p);
+    PlanBuffers pb;
+    pb.keys = reinterpret_cast<int32_t *>(ctx->plan_keys.p);
+    pb.order = reinterpret_cast<int32_t *>(ctx->plan_order.p);
+    pb.hist = ps;
+    pb.binoff = ps + kPlanBins;
+    pb.cursor = ps + 2 * kPlanBins;
+    pb.var_start = ps + 3 * kPlanBins;
+    pb.task_lo = pb.var_start + kNumVariants + 1;
+    pb.task_hi = pb.task_lo + kNumVariants;
+    pb.ntasks = pb.task_hi + kNumVariants;
+    pb.head = pb.ntasks + 1;
+
+    // ---- fill launch geometry and per-slot scratch
+    const size_t smem = fill_smem_per_warp(sc) * (fill_block_threads() / 32);
+    int bps = fill_max_blocks_per_sm(sc, smem);
+    if (bps < 1) return set_err(GSW_ECUDA, "fill kernel cannot be resident (smem %zu)", smem);
+    const int warps_per_block = fill_block_threads() / 32;
+    const int slots_per_warp = 2;  // 32 / smallest P
+    const size_t ncap = (size_t)std::max(maxn, 1);
+    const size_t per_slot = ncap * sizeof(int32_t) + 2 * ncap * sizeof(int2);
+    int grid = ctx->sms * bps;
+    {
+        // keep the scratch inside half of what the budget has left
+        size_t have = ctx->budget > ctx->used ? ctx->budget - ctx->used + ctx->fill_cm.bytes + ctx->fill_bnd.bytes : 0;
+        size_t max_slots = have / 2 / per_slot;
+        size_t want = (size_t)grid * warps_per_block * slots_per_warp;
+        if (want > max_slots) grid = (int)std::max<size_t>(1, max_slots / (warps_per_block * slots_per_warp));
+    }
+    const size_t slots = (size_t)grid * warps_per_block * slots_per_warp;
+    GSW_TRY(ensure(ctx, ctx->fill_cm, slots * ncap * sizeof(int32_t)));
+    GSW_TRY(ensure(ctx, ctx->fill_bnd, slots * 2 * ncap * sizeof(int2)));
+
+    FillLaunch fl;
+    fl.b = bv;
+    fl.sc = sc;
+    fl.plan.order = pb.order;
+    fl.plan.var_start = pb.var_start;
+    fl.plan.task_lo = pb.task_lo;
+    fl.plan.task_hi = pb.task_hi;
+    fl.plan.head = pb.head;
+    fl.plan.ntasks = pb.ntasks;
+    fl.scr.colmax = ctx->fill_cm.p;
+    fl.scr.boundary = ctx->fill_bnd.p;
+    fl.scr.ncap = (int32_t)ncap;
+    fl.scr.slots_per_warp = slots_per_warp;
+
+    auto stage = [&](int32_t mode) -> int {
+        cudaError_t e = launch_plan(bv, sc, mode, pb, st);
+        if (e != cudaSuccess) return set_err(GSW_ECUDA, "plan: %s", cudaGetErrorString(e));
+        fl.mode = mode;
+        e = launch_fill(fl, grid, smem, st);
+        if (e != cudaSuccess) return set_err(GSW_ECUDA, "fill: %s", cudaGetErrorString(e));
+        return GSW_OK;
+    };
+    GSW_TRY(stage(kFillForward));
+    if (!(bv.flags & GSW_FORCE_S32)) GSW_TRY(stage(kFillRerun));
+    if (bv.flags & (GSW_BEGIN | GSW_CIGAR)) GSW_TRY(stage(kFillReverse));
+
+    if (bv.flags & GSW_CIGAR) {
+        CUDA_TRY(launch_trace_need(bv, sc, misc + kMiscNeed, st));
+        unsigned long long *hs = reinterpret_cast<unsigned long long *>(ctx->host_small);
+        CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        const long long need_dir = (long long)hs[0], need_ops = (long long)hs[1], need_nch = (long long)hs[2];
+        const int tgrid = ctx->sms * 2;
+        const int twarps = tgrid * (trace_block_threads() / 32);
+        // pairs too large for shared memory use global scratch: size it for the largest
+        const long long dir_words = std::max<long long>(need_dir, 64);
+        const long long op_words = std::max<long long>(need_ops + 64 * need_nch, 64);
+        size_t per_warp = (size_t)(dir_words + op_words) * sizeof(uint32_t);
+        int use_warps = twarps;
+        size_t have = ctx->budget > ctx->used ? ctx->budget - ctx->used + ctx->trace_dirs.bytes + ctx->trace_ops.bytes : 0;
+        if ((size_t)use_warps * per_warp > have) use_warps = (int)std::max<size_t>(1, have / per_warp);
+        int use_grid = std::max(1, use_warps / (trace_block_threads() / 32));
+        use_warps = use_grid * (trace_block_threads() / 32);
+        GSW_TRY(ensure(ctx, ctx->trace_dirs, (size_t)use_warps * dir_words * sizeof(uint32_t)));
+        GSW_TRY(ensure(ctx, ctx->trace_ops, (size_t)use_warps * op_words * sizeof(uint32_t)));
+        TraceScratch ts;
+        ts.dirs = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
+        ts.dir_words = dir_words;
+        ts.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
+        ts.op_words = op_words;
+        ts.head = reinterpret_cast<int32_t *>(misc + kMiscTraceHead);
+        CUDA_TRY(launch_traceback(bv, sc, ts, use_grid, st));
+    }
+    return GSW_OK;
+}
+
+int check_common(gsw_ctx *ctx, int32_t npairs, uint32_t flags) {
+    if (!ctx) return set_err(GSW_EINVAL, "context is NULL");
+    if (npairs < 0) return set_err(GSW_EINVAL, "npairs < 0");
+    if (flags & ~(GSW_BEGIN | GSW_CIGAR | GSW_COLMAX | GSW_HOST_IO | GSW_FORCE_S32 | GSW_PLAIN))
+        return set_err(GSW_EINVAL, "unknown flag bits 0x%x", flags);
+    return GSW_OK;
+}
+
+int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_off, const int32_t *q_len,
+               const uint8_t *t, const int64_t *t_off, const int32_t *t_len, const Scoring &sc, uint32_t flags,
+               int32_t mask_len, gsw_result *results, uint32_t *cigar, int64_t cigar_capacity, int32_t *colmax,
+               const int64_t *colmax_off, cudaStream_t st) {
+    GSW_TRY(check_common(ctx, npairs, flags));
+    if (flags & GSW_CIGAR) flags |= GSW_BEGIN;
+    if (npairs == 0) return GSW_OK;
+    if (!q || !q_off || !q_len || !t || !t_off || !t_len || !results)
+        return set_err(GSW_EINVAL, "NULL input or result pointer");
+    if ((flags & GSW_CIGAR) && (!cigar && cigar_capacity > 0)) return set_err(GSW_EINVAL, "cigar is NULL");
+    if (cigar_capacity < 0) return set_err(GSW_EINVAL, "cigar_capacity < 0");
+    if ((flags & GSW_COLMAX) && (!colmax || !colmax_off)) return set_err(GSW_EINVAL, "colmax output missing");
+    if (mask_len > (1 << 30)) return set_err(GSW_EINVAL, "mask_len too large");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    GSW_TRY(ensure(ctx, ctx->misc, kMiscWords * sizeof(unsigned long long)));
+    unsigned long long *misc = reinterpret_cast<unsigned long long *>(ctx->misc.p);
+    BatchView bv;
+    std::memset(&bv, 0, sizeof(bv));
+    bv.npairs = npairs;
+    bv.flags = flags;
+    bv.mask_len = mask_len;
+    bv.cigar_cap = cigar_capacity;
+    bv.cigar_cursor = misc + kMiscCursor;
+    int maxm = 0, maxn = 0;
+    const bool hio = (flags & GSW_HOST_IO) != 0;
+    if (hio) {
+        int64_t qext = 0, text = 0, cmext = 0;
+        for (int32_t p = 0; p < npairs; p++) {
+            if (q_len[p] < 0 || t_len[p] < 0 || q_len[p] >= (1 << 24) || t_len[p] >= (1 << 24))
+                return set_err(GSW_EINVAL, "pair %d: length out of [0, 2^24)", p);
+            if (q_off[p] < 0 || t_off[p] < 0) return set_err(GSW_EINVAL, "pair %d: negative offset", p);
+            maxm = std::max(maxm, q_len[p]);
+            maxn = std::max(maxn, t_len[p]);
+            qext = std::max<int64_t>(qext, q_off[p] + q_len[p]);
+            text = std::max<int64_t>(text, t_off[p] + t_len[p]);
+            if (flags & GSW_COLMAX) cmext = std::max<int64_t>(cmext, colmax_off[p] + t_len[p]);
+        }
+        GSW_TRY(ensure(ctx, ctx->io_q, (size_t)std::max<int64_t>(qext, 1)));
+        GSW_TRY(ensure(ctx, ctx->io_t, (size_t)std::max<int64_t>(text, 1)));
+        GSW_TRY(ensure(ctx, ctx->io_qoff, sizeof(int64_t) * npairs));
+        GSW_TRY(ensure(ctx, ctx->io_toff, sizeof(int64_t) * npairs));
+        GSW_TRY(ensure(ctx, ctx->io_qlen, sizeof(int32_t) * npairs));
+        GSW_TRY(ensure(ctx, ctx->io_tlen, sizeof(int32_t) * npairs));
+        GSW_TRY(ensure(ctx, ctx->io_res, sizeof(gsw_result) * npairs));
+        if (flags & GSW_CIGAR) GSW_TRY(ensure(ctx, ctx->io_cigar, sizeof(uint32_t) * (size_t)std::max<int64_t>(cigar_capacity, 1)));
+        if (flags & GSW_COLMAX) {
+            GSW_TRY(ensure(ctx, ctx->io_colmax, sizeof(int32_t) * (size_t)std::max<int64_t>(cmext, 1)));
+            GSW_TRY(ensure(ctx, ctx->io_cmoff, sizeof(int64_t) * npairs));
+        }
+        CUDA_TRY(cudaMemcpyAsync(ctx->io_q.p, q, qext, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(ctx->io_t.p, t, text, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(ctx->io_qoff.p, q_off, sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(ctx->io_toff.p, t_off, sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(ctx->io_qlen.p, q_len, sizeof(int32_t) * npairs, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(ctx->io_tlen.p, t_len, sizeof(int32_t) * npairs, cudaMemcpyHostToDevice, st));
+        if (flags & GSW_COLMAX)
+            CUDA_TRY(cudaMemcpyAsync(ctx->io_cmoff.p, colmax_off, sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, st));
+        bv.q = (const uint8_t *)ctx->io_q.p;
+        bv.t = (const uint8_t *)ctx->io_t.p;
+        bv.q_off = (const int64_t *)ctx->io_qoff.p;
+        bv.t_off = (const int64_t *)ctx->io_toff.p;
+        bv.q_len = (const int32_t *)ctx->io_qlen.p;
+        bv.t_len = (const int32_t *)ctx->io_tlen.p;
+        bv.res = (gsw_result *)ctx->io_res.p;
+        bv.cigar = (uint32_t *)ctx->io_cigar.p;
+        bv.colmax = (int32_t *)ctx->io_colmax.p;
+        bv.colmax_off = (const int64_t *)ctx->io_cmoff.p;
+    } else {
+        bv.q = q;
+        bv.t = t;
+        bv.q_off = q_off;
+        bv.t_off = t_off;
+        bv.q_len = q_len;
+        bv.t_len = t_len;
+        bv.res = results;
+        bv.cigar = cigar;
+        bv.colmax = colmax;
+        bv.colmax_off = colmax_off;
+        int32_t *ml = reinterpret_cast<int32_t *>(misc + kMiscMaxLen);
+        CUDA_TRY(launch_max_lengths(q_len, t_len, npairs, ml, st));
+        int32_t *hs = reinterpret_cast<int32_t *>(ctx->host_small);
+        CUDA_TRY(cudaMemcpyAsync(hs, ml, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        maxm = hs[0];
+        maxn = hs[1];
+        if (maxm >= (1 << 24) || maxn >= (1 << 24)) return set_err(GSW_EINVAL, "a length is >= 2^24");
+    }
+    CUDA_TRY(cudaMemsetAsync(misc + kMiscCursor, 0, sizeof(unsigned long long), st));
+    CUDA_TRY(launch_validate(bv, sc, reinterpret_cast<int32_t *>(misc + kMiscValid), st));
+    GSW_TRY(run_pipeline(ctx, bv, sc, st, maxm, maxn));
+
+    // completion: invalid letters, CIGAR space
+    unsigned long long *hs = reinterpret_cast<unsigned long long *>(ctx->host_small);
+    CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscCursor, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hs + 1, misc + kMiscValid, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    if (hio) {
+        CUDA_TRY(cudaMemcpyAsync(results, bv.res, sizeof(gsw_result) * npairs, cudaMemcpyDeviceToHost, st));
+        if (flags & GSW_COLMAX) {
+            int64_t cmext = 0;
+            for (int32_t p = 0; p < npairs; p++) cmext = std::max<int64_t>(cmext, colmax_off[p] + t_len[p]);
+            CUDA_TRY(cudaMemcpyAsync(colmax, bv.colmax, sizeof(int32_t) * cmext, cudaMemcpyDeviceToHost, st));
+        }
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    const unsigned long long used_words = hs[0];
+    const int bad_letters = (int)(hs[1] & 0xFFFFFFFFu);
+    if (hio && (flags & GSW_CIGAR) && cigar_capacity > 0) {
+        const size_t n = (size_t)std::min<unsigned long long>(used_words, (unsigned long long)cigar_capacity);
+        if (n) CUDA_TRY(cudaMemcpy(cigar, bv.cigar, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    }
+    if (bad_letters) return set_err(GSW_EINVAL, "a letter code is >= the alphabet size (%d)", sc.A);
+    if ((flags & GSW_CIGAR) && used_words > (unsigned long long)cigar_capacity)
+        return set_err(GSW_ECIGAR_SPACE, "CIGAR words needed %llu > capacity %lld", used_words,
+                       (long long)cigar_capacity);
+    return GSW_OK;
+}
+
+// Baseline without batching: every pair goes through its own launch
+// sequence (plan, fill, refill, reverse, traceback) and is waited for before
+// the next one starts, as a caller aligning one pair per call would.
+int plain_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_off, const int32_t *q_len,
+               const uint8_t *t, const int64_t *t_off, const int32_t *t_len, const Scoring &sc, uint32_t flags,
+               int32_t mask_len, gsw_result *results, uint32_t *cigar, int64_t cigar_capacity, int32_t *colmax,
+               const int64_t *colmax_off, cudaStream_t st) {
+    GSW_TRY(check_common(ctx, npairs, flags));
+    flags &= ~GSW_PLAIN;
+    if ((flags & GSW_CIGAR) && (flags & GSW_HOST_IO) == 0)
+        return set_err(GSW_EINVAL, "GSW_PLAIN with GSW_CIGAR needs GSW_HOST_IO (per-pair CIGAR offsets)");
+    int64_t cig_used = 0;
+    for (int32_t p = 0; p < npairs; p++) {
+        uint32_t *cg = cigar ? cigar + cig_used : nullptr;
+        const int64_t cap = cigar ? cigar_capacity - cig_used : 0;
+        int rc = batch_impl(ctx, 1, q, q_off + p, q_len + p, t, t_off + p, t_len + p, sc, flags, mask_len,
+                            results + p, cg, cap, colmax, colmax_off ? colmax_off + p : nullptr, st);
+        if (rc != GSW_OK) return rc;
+        if ((flags & GSW_CIGAR) && results[p].cigar_len > 0) {
+            results[p].cigar_off += cig_used;
+            cig_used += results[p].cigar_len;
+        }
+    }
+    return GSW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gsw_version(void) { return "gsw 0.1 (sm_103a)"; }
+
+const char *gsw_strerror(int code) {
+    switch (code) {
+    case GSW_OK: return "ok";
+    case GSW_EINVAL: return "invalid argument";
+    case GSW_ENOMEM: return "out of memory or over budget";
+    case GSW_ECUDA: return "CUDA error";
+    case GSW_ETIMEDOUT: return "timed out";
+    case GSW_ECIGAR_SPACE: return "CIGAR buffer too small";
+    case GSW_EOVERFLOW: return "score overflow";
+    case GSW_ENOTFOUND: return "not found";
+    case GSW_ESTATE: return "invalid state";
+    default: return "unknown error";
+    }
+}
+
+const char *gsw_last_error(void) { return g_err; }
+
+int gsw_context_create(int device, size_t mem_budget_bytes, gsw_ctx **out) {
+    if (!out) return set_err(GSW_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return set_err(GSW_EINVAL, "device %d of %d", device, ndev);
+    CUDA_TRY(cudaSetDevice(device));
+    gsw_ctx *c = new (std::nothrow) gsw_ctx();
+    if (!c) return set_err(GSW_ENOMEM, "host allocation");
+    c->device = device;
+    c->budget = mem_budget_bytes ? mem_budget_bytes : ((size_t)4 << 30);
+    cudaError_t e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->host_small, 4096);
+    if (e != cudaSuccess) {
+        delete c;
+        return set_err(GSW_ECUDA, "context setup: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return GSW_OK;
+}
+
+int gsw_context_destroy(gsw_ctx *c) {
+    if (!c) return GSW_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    DevBuf *all[] = {&c->plan_keys, &c->plan_order, &c->plan_small, &c->fill_cm, &c->fill_bnd, &c->trace_dirs,
+                     &c->trace_ops, &c->misc, &c->io_q, &c->io_t, &c->io_qoff, &c->io_toff, &c->io_qlen,
+                     &c->io_tlen, &c->io_res, &c->io_cigar, &c->io_colmax, &c->io_cmoff, &c->prof_qoff,
+                     &c->prof_qlen};
+    for (DevBuf *b : all) release(c, *b);
+    if (c->host_small) cudaFreeHost(c->host_small);
+    delete c;
+    return GSW_OK;
+}
+
+int gsw_align_batch(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_off, const int32_t *q_len,
+                    const uint8_t *t, const int64_t *t_off, const int32_t *t_len, const int8_t *matrix,
+                    int32_t alphabet, int32_t gap_open, int32_t gap_extend, uint32_t flags, int32_t mask_len,
+                    gsw_result *results, uint32_t *cigar, int64_t cigar_capacity, int32_t *colmax,
+                    const int64_t *colmax_off, void *stream) {
+    Scoring sc;
+    GSW_TRY(make_scoring(matrix, alphabet, gap_open, gap_extend, &sc));
+    if (flags & GSW_PLAIN) return plain_impl(ctx, npairs, q, q_off, q_len, t, t_off, t_len, sc, flags,
+                                                  mask_len, results, cigar, cigar_capacity, colmax, colmax_off,
+                                                  (cudaStream_t)stream);
+    return batch_impl(ctx, npairs, q, q_off, q_len, t, t_off, t_len, sc, flags, mask_len, results, cigar,
+                      cigar_capacity, colmax, colmax_off, (cudaStream_t)stream);
+}
+
+int gsw_profile_create(gsw_ctx *ctx, const uint8_t *query, int32_t qlen, const int8_t *matrix, int32_t alphabet,
+                       int32_t gap_open, int32_t gap_extend, gsw_profile **out) {
+    if (!ctx || !out || (!query && qlen > 0) || qlen < 0 || qlen >= (1 << 24))
+        return set_err(GSW_EINVAL, "bad profile arguments");
+    *out = nullptr;
+    Scoring sc;
+    GSW_TRY(make_scoring(matrix, alphabet, gap_open, gap_extend, &sc));
+    for (int32_t i = 0; i < qlen; i++)
+        if (query[i] >= alphabet) return set_err(GSW_EINVAL, "query letter code %d >= alphabet", query[i]);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    gsw_profile *p = new (std::nothrow) gsw_profile();
+    if (!p) return set_err(GSW_ENOMEM, "host allocation");
+    p->ctx = ctx;
+    p->qlen = qlen;
+    p->sc = sc;
+    cudaError_t e = cudaMalloc(&p->query, std::max(qlen, 1));
+    if (e == cudaSuccess && qlen > 0) e = cudaMemcpy(p->query, query, qlen, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (p->query) cudaFree(p->query);
+        delete p;
+        return set_err(GSW_ENOMEM, "profile: %s", cudaGetErrorString(e));
+    }
+    *out = p;
+    return GSW_OK;
+}
+
+int gsw_profile_destroy(gsw_profile *p) {
+    if (!p) return GSW_OK;
+    cudaSetDevice(p->ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(p->query);
+    delete p;
+    return GSW_OK;
+}
+
+int gsw_align_profile(gsw_ctx *ctx, const gsw_profile *prof, int32_t ntargets, const uint8_t *t,
+                      const int64_t *t_off, const int32_t *t_len, uint32_t flags, int32_t mask_len,
+                      gsw_result *results, uint32_t *cigar, int64_t cigar_capacity, int32_t *colmax,
+                      const int64_t *colmax_off, void *stream) {
+    if (!ctx || !prof || prof->ctx != ctx) return set_err(GSW_EINVAL, "bad profile or context");
+    GSW_TRY(check_common(ctx, ntargets, flags));
+    if (ntargets == 0) return GSW_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    if (flags & GSW_HOST_IO) {
+        std::vector<int64_t> qo(ntargets, 0);
+        std::vector<int32_t> ql(ntargets, prof->qlen);
+        std::vector<uint8_t> qh(std::max(prof->qlen, 1));
+        if (prof->qlen) CUDA_TRY(cudaMemcpy(qh.data(), prof->query, prof->qlen, cudaMemcpyDeviceToHost));
+        return batch_impl(ctx, ntargets, qh.data(), qo.data(), ql.data(), t, t_off, t_len, prof->sc, flags,
+                          mask_len, results, cigar, cigar_capacity, colmax, colmax_off, st);
+    }
+    GSW_TRY(ensure(ctx, ctx->prof_qoff, sizeof(int64_t) * ntargets));
+    GSW_TRY(ensure(ctx, ctx->prof_qlen, sizeof(int32_t) * ntargets));
+    CUDA_TRY(launch_fill_const64((int64_t *)ctx->prof_qoff.p, 0, ntargets, st));
+    CUDA_TRY(launch_fill_const((int32_t *)ctx->prof_qlen.p, prof->qlen, ntargets, st));
+    return batch_impl(ctx, ntargets, prof->query, (const int64_t *)ctx->prof_qoff.p,
+                      (const int32_t *)ctx->prof_qlen.p, t, t_off, t_len, prof->sc, flags, mask_len, results,
+                      cigar, cigar_capacity, colmax, colmax_off, st);
+}
+
+}  // extern "C"

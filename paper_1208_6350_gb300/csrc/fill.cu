@@ -1,0 +1,549 @@
+// Local Smith-Waterman-Gotoh fill on sm_103a: the hot loop of the method
+// ("Algorithm and implementation", item (1): fill the score matrix while
+// keeping the per-column "max" array and the column holding the matrix
+// maximum; item (2): the suboptimal score from the masked max array).
+//
+// Layout ("folded ring").  One pair is handled by a group of P consecutive
+// lanes of a warp.  A strip of 2*P*R query rows is split into a low half
+// (rows [0, S)) and a high half (rows [S, 2S)), S = P*R.  Lane k owns R
+// 32-bit words; word r packs low-half row k*R + r in bits 0-15 and high-half
+// row S + k*R + r in bits 16-31, each as (value + 0x8000).  Per step, lane k
+// computes its R words for target column j = step - k in the low half and
+// column j - P in the high half, then passes its bottom row (H, F) and the
+// running column maximum to lane k+1 by a shuffle; lane P-1 passes its low
+// half to lane 0, whose high half continues that column P steps later.  So
+// every cell update is one lane of a 16x2 word, and the recurrences run on
+// full-rate instructions only:
+//     H  = max(H(i-1,j-1) + W, E, 0, F)      (IADD, 3x VIMNMX.U16x2)
+//     m  = max(m, H)                          (column max, VIMNMX)
+//     E' = max(E - X, H - O),  F' = max(F - X, H - O)   (2 IADD + 2 VIMNMX + IADD)
+// Adds are exact per lane because every lane value stays in [0, 0xFFFF] as
+// long as no score exceeds 32767 - max W; a pair whose maximum does is
+// flagged and re-filled in 32-bit lanes (same ring, one row per word).
+//
+// The score lookup W(q_i, t_j) comes from a per-lane shared-memory profile:
+// for DNA (4 letters) one word per (row pair, low letter, high letter), i.e.
+// 16 x R words; for other alphabets one low table and one high table.
+//
+// End position (the paper's "recorded column"): every lane tracks, per half,
+// the first column where its running column maximum (the maximum over rows 0
+// .. its last row) strictly improved, and keeps a copy of its own rows of that
+// column.  The lane-(P-1) high-half tracker gives score1 and the end column;
+// the first lane/half whose tracker holds (score1, end column) holds the end
+// row in its saved copy.
+#include "gsw_impl.cuh"
+
+#include <climits>
+#include <type_traits>
+
+namespace gsw {
+namespace {
+
+constexpr int kBlock = 128;
+
+// ---------------------------------------------------------------- lanes
+struct L16 {
+    static constexpr bool FOLD = true;
+    using cm_t = uint16_t;
+    using bnd_t = uint32_t;
+    static constexpr uint32_t Z = 0x8000u;    // bias of one lane
+    static constexpr uint32_t Z2 = 0x80008000u;
+    static __device__ __forceinline__ uint32_t vmax(uint32_t a, uint32_t b) { return __vmaxu2(a, b); }
+    static __device__ __forceinline__ uint32_t lane1(int v) { return (uint32_t)(v + 0x8000) & 0xFFFFu; }
+    static __device__ __forceinline__ uint32_t both(int v) { return lane1(v) | (lane1(v) << 16); }
+    // integer that adds c to both lanes of a word
+    static __device__ __forceinline__ uint32_t addk(int c) { return (uint32_t)(c * 65537); }
+};
+
+struct L32 {
+    static constexpr bool FOLD = false;
+    using cm_t = int32_t;
+    using bnd_t = int2;
+    static constexpr uint32_t Z2 = 0u;
+    static __device__ __forceinline__ uint32_t vmax(uint32_t a, uint32_t b) {
+        return (uint32_t)max((int)a, (int)b);
+    }
+    static __device__ __forceinline__ uint32_t lane1(int v) { return (uint32_t)v; }
+    static __device__ __forceinline__ uint32_t both(int v) { return (uint32_t)v; }
+    static __device__ __forceinline__ uint32_t addk(int c) { return (uint32_t)c; }
+};
+
+// words of the per-lane profile region
+__host__ __device__ constexpr int prof_words(int R, bool fold, bool dna, int A) {
+    return (dna ? (fold ? 16 * R : 4 * R) : (fold ? 2 * A * R : A * R)) + 4;
+}
+
+// One fill job for a group (one pair).
+struct Job {
+    const uint8_t *q;  // query row i at q[i * qs]
+    int qs;
+    int mrows;
+    const uint8_t *t;  // target column j at t[j * ts]
+    int ts;
+    int ncols;
+    uint32_t stop_u;   // reverse mode: stop at the first full column whose max equals this (biased); 0 = never
+    void *cms;         // column-max scratch (ncols entries)
+    void *bnd;         // strip boundary scratch (2 x ncols entries, ping-pong)
+};
+
+struct RingResult {
+    int score;  // max over the matrix (>= 0)
+    int col;    // first column reaching it (-1 if score == 0)
+    int row;    // first row of that column holding it, in padded row space
+    int pad_top;
+};
+
+template <int R>
+__device__ __forceinline__ void load_words(const uint32_t *p, uint32_t (&w)[R]) {
+    if constexpr (R % 4 == 0) {
+#pragma unroll
+        for (int r = 0; r < R; r += 4) {
+            uint4 v = *reinterpret_cast<const uint4 *>(p + r);
+            w[r] = v.x; w[r + 1] = v.y; w[r + 2] = v.z; w[r + 3] = v.w;
+        }
+    } else if constexpr (R % 2 == 0) {
+#pragma unroll
+        for (int r = 0; r < R; r += 2) {
+            uint2 v = *reinterpret_cast<const uint2 *>(p + r);
+            w[r] = v.x; w[r + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; r++) w[r] = p[r];
+    }
+}
+
+__device__ __forceinline__ int sc_w(const Scoring &sc, int a, int b) { return sc.W[a * sc.A + b]; }
+
+// Builds this lane's profile for strip `st` (padded rows of the strip:
+// [st*SP, st*SP + SP); padded row rho holds query row rho - pad_top).
+template <int P, int R, class L, bool DNA>
+__device__ __forceinline__ void build_profile(uint32_t *psm, const Job &job, const Scoring &sc, int k, int st,
+                                              int pad_top) {
+    constexpr int S = P * R;
+    constexpr int SP = L::FOLD ? 2 * S : S;
+    const int A = sc.A;
+#pragma unroll 1
+    for (int r = 0; r < R; r++) {
+        int rho_lo = st * SP + k * R + r - pad_top;
+        int qlo = rho_lo >= 0 ? min((int)job.q[(long long)rho_lo * job.qs], A - 1) : -1;
+        int qhi = -1;
+        if constexpr (L::FOLD) {
+            int rho_hi = st * SP + S + k * R + r - pad_top;
+            qhi = rho_hi >= 0 ? min((int)job.q[(long long)rho_hi * job.qs], A - 1) : -1;
+        }
+        if constexpr (DNA) {
+            if constexpr (L::FOLD) {
+#pragma unroll
+                for (int a = 0; a < 4; a++)
+#pragma unroll
+                    for (int b = 0; b < 4; b++) {
+                        int wl = qlo >= 0 ? sc_w(sc, qlo, a) : 0;
+                        int wh = qhi >= 0 ? sc_w(sc, qhi, b) : 0;
+                        psm[(a * 4 + b) * R + r] = (uint32_t)(wl + wh * 65536);
+                    }
+            } else {
+#pragma unroll
+                for (int a = 0; a < 4; a++) psm[a * R + r] = (uint32_t)(qlo >= 0 ? sc_w(sc, qlo, a) : 0);
+            }
+        } else {
+            for (int a = 0; a < A; a++) {
+                psm[a * R + r] = (uint32_t)(qlo >= 0 ? sc_w(sc, qlo, a) : 0);
+                if constexpr (L::FOLD) psm[(A + a) * R + r] = (uint32_t)((qhi >= 0 ? sc_w(sc, qhi, a) : 0) * 65536);
+            }
+        }
+    }
+}
+
+template <class L>
+__device__ __forceinline__ int lane_lo(uint32_t w) {
+    if constexpr (L::FOLD) return (int)(w & 0xFFFFu) - 0x8000;
+    else return (int)w;
+}
+template <class L>
+__device__ __forceinline__ int lane_hi(uint32_t w) {
+    if constexpr (L::FOLD) return (int)(w >> 16) - 0x8000;
+    else return (int)w;
+}
+
+// The ring fill of one pair by the P lanes of a group.  All lanes of the
+// group call it with the same job and return the same result.
+template <int P, int R, class L, bool DNA>
+__device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm, int k, unsigned gmask,
+                                int gbase) {
+    constexpr int S = P * R;
+    constexpr int SP = L::FOLD ? 2 * S : S;
+    constexpr uint32_t Z2 = L::Z2;
+    const int n = job.ncols;
+    const int nstrips = (job.mrows + SP - 1) / SP;
+    const int pad_top = nstrips * SP - job.mrows;
+    const uint32_t kO = L::addk(-sc.O), kX = L::addk(-sc.X);
+    const uint32_t NEGE = L::both(-sc.O);  // E and F on the boundary: exactly -O after one step
+    const int A = sc.A;
+    const int src = gbase + ((k + P - 1) & (P - 1));
+    const int nsteps = n + (L::FOLD ? 2 * P - 1 : P - 1);
+    typename L::cm_t *cms = reinterpret_cast<typename L::cm_t *>(job.cms);
+    typename L::bnd_t *bnd = reinterpret_cast<typename L::bnd_t *>(job.bnd);
+
+    RingResult res{0, -1, -1, pad_top};
+    int g_score = 0, g_col = -1, g_row = -1;
+
+#pragma unroll 1
+    for (int st = 0; st < nstrips; st++) {
+        build_profile<P, R, L, DNA>(psm, job, sc, k, st, pad_top);
+        __syncwarp(gmask);
+        const typename L::bnd_t *bin = bnd + (size_t)((st + 1) & 1) * n;  // written by strip st-1
+        typename L::bnd_t *bout = bnd + (size_t)(st & 1) * n;             // read by strip st+1
+        const bool last_strip = st == nstrips - 1;
+
+        uint32_t H[R], E[R], SV[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) { H[r] = Z2; E[r] = NEGE; SV[r] = Z2; }
+        uint32_t hdiag = Z2;
+        uint32_t best = Z2;
+        int c_lo = -1, c_hi = -1;
+        uint32_t xh = Z2, xf = NEGE, xc = Z2;  // values received from lane k-1
+
+#pragma unroll 1
+        for (int s = 0; s < nsteps; s++) {
+            const int jlo = s - k;
+            const int jhi = L::FOLD ? jlo - P : jlo;
+            // inputs from the row above
+            uint32_t hin = xh, fin = xf, cmin = xc;
+            if (k == 0) {
+                uint32_t bh = L::lane1(0), bf = L::lane1(-sc.O);
+                if (st > 0 && jlo >= 0 && jlo < n) {
+                    if constexpr (L::FOLD) {
+                        uint32_t w = bin[jlo];
+                        bh = w & 0xFFFFu;
+                        bf = w >> 16;
+                    } else {
+                        int2 w = bin[jlo];
+                        bh = (uint32_t)w.x;
+                        bf = (uint32_t)w.y;
+                    }
+                }
+                if constexpr (L::FOLD) {
+                    hin = (xh << 16) | bh;
+                    fin = (xf << 16) | bf;
+                    cmin = (xc << 16) | L::Z;
+                } else {
+                    hin = bh;
+                    fin = bf;
+                    cmin = Z2;
+                }
+            }
+            // letters of this lane's columns
+            const int al = (jlo >= 0 && jlo < n) ? min((int)job.t[(long long)jlo * job.ts], A - 1) : 0;
+            uint32_t pw[R];
+            if constexpr (DNA) {
+                if constexpr (L::FOLD) {
+                    const int ah = (jhi >= 0 && jhi < n) ? min((int)job.t[(long long)jhi * job.ts], A - 1) : 0;
+                    load_words<R>(psm + (al * 4 + ah) * R, pw);
+                } else {
+                    load_words<R>(psm + al * R, pw);
+                }
+            } else {
+                load_words<R>(psm + al * R, pw);
+                if constexpr (L::FOLD) {
+                    const int ah = (jhi >= 0 && jhi < n) ? min((int)job.t[(long long)jhi * job.ts], A - 1) : 0;
+                    uint32_t ph[R];
+                    load_words<R>(psm + (A + ah) * R, ph);
+#pragma unroll
+                    for (int r = 0; r < R; r++) pw[r] += ph[r];
+                }
+            }
+            uint32_t diag = hdiag;
+            hdiag = hin;
+            uint32_t f = fin, m = cmin;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                uint32_t h = L::vmax(diag + pw[r], E[r]);
+                h = L::vmax(h, Z2);
+                h = L::vmax(h, f);
+                diag = H[r];
+                H[r] = h;
+                m = L::vmax(m, h);
+                const uint32_t ho = h + kO;
+                E[r] = L::vmax(E[r] + kX, ho);
+                f = L::vmax(f + kX, ho);
+            }
+            // before a half's first column its state must be the left boundary
+            if (jhi < 0) {
+                const uint32_t keep = (L::FOLD && jlo >= 0) ? 0x0000FFFFu : 0u;
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    H[r] = (H[r] & keep) | (Z2 & ~keep);
+                    E[r] = (E[r] & keep) | (NEGE & ~keep);
+                }
+                hdiag = (hdiag & keep) | (Z2 & ~keep);
+            }
+            // tracker: first column where the running column max strictly improved
+            {
+                uint32_t vm = 0;
+                if (jlo >= 0 && jlo < n) vm |= L::FOLD ? 0x0000FFFFu : 0xFFFFFFFFu;
+                if (L::FOLD && jhi >= 0 && jhi < n) vm |= 0xFFFF0000u;
+                const uint32_t cme = (m & vm) | (Z2 & ~vm);
+                const uint32_t nb = L::vmax(cme, best);
+                if (nb != best) {
+                    const uint32_t diff = nb ^ best;
+                    uint32_t mk;
+                    if constexpr (L::FOLD) {
+                        mk = ((diff & 0xFFFFu) ? 0x0000FFFFu : 0u) | ((diff >> 16) ? 0xFFFF0000u : 0u);
+                        if (diff & 0xFFFFu) c_lo = jlo;
+                        if (diff >> 16) c_hi = jhi;
+                    } else {
+                        mk = 0xFFFFFFFFu;
+                        c_lo = jlo;
+                    }
+                    best = nb;
+#pragma unroll
+                    for (int r = 0; r < R; r++) SV[r] = (H[r] & mk) | (SV[r] & ~mk);
+                }
+            }
+            // the last lane holds complete columns: column max and strip boundary
+            bool found = false;
+            if (k == P - 1 && jhi >= 0 && jhi < n) {
+                if constexpr (L::FOLD) {
+                    const uint32_t full = m >> 16;
+                    if (job.cms) {
+                        if (st == 0) cms[jhi] = (uint16_t)full;
+                        else cms[jhi] = (uint16_t)max((uint32_t)cms[jhi], full);
+                    }
+                    if (!last_strip) bout[jhi] = (H[R - 1] >> 16) | (f & 0xFFFF0000u);
+                    found = job.stop_u && full == job.stop_u;
+                } else {
+                    if (job.cms) {
+                        if (st == 0) cms[jhi] = (int)m;
+                        else cms[jhi] = max(cms[jhi], (int)m);
+                    }
+                    if (!last_strip) bout[jhi] = make_int2((int)H[R - 1], (int)f);
+                    found = job.stop_u && m == job.stop_u;
+                }
+            }
+            if (job.stop_u && nstrips == 1 && __any_sync(gmask, found)) break;
+            xh = __shfl_sync(gmask, H[R - 1], src);
+            xf = __shfl_sync(gmask, f, src);
+            xc = __shfl_sync(gmask, m, src);
+        }
+
+        // ---- strip epilogue: the strip's maximum, its first column, its first row
+        const uint32_t bl = __shfl_sync(gmask, best, gbase + P - 1);
+        const int cl = __shfl_sync(gmask, L::FOLD ? c_hi : c_lo, gbase + P - 1);
+        const int vfull = lane_hi<L>(bl);
+        int cand = INT_MAX;
+        if (vfull > 0) {
+            if (lane_lo<L>(best) == vfull && c_lo == cl) {
+#pragma unroll
+                for (int r = R - 1; r >= 0; r--)
+                    if (lane_lo<L>(SV[r]) == vfull) cand = k * R + r;
+            } else if (L::FOLD && lane_hi<L>(best) == vfull && c_hi == cl) {
+#pragma unroll
+                for (int r = R - 1; r >= 0; r--)
+                    if (lane_hi<L>(SV[r]) == vfull) cand = S + k * R + r;
+            }
+        }
+#pragma unroll
+        for (int d = 1; d < P; d <<= 1) cand = min(cand, __shfl_xor_sync(gmask, cand, d));
+        if (vfull > g_score || (vfull == g_score && vfull > 0 && cl < g_col)) {
+            g_score = vfull;
+            g_col = cl;
+            g_row = st * SP + cand;
+        }
+        __syncwarp(gmask);
+    }
+    res.score = g_score;
+    res.col = g_score > 0 ? g_col : -1;
+    res.row = g_score > 0 ? g_row : -1;
+    return res;
+}
+
+// Secondary score (item (2)): largest max-array value outside the window
+// [end - L, end + L], first column holding it; and the optional max-array
+// output.  Reads the column maxima the fill left in the slot scratch.
+template <int P, class L>
+__device__ void secondary(const BatchView &b, int pair, const Job &job, int end_t, int m, int k, unsigned gmask,
+                          int *score2, int *end2) {
+    const typename L::cm_t *cms = reinterpret_cast<const typename L::cm_t *>(job.cms);
+    const int n = job.ncols;
+    const int Lm = b.mask_len >= 0 ? b.mask_len : max(m / 2, 15);
+    const long long lo = (long long)end_t - Lm, hi = (long long)end_t + Lm;
+    int bv = 0, bj = INT_MAX;
+    int32_t *out = (b.flags & GSW_COLMAX) ? b.colmax + b.colmax_off[pair] : nullptr;
+    for (int j = k; j < n; j += P) {
+        int v;
+        if constexpr (L::FOLD) v = (int)cms[j] - 0x8000;
+        else v = cms[j];
+        if (out) out[j] = v;
+        if (end_t >= 0 && j >= lo && j <= hi) continue;
+        if (v > bv) { bv = v; bj = j; }
+    }
+#pragma unroll
+    for (int d = 1; d < P; d <<= 1) {
+        int ov = __shfl_xor_sync(gmask, bv, d);
+        int oj = __shfl_xor_sync(gmask, bj, d);
+        if (ov > bv || (ov == bv && oj < bj)) { bv = ov; bj = oj; }
+    }
+    *score2 = bv;
+    *end2 = bv > 0 ? bj : -1;
+}
+
+template <int P, int R, class L, bool DNA>
+__device__ void run_task(const FillLaunch &fl, int first, int last, uint32_t *wsm, int lane, int slot_base) {
+    const int g = lane / P, k = lane % P, gbase = g * P;
+    const unsigned gmask = (P == 32) ? 0xFFFFFFFFu : (((1u << P) - 1u) << gbase);
+    const int idx = first + g;
+    if (idx >= last) return;
+    const BatchView &b = fl.b;
+    const Scoring &sc = fl.sc;
+    const int pair = fl.plan.order[idx];
+    gsw_result *rp = b.res + pair;
+    const int m = b.q_len[pair], n = b.t_len[pair];
+    const uint8_t *qp = b.q + b.q_off[pair];
+    const uint8_t *tp = b.t + b.t_off[pair];
+    const int slot = slot_base + g;
+    constexpr int PW = prof_words(R, L::FOLD, DNA, 0);
+    uint32_t *psm = wsm + lane * (DNA ? PW : prof_words(R, L::FOLD, false, sc.A));
+    Job job;
+    const size_t ncap = (size_t)fl.scr.ncap;
+    // one stride for every variant, so slots never overlap when 16-bit and
+    // 32-bit tasks run in the same launch
+    job.cms = (char *)fl.scr.colmax + slot * ncap * sizeof(int32_t);
+    job.bnd = (char *)fl.scr.boundary + slot * 2 * ncap * sizeof(int2);
+    job.stop_u = 0;
+
+    if (fl.mode == kFillReverse) {
+        const int s1 = rp->score1, eq = rp->read_end1, et = rp->ref_end1;
+        job.q = qp + eq;
+        job.qs = -1;
+        job.mrows = eq + 1;
+        job.t = tp + et;
+        job.ts = -1;
+        job.ncols = reverse_window(eq, et, s1, sc);
+        job.stop_u = L::lane1(s1);
+        job.cms = nullptr;
+        RingResult rr = ring_fill<P, R, L, DNA>(job, sc, psm, k, gmask, gbase);
+        if (k == 0) {
+            if (rr.score == s1 && rr.col >= 0) {
+                rp->ref_begin1 = et - rr.col;
+                rp->read_begin1 = eq - (rr.row - rr.pad_top);
+            } else {
+                rp->flags |= kResInternal;  // reversed maximum differs from score1
+            }
+        }
+        return;
+    }
+    // forward (16-bit first pass, or 32-bit rerun)
+    if (m <= 0 || n <= 0) {
+        if (k == 0) {
+            rp->score1 = 0; rp->score2 = 0; rp->ref_begin1 = -1; rp->ref_end1 = -1;
+            rp->read_begin1 = -1; rp->read_end1 = -1; rp->ref_end2 = -1; rp->cigar_len = 0;
+            rp->cigar_off = -1; rp->flags = L::FOLD ? 0 : GSW_RES_S32; rp->reserved = 0;
+        }
+        if ((b.flags & GSW_COLMAX) && n > 0)
+            for (int j = k; j < n; j += P) b.colmax[b.colmax_off[pair] + j] = 0;
+        return;
+    }
+    job.q = qp;
+    job.qs = 1;
+    job.mrows = m;
+    job.t = tp;
+    job.ts = 1;
+    job.ncols = n;
+    RingResult rr = ring_fill<P, R, L, DNA>(job, sc, psm, k, gmask, gbase);
+    const bool overflow = L::FOLD && rr.score > 32767 - sc.wmax;
+    int s2 = 0, e2 = -1;
+    const int end_t = rr.col, end_q = rr.score > 0 ? rr.row - rr.pad_top : -1;
+    if (!overflow) {
+        __syncwarp(gmask);
+        secondary<P, L>(b, pair, job, end_t, m, k, gmask, &s2, &e2);
+    }
+    if (k == 0) {
+        rp->score1 = rr.score;
+        rp->score2 = s2;
+        rp->ref_end1 = end_t;
+        rp->read_end1 = end_q;
+        rp->ref_begin1 = -1;
+        rp->read_begin1 = -1;
+        rp->ref_end2 = e2;
+        rp->cigar_len = 0;
+        rp->cigar_off = -1;
+        rp->flags = overflow ? (GSW_RES_S32 | kResPendingS32) : (L::FOLD ? 0 : GSW_RES_S32);
+        rp->reserved = 0;
+    }
+}
+
+// Persistent fill kernel: warps take tasks (32/P pairs of one variant) from a
+// queue ordered heaviest variant first, target length descending.
+template <bool DNA>
+__global__ void __launch_bounds__(kBlock) k_fill(FillLaunch fl, int warp_words) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gwarp = blockIdx.x * (kBlock / 32) + warp;
+    uint32_t *wsm = smem + (size_t)warp * warp_words;
+    const int slot_base = gwarp * fl.scr.slots_per_warp;
+    const int ntasks = *fl.plan.ntasks;
+    for (;;) {
+        int task = 0;
+        if (lane == 0) task = atomicAdd(fl.plan.head, 1);
+        task = __shfl_sync(0xFFFFFFFFu, task, 0);
+        if (task >= ntasks) break;
+        int v = 0;
+        while (v < kNumVariants - 1 && !(task >= fl.plan.task_lo[v] && task < fl.plan.task_hi[v])) v++;
+        const int per = 32 / variant_at(v).P;
+        const int first = fl.plan.var_start[v] + (task - fl.plan.task_lo[v]) * per;
+        const int last = fl.plan.var_start[v + 1];
+        switch (v) {
+#define GSW_RUN_CASE(id, P, R, S32)                                                         \
+    case id:                                                                                \
+        run_task<P, R, std::conditional_t<S32 != 0, L32, L16>, DNA>(fl, first, last, wsm, lane, \
+                                                                    slot_base);             \
+        break;
+            GSW_FILL_VARIANTS(GSW_RUN_CASE)
+#undef GSW_RUN_CASE
+        default: break;
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+int fill_block_threads() { return kBlock; }
+
+// shared memory words per warp: the largest per-lane profile of any variant
+size_t fill_smem_per_warp(const Scoring &sc) {
+    const bool dna = sc.dna4 != 0;
+    int w = 0;
+    for (int v = 0; v < kNumVariants; v++) {
+        int pw = prof_words(variant_at(v).R, !variant_at(v).s32, dna, sc.A);
+        w = w > pw ? w : pw;
+    }
+    return (size_t)w * 32 * sizeof(uint32_t);
+}
+
+int fill_max_blocks_per_sm(const Scoring &sc, size_t smem) {
+    int nb = 0;
+    if (sc.dna4) {
+        cudaFuncSetAttribute(k_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fill<true>, kBlock, smem);
+    } else {
+        cudaFuncSetAttribute(k_fill<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fill<false>, kBlock, smem);
+    }
+    return nb;
+}
+
+cudaError_t launch_fill(const FillLaunch &fl, int grid, size_t smem, cudaStream_t st) {
+    const int warp_words = (int)(smem / sizeof(uint32_t) / (kBlock / 32));
+    if (fl.sc.dna4) {
+        cudaFuncSetAttribute(k_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_fill<true><<<grid, kBlock, smem, st>>>(fl, warp_words);
+    } else {
+        cudaFuncSetAttribute(k_fill<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_fill<false><<<grid, kBlock, smem, st>>>(fl, warp_words);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gsw

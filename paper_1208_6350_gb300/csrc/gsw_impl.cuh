@@ -1,0 +1,200 @@
+// Internal declarations shared by the library's translation units (device
+// kernels and the host runtime behind include/gsw.h).  Nothing here is part of
+// the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gsw.h"
+
+namespace gsw {
+
+constexpr int kMaxAlpha = 32;
+
+// Scoring scheme, passed by value to kernels (lives in the parameter bank).
+struct Scoring {
+    int32_t A;      // alphabet size
+    int32_t O, X;   // gap open / extend, positive, O >= X: a gap of length k costs O + (k-1) X
+    int32_t wmax;   // max matrix entry
+    int32_t wmin;   // min matrix entry
+    int32_t dna4;   // 1 when A == 4: the fill uses the letter-pair profile
+    int8_t W[kMaxAlpha * kMaxAlpha];  // W[a * A + b]: query letter a vs target letter b
+};
+
+// Batch view (device pointers) shared by every stage.
+struct BatchView {
+    const uint8_t *q;
+    const int64_t *q_off;
+    const int32_t *q_len;
+    const uint8_t *t;
+    const int64_t *t_off;
+    const int32_t *t_len;
+    gsw_result *res;
+    int32_t npairs;
+    uint32_t flags;
+    int32_t mask_len;  // < 0: max(m/2, 15)
+    int32_t *colmax;
+    const int64_t *colmax_off;
+    uint32_t *cigar;
+    int64_t cigar_cap;
+    unsigned long long *cigar_cursor;
+};
+
+// Stage of the pipeline a fill launch serves.
+enum FillMode : int32_t {
+    kFillForward = 0,  // forward local fill: score1, ends, max array, secondary
+    kFillRerun = 1,    // forward fill in 32-bit lanes for pairs whose 16-bit fill overflowed
+    kFillReverse = 2,  // reversed fill from the end: begins
+};
+
+// Kernel variants: (threads per pair P, row-words per thread R, 32-bit
+// lanes).  A 16-bit variant covers 2*P*R query rows per strip, a 32-bit one
+// P*R; longer queries run in several strips.  X(id, P, R, s32)
+#define GSW_FILL_VARIANTS(X) \
+    X(0, 16, 2, 0)           \
+    X(1, 16, 3, 0)           \
+    X(2, 16, 4, 0)           \
+    X(3, 16, 5, 0)           \
+    X(4, 16, 6, 0)           \
+    X(5, 16, 7, 0)           \
+    X(6, 16, 8, 0)           \
+    X(7, 32, 8, 1)
+struct Variant {
+    int P, R, s32;
+};
+constexpr int kNumVariants = 8;
+constexpr int kVarS32 = 7;
+constexpr int kVarMaxS16 = 6;
+__host__ __device__ inline Variant variant_at(int v) {
+    switch (v) {
+#define GSW_VARIANT_CASE(id, P, R, S32) \
+    case id: return Variant{P, R, S32};
+        GSW_FILL_VARIANTS(GSW_VARIANT_CASE)
+#undef GSW_VARIANT_CASE
+    default: return Variant{32, 8, 1};
+    }
+}
+__host__ __device__ inline int variant_rows(int v) {
+    Variant x = variant_at(v);
+    return x.s32 ? x.P * x.R : 2 * x.P * x.R;
+}
+
+// Work plan of one fill launch: pairs sorted by (variant, cost descending),
+// cut into warp tasks of 32/P pairs of one variant.  Task indices are handed
+// out heaviest variant first (variant index descending).
+struct FillPlan {
+    const int32_t *order;      // sorted pair indices
+    const int32_t *var_start;  // [kNumVariants+1] start of each variant's pairs in `order`
+    const int32_t *task_lo;    // [kNumVariants] first task index of each variant
+    const int32_t *task_hi;    // [kNumVariants] one past its last task index
+    int32_t *head;             // task counter (zeroed by the plan)
+    const int32_t *ntasks;     // total tasks
+};
+
+// Per-slot scratch of a persistent fill launch (one slot per pair in flight).
+struct FillScratch {
+    void *colmax;    // slots x ncap elements (uint16 biased for 16-bit, int32 for 32-bit)
+    void *boundary;  // slots x 2 x ncap boundary words (uint32 for 16-bit, int2 for 32-bit)
+    int32_t ncap;    // columns per slot
+    int32_t slots_per_warp;
+};
+
+struct FillLaunch {
+    BatchView b;
+    Scoring sc;
+    FillPlan plan;
+    FillScratch scr;
+    int32_t mode;
+};
+
+// internal per-pair bits (besides the public GSW_RES_*)
+constexpr int32_t kResPendingS32 = 0x40;  // 16-bit fill overflowed: refill in 32-bit lanes
+constexpr int32_t kResInternal = 0x80;    // a consistency check failed (should never happen)
+
+constexpr int kPlanBinsPerVariant = 1024;
+constexpr int kPlanBins = kNumVariants * kPlanBinsPerVariant;
+
+// Width of the window the reversed fill scans, ending at the end column: an
+// optimal alignment ending at (end_q, end_t) with score1 has at most
+// D = ((end_q+1)*wmax - score1 - O)/X + 1 target letters against gaps (every
+// gap run costs at least O + (len-1)X when O >= X), so it begins within
+// end_q + 1 + D columns of the end.
+__host__ __device__ inline int reverse_window(int end_q, int end_t, int score1, const Scoring &sc) {
+    if (sc.X <= 0) return end_t + 1;
+    long long d = (long long)(end_q + 1) * sc.wmax - score1 - sc.O;
+    d = d < 0 ? 0 : d / sc.X + 1;
+    long long w = (long long)end_q + 1 + d;
+    long long lim = (long long)end_t + 1;
+    return (int)(w < lim ? w : lim);
+}
+
+// Half-width of the band of the global alignment between begin and end
+// (la x lb letters, optimum score1): a path through diagonal d has at least
+// g = |d| + |lb - la - d| gap letters and (la + lb - g)/2 aligned pairs, so
+// scores at most wmax*floor((la+lb-g)/2) - O - (g-1)X; diagonals where that
+// bound is below score1 carry no optimal path.  Returns w such that the band
+// is [min(0, lb-la) - w, max(0, lb-la) + w].
+__host__ __device__ inline int band_halfwidth(int la, int lb, int score1, const Scoring &sc) {
+    const int delta = lb - la;
+    const int g0 = delta < 0 ? -delta : delta;
+    auto ub = [&](long long g) -> long long {
+        long long aligned = ((long long)la + lb - g) / 2;
+        long long s = (long long)sc.wmax * aligned;
+        if (g > 0) s -= sc.O + (g - 1) * (long long)sc.X;
+        return s;
+    };
+    // largest w with ub(g0 + 2w) >= score1 (ub is non-increasing in g)
+    int lo = 0, hi = la + lb + 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (ub(g0 + 2LL * mid) >= score1) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// stage launchers (host side, enqueue on `st`)
+int fill_block_threads();
+size_t fill_smem_per_warp(const Scoring &sc);
+int fill_max_blocks_per_sm(const Scoring &sc, size_t smem);
+cudaError_t launch_fill(const FillLaunch &fl, int grid, size_t smem, cudaStream_t st);
+
+struct PlanBuffers {
+    int32_t *keys;       // [npairs]
+    int32_t *hist;       // [kPlanBins]
+    int32_t *binoff;     // [kPlanBins]
+    int32_t *cursor;     // [kPlanBins]
+    int32_t *order;      // [npairs]
+    int32_t *var_start;  // [kNumVariants+1]
+    int32_t *task_lo;    // [kNumVariants]
+    int32_t *task_hi;    // [kNumVariants]
+    int32_t *ntasks;     // [1]
+    int32_t *head;       // [1]
+};
+cudaError_t launch_plan(const BatchView &b, const Scoring &sc, int32_t mode, const PlanBuffers &pb,
+                        cudaStream_t st);
+
+struct TraceScratch {
+    uint32_t *dirs;        // per warp: dir_words words (global direction bit-planes)
+    int64_t dir_words;     // per warp
+    uint32_t *ops;         // per warp: op_words words (reversed CIGAR runs)
+    int64_t op_words;      // per warp
+    int32_t *head;         // pair counter
+};
+int trace_block_threads();
+size_t trace_smem_bytes();
+// max over the batch of [0] direction words, [1] op words, [2] chunks of 32 diagonals
+cudaError_t launch_trace_need(const BatchView &b, const Scoring &sc, unsigned long long *max_need,
+                              cudaStream_t st);
+cudaError_t launch_traceback(const BatchView &b, const Scoring &sc, const TraceScratch &ts, int grid,
+                             cudaStream_t st);
+
+// small helpers (misc.cu)
+cudaError_t launch_max_lengths(const int32_t *q_len, const int32_t *t_len, int32_t n, int32_t *out2,
+                               cudaStream_t st);
+cudaError_t launch_validate(const BatchView &b, const Scoring &sc, int32_t *bad, cudaStream_t st);
+cudaError_t launch_fill_const(int32_t *dst, int32_t v, int32_t n, cudaStream_t st);
+cudaError_t launch_fill_const64(int64_t *dst, int64_t v, int32_t n, cudaStream_t st);
+
+}  // namespace gsw

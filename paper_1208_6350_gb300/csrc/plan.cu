@@ -1,0 +1,127 @@
+// Work planning for the persistent fill launches, entirely on the device so
+// that a batch needs no host round trip and the stage chain can be captured
+// in a CUDA graph.  A counting sort groups pairs by fill variant (how many
+// query rows a strip covers) and, inside a variant, by estimated cost
+// (strips x steps) descending; the persistent kernel then hands out warp
+// tasks heaviest variant first, so long pairs start early and the tail is
+// made of short ones.
+#include "gsw_impl.cuh"
+
+namespace gsw {
+namespace {
+
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ int pick_s16(int rows) {
+    for (int v = 0; v <= kVarMaxS16; v++)
+        if (variant_rows(v) >= rows) return v;
+    return kVarMaxS16;  // several strips
+}
+
+__device__ __forceinline__ int cost_bin(long long cost) {
+    // 32 bins per doubling of cost, descending order inside a variant
+    float lg = log2f((float)(cost < 1 ? 1 : cost));
+    int bin = (int)(lg * 32.0f);
+    bin = bin < 0 ? 0 : (bin > kPlanBinsPerVariant - 1 ? kPlanBinsPerVariant - 1 : bin);
+    return kPlanBinsPerVariant - 1 - bin;
+}
+
+__global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys, int32_t *hist) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.npairs) return;
+    int rows, cols, v;
+    if (mode == kFillForward) {
+        rows = b.q_len[p];
+        cols = b.t_len[p];
+        v = (b.flags & GSW_FORCE_S32) ? kVarS32 : pick_s16(rows);
+    } else if (mode == kFillRerun) {
+        if (!(b.res[p].flags & kResPendingS32)) { keys[p] = -1; return; }
+        rows = b.q_len[p];
+        cols = b.t_len[p];
+        v = kVarS32;
+    } else {
+        const gsw_result r = b.res[p];
+        if (r.score1 <= 0 || (r.flags & kResInternal)) { keys[p] = -1; return; }
+        rows = r.read_end1 + 1;
+        cols = reverse_window(r.read_end1, r.ref_end1, r.score1, sc);
+        v = (r.flags & GSW_RES_S32) ? kVarS32 : pick_s16(rows);
+    }
+    const Variant var = variant_at(v);
+    const int sp = variant_rows(v);
+    const long long strips = rows <= 0 ? 1 : (rows + sp - 1) / sp;
+    const long long steps = (long long)cols + (var.s32 ? var.P : 2 * var.P);
+    const int key = v * kPlanBinsPerVariant + cost_bin(strips * steps);
+    keys[p] = key;
+    atomicAdd(&hist[key], 1);
+}
+
+// Exclusive scan of the bins (one block), variant boundaries and task ranges.
+__global__ void __launch_bounds__(kScanThreads) k_plan_scan(const int32_t *hist, int32_t *binoff,
+                                                             int32_t *var_start, int32_t *task_lo,
+                                                             int32_t *task_hi, int32_t *ntasks, int32_t *head) {
+    constexpr int PER = kPlanBins / kScanThreads;
+    static_assert(kPlanBins % kScanThreads == 0, "bins");
+    __shared__ int32_t part[kScanThreads];
+    const int tid = threadIdx.x;
+    int32_t loc[PER];
+    int32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        loc[i] = sum;
+        sum += hist[tid * PER + i];
+    }
+    part[tid] = sum;
+    __syncthreads();
+    for (int d = 1; d < kScanThreads; d <<= 1) {
+        int32_t v = tid >= d ? part[tid - d] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    const int32_t base = part[tid] - sum;
+#pragma unroll
+    for (int i = 0; i < PER; i++) binoff[tid * PER + i] = base + loc[i];
+    __syncthreads();
+    if (tid == 0) {
+        int32_t starts[kNumVariants + 1];
+        for (int v = 0; v < kNumVariants; v++) starts[v] = binoff[v * kPlanBinsPerVariant];
+        starts[kNumVariants] = part[kScanThreads - 1];
+        for (int v = 0; v <= kNumVariants; v++) var_start[v] = starts[v];
+        int32_t t = 0;
+        for (int v = kNumVariants - 1; v >= 0; v--) {
+            const int per = 32 / variant_at(v).P;
+            const int32_t cnt = starts[v + 1] - starts[v];
+            task_lo[v] = t;
+            t += (cnt + per - 1) / per;
+            task_hi[v] = t;
+        }
+        *ntasks = t;
+        *head = 0;
+    }
+}
+
+__global__ void k_plan_scatter(int32_t npairs, const int32_t *keys, const int32_t *binoff, int32_t *cursor,
+                               int32_t *order) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs) return;
+    const int key = keys[p];
+    if (key < 0) return;
+    order[binoff[key] + atomicAdd(&cursor[key], 1)] = p;
+}
+
+}  // namespace
+
+cudaError_t launch_plan(const BatchView &b, const Scoring &sc, int32_t mode, const PlanBuffers &pb,
+                        cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(pb.hist, 0, sizeof(int32_t) * kPlanBins, st))) return e;
+    if ((e = cudaMemsetAsync(pb.cursor, 0, sizeof(int32_t) * kPlanBins, st))) return e;
+    const int nb = (b.npairs + 255) / 256;
+    if (nb > 0) k_plan_keys<<<nb, 256, 0, st>>>(b, sc, mode, pb.keys, pb.hist);
+    k_plan_scan<<<1, kScanThreads, 0, st>>>(pb.hist, pb.binoff, pb.var_start, pb.task_lo, pb.task_hi,
+                                            pb.ntasks, pb.head);
+    if (nb > 0) k_plan_scatter<<<nb, 256, 0, st>>>(b.npairs, pb.keys, pb.binoff, pb.cursor, pb.order);
+    return cudaGetLastError();
+}
+
+}  // namespace gsw

@@ -1,0 +1,218 @@
+"""Python binding of the C ABI in include/gsw.h (argument marshalling only).
+
+Every function here forwards to libgsw.so, the CUDA library built from
+csrc/.  There is no fallback: if the library is missing the calls raise.
+PyTorch tensors (device memory, streams) and numpy arrays (host memory, with
+GSW_HOST_IO) are accepted wherever the C call takes a pointer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+GSW_OK = 0
+GSW_EINVAL = -1
+GSW_ENOMEM = -2
+GSW_ECUDA = -3
+GSW_ETIMEDOUT = -4
+GSW_ECIGAR_SPACE = -5
+GSW_EOVERFLOW = -6
+GSW_ENOTFOUND = -7
+GSW_ESTATE = -8
+
+GSW_BEGIN = 0x1
+GSW_CIGAR = 0x2
+GSW_COLMAX = 0x4
+GSW_HOST_IO = 0x8
+GSW_FORCE_S32 = 0x10
+GSW_PLAIN = 0x20
+
+GSW_RES_S32 = 0x1
+GSW_RES_CIGAR_SPACE = 0x2
+
+RESULT_DTYPE = np.dtype([
+    ("score1", np.int32), ("score2", np.int32), ("ref_begin1", np.int32), ("ref_end1", np.int32),
+    ("read_begin1", np.int32), ("read_end1", np.int32), ("ref_end2", np.int32),
+    ("cigar_len", np.int32), ("cigar_off", np.int64), ("flags", np.int32), ("reserved", np.int32),
+])
+assert RESULT_DTYPE.itemsize == 48
+
+_lib = None
+
+
+class GswError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code}): {last_error()}")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libgsw.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library not built: {_build.LIB}")
+    lib = ctypes.CDLL(_build.LIB)
+    P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    lib.gsw_context_create.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(P)]
+    lib.gsw_context_destroy.argtypes = [P]
+    lib.gsw_align_batch.argtypes = [P, i32, P, P, P, P, P, P, P, i32, i32, i32, u32, i32, P, P, i64, P,
+                                    P, P]
+    lib.gsw_profile_create.argtypes = [P, P, i32, P, i32, i32, i32, ctypes.POINTER(P)]
+    lib.gsw_profile_destroy.argtypes = [P]
+    lib.gsw_align_profile.argtypes = [P, P, i32, P, P, P, u32, i32, P, P, i64, P, P, P]
+    for f in (lib.gsw_context_create, lib.gsw_context_destroy, lib.gsw_align_batch,
+              lib.gsw_profile_create, lib.gsw_profile_destroy, lib.gsw_align_profile):
+        f.restype = ctypes.c_int
+    lib.gsw_strerror.argtypes = [ctypes.c_int]
+    lib.gsw_strerror.restype = ctypes.c_char_p
+    lib.gsw_last_error.restype = ctypes.c_char_p
+    lib.gsw_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().gsw_strerror(code).decode()
+
+
+def last_error() -> str:
+    return load().gsw_last_error().decode()
+
+
+def gsw_version() -> str:
+    return load().gsw_version().decode()
+
+
+def _ptr(x):
+    """Address of a torch tensor, numpy array, or an int; None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _check(rc, what):
+    if rc != GSW_OK:
+        raise GswError(rc, what)
+    return rc
+
+
+def gsw_context_create(device: int = 0, mem_budget_bytes: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _check(load().gsw_context_create(device, mem_budget_bytes, ctypes.byref(out)), "gsw_context_create")
+    return out.value
+
+
+def gsw_context_destroy(ctx: int) -> None:
+    _check(load().gsw_context_destroy(ctx), "gsw_context_destroy")
+
+
+def gsw_align_batch(ctx, npairs, q, q_off, q_len, t, t_off, t_len, matrix, gap_open, gap_extend,
+                    flags=0, mask_len=-1, results=None, cigar=None, cigar_capacity=0, colmax=None,
+                    colmax_off=None, stream=None, check=True) -> int:
+    """Direct call of gsw_align_batch; pointer arguments may be tensors/arrays."""
+    m = np.ascontiguousarray(matrix, dtype=np.int8)
+    A = m.shape[0]
+    st = _stream_handle(stream)
+    rc = load().gsw_align_batch(ctx, npairs, _ptr(q), _ptr(q_off), _ptr(q_len), _ptr(t), _ptr(t_off),
+                                _ptr(t_len), m.ctypes.data, A, gap_open, gap_extend, flags, mask_len,
+                                _ptr(results), _ptr(cigar), cigar_capacity, _ptr(colmax),
+                                _ptr(colmax_off), st)
+    if check and rc != GSW_ECIGAR_SPACE:
+        _check(rc, "gsw_align_batch")
+    return rc
+
+
+def gsw_profile_create(ctx, query, matrix, gap_open, gap_extend) -> int:
+    q = np.ascontiguousarray(query, dtype=np.uint8)
+    m = np.ascontiguousarray(matrix, dtype=np.int8)
+    out = ctypes.c_void_p()
+    _check(load().gsw_profile_create(ctx, q.ctypes.data, len(q), m.ctypes.data, m.shape[0], gap_open,
+                                     gap_extend, ctypes.byref(out)), "gsw_profile_create")
+    return out.value
+
+
+def gsw_profile_destroy(prof) -> None:
+    _check(load().gsw_profile_destroy(prof), "gsw_profile_destroy")
+
+
+def gsw_align_profile(ctx, prof, ntargets, t, t_off, t_len, flags=0, mask_len=-1, results=None,
+                      cigar=None, cigar_capacity=0, colmax=None, colmax_off=None, stream=None,
+                      check=True) -> int:
+    rc = load().gsw_align_profile(ctx, prof, ntargets, _ptr(t), _ptr(t_off), _ptr(t_len), flags,
+                                  mask_len, _ptr(results), _ptr(cigar), cigar_capacity, _ptr(colmax),
+                                  _ptr(colmax_off), _stream_handle(stream))
+    if check and rc != GSW_ECIGAR_SPACE:
+        _check(rc, "gsw_align_profile")
+    return rc
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+class Context:
+    """Owns a gsw context; convenience wrappers over the C calls."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        self.device = device
+        self.handle = gsw_context_create(device, mem_budget_bytes)
+
+    def close(self):
+        if self.handle:
+            gsw_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def align_host(self, q, q_off, q_len, t, t_off, t_len, matrix, gap_open, gap_extend,
+                   flags=GSW_CIGAR, mask_len=-1, cigar_capacity=None, colmax=False):
+        """Host numpy arrays in, host results out (GSW_HOST_IO)."""
+        q = np.ascontiguousarray(q, np.uint8)
+        t = np.ascontiguousarray(t, np.uint8)
+        q_off = np.ascontiguousarray(q_off, np.int64)
+        t_off = np.ascontiguousarray(t_off, np.int64)
+        q_len = np.ascontiguousarray(q_len, np.int32)
+        t_len = np.ascontiguousarray(t_len, np.int32)
+        n = len(q_len)
+        res = np.zeros(n, RESULT_DTYPE)
+        if cigar_capacity is None:
+            cigar_capacity = int(16 * n + 1024) if flags & GSW_CIGAR else 0
+        cig = np.zeros(max(cigar_capacity, 1), np.uint32)
+        cm = cmoff = None
+        if colmax:
+            flags |= GSW_COLMAX
+            cmoff = np.zeros(n, np.int64)
+            if n:
+                cmoff[1:] = np.cumsum(t_len.astype(np.int64))[:-1]
+            cm = np.zeros(max(int(t_len.sum()), 1), np.int32)
+        rc = gsw_align_batch(self.handle, n, q, q_off, q_len, t, t_off, t_len, matrix, gap_open,
+                             gap_extend, flags | GSW_HOST_IO, mask_len, res, cig, cigar_capacity, cm,
+                             cmoff)
+        return res, cig, (cm, cmoff), rc

@@ -1,0 +1,60 @@
+"""CPU checks of the boundary: the library builds, loads and exports every
+function include/gsw.h declares; argument validation that needs no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1208_6350_gb300 import _build, gsw
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in ("gsw.h",):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(gsw_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    lib = ctypes.CDLL(_build.build())
+    names = declared_functions()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/gsw.h but not exported"
+
+
+def test_strerror_and_version_need_no_gpu():
+    assert gsw.strerror(gsw.GSW_EINVAL) == "invalid argument"
+    assert gsw.strerror(gsw.GSW_ECIGAR_SPACE) == "CIGAR buffer too small"
+    assert "sm_103a" in gsw.gsw_version()
+
+
+def test_result_record_layout():
+    assert gsw.RESULT_DTYPE.itemsize == 48
+    assert gsw.RESULT_DTYPE.fields["cigar_off"][1] == 32
+
+
+def test_null_context_rejected_without_gpu():
+    import numpy as np
+    W = np.eye(4, dtype=np.int8)
+    rc = gsw.load().gsw_align_batch(None, 1, None, None, None, None, None, None,
+                                    W.ctypes.data, 4, 3, 1, 0, -1, None, None, 0, None, None, None)
+    assert rc == gsw.GSW_EINVAL
+
+
+def test_bad_scoring_rejected_without_gpu():
+    import numpy as np
+    W = np.eye(4, dtype=np.int8)
+    lib = gsw.load()
+    # gap_extend > gap_open is rejected before any device work
+    rc = lib.gsw_align_batch(None, 1, None, None, None, None, None, None, W.ctypes.data, 4, 1, 3, 0,
+                             -1, None, None, 0, None, None, None)
+    assert rc == gsw.GSW_EINVAL
+    rc = lib.gsw_align_batch(None, 1, None, None, None, None, None, None, W.ctypes.data, 40, 3, 1,
+                             0, -1, None, None, 0, None, None, None)
+    assert rc == gsw.GSW_EINVAL

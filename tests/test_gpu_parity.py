@@ -1,0 +1,189 @@
+"""GPU parity: every output of the CUDA path equals the oracle's, element by
+element (integers: zero tolerance), on seeded inputs shaped like the paper's
+workloads, at sizes that span several fill variants, strips and a ragged
+tail, plus constructed edge cases (empty and length-1 sequences, no shared
+letters, exact ties, 16-bit overflow threshold, multi-strip queries)."""
+import numpy as np
+import pytest
+
+from paper_1208_6350_gb300 import gsw, workloads as wl
+from parity_util import compare, run_gpu_device, run_gpu_host, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gsw.Context(0, 8 << 30)
+    yield c
+    c.close()
+
+
+def mixed_dna(seed, npairs, qmax, tmax, match=2, mismatch=-2, O=3, X=1, related=0.7):
+    """Ragged DNA pairs: lengths from 0 to the maxima, many with an implanted
+    mutated copy of the query."""
+    rng = np.random.default_rng(seed)
+    ql = rng.integers(0, qmax + 1, npairs)
+    tl = rng.integers(0, tmax + 1, npairs)
+    ql[:4] = [0, 1, 0, 1]
+    tl[:4] = [0, 0, 1, 1]
+    qs = [rng.integers(0, 4, n).astype(np.uint8) for n in ql]
+    ts = []
+    for p in range(npairs):
+        t = rng.integers(0, 4, tl[p]).astype(np.uint8)
+        if rng.random() < related and len(qs[p]) and len(t) >= len(qs[p]):
+            cp = qs[p].copy()
+            mut = rng.random(len(cp)) < 0.05
+            cp[mut] = rng.integers(0, 4, int(mut.sum()))
+            o = int(rng.integers(0, len(t) - len(cp) + 1))
+            t[o:o + len(cp)] = cp
+        ts.append(t)
+    return _batch(qs, ts, wl.dna_matrix(match, mismatch), O, X, "mixed")
+
+
+def _batch(qs, ts, W, O, X, name, alphabet="ACGT"):
+    ql = np.array([len(x) for x in qs], np.int32)
+    tl = np.array([len(x) for x in ts], np.int32)
+    qo = np.concatenate([[0], np.cumsum(ql)[:-1]]).astype(np.int64)
+    to = np.concatenate([[0], np.cumsum(tl)[:-1]]).astype(np.int64)
+    q = np.concatenate(qs + [np.zeros(0, np.uint8)]).astype(np.uint8)
+    t = np.concatenate(ts + [np.zeros(0, np.uint8)]).astype(np.uint8)
+    return wl.Batch(name, q, qo, ql, t, to, tl, W, O, X, alphabet)
+
+
+def test_mixed_small_all_outputs_host_io(ctx):
+    b = mixed_dna(1, 400, 300, 700)
+    compare(b, run_oracle(b), run_gpu_host(ctx, b))
+
+
+def test_mixed_small_device_path(ctx):
+    b = mixed_dna(2, 300, 260, 500)
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
+def test_config1_subset(ctx):
+    b = wl.config1().subset(np.arange(0, 1000, 4))
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
+def test_config2_sample_with_decoys(ctx):
+    b = wl.config2(4000, seed=11)
+    idx = np.random.default_rng(0).permutation(b.npairs)[:1500]
+    s = b.subset(idx)
+    assert s.meta["decoy"].any()
+    compare(s, run_oracle(s), run_gpu_device(ctx, s))
+
+
+def test_forced_32bit_lanes(ctx):
+    b = mixed_dna(3, 200, 300, 600)
+    got = run_gpu_host(ctx, b, flags=gsw.GSW_CIGAR | gsw.GSW_FORCE_S32)
+    assert (got[0]["flags"] & gsw.GSW_RES_S32).all()
+    compare(b, run_oracle(b), got)
+
+
+def test_score_only_and_begin_only(ctx):
+    b = mixed_dna(4, 200, 200, 400)
+    ora = run_oracle(b)
+    got = run_gpu_host(ctx, b, flags=0)
+    compare(b, ora, got, check_begin=False, check_cigar=False)
+    assert (got[0]["ref_begin1"] == -1).all() and (got[0]["cigar_len"] == 0).all()
+    got = run_gpu_host(ctx, b, flags=gsw.GSW_BEGIN)
+    compare(b, ora, got, check_cigar=False)
+
+
+@pytest.mark.parametrize("mask_len", [0, 5, 40, 1000])
+def test_mask_lengths(ctx, mask_len):
+    b = mixed_dna(5, 150, 120, 600)
+    compare(b, run_oracle(b, mask_len), run_gpu_host(ctx, b, mask_len=mask_len))
+
+
+def test_sixteen_bit_overflow_threshold(ctx):
+    # match 100: a self-alignment of length L scores 100 L; 16-bit lanes are
+    # exact up to 32767 - 100 = 32667, so L = 326 stays in 16 bits and
+    # L = 327 must be refilled in 32-bit lanes.
+    rng = np.random.default_rng(6)
+    W = wl.dna_matrix(100, -100)
+    qs, ts = [], []
+    for L in (325, 326, 327, 328, 400):
+        q = rng.integers(0, 4, L).astype(np.uint8)
+        qs.append(q)
+        ts.append(np.concatenate([rng.integers(0, 4, 50), q, rng.integers(0, 4, 30)]).astype(np.uint8))
+    b = _batch(qs, ts, W, 30, 10, "overflow")
+    got = run_gpu_host(ctx, b)
+    s32 = (got[0]["flags"] & gsw.GSW_RES_S32) != 0
+    assert list(s32) == [False, False, True, True, True]
+    compare(b, run_oracle(b), got)
+
+
+def test_multi_strip_long_queries(ctx):
+    b = wl.dna_long_reads(12, 600, 2500, seed=7)
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
+def test_protein_general_matrix(ctx):
+    ps = wl.protein_search(20, 200, seed=8)
+    rng = np.random.default_rng(9)
+    qi = rng.integers(0, 20, 300)
+    di = rng.integers(0, 200, 300)
+    qi[:10] = ps.queries.meta["homolog_query"][:10]
+    di[:10] = ps.queries.meta["homolog_db"][:10]
+    b = ps.pairs(qi, di).subset(np.arange(300))
+    compare(b, run_oracle(b), run_gpu_host(ctx, b))
+
+
+def test_small_alphabet_and_odd_scoring(ctx):
+    rng = np.random.default_rng(10)
+    A = 3
+    W = rng.integers(-3, 4, (A, A)).astype(np.int8)
+    W[0, 0] = 3
+    qs = [rng.integers(0, A, int(n)).astype(np.uint8) for n in rng.integers(0, 90, 120)]
+    ts = [rng.integers(0, A, int(n)).astype(np.uint8) for n in rng.integers(0, 200, 120)]
+    for O, X in ((2, 2), (5, 1), (0, 0), (4, 0)):
+        b = _batch(qs, ts, W, O, X, "odd", "ACG")
+        compare(b, run_oracle(b), run_gpu_host(ctx, b))
+
+
+def test_profile_api_matches_batch(ctx):
+    rng = np.random.default_rng(12)
+    W = wl.dna_matrix(2, -3)
+    q = rng.integers(0, 4, 150).astype(np.uint8)
+    ts = []
+    for k in range(64):
+        t = rng.integers(0, 4, int(rng.integers(100, 900))).astype(np.uint8)
+        if k % 2 and len(t) > 160:
+            o = int(rng.integers(0, len(t) - 150))
+            t[o:o + 150] = q
+        ts.append(t)
+    b = _batch([q] * 64, ts, W, 5, 2, "profile")
+    prof = gsw.gsw_profile_create(ctx.handle, q, W, 5, 2)
+    try:
+        res = np.zeros(64, gsw.RESULT_DTYPE)
+        cap = 64 * 200
+        cig = np.zeros(cap, np.uint32)
+        gsw.gsw_align_profile(ctx.handle, prof, 64, b.t, b.t_off, b.t_len,
+                              gsw.GSW_CIGAR | gsw.GSW_HOST_IO, -1, res, cig, cap)
+    finally:
+        gsw.gsw_profile_destroy(prof)
+    compare(b, run_oracle(b), (res, cig, (None, None)), check_colmax=False)
+
+
+def test_cigar_space_error_reported(ctx):
+    b = mixed_dna(13, 50, 100, 200, related=1.0)
+    res, cig, _, rc = ctx.align_host(b.q, b.q_off, b.q_len, b.t, b.t_off, b.t_len, b.W, 3, 1,
+                                     gsw.GSW_CIGAR, -1, cigar_capacity=3)
+    assert rc == gsw.GSW_ECIGAR_SPACE
+    assert (res["flags"] & gsw.GSW_RES_CIGAR_SPACE).any()
+
+
+def test_invalid_letter_rejected(ctx):
+    b = mixed_dna(14, 10, 50, 60)
+    b.t[b.t_off[5]] = 7  # not in the 4-letter alphabet
+    with pytest.raises(gsw.GswError) as ei:
+        ctx.align_host(b.q, b.q_off, b.q_len, b.t, b.t_off, b.t_len, b.W, 3, 1)
+    assert ei.value.code == gsw.GSW_EINVAL
+
+
+def test_plain_per_pair_baseline_matches(ctx):
+    b = mixed_dna(15, 40, 120, 300)
+    got = run_gpu_host(ctx, b, flags=gsw.GSW_CIGAR | gsw.GSW_PLAIN)
+    compare(b, run_oracle(b), got)
