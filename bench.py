@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Throughput of the SSW hot path on GB300: GCUPS, bit-exact against the oracle.
+
+Workload: short-read extension, 1,000,000 DNA pairs (queries U[100, 250] nt,
+targets U[300, 1000] nt holding the mutated query, 10 % decoys; +2/-2, gap
+open 3, extend 1), seeded and synthetic.  One step = the whole hot path over
+the batch: forward fill (max array, ends, secondary), 32-bit refill of the
+pairs whose 16-bit lanes overflowed, reversed fill (begins), banded
+traceback (CIGAR).  GCUPS counts forward-fill cells (sum of m*n) per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gsw|reference]
+
+Under torchrun every rank aligns its own batch of the same size (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GCUPS (forward-fill cell updates/s), bit-exact vs oracle"
+UNIT = "GCUPS"
+ALGO_OPS_PER_CELL = 10  # 2-input integer ops of one Gotoh cell update (add, 3 sub, 6 max)
+WORKLOAD = "dna_short_read_extension_1M"
+
+
+def workload_config(npairs):
+    return {"workload": WORKLOAD, "pairs": npairs, "query_nt": [100, 250], "target_nt": [300, 1000],
+            "subst": 0.01, "indel": 0.001, "decoys": 0.10, "scoring": "+2/-2, open 3, extend 1",
+            "outputs": "score1, ends, score2, ref_end2, begins, CIGAR",
+            "l2": "inputs ~0.8 GB per step, larger than the 129 MB L2 (no flush)"}
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------- CPU baseline
+def cpu_baseline(b, target_s=10.0, max_pairs=200_000):
+    """The oracle as it stands, on all host cores, over a bounded sample."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(123)
+    pilot = b.subset(rng.permutation(b.npairs)[:1000])
+    t0 = time.perf_counter()
+    oracle.align_batch(pilot.q, pilot.q_off, pilot.q_len, pilot.t, pilot.t_off, pilot.t_len, pilot.W,
+                       pilot.gap_open, pilot.gap_extend, nthreads=cores, cigar_stride=1300)
+    rate = pilot.cells / max(time.perf_counter() - t0, 1e-6)
+    n = int(min(max_pairs, b.npairs, max(1000, target_s * rate / (b.cells / b.npairs))))
+    s = b.subset(rng.permutation(b.npairs)[:n])
+    t0 = time.perf_counter()
+    res, _, _ = oracle.align_batch(s.q, s.q_off, s.q_len, s.t, s.t_off, s.t_len, s.W, s.gap_open,
+                                   s.gap_extend, nthreads=cores, cigar_stride=1300)
+    dt = time.perf_counter() - t0
+    return {"value": s.cells / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} random pairs of the workload ({s.cells / 1e9:.2f} G cells), full outputs, "
+                      f"{dt:.1f} s wall", "cpu": _cpu_model()}
+
+
+def _cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def fill_traffic_bytes(cells):
+    """DRAM bytes per forward-fill launch from the committed ncu summary, if it
+    was taken on the current fill kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "fill_fwd_traffic.txt")
+    src = os.path.join(ROOT, "paper_1208_6350_gb300", "csrc", "fill.cu")
+    try:
+        kv = dict(ln.strip().split("=", 1) for ln in open(path) if "=" in ln and not ln.startswith("#"))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if kv.get("fill_cu_sha256_16") != sha:
+            return None
+        return float(kv["dram_bytes_per_cell"]) * cells
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------ GPU arm
+def run_gsw(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1208_6350_gb300 import gsw, workloads as wl
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    b = wl.config2(args.pairs, seed=1 + rank)
+    cells = b.cells
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    q, t = T(b.q), T(b.t)
+    qo, to = T(b.q_off.astype(np.int64)), T(b.t_off.astype(np.int64))
+    ql, tl = T(b.q_len.astype(np.int32)), T(b.t_len.astype(np.int32))
+    n = b.npairs
+    res = torch.zeros(n * 12, dtype=torch.int32, device=dev)
+    cap = 32 * n + 1024
+    cig = torch.zeros(cap, dtype=torch.int32, device=dev)
+    ctx = gsw.Context(local, args.budget_gb << 30)
+    stream = torch.cuda.current_stream(dev)
+    flags = gsw.GSW_CIGAR | gsw.GSW_TIMING
+
+    def step():
+        gsw.gsw_align_batch(ctx.handle, n, q, qo, ql, t, to, tl, b.W, b.gap_open, b.gap_extend, flags,
+                            -1, res, cig, cap, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    # correctness of what is timed: a random sample against the oracle
+    checked = check_sample(b, res, cig, rank) if not args.no_check else 0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fill_ms, pipe_ms, launches = [], [], 0
+    stage_sum = {}
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+        st = gsw.gsw_last_stats(ctx.handle)
+        launches += st["kernel_launches"]
+        fill_ms.append(st["stage_ms"]["fill_fwd"])
+        pipe_ms.append(st["stage_ms"]["pipeline"])
+        for k, v in st["stage_ms"].items():
+            stage_sum[k] = stage_sum.get(k, 0.0) + v
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = ms
+    if world > 1:
+        x = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        ms_max = float(x.item())
+    value = world * cells / (ms_max / 1e3) / 1e9
+
+    # e2e: the same call on host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, gsw, b, ctx, stream, dev, torch)
+
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak_gops = sms * 128 * 2 * max_mhz * 1e6 / 1e9  # 16-bit lane ops/s at full-rate 16x2 instructions
+    fill_s = float(np.mean(fill_ms)) / 1e3
+    achieved = ALGO_OPS_PER_CELL * cells / fill_s / 1e9
+    roof = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak_gops, 1), "unit": "Gop/s",
+            "frac": round(achieved / peak_gops, 4), "traffic": fill_traffic_bytes(cells),
+            "kernel": "k_fill (forward, 16-bit folded ring)",
+            "fill_ms": round(float(np.mean(fill_ms)), 3),
+            "fill_gcups": round(cells / fill_s / 1e9, 1),
+            "peak_basis": f"{sms} SMs x 128 lanes x 2 16-bit lanes x {max_mhz:.0f} MHz (max SM clock)"}
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i16x2 (i32 refill)",
+            "data": "synthetic (seeded; stands in for simulated short reads)",
+            "config": workload_config(args.pairs), "e2e": e2e,
+            "gpu_launches": launches,
+            "stage_ms": {k: round(v / args.steps, 3) for k, v in stage_sum.items()},
+            "checked_pairs": checked, "clocks": clocks, "roofline": roof}
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(b, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, gsw, b, ctx, stream, dev, torch):
+    n = b.npairs
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    q, t = pin(b.q), pin(b.t)
+    qo, to = pin(b.q_off.astype(np.int64)), pin(b.t_off.astype(np.int64))
+    ql, tl = pin(b.q_len.astype(np.int32)), pin(b.t_len.astype(np.int32))
+    res = pin(np.zeros(n, gsw.RESULT_DTYPE).view(np.int32))
+    cap = 32 * n + 1024
+    cig = pin(np.zeros(cap, np.uint32))
+    flags = gsw.GSW_CIGAR | gsw.GSW_HOST_IO
+
+    def step():
+        gsw.gsw_align_batch(ctx.handle, n, q, qo, ql, t, to, tl, b.W, b.gap_open, b.gap_extend, flags,
+                            -1, res, cig, cap, stream=stream)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    steps = max(1, args.steps)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize(dev)
+    dt = (time.perf_counter() - t0) / steps
+    r = res.view(gsw.RESULT_DTYPE)
+    cig_words = int(np.maximum(r["cigar_len"], 0).sum())
+    h2d = q.nbytes + t.nbytes + qo.nbytes + to.nbytes + ql.nbytes + tl.nbytes
+    d2h = res.nbytes + 4 * cig_words
+    return {"value": round(b.cells / dt / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 3),
+            "api": "gsw_align_batch with GSW_HOST_IO (pinned host buffers)"}
+
+
+def check_sample(b, res, cig, rank, k=300):
+    import oracle
+    from paper_1208_6350_gb300 import gsw
+    rng = np.random.default_rng(7 + rank)
+    idx = rng.permutation(b.npairs)[:k]
+    s = b.subset(idx)
+    ores, ocg, _ = oracle.align_batch(s.q, s.q_off, s.q_len, s.t, s.t_off, s.t_len, s.W, s.gap_open,
+                                      s.gap_extend, cigar_stride=1300)
+    r = res.cpu().numpy().view(gsw.RESULT_DTYPE)
+    c = cig.cpu().numpy().view(np.uint32)
+    for j, p in enumerate(idx):
+        for f in ("score1", "score2", "ref_begin1", "ref_end1", "read_begin1", "read_end1", "ref_end2"):
+            if int(r[f][p]) != int(ores[f][j]):
+                raise SystemExit(f"bench check failed: pair {p} field {f}: {int(r[f][p])} != {int(ores[f][j])}")
+        o, n_ = int(r["cigar_off"][p]), int(r["cigar_len"][p])
+        if list(c[o:o + n_]) != list(ocg[j, : ores["cigar_len"][j]]):
+            raise SystemExit(f"bench check failed: pair {p} CIGAR")
+    return k
+
+
+# ------------------------------------------------------ reference arm
+def run_reference(args):
+    """The oracle (this method's plain CPU definition) as the reference arm."""
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1208_6350_gb300 import workloads as wl
+
+    cores = len(os.sched_getaffinity(0))
+    b = wl.config2(args.pairs, seed=1)
+    rng = np.random.default_rng(99)
+    per_step = args.ref_pairs
+    total = 0.0
+    cells = 0
+    for k in range(args.warmup + args.steps):
+        s = b.subset(rng.permutation(b.npairs)[:per_step])
+        t0 = time.perf_counter()
+        oracle.align_batch(s.q, s.q_off, s.q_len, s.t, s.t_off, s.t_len, s.W, s.gap_open, s.gap_extend,
+                           nthreads=cores, cigar_stride=1300)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            total += dt
+            cells += s.cells
+    value = cells / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", 1)), "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+            "config": workload_config(args.pairs),
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} random pairs of the workload per step, full outputs",
+                             "cpu": _cpu_model()},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gsw", choices=["gsw", "reference"])
+    ap.add_argument("--pairs", type=int, default=1_000_000)
+    ap.add_argument("--budget-gb", type=int, default=24)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-pairs", type=int, default=4000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gsw(args)
+
+
+if __name__ == "__main__":
+    main()

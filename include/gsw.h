@@ -60,6 +60,8 @@ extern "C" {
 #define GSW_FORCE_S32 0x10u /* skip the 16-bit lanes (32-bit fill for every pair) */
 #define GSW_PLAIN 0x20u     /* baseline: one fill/reverse/traceback launch
                                sequence per pair, no batching */
+#define GSW_TIMING 0x40u    /* record CUDA events around each stage of the call
+                               (read them with gsw_last_stats) */
 
 /* CIGAR words: (run_length << 4) | op, op 0 = M (match or mismatch column),
  * 1 = I (query letter against a gap), 2 = D (target letter against a gap). */
@@ -99,9 +101,10 @@ typedef struct gsw_profile gsw_profile;
  * Creates a context on CUDA device `device`.  The context owns the device
  * scratch (work queues, per-slot column-max and strip-boundary buffers,
  * traceback scratch) and pinned staging for GSW_HOST_IO; it never holds more
- * than `mem_budget_bytes` of device memory (0 = 4 GiB).  Batches that need
- * more scratch are processed in chunks.  One context may be used by one host
- * thread at a time.  Errors: GSW_EINVAL (bad device), GSW_ECUDA, GSW_ENOMEM.
+ * than `mem_budget_bytes` of device memory (0 = 4 GiB); when a batch's
+ * per-slot scratch would exceed it, fewer pairs run at a time.  One context
+ * may be used by one host thread at a time.  Errors: GSW_EINVAL (bad
+ * device), GSW_ECUDA, GSW_ENOMEM.
  */
 int gsw_context_create(int device, size_t mem_budget_bytes, gsw_ctx **out);
 
@@ -125,8 +128,9 @@ int gsw_context_destroy(gsw_ctx *ctx);
  * the suboptimal score is taken; negative means max(q_len/2, 15).
  *
  * Stream: work is queued on `stream` (a cudaStream_t; NULL = the legacy
- * default stream) and the call returns without synchronizing, except with
- * GSW_HOST_IO, where it returns when the host results are ready.
+ * default stream).  The call reads a few values back from the device on that
+ * stream (the longest query and target, the traceback scratch size, the CIGAR
+ * words used), so it returns only when the batch's results are complete.
  *
  * Errors: GSW_EINVAL (alphabet not in [1, 32], matrix entries outside
  * [-127, 127], O < X, O or X > 255 or negative, npairs < 0, mask_len too
@@ -161,6 +165,29 @@ int gsw_align_profile(gsw_ctx *ctx, const gsw_profile *prof, int32_t ntargets,
                       uint32_t flags, int32_t mask_len, gsw_result *results,
                       uint32_t *cigar, int64_t cigar_capacity, int32_t *colmax,
                       const int64_t *colmax_off, void *stream);
+
+/*
+ * Statistics of the last gsw_align_batch / gsw_align_profile call on a
+ * context.  kernel_launches counts the kernels the call enqueued.  With
+ * GSW_TIMING, stage_ms holds CUDA-event times measured on the call's stream:
+ *   [0] forward plan (device counting sort into warp tasks)
+ *   [1] forward fill kernel (16-bit lanes, or 32-bit with GSW_FORCE_S32)
+ *   [2] 32-bit refill of overflowed pairs (plan + kernel)
+ *   [3] reversed fill in the ring kernel, for pairs whose reverse band is
+ *       wider than 32 diagonals (plan + kernel)
+ *   [4] thread-per-pair banded reverse and traceback (plan + kernels)
+ *   [5] warp traceback of pairs whose traceback band is wider than 32
+ *   [6] whole device pipeline ([0] .. [5])
+ * Stages that did not run read 0.  The call has already waited for its work,
+ * so reading the stats does not block.  Errors: GSW_EINVAL (NULL).
+ */
+#define GSW_NSTAGES 7
+typedef struct gsw_stats {
+    int32_t kernel_launches;
+    int32_t timed;
+    float stage_ms[8];
+} gsw_stats;
+int gsw_last_stats(const gsw_ctx *ctx, gsw_stats *out);
 
 /* Name of an error code (static string). */
 const char *gsw_strerror(int code);

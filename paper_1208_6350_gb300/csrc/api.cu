@@ -4,6 +4,7 @@
 #include "gsw_impl.cuh"
 
 #include <algorithm>
+#include <climits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -50,11 +51,15 @@ struct gsw_ctx {
     int sms = 0;
     DevBuf plan_keys, plan_order, plan_small;
     DevBuf fill_cm, fill_bnd;
-    DevBuf trace_dirs, trace_ops;
+    DevBuf trace_dirs, trace_ops, band_scr;
     DevBuf misc;  // counters: trace head, cigar cursor, trace need, max lengths
     DevBuf io_q, io_t, io_qoff, io_toff, io_qlen, io_tlen, io_res, io_cigar, io_colmax, io_cmoff;
     DevBuf prof_qoff, prof_qlen;
     void *host_small = nullptr;  // pinned readback area
+    cudaEvent_t ev[GSW_NSTAGES + 1] = {};
+    bool timing = false;
+    int launches = 0;
+    int stage_done[GSW_NSTAGES] = {};
 };
 
 struct gsw_profile {
@@ -122,13 +127,20 @@ int make_scoring(const int8_t *matrix, int32_t A, int32_t O, int32_t X, Scoring 
 // device scratch layout of ctx->misc (64-bit words)
 enum MiscSlot { kMiscTraceHead = 0, kMiscCursor = 1, kMiscNeed = 2 /* 3 words */, kMiscMaxLen = 5, kMiscValid = 6, kMiscWords = 8 };
 
+// event e[k] marks the end of stage k-1 / start of stage k
+int mark(gsw_ctx *ctx, int k, cudaStream_t st) {
+    if (!ctx->timing) return GSW_OK;
+    CUDA_TRY(cudaEventRecord(ctx->ev[k], st));
+    return GSW_OK;
+}
+
 int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st, int maxm, int maxn) {
     const int npairs = bv.npairs;
     unsigned long long *misc = reinterpret_cast<unsigned long long *>(ctx->misc.p);
     // ---- plan buffers
     GSW_TRY(ensure(ctx, ctx->plan_keys, sizeof(int32_t) * (size_t)std::max(npairs, 1)));
     GSW_TRY(ensure(ctx, ctx->plan_order, sizeof(int32_t) * (size_t)std::max(npairs, 1)));
-    const size_t small_words = 3 * (size_t)kPlanBins + 3 * kNumVariants + 8;
+    const size_t small_words = 3 * (size_t)kPlanBins + 4 * kNumVariants + 8;
     GSW_TRY(ensure(ctx, ctx->plan_small, sizeof(int32_t) * small_words));
     int32_t *ps = reinterpret_cast<int32_t *>(ctx->plan_small.p);
     PlanBuffers pb;
@@ -144,22 +156,22 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
     pb.head = pb.ntasks + 1;
 
     // ---- fill launch geometry and per-slot scratch
-    const size_t smem = fill_smem_per_warp(sc) * (fill_block_threads() / 32);
-    int bps = fill_max_blocks_per_sm(sc, smem);
-    if (bps < 1) return set_err(GSW_ECUDA, "fill kernel cannot be resident (smem %zu)", smem);
     const int warps_per_block = fill_block_threads() / 32;
-    const int slots_per_warp = 2;  // 32 / smallest P
     const size_t ncap = (size_t)std::max(maxn, 1);
     const size_t per_slot = ncap * sizeof(int32_t) + 2 * ncap * sizeof(int2);
-    int grid = ctx->sms * bps;
+    size_t slots = (size_t)fill_slots(sc, ctx->sms);
+    if (slots == 0) return set_err(GSW_ECUDA, "fill kernels cannot be resident");
+    int max_blocks = INT32_MAX;
     {
         // keep the scratch inside half of what the budget has left
         size_t have = ctx->budget > ctx->used ? ctx->budget - ctx->used + ctx->fill_cm.bytes + ctx->fill_bnd.bytes : 0;
-        size_t max_slots = have / 2 / per_slot;
-        size_t want = (size_t)grid * warps_per_block * slots_per_warp;
-        if (want > max_slots) grid = (int)std::max<size_t>(1, max_slots / (warps_per_block * slots_per_warp));
+        size_t cap_slots = have / 2 / per_slot;
+        if (slots > cap_slots) {
+            // every variant has at most 2 slots per warp
+            max_blocks = (int)std::max<size_t>(1, cap_slots / (2 * warps_per_block));
+            slots = (size_t)max_blocks * warps_per_block * 2;
+        }
     }
-    const size_t slots = (size_t)grid * warps_per_block * slots_per_warp;
     GSW_TRY(ensure(ctx, ctx->fill_cm, slots * ncap * sizeof(int32_t)));
     GSW_TRY(ensure(ctx, ctx->fill_bnd, slots * 2 * ncap * sizeof(int2)));
 
@@ -175,54 +187,103 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
     fl.scr.colmax = ctx->fill_cm.p;
     fl.scr.boundary = ctx->fill_bnd.p;
     fl.scr.ncap = (int32_t)ncap;
-    fl.scr.slots_per_warp = slots_per_warp;
+    fl.scr.slots_per_warp = 2;
 
-    auto stage = [&](int32_t mode) -> int {
+    auto plan = [&](int32_t mode) -> int {
         cudaError_t e = launch_plan(bv, sc, mode, pb, st);
         if (e != cudaSuccess) return set_err(GSW_ECUDA, "plan: %s", cudaGetErrorString(e));
-        fl.mode = mode;
-        e = launch_fill(fl, grid, smem, st);
-        if (e != cudaSuccess) return set_err(GSW_ECUDA, "fill: %s", cudaGetErrorString(e));
+        ctx->launches += 3;
         return GSW_OK;
     };
-    GSW_TRY(stage(kFillForward));
-    if (!(bv.flags & GSW_FORCE_S32)) GSW_TRY(stage(kFillRerun));
-    if (bv.flags & (GSW_BEGIN | GSW_CIGAR)) GSW_TRY(stage(kFillReverse));
+    auto fill = [&](int32_t mode) -> int {
+        fl.mode = mode;
+        cudaError_t e = launch_fill(fl, ctx->sms, max_blocks, st);
+        if (e != cudaSuccess) return set_err(GSW_ECUDA, "fill: %s", cudaGetErrorString(e));
+        ctx->launches += kNumVariants;
+        return GSW_OK;
+    };
+    GSW_TRY(mark(ctx, 0, st));
+    GSW_TRY(plan(kFillForward));
+    GSW_TRY(mark(ctx, 1, st));
+    GSW_TRY(fill(kFillForward));
+    GSW_TRY(mark(ctx, 2, st));
+    ctx->stage_done[0] = ctx->stage_done[1] = 1;
+    if (!(bv.flags & GSW_FORCE_S32)) {
+        GSW_TRY(plan(kFillRerun));
+        GSW_TRY(fill(kFillRerun));
+        ctx->stage_done[2] = 1;
+    }
+    GSW_TRY(mark(ctx, 3, st));
+    if (bv.flags & (GSW_BEGIN | GSW_CIGAR)) {
+        // reversed fill in the ring kernel for pairs whose reverse band is wide
+        GSW_TRY(plan(kFillReverse));
+        GSW_TRY(fill(kFillReverse));
+        ctx->stage_done[3] = 1;
+    }
+    GSW_TRY(mark(ctx, 4, st));
+    if (bv.flags & (GSW_BEGIN | GSW_CIGAR)) {
+        // thread-per-pair banded reverse and traceback for narrow bands
+        GSW_TRY(plan(kPlanBand));
+        const int rows_cap = std::min(std::max(maxm, 1), kBandMaxRows);
+        const int64_t words = (int64_t)(rows_cap + 1) * 32 * 4;  // widest class: 4 words per lane and row
+        int bgrid = ctx->sms * 8;
+        const int bwarps_per_block = band_block_threads() / 32;
+        {
+            size_t have = ctx->budget > ctx->used ? ctx->budget - ctx->used + ctx->band_scr.bytes : 0;
+            size_t per_warp = (size_t)words * sizeof(uint32_t);
+            size_t max_warps = have / 2 / per_warp;
+            if ((size_t)bgrid * bwarps_per_block > max_warps)
+                bgrid = (int)std::max<size_t>(1, max_warps / bwarps_per_block);
+        }
+        GSW_TRY(ensure(ctx, ctx->band_scr, (size_t)bgrid * bwarps_per_block * words * sizeof(uint32_t)));
+        CUDA_TRY(launch_band(bv, sc, pb, ctx->band_scr.p, words, bgrid, st));
+        ctx->launches += 3;
+        ctx->stage_done[4] = 1;
+    }
+    GSW_TRY(mark(ctx, 5, st));
 
     if (bv.flags & GSW_CIGAR) {
+        // warp traceback for the pairs the band kernel left (band wider than 32)
+        GSW_TRY(plan(kPlanTrace));
         CUDA_TRY(launch_trace_need(bv, sc, misc + kMiscNeed, st));
+        ctx->launches += 1;
         unsigned long long *hs = reinterpret_cast<unsigned long long *>(ctx->host_small);
         CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
         const long long need_dir = (long long)hs[0], need_ops = (long long)hs[1], need_nch = (long long)hs[2];
-        const int tgrid = ctx->sms * 2;
-        const int twarps = tgrid * (trace_block_threads() / 32);
-        // pairs too large for shared memory use global scratch: size it for the largest
-        const long long dir_words = std::max<long long>(need_dir, 64);
-        const long long op_words = std::max<long long>(need_ops + 64 * need_nch, 64);
-        size_t per_warp = (size_t)(dir_words + op_words) * sizeof(uint32_t);
-        int use_warps = twarps;
-        size_t have = ctx->budget > ctx->used ? ctx->budget - ctx->used + ctx->trace_dirs.bytes + ctx->trace_ops.bytes : 0;
-        if ((size_t)use_warps * per_warp > have) use_warps = (int)std::max<size_t>(1, have / per_warp);
-        int use_grid = std::max(1, use_warps / (trace_block_threads() / 32));
-        use_warps = use_grid * (trace_block_threads() / 32);
-        GSW_TRY(ensure(ctx, ctx->trace_dirs, (size_t)use_warps * dir_words * sizeof(uint32_t)));
-        GSW_TRY(ensure(ctx, ctx->trace_ops, (size_t)use_warps * op_words * sizeof(uint32_t)));
-        TraceScratch ts;
-        ts.dirs = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
-        ts.dir_words = dir_words;
-        ts.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
-        ts.op_words = op_words;
-        ts.head = reinterpret_cast<int32_t *>(misc + kMiscTraceHead);
-        CUDA_TRY(launch_traceback(bv, sc, ts, use_grid, st));
+        if (need_nch > 0) {
+            const int tgrid = ctx->sms * 2;
+            const int twarps = tgrid * (trace_block_threads() / 32);
+            const long long dir_words = std::max<long long>(need_dir, 64);
+            const long long op_words = std::max<long long>(need_ops + 64 * need_nch, 64);
+            size_t per_warp = (size_t)(dir_words + op_words) * sizeof(uint32_t);
+            int use_warps = twarps;
+            size_t have = ctx->budget > ctx->used ? ctx->budget - ctx->used + ctx->trace_dirs.bytes + ctx->trace_ops.bytes : 0;
+            if ((size_t)use_warps * per_warp > have) use_warps = (int)std::max<size_t>(1, have / per_warp);
+            int use_grid = std::max(1, use_warps / (trace_block_threads() / 32));
+            use_warps = use_grid * (trace_block_threads() / 32);
+            GSW_TRY(ensure(ctx, ctx->trace_dirs, (size_t)use_warps * dir_words * sizeof(uint32_t)));
+            GSW_TRY(ensure(ctx, ctx->trace_ops, (size_t)use_warps * op_words * sizeof(uint32_t)));
+            TraceScratch ts;
+            ts.dirs = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
+            ts.dir_words = dir_words;
+            ts.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
+            ts.op_words = op_words;
+            ts.order = pb.order;
+            ts.var_start = pb.var_start;
+            CUDA_TRY(launch_traceback(bv, sc, ts, use_grid, st));
+            ctx->launches += 1;
+        }
+        ctx->stage_done[5] = 1;
     }
+    GSW_TRY(mark(ctx, 6, st));
     return GSW_OK;
 }
 
 int check_common(gsw_ctx *ctx, int32_t npairs, uint32_t flags) {
     if (!ctx) return set_err(GSW_EINVAL, "context is NULL");
     if (npairs < 0) return set_err(GSW_EINVAL, "npairs < 0");
-    if (flags & ~(GSW_BEGIN | GSW_CIGAR | GSW_COLMAX | GSW_HOST_IO | GSW_FORCE_S32 | GSW_PLAIN))
+    if (flags & ~(GSW_BEGIN | GSW_CIGAR | GSW_COLMAX | GSW_HOST_IO | GSW_FORCE_S32 | GSW_PLAIN | GSW_TIMING))
         return set_err(GSW_EINVAL, "unknown flag bits 0x%x", flags);
     return GSW_OK;
 }
@@ -242,6 +303,11 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
     if (mask_len > (1 << 30)) return set_err(GSW_EINVAL, "mask_len too large");
     CUDA_TRY(cudaSetDevice(ctx->device));
     GSW_TRY(ensure(ctx, ctx->misc, kMiscWords * sizeof(unsigned long long)));
+    ctx->launches = 0;
+    for (int k = 0; k < GSW_NSTAGES; k++) ctx->stage_done[k] = 0;
+    ctx->timing = (flags & GSW_TIMING) != 0;
+    if (ctx->timing && !ctx->ev[0])
+        for (int k = 0; k <= GSW_NSTAGES; k++) CUDA_TRY(cudaEventCreate(&ctx->ev[k]));
     unsigned long long *misc = reinterpret_cast<unsigned long long *>(ctx->misc.p);
     BatchView bv;
     std::memset(&bv, 0, sizeof(bv));
@@ -307,6 +373,7 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
         bv.colmax_off = colmax_off;
         int32_t *ml = reinterpret_cast<int32_t *>(misc + kMiscMaxLen);
         CUDA_TRY(launch_max_lengths(q_len, t_len, npairs, ml, st));
+        ctx->launches += 1;
         int32_t *hs = reinterpret_cast<int32_t *>(ctx->host_small);
         CUDA_TRY(cudaMemcpyAsync(hs, ml, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
@@ -316,6 +383,7 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
     }
     CUDA_TRY(cudaMemsetAsync(misc + kMiscCursor, 0, sizeof(unsigned long long), st));
     CUDA_TRY(launch_validate(bv, sc, reinterpret_cast<int32_t *>(misc + kMiscValid), st));
+    ctx->launches += 1;
     GSW_TRY(run_pipeline(ctx, bv, sc, st, maxm, maxn));
 
     // completion: invalid letters, CIGAR space
@@ -393,6 +461,24 @@ const char *gsw_strerror(int code) {
 
 const char *gsw_last_error(void) { return g_err; }
 
+int gsw_last_stats(const gsw_ctx *ctx, gsw_stats *out) {
+    if (!ctx || !out) return set_err(GSW_EINVAL, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    out->kernel_launches = ctx->launches;
+    if (!ctx->timing || !ctx->ev[0]) return GSW_OK;
+    out->timed = 1;
+    // stage k spans events k..k+1, except: [0] = e0..e1, [1] = e1..e2, [2] = e2..e3,
+    // [3] = e3..e4, [4] = e4..e5, [5] = e5..e6, [6] = e0..e6
+    for (int k = 0; k < 6; k++) {
+        float ms = 0.f;
+        if (ctx->stage_done[k] && cudaEventElapsedTime(&ms, ctx->ev[k], ctx->ev[k + 1]) == cudaSuccess)
+            out->stage_ms[k] = ms;
+    }
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[6]) == cudaSuccess) out->stage_ms[6] = ms;
+    return GSW_OK;
+}
+
 int gsw_context_create(int device, size_t mem_budget_bytes, gsw_ctx **out) {
     if (!out) return set_err(GSW_EINVAL, "out is NULL");
     *out = nullptr;
@@ -419,11 +505,13 @@ int gsw_context_destroy(gsw_ctx *c) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     DevBuf *all[] = {&c->plan_keys, &c->plan_order, &c->plan_small, &c->fill_cm, &c->fill_bnd, &c->trace_dirs,
-                     &c->trace_ops, &c->misc, &c->io_q, &c->io_t, &c->io_qoff, &c->io_toff, &c->io_qlen,
+                     &c->trace_ops, &c->band_scr, &c->misc, &c->io_q, &c->io_t, &c->io_qoff, &c->io_toff, &c->io_qlen,
                      &c->io_tlen, &c->io_res, &c->io_cigar, &c->io_colmax, &c->io_cmoff, &c->prof_qoff,
                      &c->prof_qlen};
     for (DevBuf *b : all) release(c, *b);
     if (c->host_small) cudaFreeHost(c->host_small);
+    for (int k = 0; k <= GSW_NSTAGES; k++)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;
     return GSW_OK;
 }

@@ -1,0 +1,349 @@
+// Begin and CIGAR for pairs whose bands are narrow: one thread per pair.
+//
+// Reversed SW from the end ("Algorithm and implementation", item (1)), as a
+// banded DP.  Every alignment scoring score1 inside the rectangle
+// q[0..end_q] x t[0..end_t] ends exactly at (end_q, end_t) (the end is the
+// first column, then first row, holding score1).  On the reversed sequences
+// these alignments all start at the origin, so the cells that reach score1 are
+// the same in the local DP and in the DP anchored at the origin (no restarts),
+// and an anchored path reaching score1 has at most
+// G = ((end_q+1)*wmax - score1 - O)/X + 1 gap letters, hence never leaves the
+// diagonals |j - i| <= G.  The anchored banded DP therefore finds the same
+// first column (then first row) holding score1 as the full local reversed DP.
+//
+// Banded SW between begin and end (item (1)): global Gotoh restricted to the
+// provable band (band_halfwidth), with 4 decision bits per cell and the same
+// traceback preferences as the oracle.  The traceback band is never wider than
+// the reverse band (it bounds the same gap letters with fewer aligned pairs).
+//
+// Lanes of a warp take consecutive pairs of a list sorted by rows, so their
+// loops have similar lengths.  Each lane keeps its band row in registers
+// (W cells) and stores each row's decision nibbles into a per-warp scratch
+// interleaved by lane (coalesced).  The CIGAR is walked twice: once to count
+// runs, once to write them in forward order at the reserved offset.
+#include "gsw_impl.cuh"
+
+namespace gsw {
+namespace {
+
+constexpr int kBBlock = 128;
+constexpr int kNegB = -(1 << 28);
+constexpr int kNegBHalf = -(1 << 27);
+
+template <int W>
+struct DirWord;
+template <>
+struct DirWord<8> {
+    using T = uint32_t;
+};
+template <>
+struct DirWord<16> {
+    using T = uint2;
+};
+template <>
+struct DirWord<32> {
+    using T = uint4;
+};
+
+template <int W>
+__device__ __forceinline__ void put_nib(typename DirWord<W>::T &w, int k, uint32_t nib) {
+    if constexpr (W == 8) {
+        w |= nib << (4 * k);
+    } else if constexpr (W == 16) {
+        if (k < 8) w.x |= nib << (4 * k);
+        else w.y |= nib << (4 * (k - 8));
+    } else {
+        const int s = 4 * (k & 7);
+        if (k < 8) w.x |= nib << s;
+        else if (k < 16) w.y |= nib << s;
+        else if (k < 24) w.z |= nib << s;
+        else w.w |= nib << s;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ uint32_t get_nib(const typename DirWord<W>::T &w, int k) {
+    if constexpr (W == 8) {
+        return (w >> (4 * k)) & 15u;
+    } else if constexpr (W == 16) {
+        return ((k < 8 ? w.x : w.y) >> (4 * (k & 7))) & 15u;
+    } else {
+        const uint32_t v = k < 8 ? w.x : k < 16 ? w.y : k < 24 ? w.z : w.w;
+        return (v >> (4 * (k & 7))) & 15u;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void zero(typename DirWord<W>::T &w) {
+    if constexpr (W == 8) w = 0u;
+    else if constexpr (W == 16) w = make_uint2(0u, 0u);
+    else w = make_uint4(0u, 0u, 0u, 0u);
+}
+
+struct BandSeq {
+    const uint8_t *q;  // row i (1-based) letter at q[(i-1) * qs]
+    int qs;
+    int rows;
+    const uint8_t *t;  // column j (1-based) letter at t[(j-1) * ts]
+    int ts;
+    int cols;
+};
+
+// Banded global-start DP over rows 0..rows, band diagonals [dlo, dlo + wb).
+// REV: finds the first column (then row) holding `target`; returns false if
+// none.  !REV: stores decision nibbles per row and returns H(rows, cols).
+template <int W, bool REV, bool DNA>
+__device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int A, int O, int X, int target,
+                        typename DirWord<W>::T *dirs, int *out_i, int *out_j, int *final_h) {
+    int Hp[W], Fp[W];
+    int tw[W];  // target letter of each band cell's column in the current row (sliding window)
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+        Hp[k] = kNegB;
+        Fp[k] = kNegB;
+        const int jj = dlo + k - 1;  // row 0: letter index j - 1 = dlo + k - 1 (shifted in before use)
+        tw[k] = (jj >= 0 && jj < s.cols) ? min((int)s.t[(long long)jj * s.ts], A - 1) : 0;
+    }
+    int best_j = INT_MAX, best_i = -1;
+    int fin = kNegB;
+    for (int i = 0; i <= s.rows; i++) {
+        const int qa = i >= 1 ? min((int)s.q[(long long)(i - 1) * s.qs], A - 1) : 0;
+        uint32_t wpack = 0;  // DNA: the 4 scores of the query letter, one byte each
+        const int8_t *wrow = sW + qa * A;
+        if constexpr (DNA) wpack = *reinterpret_cast<const uint32_t *>(wrow);
+        if (i >= 1) {
+            // the window moves one column right per row
+#pragma unroll
+            for (int k = 0; k < W - 1; k++) tw[k] = tw[k + 1];
+            const int jj = i + dlo + W - 2;
+            tw[W - 1] = (jj >= 0 && jj < s.cols) ? min((int)s.t[(long long)jj * s.ts], A - 1) : 0;
+        }
+        int hleft = kNegB, eleft = kNegB;
+        typename DirWord<W>::T dw;
+        zero<W>(dw);
+        int row_hit = -1;
+#pragma unroll
+        for (int k = 0; k < W; k++) {
+            const int j = i + dlo + k;
+            const bool valid = k < wb && j >= 0 && j <= s.cols;
+            const int hup = k + 1 < W ? Hp[k + 1] : kNegB;
+            const int fup = k + 1 < W ? Fp[k + 1] : kNegB;
+            int F = kNegB, hdg = kNegB, E = kNegB, H;
+            bool fopen = false, eopen = false;
+            if (i >= 1) {
+                const int fo = hup - O;
+                F = max(fo, fup - X);
+                fopen = F == fo;
+            }
+            if (i >= 1 && j >= 1 && valid) {
+                int w;
+                if constexpr (DNA) w = (int)(int8_t)(uint8_t)(wpack >> (8 * tw[k]));
+                else w = wrow[tw[k]];
+                hdg = Hp[k] + w;
+            }
+            if (j >= 1) {
+                const int eo = hleft - O;
+                E = max(eo, eleft - X);
+                eopen = E == eo;
+            }
+            H = max(hdg, max(E, F));
+            if (i == 0 && j == 0) H = 0;
+            if (!valid || H < kNegBHalf) {
+                H = kNegB;
+                E = kNegB;
+                F = kNegB;
+            }
+            if constexpr (REV) {
+                if (i >= 1 && j >= 1 && H == target && row_hit < 0) row_hit = j;
+            } else {
+                const uint32_t src = (i >= 1 && j >= 1 && hdg > kNegBHalf && H == hdg) ? 0u : (H == E ? 1u : 2u);
+                put_nib<W>(dw, k, src | (eopen ? 4u : 0u) | (fopen ? 8u : 0u));
+                if (i == s.rows && j == s.cols) fin = H;
+            }
+            // this row's value becomes the next row's "previous row"
+            Hp[k] = H;
+            Fp[k] = F;
+            hleft = H;
+            eleft = E;
+        }
+        if constexpr (REV) {
+            if (row_hit >= 0 && row_hit < best_j) {
+                best_j = row_hit;
+                best_i = i;
+            }
+            // no later row can reach a column <= best_j inside the band
+            if (best_j != INT_MAX && i + 1 + dlo >= best_j) break;
+        } else {
+            dirs[(long long)i * 32] = dw;
+        }
+    }
+    if constexpr (REV) {
+        *out_i = best_i;
+        *out_j = best_j;
+        return best_j != INT_MAX;
+    } else {
+        *final_h = fin;
+        return true;
+    }
+}
+
+// Walks the decision nibbles from (la, lb) back to (0, 0).  With WRITE the
+// runs go to out[0..nr) in forward order; returns the run count or -1.
+template <int W, bool WRITE>
+__device__ int band_walk(const typename DirWord<W>::T *dirs, int la, int lb, int dlo, int wb, uint32_t *out, int nr) {
+    int i = la, j = lb, state = 0, cur = -1, len = 0, runs = 0, guard = 2 * (la + lb) + 4;
+    while ((i > 0 || j > 0) && guard-- > 0) {
+        const int k = j - i - dlo;
+        if (i < 0 || j < 0 || k < 0 || k >= wb) return -1;
+        const uint32_t nib = get_nib<W>(dirs[(long long)i * 32], k);
+        int op;
+        if (state == 0) {
+            const int src = nib & 3;
+            if (src == 0) {
+                op = GSW_CIGAR_M;
+                i--;
+                j--;
+            } else {
+                state = src;
+                continue;
+            }
+        } else if (state == 1) {
+            op = GSW_CIGAR_D;
+            state = (nib & 4) ? 0 : 1;
+            j--;
+        } else {
+            op = GSW_CIGAR_I;
+            state = (nib & 8) ? 0 : 2;
+            i--;
+        }
+        if (op == cur) {
+            len++;
+        } else {
+            if (len) {
+                if (WRITE) out[nr - 1 - runs] = ((uint32_t)len << 4) | (uint32_t)cur;
+                runs++;
+            }
+            cur = op;
+            len = 1;
+        }
+    }
+    if (i != 0 || j != 0) return -1;
+    if (len) {
+        if (WRITE) out[nr - 1 - runs] = ((uint32_t)len << 4) | (uint32_t)cur;
+        runs++;
+    }
+    return runs;
+}
+
+struct BandLaunch {
+    BatchView b;
+    Scoring sc;
+    const int32_t *order;
+    const int32_t *var_start;  // per class
+    int32_t *head;             // per class task counters
+    void *scratch;             // per warp: (maxrows + 1) * 32 direction words of the class width
+    int64_t scratch_words;     // per warp, in 32-bit words
+};
+
+template <int W>
+__device__ void band_pair(const BandLaunch &L, int p, const int8_t *sW, typename DirWord<W>::T *dirs) {
+    const BatchView &b = L.b;
+    const Scoring &sc = L.sc;
+    gsw_result *rp = b.res + p;
+    const int s1 = rp->score1, eq = rp->read_end1, et = rp->ref_end1;
+    const uint8_t *qp = b.q + b.q_off[p];
+    const uint8_t *tp = b.t + b.t_off[p];
+    int bq = rp->read_begin1, bt = rp->ref_begin1;
+    if (bq < 0 || bt < 0) {
+        const int G = reverse_gap_bound(eq, s1, sc);
+        BandSeq s{qp + eq, -1, eq + 1, tp + et, -1, reverse_window(eq, et, s1, sc)};
+        int bi, bj, dummy;
+        const bool ok = sc.dna4 ? band_dp<W, true, true>(s, -G, 2 * G + 1, sW, sc.A, sc.O, sc.X, s1, nullptr, &bi, &bj, &dummy)
+                                : band_dp<W, true, false>(s, -G, 2 * G + 1, sW, sc.A, sc.O, sc.X, s1, nullptr, &bi, &bj, &dummy);
+        if (!ok) {
+            rp->flags |= kResInternal;
+            return;
+        }
+        bq = eq - (bi - 1);
+        bt = et - (bj - 1);
+        rp->read_begin1 = bq;
+        rp->ref_begin1 = bt;
+    }
+    if (!(b.flags & GSW_CIGAR)) return;
+    const int la = eq - bq + 1, lb = et - bt + 1;
+    const int w = band_halfwidth(la, lb, s1, sc);
+    const int delta = lb - la;
+    const int dlo = max(min(0, delta) - w, -la), dhi = min(max(0, delta) + w, lb);
+    const int wb = dhi - dlo + 1;
+    if (wb > W) {
+        rp->flags |= kResPendingTrace;  // the warp traceback takes it
+        return;
+    }
+    BandSeq s{qp + bq, 1, la, tp + bt, 1, lb};
+    int fin = 0, di, dj;
+    if (sc.dna4) band_dp<W, false, true>(s, dlo, wb, sW, sc.A, sc.O, sc.X, 0, dirs, &di, &dj, &fin);
+    else band_dp<W, false, false>(s, dlo, wb, sW, sc.A, sc.O, sc.X, 0, dirs, &di, &dj, &fin);
+    if (fin != s1) {
+        rp->flags |= kResInternal;
+        return;
+    }
+    const int nr = band_walk<W, false>(dirs, la, lb, dlo, wb, nullptr, 0);
+    if (nr < 0) {
+        rp->flags |= kResInternal;
+        return;
+    }
+    const unsigned long long off = atomicAdd(b.cigar_cursor, (unsigned long long)nr);
+    if ((long long)(off + nr) > b.cigar_cap) {
+        rp->flags |= GSW_RES_CIGAR_SPACE;
+        rp->cigar_len = -nr;
+        rp->cigar_off = -1;
+        return;
+    }
+    band_walk<W, true>(dirs, la, lb, dlo, wb, b.cigar + off, nr);
+    rp->cigar_len = nr;
+    rp->cigar_off = (int64_t)off;
+}
+
+template <int W, int CLS>
+__global__ void __launch_bounds__(kBBlock) k_band(BandLaunch L) {
+    __shared__ __align__(4) int8_t sW[kMaxAlpha * kMaxAlpha];
+    for (int i = threadIdx.x; i < L.sc.A * L.sc.A; i += blockDim.x) sW[i] = L.sc.W[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gwarp = blockIdx.x * (kBBlock / 32) + warp;
+    using DW = typename DirWord<W>::T;
+    DW *dirs = reinterpret_cast<DW *>(reinterpret_cast<uint32_t *>(L.scratch) + (size_t)gwarp * L.scratch_words) + lane;
+    const int first = L.var_start[CLS], last = L.var_start[CLS + 1];
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&L.head[CLS], 1);
+        t = __shfl_sync(0xFFFFFFFFu, t, 0);
+        const int idx = first + t * 32 + lane;
+        if (first + t * 32 >= last) break;
+        if (idx < last) band_pair<W>(L, L.order[idx], sW, dirs);
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+int band_block_threads() { return kBBlock; }
+
+cudaError_t launch_band(const BatchView &b, const Scoring &sc, const PlanBuffers &pb, void *scratch,
+                        int64_t scratch_words, int grid, cudaStream_t st) {
+    BandLaunch L;
+    L.b = b;
+    L.sc = sc;
+    L.order = pb.order;
+    L.var_start = pb.var_start;
+    L.head = pb.task_lo;  // reused as per-class counters (zeroed below)
+    L.scratch = scratch;
+    L.scratch_words = scratch_words;
+    cudaMemsetAsync(pb.task_lo, 0, sizeof(int32_t) * kNumVariants, st);
+    k_band<8, 0><<<grid, kBBlock, 0, st>>>(L);
+    k_band<16, 1><<<grid, kBBlock, 0, st>>>(L);
+    k_band<32, 2><<<grid, kBBlock, 0, st>>>(L);
+    return cudaGetLastError();
+}
+
+}  // namespace gsw

@@ -21,9 +21,16 @@
 // long as no score exceeds 32767 - max W; a pair whose maximum does is
 // flagged and re-filled in 32-bit lanes (same ring, one row per word).
 //
-// The score lookup W(q_i, t_j) comes from a per-lane shared-memory profile:
-// for DNA (4 letters) one word per (row pair, low letter, high letter), i.e.
-// 16 x R words; for other alphabets one low table and one high table.
+// The score lookup W(q_i, t_j) comes from a shared-memory profile: for DNA (4
+// letters) one word per (row pair, low letter, high letter), i.e. 16 x R words
+// per lane; for other alphabets one low table and one high table.  The words
+// of the 32 lanes of a warp are interleaved (lane-minor, 16-byte vectors), so
+// the vector loads of a warp never collide in a bank although every lane reads
+// a different letter pair.
+//
+// Critical path.  With O >= X, max(F - X, H - O) = max(F - X, T - O) where
+// T = max(H(i-1,j-1) + W, E, 0) does not depend on F, so the F chain down a
+// lane's rows is one add and one max per row.
 //
 // End position (the paper's "recorded column"): every lane tracks, per half,
 // the first column where its running column maximum (the maximum over rows 0
@@ -68,9 +75,18 @@ struct L32 {
     static __device__ __forceinline__ uint32_t addk(int c) { return (uint32_t)c; }
 };
 
-// words of the per-lane profile region
+// words of one lane's profile (the warp region holds 32 lanes' worth)
 __host__ __device__ constexpr int prof_words(int R, bool fold, bool dna, int A) {
-    return (dna ? (fold ? 16 * R : 4 * R) : (fold ? 2 * A * R : A * R)) + 4;
+    return dna ? (fold ? 16 * R : 4 * R) : (fold ? 2 * A * R : A * R);
+}
+
+// Index of profile word (table c, row r) of lane l inside the warp region:
+// lane-minor groups of 4, 2 or 1 consecutive rows (the vector width).
+template <int R>
+__device__ __forceinline__ int pidx(int c, int r, int l) {
+    if constexpr (R % 4 == 0) return ((c * (R / 4) + r / 4) * 32 + l) * 4 + (r & 3);
+    else if constexpr (R % 2 == 0) return ((c * (R / 2) + r / 2) * 32 + l) * 2 + (r & 1);
+    else return (c * R + r) * 32 + l;
 }
 
 // One fill job for a group (one pair).
@@ -93,23 +109,24 @@ struct RingResult {
     int pad_top;
 };
 
+// Loads the R words of table c for lane l.
 template <int R>
-__device__ __forceinline__ void load_words(const uint32_t *p, uint32_t (&w)[R]) {
+__device__ __forceinline__ void load_words(const uint32_t *base, int c, int l, uint32_t (&w)[R]) {
     if constexpr (R % 4 == 0) {
 #pragma unroll
         for (int r = 0; r < R; r += 4) {
-            uint4 v = *reinterpret_cast<const uint4 *>(p + r);
+            const uint4 v = *reinterpret_cast<const uint4 *>(base + pidx<R>(c, r, l));
             w[r] = v.x; w[r + 1] = v.y; w[r + 2] = v.z; w[r + 3] = v.w;
         }
     } else if constexpr (R % 2 == 0) {
 #pragma unroll
         for (int r = 0; r < R; r += 2) {
-            uint2 v = *reinterpret_cast<const uint2 *>(p + r);
+            const uint2 v = *reinterpret_cast<const uint2 *>(base + pidx<R>(c, r, l));
             w[r] = v.x; w[r + 1] = v.y;
         }
     } else {
 #pragma unroll
-        for (int r = 0; r < R; r++) w[r] = p[r];
+        for (int r = 0; r < R; r++) w[r] = base[pidx<R>(c, r, l)];
     }
 }
 
@@ -118,8 +135,8 @@ __device__ __forceinline__ int sc_w(const Scoring &sc, int a, int b) { return sc
 // Builds this lane's profile for strip `st` (padded rows of the strip:
 // [st*SP, st*SP + SP); padded row rho holds query row rho - pad_top).
 template <int P, int R, class L, bool DNA>
-__device__ __forceinline__ void build_profile(uint32_t *psm, const Job &job, const Scoring &sc, int k, int st,
-                                              int pad_top) {
+__device__ __forceinline__ void build_profile(uint32_t *psm, const Job &job, const Scoring &sc, int k, int lane,
+                                              int st, int pad_top) {
     constexpr int S = P * R;
     constexpr int SP = L::FOLD ? 2 * S : S;
     const int A = sc.A;
@@ -140,16 +157,17 @@ __device__ __forceinline__ void build_profile(uint32_t *psm, const Job &job, con
                     for (int b = 0; b < 4; b++) {
                         int wl = qlo >= 0 ? sc_w(sc, qlo, a) : 0;
                         int wh = qhi >= 0 ? sc_w(sc, qhi, b) : 0;
-                        psm[(a * 4 + b) * R + r] = (uint32_t)(wl + wh * 65536);
+                        psm[pidx<R>(a * 4 + b, r, lane)] = (uint32_t)(wl + wh * 65536);
                     }
             } else {
 #pragma unroll
-                for (int a = 0; a < 4; a++) psm[a * R + r] = (uint32_t)(qlo >= 0 ? sc_w(sc, qlo, a) : 0);
+                for (int a = 0; a < 4; a++) psm[pidx<R>(a, r, lane)] = (uint32_t)(qlo >= 0 ? sc_w(sc, qlo, a) : 0);
             }
         } else {
             for (int a = 0; a < A; a++) {
-                psm[a * R + r] = (uint32_t)(qlo >= 0 ? sc_w(sc, qlo, a) : 0);
-                if constexpr (L::FOLD) psm[(A + a) * R + r] = (uint32_t)((qhi >= 0 ? sc_w(sc, qhi, a) : 0) * 65536);
+                psm[pidx<R>(a, r, lane)] = (uint32_t)(qlo >= 0 ? sc_w(sc, qlo, a) : 0);
+                if constexpr (L::FOLD)
+                    psm[pidx<R>(A + a, r, lane)] = (uint32_t)((qhi >= 0 ? sc_w(sc, qhi, a) : 0) * 65536);
             }
         }
     }
@@ -170,7 +188,7 @@ __device__ __forceinline__ int lane_hi(uint32_t w) {
 // group call it with the same job and return the same result.
 template <int P, int R, class L, bool DNA>
 __device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm, int k, unsigned gmask,
-                                int gbase) {
+                                int gbase, int lane) {
     constexpr int S = P * R;
     constexpr int SP = L::FOLD ? 2 * S : S;
     constexpr uint32_t Z2 = L::Z2;
@@ -190,7 +208,7 @@ __device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm
 
 #pragma unroll 1
     for (int st = 0; st < nstrips; st++) {
-        build_profile<P, R, L, DNA>(psm, job, sc, k, st, pad_top);
+        build_profile<P, R, L, DNA>(psm, job, sc, k, lane, st, pad_top);
         __syncwarp(gmask);
         const typename L::bnd_t *bin = bnd + (size_t)((st + 1) & 1) * n;  // written by strip st-1
         typename L::bnd_t *bout = bnd + (size_t)(st & 1) * n;             // read by strip st+1
@@ -203,6 +221,8 @@ __device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm
         uint32_t best = Z2;
         int c_lo = -1, c_hi = -1;
         uint32_t xh = Z2, xf = NEGE, xc = Z2;  // values received from lane k-1
+        int nal = (-k >= 0 && -k < n) ? min((int)job.t[0], A - 1) : 0;
+        int nah = 0;
 
 #pragma unroll 1
         for (int s = 0; s < nsteps; s++) {
@@ -233,22 +253,21 @@ __device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm
                     cmin = Z2;
                 }
             }
-            // letters of this lane's columns
-            const int al = (jlo >= 0 && jlo < n) ? min((int)job.t[(long long)jlo * job.ts], A - 1) : 0;
+            // letters of this lane's columns (loaded one step ahead)
+            const int al = nal, ah = nah;
+            {
+                const int j1 = jlo + 1, j2 = jhi + 1;
+                nal = (j1 >= 0 && j1 < n) ? min((int)job.t[(long long)j1 * job.ts], A - 1) : 0;
+                if constexpr (L::FOLD) nah = (j2 >= 0 && j2 < n) ? min((int)job.t[(long long)j2 * job.ts], A - 1) : 0;
+            }
             uint32_t pw[R];
             if constexpr (DNA) {
-                if constexpr (L::FOLD) {
-                    const int ah = (jhi >= 0 && jhi < n) ? min((int)job.t[(long long)jhi * job.ts], A - 1) : 0;
-                    load_words<R>(psm + (al * 4 + ah) * R, pw);
-                } else {
-                    load_words<R>(psm + al * R, pw);
-                }
+                load_words<R>(psm, L::FOLD ? al * 4 + ah : al, lane, pw);
             } else {
-                load_words<R>(psm + al * R, pw);
+                load_words<R>(psm, al, lane, pw);
                 if constexpr (L::FOLD) {
-                    const int ah = (jhi >= 0 && jhi < n) ? min((int)job.t[(long long)jhi * job.ts], A - 1) : 0;
                     uint32_t ph[R];
-                    load_words<R>(psm + (A + ah) * R, ph);
+                    load_words<R>(psm, A + ah, lane, ph);
 #pragma unroll
                     for (int r = 0; r < R; r++) pw[r] += ph[r];
                 }
@@ -258,15 +277,15 @@ __device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm
             uint32_t f = fin, m = cmin;
 #pragma unroll
             for (int r = 0; r < R; r++) {
-                uint32_t h = L::vmax(diag + pw[r], E[r]);
-                h = L::vmax(h, Z2);
-                h = L::vmax(h, f);
+                uint32_t tt = L::vmax(diag + pw[r], E[r]);
+                tt = L::vmax(tt, Z2);
+                const uint32_t to = tt + kO;
+                const uint32_t h = L::vmax(tt, f);
+                f = L::vmax(f + kX, to);  // = max(F - X, H - O) since O >= X
                 diag = H[r];
                 H[r] = h;
                 m = L::vmax(m, h);
-                const uint32_t ho = h + kO;
-                E[r] = L::vmax(E[r] + kX, ho);
-                f = L::vmax(f + kX, ho);
+                E[r] = L::vmax(E[r] + kX, h + kO);
             }
             // before a half's first column its state must be the left boundary
             if (jhi < 0) {
@@ -402,8 +421,7 @@ __device__ void run_task(const FillLaunch &fl, int first, int last, uint32_t *ws
     const uint8_t *qp = b.q + b.q_off[pair];
     const uint8_t *tp = b.t + b.t_off[pair];
     const int slot = slot_base + g;
-    constexpr int PW = prof_words(R, L::FOLD, DNA, 0);
-    uint32_t *psm = wsm + lane * (DNA ? PW : prof_words(R, L::FOLD, false, sc.A));
+    uint32_t *psm = wsm;  // the warp's profile region (lane-interleaved)
     Job job;
     const size_t ncap = (size_t)fl.scr.ncap;
     // one stride for every variant, so slots never overlap when 16-bit and
@@ -422,7 +440,7 @@ __device__ void run_task(const FillLaunch &fl, int first, int last, uint32_t *ws
         job.ncols = reverse_window(eq, et, s1, sc);
         job.stop_u = L::lane1(s1);
         job.cms = nullptr;
-        RingResult rr = ring_fill<P, R, L, DNA>(job, sc, psm, k, gmask, gbase);
+        RingResult rr = ring_fill<P, R, L, DNA>(job, sc, psm, k, gmask, gbase, lane);
         if (k == 0) {
             if (rr.score == s1 && rr.col >= 0) {
                 rp->ref_begin1 = et - rr.col;
@@ -450,7 +468,7 @@ __device__ void run_task(const FillLaunch &fl, int first, int last, uint32_t *ws
     job.t = tp;
     job.ts = 1;
     job.ncols = n;
-    RingResult rr = ring_fill<P, R, L, DNA>(job, sc, psm, k, gmask, gbase);
+    RingResult rr = ring_fill<P, R, L, DNA>(job, sc, psm, k, gmask, gbase, lane);
     const bool overflow = L::FOLD && rr.score > 32767 - sc.wmax;
     int s2 = 0, e2 = -1;
     const int end_t = rr.col, end_q = rr.score > 0 ? rr.row - rr.pad_top : -1;
@@ -473,77 +491,102 @@ __device__ void run_task(const FillLaunch &fl, int first, int last, uint32_t *ws
     }
 }
 
-// Persistent fill kernel: warps take tasks (32/P pairs of one variant) from a
-// queue ordered heaviest variant first, target length descending.
-template <bool DNA>
+template <int VID>
+struct VarC;
+#define GSW_VARC(id, P_, R_, S32_)              \
+    template <>                                 \
+    struct VarC<id> {                           \
+        static constexpr int P = P_, R = R_;    \
+        using Lanes = std::conditional_t<S32_ != 0, L32, L16>; \
+    };
+GSW_FILL_VARIANTS(GSW_VARC)
+#undef GSW_VARC
+
+// Persistent fill kernel of one variant: warps take tasks (32/P pairs) from
+// the variant's counter; the plan sorted them by cost, descending.
+template <bool DNA, int VID>
 __global__ void __launch_bounds__(kBlock) k_fill(FillLaunch fl, int warp_words) {
+    using V = VarC<VID>;
     extern __shared__ __align__(16) uint32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gwarp = blockIdx.x * (kBlock / 32) + warp;
     uint32_t *wsm = smem + (size_t)warp * warp_words;
-    const int slot_base = gwarp * fl.scr.slots_per_warp;
-    const int ntasks = *fl.plan.ntasks;
+    const int slot_base = gwarp * (32 / V::P);
+    const int ntasks = fl.plan.task_hi[VID] - fl.plan.task_lo[VID];
+    const int first0 = fl.plan.var_start[VID], last = fl.plan.var_start[VID + 1];
+    constexpr int per = 32 / V::P;
     for (;;) {
         int task = 0;
-        if (lane == 0) task = atomicAdd(fl.plan.head, 1);
+        if (lane == 0) task = atomicAdd(&fl.plan.head[VID], 1);
         task = __shfl_sync(0xFFFFFFFFu, task, 0);
         if (task >= ntasks) break;
-        int v = 0;
-        while (v < kNumVariants - 1 && !(task >= fl.plan.task_lo[v] && task < fl.plan.task_hi[v])) v++;
-        const int per = 32 / variant_at(v).P;
-        const int first = fl.plan.var_start[v] + (task - fl.plan.task_lo[v]) * per;
-        const int last = fl.plan.var_start[v + 1];
-        switch (v) {
-#define GSW_RUN_CASE(id, P, R, S32)                                                         \
-    case id:                                                                                \
-        run_task<P, R, std::conditional_t<S32 != 0, L32, L16>, DNA>(fl, first, last, wsm, lane, \
-                                                                    slot_base);             \
-        break;
-            GSW_FILL_VARIANTS(GSW_RUN_CASE)
-#undef GSW_RUN_CASE
-        default: break;
-        }
+        run_task<V::P, V::R, typename V::Lanes, DNA>(fl, first0 + task * per, last, wsm, lane, slot_base);
         __syncwarp();
     }
+}
+
+template <bool DNA, int VID>
+size_t smem_bytes(int A) {
+    using V = VarC<VID>;
+    return (size_t)prof_words(V::R, V::Lanes::FOLD, DNA, A) * 32 * sizeof(uint32_t) * (kBlock / 32);
+}
+
+template <bool DNA, int VID>
+int occupancy(int A) {
+    const size_t sm = smem_bytes<DNA, VID>(A);
+    cudaFuncSetAttribute(k_fill<DNA, VID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fill<DNA, VID>, kBlock, sm);
+    return nb;
+}
+
+template <bool DNA, int VID>
+cudaError_t launch_one(const FillLaunch &fl, int sms, int max_blocks, cudaStream_t st) {
+    const size_t sm = smem_bytes<DNA, VID>(fl.sc.A);
+    int nb = occupancy<DNA, VID>(fl.sc.A);
+    if (nb < 1) return cudaErrorInvalidConfiguration;
+    int grid = sms * nb;
+    if (grid > max_blocks) grid = max_blocks;
+    k_fill<DNA, VID><<<grid, kBlock, sm, st>>>(fl, (int)(sm / sizeof(uint32_t) / (kBlock / 32)));
+    return cudaGetLastError();
+}
+
+template <bool DNA>
+cudaError_t launch_all(const FillLaunch &fl, int sms, int max_blocks, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    // heaviest variants first
+#define GSW_LAUNCH(id, P_, R_, S_) \
+    if (e == cudaSuccess) e = launch_one<DNA, kNumVariants - 1 - id>(fl, sms, max_blocks, st);
+    GSW_FILL_VARIANTS(GSW_LAUNCH)
+#undef GSW_LAUNCH
+    return e;
+}
+
+template <bool DNA>
+int max_slots(int A, int sms) {
+    int best = 0;
+#define GSW_SLOTS(id, P_, R_, S_)                                                   \
+    {                                                                             \
+        const int nb = occupancy<DNA, id>(A);                                     \
+        const int slots = sms * nb * (kBlock / 32) * (32 / VarC<id>::P);          \
+        best = slots > best ? slots : best;                                       \
+    }
+    GSW_FILL_VARIANTS(GSW_SLOTS)
+#undef GSW_SLOTS
+    return best;
 }
 
 }  // namespace
 
 int fill_block_threads() { return kBlock; }
 
-// shared memory words per warp: the largest per-lane profile of any variant
-size_t fill_smem_per_warp(const Scoring &sc) {
-    const bool dna = sc.dna4 != 0;
-    int w = 0;
-    for (int v = 0; v < kNumVariants; v++) {
-        int pw = prof_words(variant_at(v).R, !variant_at(v).s32, dna, sc.A);
-        w = w > pw ? w : pw;
-    }
-    return (size_t)w * 32 * sizeof(uint32_t);
-}
+// Slots (pairs in flight) the largest variant launch can hold, at full
+// occupancy on `sms` SMs; a launch is never given more blocks than
+// max_blocks, so callers can cap the scratch.
+int fill_slots(const Scoring &sc, int sms) { return sc.dna4 ? max_slots<true>(sc.A, sms) : max_slots<false>(sc.A, sms); }
 
-int fill_max_blocks_per_sm(const Scoring &sc, size_t smem) {
-    int nb = 0;
-    if (sc.dna4) {
-        cudaFuncSetAttribute(k_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fill<true>, kBlock, smem);
-    } else {
-        cudaFuncSetAttribute(k_fill<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fill<false>, kBlock, smem);
-    }
-    return nb;
-}
-
-cudaError_t launch_fill(const FillLaunch &fl, int grid, size_t smem, cudaStream_t st) {
-    const int warp_words = (int)(smem / sizeof(uint32_t) / (kBlock / 32));
-    if (fl.sc.dna4) {
-        cudaFuncSetAttribute(k_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_fill<true><<<grid, kBlock, smem, st>>>(fl, warp_words);
-    } else {
-        cudaFuncSetAttribute(k_fill<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_fill<false><<<grid, kBlock, smem, st>>>(fl, warp_words);
-    }
-    return cudaGetLastError();
+cudaError_t launch_fill(const FillLaunch &fl, int sms, int max_blocks, cudaStream_t st) {
+    return fl.sc.dna4 ? launch_all<true>(fl, sms, max_blocks, st) : launch_all<false>(fl, sms, max_blocks, st);
 }
 
 }  // namespace gsw

@@ -45,7 +45,9 @@ struct BatchView {
 enum FillMode : int32_t {
     kFillForward = 0,  // forward local fill: score1, ends, max array, secondary
     kFillRerun = 1,    // forward fill in 32-bit lanes for pairs whose 16-bit fill overflowed
-    kFillReverse = 2,  // reversed fill from the end: begins
+    kFillReverse = 2,  // reversed fill from the end: begins (pairs whose reverse band is wide)
+    kPlanBand = 3,     // not a fill: classes of the thread-per-pair band kernel
+    kPlanTrace = 4,    // not a fill: pairs left to the warp traceback
 };
 
 // Kernel variants: (threads per pair P, row-words per thread R, 32-bit
@@ -88,7 +90,7 @@ struct FillPlan {
     const int32_t *var_start;  // [kNumVariants+1] start of each variant's pairs in `order`
     const int32_t *task_lo;    // [kNumVariants] first task index of each variant
     const int32_t *task_hi;    // [kNumVariants] one past its last task index
-    int32_t *head;             // task counter (zeroed by the plan)
+    int32_t *head;             // [kNumVariants] task counters (zeroed by the plan)
     const int32_t *ntasks;     // total tasks
 };
 
@@ -111,6 +113,13 @@ struct FillLaunch {
 // internal per-pair bits (besides the public GSW_RES_*)
 constexpr int32_t kResPendingS32 = 0x40;  // 16-bit fill overflowed: refill in 32-bit lanes
 constexpr int32_t kResInternal = 0x80;    // a consistency check failed (should never happen)
+constexpr int32_t kResPendingTrace = 0x100;  // band too wide for one thread: warp traceback
+
+// The thread-per-pair band kernel handles bands up to this many diagonals and
+// this many rows; wider or longer pairs use the ring reverse fill and the warp
+// traceback.
+constexpr int kBandMaxWidth = 32;
+constexpr int kBandMaxRows = 4096;
 
 constexpr int kPlanBinsPerVariant = 1024;
 constexpr int kPlanBins = kNumVariants * kPlanBinsPerVariant;
@@ -127,6 +136,17 @@ __host__ __device__ inline int reverse_window(int end_q, int end_t, int score1, 
     long long w = (long long)end_q + 1 + d;
     long long lim = (long long)end_t + 1;
     return (int)(w < lim ? w : lim);
+}
+
+// Largest number of gap letters an alignment ending at (end_q, end_t) with
+// score1 can hold: its at most end_q+1 aligned pairs score <= (end_q+1)*wmax,
+// and g gap letters cost at least O + (g-1)X (O >= X).  -1 means unbounded.
+__host__ __device__ inline int reverse_gap_bound(int end_q, int score1, const Scoring &sc) {
+    long long num = (long long)(end_q + 1) * sc.wmax - score1 - sc.O;
+    if (num < 0) return 0;
+    if (sc.X <= 0) return -1;
+    long long g = num / sc.X + 1;
+    return g > (1 << 30) ? (1 << 30) : (int)g;
 }
 
 // Half-width of the band of the global alignment between begin and end
@@ -154,11 +174,24 @@ __host__ __device__ inline int band_halfwidth(int la, int lb, int score1, const 
     return lo;
 }
 
+// Diagonal range [dlo, dhi] of the traceback band, clipped to the rectangle.
+__host__ __device__ inline int band_range(int la, int lb, int score1, const Scoring &sc, int *dlo, int *dhi) {
+    const int w = band_halfwidth(la, lb, score1, sc);
+    const int delta = lb - la;
+    int lo = (delta < 0 ? delta : 0) - w, hi = (delta > 0 ? delta : 0) + w;
+    lo = lo < -la ? -la : lo;
+    hi = hi > lb ? lb : hi;
+    *dlo = lo;
+    *dhi = hi;
+    return hi - lo + 1;
+}
+
 // stage launchers (host side, enqueue on `st`)
 int fill_block_threads();
-size_t fill_smem_per_warp(const Scoring &sc);
-int fill_max_blocks_per_sm(const Scoring &sc, size_t smem);
-cudaError_t launch_fill(const FillLaunch &fl, int grid, size_t smem, cudaStream_t st);
+// largest number of slots (pairs in flight) of any variant's launch
+int fill_slots(const Scoring &sc, int sms);
+// one persistent launch per variant, heaviest first; each grid capped at max_blocks
+cudaError_t launch_fill(const FillLaunch &fl, int sms, int max_blocks, cudaStream_t st);
 
 struct PlanBuffers {
     int32_t *keys;       // [npairs]
@@ -170,17 +203,18 @@ struct PlanBuffers {
     int32_t *task_lo;    // [kNumVariants]
     int32_t *task_hi;    // [kNumVariants]
     int32_t *ntasks;     // [1]
-    int32_t *head;       // [1]
+    int32_t *head;       // [kNumVariants]
 };
 cudaError_t launch_plan(const BatchView &b, const Scoring &sc, int32_t mode, const PlanBuffers &pb,
                         cudaStream_t st);
 
 struct TraceScratch {
-    uint32_t *dirs;        // per warp: dir_words words (global direction bit-planes)
-    int64_t dir_words;     // per warp
-    uint32_t *ops;         // per warp: op_words words (reversed CIGAR runs)
-    int64_t op_words;      // per warp
-    int32_t *head;         // pair counter
+    uint32_t *dirs;         // per warp: dir_words words (global direction bit-planes)
+    int64_t dir_words;      // per warp
+    uint32_t *ops;          // per warp: op_words words (reversed CIGAR runs)
+    int64_t op_words;       // per warp
+    const int32_t *order;   // pairs to trace: order[var_start[0] .. var_start[1])
+    const int32_t *var_start;
 };
 int trace_block_threads();
 size_t trace_smem_bytes();
@@ -189,6 +223,10 @@ cudaError_t launch_trace_need(const BatchView &b, const Scoring &sc, unsigned lo
                               cudaStream_t st);
 cudaError_t launch_traceback(const BatchView &b, const Scoring &sc, const TraceScratch &ts, int grid,
                              cudaStream_t st);
+
+int band_block_threads();
+cudaError_t launch_band(const BatchView &b, const Scoring &sc, const PlanBuffers &pb, void *scratch,
+                        int64_t scratch_words, int grid, cudaStream_t st);
 
 // small helpers (misc.cu)
 cudaError_t launch_max_lengths(const int32_t *q_len, const int32_t *t_len, int32_t n, int32_t *out2,

@@ -7,6 +7,8 @@
 // made of short ones.
 #include "gsw_impl.cuh"
 
+#include <climits>
+
 namespace gsw {
 namespace {
 
@@ -39,12 +41,60 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
         rows = b.q_len[p];
         cols = b.t_len[p];
         v = kVarS32;
-    } else {
+    } else if (mode == kFillReverse) {
+        // the ring fill takes the reverse of pairs whose band is too wide or
+        // too long for one thread
         const gsw_result r = b.res[p];
         if (r.score1 <= 0 || (r.flags & kResInternal)) { keys[p] = -1; return; }
         rows = r.read_end1 + 1;
+        const int G = reverse_gap_bound(r.read_end1, r.score1, sc);
+        if (G >= 0 && 2 * G + 1 <= kBandMaxWidth && rows <= kBandMaxRows) { keys[p] = -1; return; }
         cols = reverse_window(r.read_end1, r.ref_end1, r.score1, sc);
         v = (r.flags & GSW_RES_S32) ? kVarS32 : pick_s16(rows);
+    } else if (mode == kPlanTrace) {
+        const gsw_result r = b.res[p];
+        if (r.score1 <= 0 || !(r.flags & kResPendingTrace) || (r.flags & kResInternal) || r.read_begin1 < 0) {
+            keys[p] = -1;
+            return;
+        }
+        const int la = r.read_end1 - r.read_begin1 + 1, lb = r.ref_end1 - r.ref_begin1 + 1;
+        int dlo, dhi;
+        const int width = band_range(la, lb, r.score1, sc, &dlo, &dhi);
+        const int key = cost_bin((long long)(la + 1) * ((width + 31) / 32));
+        keys[p] = key;
+        atomicAdd(&hist[key], 1);
+        return;
+    } else {
+        // kPlanBand: classes 0/1/2 = band width <= 8/16/32 diagonals
+        const gsw_result r = b.res[p];
+        if (r.score1 <= 0 || (r.flags & kResInternal)) { keys[p] = -1; return; }
+        int width;
+        if (r.read_begin1 < 0) {
+            const int G = reverse_gap_bound(r.read_end1, r.score1, sc);
+            rows = r.read_end1 + 1;
+            width = G < 0 ? INT_MAX : 2 * G + 1;
+            if (width > kBandMaxWidth || rows > kBandMaxRows) {
+                b.res[p].flags |= kResInternal;  // the ring reverse should have taken it
+                keys[p] = -1;
+                return;
+            }
+        } else {
+            if (!(b.flags & GSW_CIGAR)) { keys[p] = -1; return; }
+            const int la = r.read_end1 - r.read_begin1 + 1, lb = r.ref_end1 - r.ref_begin1 + 1;
+            int dlo, dhi;
+            width = band_range(la, lb, r.score1, sc, &dlo, &dhi);
+            rows = la;
+            if (width > kBandMaxWidth || rows > kBandMaxRows) {
+                b.res[p].flags |= kResPendingTrace;
+                keys[p] = -1;
+                return;
+            }
+        }
+        const int cls = width <= 8 ? 0 : (width <= 16 ? 1 : 2);
+        const int key = cls * kPlanBinsPerVariant + cost_bin(rows);
+        keys[p] = key;
+        atomicAdd(&hist[key], 1);
+        return;
     }
     const Variant var = variant_at(v);
     const int sp = variant_rows(v);
@@ -96,7 +146,7 @@ __global__ void __launch_bounds__(kScanThreads) k_plan_scan(const int32_t *hist,
             task_hi[v] = t;
         }
         *ntasks = t;
-        *head = 0;
+        for (int v = 0; v < kNumVariants; v++) head[v] = 0;
     }
 }
 

@@ -18,6 +18,8 @@
 // planes per row and chunk.  Lane 0 then walks back from (la, lb).
 #include "gsw_impl.cuh"
 
+#include <climits>
+
 namespace gsw {
 namespace {
 
@@ -55,19 +57,32 @@ __device__ Need pair_need(const gsw_result &r, const Scoring &sc) {
     return nd;
 }
 
+// pairs the thread-per-pair band kernel left to this kernel (band too wide)
 __device__ __forceinline__ bool wants_trace(const gsw_result &r) {
-    return r.score1 > 0 && !(r.flags & kResInternal) && r.read_begin1 >= 0 && r.ref_begin1 >= 0;
+    return r.score1 > 0 && (r.flags & kResPendingTrace) && !(r.flags & kResInternal) && r.read_begin1 >= 0 &&
+           r.ref_begin1 >= 0;
 }
 
 __global__ void k_trace_need(BatchView b, Scoring sc, unsigned long long *max_need) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= b.npairs) return;
-    const gsw_result r = b.res[p];
-    if (!wants_trace(r)) return;
-    const Need nd = pair_need(r, sc);
-    atomicMax(&max_need[0], (unsigned long long)nd.dir);
-    atomicMax(&max_need[1], (unsigned long long)nd.ops);
-    atomicMax(&max_need[2], (unsigned long long)nd.nch);
+    unsigned d = 0, o = 0, c = 0;
+    if (p < b.npairs) {
+        const gsw_result r = b.res[p];
+        if (wants_trace(r)) {
+            const Need nd = pair_need(r, sc);
+            d = (unsigned)min(nd.dir, (long long)UINT_MAX);
+            o = (unsigned)min(nd.ops, (long long)UINT_MAX);
+            c = (unsigned)nd.nch;
+        }
+    }
+    d = __reduce_max_sync(0xFFFFFFFFu, d);
+    o = __reduce_max_sync(0xFFFFFFFFu, o);
+    c = __reduce_max_sync(0xFFFFFFFFu, c);
+    if ((threadIdx.x & 31) == 0 && c > 0) {
+        atomicMax(&max_need[0], (unsigned long long)d);
+        atomicMax(&max_need[1], (unsigned long long)o);
+        atomicMax(&max_need[2], (unsigned long long)c);
+    }
 }
 
 __device__ void trace_pair(const BatchView &b, const Scoring &sc, int p, const gsw_result &r, const Need &nd,
@@ -210,6 +225,7 @@ __device__ void trace_pair(const BatchView &b, const Scoring &sc, int p, const g
     if (lane == 0) {
         rp->cigar_len = nr;
         rp->cigar_off = (int64_t)off;
+        rp->flags &= ~kResPendingTrace;
     }
 }
 
@@ -225,11 +241,11 @@ __global__ void __launch_bounds__(kTBlock) k_traceback(BatchView b, Scoring sc, 
     int *sst = reinterpret_cast<int *>(sops + cfg.smem_op_words);
     uint32_t *gdir = ts.dirs + (size_t)gwarp * ts.dir_words;
     uint32_t *gops = ts.ops + (size_t)gwarp * ts.op_words;  // ops, then the chunk state
-    for (;;) {
-        int p = 0;
-        if (lane == 0) p = atomicAdd(ts.head, 1);
-        p = __shfl_sync(0xFFFFFFFFu, p, 0);
-        if (p >= b.npairs) break;
+    // the planned list (sorted by cost, descending) is dealt round-robin
+    const int first = ts.var_start[0], last = ts.var_start[1];
+    const int nwarps = gridDim.x * (kTBlock / 32);
+    for (int idx = first + gwarp; idx < last; idx += nwarps) {
+        const int p = ts.order[idx];
         const gsw_result r = b.res[p];
         if (!wants_trace(r)) continue;
         const Need nd = pair_need(r, sc);
@@ -271,7 +287,6 @@ cudaError_t launch_traceback(const BatchView &b, const Scoring &sc, const TraceS
                              cudaStream_t st) {
     const size_t smem = trace_smem_bytes();
     cudaFuncSetAttribute(k_traceback, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaMemsetAsync(ts.head, 0, sizeof(int32_t), st);
     k_traceback<<<grid, kTBlock, smem, st>>>(b, sc, ts, trace_cfg());
     return cudaGetLastError();
 }

@@ -30,6 +30,9 @@ GSW_COLMAX = 0x4
 GSW_HOST_IO = 0x8
 GSW_FORCE_S32 = 0x10
 GSW_PLAIN = 0x20
+GSW_TIMING = 0x40
+GSW_NSTAGES = 7
+STAGE_NAMES = ("plan_fwd", "fill_fwd", "refill_s32", "reverse_wide", "band", "trace_wide", "pipeline")
 
 GSW_RES_S32 = 0x1
 GSW_RES_CIGAR_SPACE = 0x2
@@ -42,6 +45,11 @@ RESULT_DTYPE = np.dtype([
 assert RESULT_DTYPE.itemsize == 48
 
 _lib = None
+
+
+class GswStats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int32), ("timed", ctypes.c_int32),
+                ("stage_ms", ctypes.c_float * 8)]
 
 
 class GswError(RuntimeError):
@@ -75,6 +83,8 @@ def load(build_if_missing: bool = True):
     for f in (lib.gsw_context_create, lib.gsw_context_destroy, lib.gsw_align_batch,
               lib.gsw_profile_create, lib.gsw_profile_destroy, lib.gsw_align_profile):
         f.restype = ctypes.c_int
+    lib.gsw_last_stats.argtypes = [P, ctypes.POINTER(GswStats)]
+    lib.gsw_last_stats.restype = ctypes.c_int
     lib.gsw_strerror.argtypes = [ctypes.c_int]
     lib.gsw_strerror.restype = ctypes.c_char_p
     lib.gsw_last_error.restype = ctypes.c_char_p
@@ -139,6 +149,15 @@ def gsw_align_batch(ctx, npairs, q, q_off, q_len, t, t_off, t_len, matrix, gap_o
     if check and rc != GSW_ECIGAR_SPACE:
         _check(rc, "gsw_align_batch")
     return rc
+
+
+def gsw_last_stats(ctx) -> dict:
+    st = GswStats()
+    _check(load().gsw_last_stats(ctx, ctypes.byref(st)), "gsw_last_stats")
+    out = {"kernel_launches": st.kernel_launches, "timed": bool(st.timed)}
+    if st.timed:
+        out["stage_ms"] = {n: float(st.stage_ms[k]) for k, n in enumerate(STAGE_NAMES)}
+    return out
 
 
 def gsw_profile_create(ctx, query, matrix, gap_open, gap_extend) -> int:

@@ -119,12 +119,12 @@ def mutate(rng, arena, off, length, p_sub, p_ins, p_del, max_indel=1, alpha=4):
         return src, _offsets(length), length.astype(np.int32)
     seq = np.repeat(np.arange(len(length)), length)
     seq_end = np.repeat(_offsets(length) + length, length)
-    u = rng.random(n)
-    k = rng.integers(1, max_indel + 1, n)
+    u = rng.random(n, dtype=np.float32)
+    k = rng.integers(1, max_indel + 1, n, dtype=np.int8).astype(np.int64) if max_indel > 1 else np.ones(n, np.int64)
     sub = u < p_sub
     ins = (u >= p_sub) & (u < p_sub + p_ins)
     dele = (u >= p_sub + p_ins) & (u < p_sub + p_ins + p_del)
-    src[sub] = (src[sub] + rng.integers(1, alpha, int(sub.sum()))) % alpha
+    src[sub] = (src[sub] + rng.integers(1, alpha, int(sub.sum()), dtype=np.uint8)) % alpha
     pos = np.arange(n, dtype=np.int64)
     diff = np.zeros(n + 1, dtype=np.int64)
     dpos = pos[dele]
@@ -137,7 +137,7 @@ def mutate(rng, arena, off, length, p_sub, p_ins, p_del, max_indel=1, alpha=4):
     owner = np.repeat(pos, counts)
     first = np.repeat(np.cumsum(counts) - counts, counts)
     rank = np.arange(total, dtype=np.int64) - first
-    out = rng.integers(0, alpha, total).astype(np.uint8)
+    out = rng.integers(0, alpha, total, dtype=np.uint8)
     keep_slot = (rank == 0) & ~deleted[owner]
     out[keep_slot] = src[owner[keep_slot]]
     new_len = np.bincount(seq[owner], minlength=len(length)).astype(np.int32)
@@ -146,7 +146,7 @@ def mutate(rng, arena, off, length, p_sub, p_ins, p_del, max_indel=1, alpha=4):
 
 def _random_arena(rng, lengths, alpha=4):
     ln = np.asarray(lengths, dtype=np.int32)
-    return rng.integers(0, alpha, int(ln.sum(dtype=np.int64))).astype(np.uint8), _offsets(ln), ln
+    return rng.integers(0, alpha, int(ln.sum(dtype=np.int64)), dtype=np.uint8), _offsets(ln), ln
 
 
 def _implant_vec(rng, bg, bg_off, bg_len, ins, ins_off, ins_len, rows):
