@@ -189,6 +189,42 @@ typedef struct gsw_stats {
 } gsw_stats;
 int gsw_last_stats(const gsw_ctx *ctx, gsw_stats *out);
 
+/*
+ * Allocation-free forward fill.  The paper has no counterpart: this entry
+ * exists for callers that cannot allocate device memory -- code running where
+ * cudaMalloc is forbidden or unsafe (inside a host callback or a memory-pool
+ * / arena owned by someone else, a hard real-time loop that must not block on
+ * the allocator, or a process whose device memory was reserved up front by a
+ * framework).  It needs no context and allocates nothing: the caller passes
+ * inputs and outputs, and the scratch of the pairs in flight (their column
+ * maxima and strip boundaries) lives in one file-scope device array of the
+ * library, GSW_STATIC_SCRATCH_BYTES (about 24 MiB) per GPU that loads the
+ * library, held until the process exits.
+ *
+ * It computes what gsw_align_batch computes without GSW_BEGIN / GSW_CIGAR:
+ * score1, ref_end1, read_end1, score2, ref_end2 (begins -1, no CIGAR), and
+ * with GSW_COLMAX the per-column max array.  Arguments are as for
+ * gsw_align_batch, device pointers only (no GSW_HOST_IO); flags may be 0 or
+ * GSW_COLMAX.  max_target_len must be at least the longest t_len of the batch
+ * and at most GSW_STATIC_MAX_TARGET (1024); larger values are rejected with
+ * GSW_EINVAL before any work, and a pair whose target is nevertheless longer
+ * is not aligned (its record has score1 = 0) and the call returns GSW_EINVAL.
+ *
+ * The first call on a device looks up the device address of the array (and
+ * sets the kernel's shared-memory limit); make that first call before any
+ * stream capture.  Every call shares the one array and the call waits for its
+ * stream before returning, so calls that overlap on the GPU (from several
+ * host threads or streams at once) race and must be serialized by the caller.
+ */
+#define GSW_STATIC_MAX_TARGET 1024
+#define GSW_STATIC_SCRATCH_BYTES (1216u * 1024u * 20u + 256u)
+int gsw_fill_static(int32_t npairs, const uint8_t *q, const int64_t *q_off, const int32_t *q_len,
+                    const uint8_t *t, const int64_t *t_off, const int32_t *t_len,
+                    int32_t max_target_len, const int8_t *matrix, int32_t alphabet,
+                    int32_t gap_open, int32_t gap_extend, uint32_t flags, int32_t mask_len,
+                    gsw_result *results, int32_t *colmax, const int64_t *colmax_off,
+                    void *stream);
+
 /* Name of an error code (static string). */
 const char *gsw_strerror(int code);
 

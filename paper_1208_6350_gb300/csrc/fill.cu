@@ -42,6 +42,8 @@
 
 #include <climits>
 #include <type_traits>
+#include <cstring>
+#include <mutex>
 
 namespace gsw {
 namespace {
@@ -589,4 +591,192 @@ cudaError_t launch_fill(const FillLaunch &fl, int sms, int max_blocks, cudaStrea
     return fl.sc.dna4 ? launch_all<true>(fl, sms, max_blocks, st) : launch_all<false>(fl, sms, max_blocks, st);
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free forward fill (gsw_fill_static).  Its per-slot scratch (the
+// column maxima and strip boundaries of a pair in flight) lives in a
+// file-scope device array instead of context memory.
+namespace {
+
+constexpr int kStaticMaxTarget = GSW_STATIC_MAX_TARGET;
+constexpr size_t kStaticSlotBytes = (size_t)kStaticMaxTarget * sizeof(int32_t) + 2 * (size_t)kStaticMaxTarget * sizeof(int2);
+constexpr int kStaticWarps = 152 * 4;                 // warps of one launch
+constexpr int kStaticSlots = kStaticWarps * 2;        // two pairs in flight per warp
+constexpr size_t kStaticErrOff = kStaticSlotBytes * kStaticSlots;
+constexpr size_t kStaticBytes = kStaticErrOff + 256;  // + the per-call error word
+static_assert(kStaticBytes == GSW_STATIC_SCRATCH_BYTES, "header states the scratch size");
+
+static __device__ __align__(256) uint8_t g_static_scratch[kStaticBytes];
+
+template <int R, class L, bool DNA>
+__device__ bool static_fill_pair(const BatchView &b, const Scoring &sc, int pair, uint32_t *wsm, int lane, int k,
+                                 unsigned gmask, int gbase, uint8_t *slot) {
+    gsw_result *rp = b.res + pair;
+    Job job;
+    job.q = b.q + b.q_off[pair];
+    job.qs = 1;
+    job.mrows = b.q_len[pair];
+    job.t = b.t + b.t_off[pair];
+    job.ts = 1;
+    job.ncols = b.t_len[pair];
+    job.stop_u = 0;
+    job.cms = slot;
+    job.bnd = slot + (size_t)kStaticMaxTarget * sizeof(int32_t);
+    const RingResult rr = ring_fill<16, R, L, DNA>(job, sc, wsm, k, gmask, gbase, lane);
+    if (L::FOLD && rr.score > 32767 - sc.wmax) return false;  // refill in 32-bit lanes
+    int s2 = 0, e2 = -1;
+    const int end_t = rr.col, end_q = rr.score > 0 ? rr.row - rr.pad_top : -1;
+    __syncwarp(gmask);
+    secondary<16, L>(b, pair, job, end_t, job.mrows, k, gmask, &s2, &e2);
+    if (k == 0) {
+        rp->score1 = rr.score;
+        rp->score2 = s2;
+        rp->ref_end1 = end_t;
+        rp->read_end1 = end_q;
+        rp->ref_begin1 = -1;
+        rp->read_begin1 = -1;
+        rp->ref_end2 = e2;
+        rp->cigar_len = 0;
+        rp->cigar_off = -1;
+        rp->flags = L::FOLD ? 0 : GSW_RES_S32;
+        rp->reserved = 0;
+    }
+    return true;
+}
+
+// Warps take two pairs at a time (one per 16-lane group), grid-stride.  Both
+// groups of a warp use the same row-word count R, because their profiles
+// share the warp's interleaved shared-memory region; a group whose 16-bit
+// fill overflowed refills afterwards in 32-bit lanes.
+template <bool DNA>
+__global__ void __launch_bounds__(kBlock) k_fill_static(BatchView b, Scoring sc, uint8_t *scratch, int warp_words) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 4, k = lane & 15, gbase = g * 16;
+    const unsigned gmask = 0xFFFFu << gbase;
+    const int gwarp = blockIdx.x * (blockDim.x / 32) + warp;
+    const int nwarps = gridDim.x * (blockDim.x / 32);
+    uint32_t *wsm = smem + (size_t)warp * warp_words;
+    uint8_t *slot = scratch + (size_t)(gwarp * 2 + g) * kStaticSlotBytes;
+    int32_t *err = reinterpret_cast<int32_t *>(scratch + kStaticErrOff);
+    for (int base = gwarp * 2; base < b.npairs; base += nwarps * 2) {
+        const int pair = base + g;
+        const bool has = pair < b.npairs;
+        const int m = has ? b.q_len[pair] : 0, n = has ? b.t_len[pair] : 0;
+        const bool too_long = has && n > kStaticMaxTarget;
+        const bool empty = has && !too_long && (m <= 0 || n <= 0);
+        const bool run = has && !too_long && !empty;
+        if (has && k == 0 && (too_long || empty)) {
+            gsw_result *rp = b.res + pair;
+            rp->score1 = 0; rp->score2 = 0; rp->ref_begin1 = -1; rp->ref_end1 = -1; rp->read_begin1 = -1;
+            rp->read_end1 = -1; rp->ref_end2 = -1; rp->cigar_len = 0; rp->cigar_off = -1;
+            rp->flags = too_long ? kResInternal : 0;
+            rp->reserved = 0;
+            if (too_long) atomicOr(err, 1);
+        }
+        if (empty && (b.flags & GSW_COLMAX))
+            for (int j = k; j < n; j += 16) b.colmax[b.colmax_off[pair] + j] = 0;
+        const int rows = __reduce_max_sync(0xFFFFFFFFu, run ? m : 0);
+        bool ok = true;
+        if (run) {
+            if (rows <= 64) ok = static_fill_pair<2, L16, DNA>(b, sc, pair, wsm, lane, k, gmask, gbase, slot);
+            else if (rows <= 128) ok = static_fill_pair<4, L16, DNA>(b, sc, pair, wsm, lane, k, gmask, gbase, slot);
+            else if (rows <= 192) ok = static_fill_pair<6, L16, DNA>(b, sc, pair, wsm, lane, k, gmask, gbase, slot);
+            else ok = static_fill_pair<8, L16, DNA>(b, sc, pair, wsm, lane, k, gmask, gbase, slot);
+        }
+        __syncwarp();
+        if (!ok) static_fill_pair<8, L32, DNA>(b, sc, pair, wsm, lane, k, gmask, gbase, slot);
+        __syncwarp();
+    }
+}
+
+struct StaticSetup {
+    bool done = false;
+    uint8_t *ptr = nullptr;
+};
+StaticSetup g_static_setup[64];
+std::mutex g_static_mu;
+
+}  // namespace
+
+}  // namespace gsw
+
+extern "C" int gsw_fill_static(int32_t npairs, const uint8_t *q, const int64_t *q_off, const int32_t *q_len,
+                               const uint8_t *t, const int64_t *t_off, const int32_t *t_len,
+                               int32_t max_target_len, const int8_t *matrix, int32_t alphabet, int32_t gap_open,
+                               int32_t gap_extend, uint32_t flags, int32_t mask_len, gsw_result *results,
+                               int32_t *colmax, const int64_t *colmax_off, void *stream) {
+    using namespace gsw;
+    if (npairs < 0 || (flags & ~(uint32_t)GSW_COLMAX)) return GSW_EINVAL;
+    if (max_target_len < 0 || max_target_len > kStaticMaxTarget) return GSW_EINVAL;
+    if (!matrix || alphabet < 1 || alphabet > kMaxAlpha || gap_extend < 0 || gap_open < gap_extend || gap_open > 255)
+        return GSW_EINVAL;
+    if (npairs == 0) return GSW_OK;
+    if (!q || !q_off || !q_len || !t || !t_off || !t_len || !results) return GSW_EINVAL;
+    if ((flags & GSW_COLMAX) && (!colmax || !colmax_off)) return GSW_EINVAL;
+    Scoring sc;
+    memset(&sc, 0, sizeof(sc));
+    sc.A = alphabet;
+    sc.O = gap_open;
+    sc.X = gap_extend;
+    int wmax = -128, wmin = 127;
+    for (int i = 0; i < alphabet * alphabet; i++) {
+        if (matrix[i] < -127) return GSW_EINVAL;
+        sc.W[i] = matrix[i];
+        wmax = matrix[i] > wmax ? matrix[i] : wmax;
+        wmin = matrix[i] < wmin ? matrix[i] : wmin;
+    }
+    sc.wmax = wmax;
+    sc.wmin = wmin;
+    sc.dna4 = alphabet == 4;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GSW_ECUDA;
+    const size_t per_warp = (size_t)prof_words(8, true, sc.dna4 != 0, alphabet) * 32 * sizeof(uint32_t);
+    int wpb = (int)((200u << 10) / per_warp);
+    wpb = wpb > 4 ? 4 : (wpb < 1 ? 1 : wpb);
+    const size_t smem = per_warp * wpb;
+    uint8_t *scratch;
+    {
+        // once per device, with that device current: the device address of
+        // the static scratch (the host-side symbol is only a stand-in)
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        StaticSetup &su = g_static_setup[dev];
+        if (!su.done) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess) return GSW_ECUDA;
+            if (cudaFuncSetAttribute(k_fill_static<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10) !=
+                    cudaSuccess ||
+                cudaFuncSetAttribute(k_fill_static<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10) !=
+                    cudaSuccess)
+                return GSW_ECUDA;
+            su.ptr = static_cast<uint8_t *>(ptr);
+            su.done = true;
+        }
+        scratch = su.ptr;
+    }
+    BatchView bv;
+    memset(&bv, 0, sizeof(bv));
+    bv.q = q; bv.q_off = q_off; bv.q_len = q_len;
+    bv.t = t; bv.t_off = t_off; bv.t_len = t_len;
+    bv.res = results;
+    bv.npairs = npairs;
+    bv.flags = flags;
+    bv.mask_len = mask_len;
+    bv.colmax = colmax;
+    bv.colmax_off = colmax_off;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the error word must start at zero; the slots need no clearing
+    if (cudaMemsetAsync(scratch + kStaticErrOff, 0, sizeof(int32_t), st) != cudaSuccess) return GSW_ECUDA;
+    const int grid = kStaticWarps / wpb;
+    if (sc.dna4) k_fill_static<true><<<grid, wpb * 32, smem, st>>>(bv, sc, scratch, (int)(per_warp / 4));
+    else k_fill_static<false><<<grid, wpb * 32, smem, st>>>(bv, sc, scratch, (int)(per_warp / 4));
+    if (cudaGetLastError() != cudaSuccess) return GSW_ECUDA;
+    int32_t err = 0;
+    if (cudaMemcpyAsync(&err, scratch + kStaticErrOff, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return GSW_ECUDA;
+    return err ? GSW_EINVAL : GSW_OK;
+}
+
+namespace gsw {
 }  // namespace gsw

@@ -83,6 +83,8 @@ def load(build_if_missing: bool = True):
     for f in (lib.gsw_context_create, lib.gsw_context_destroy, lib.gsw_align_batch,
               lib.gsw_profile_create, lib.gsw_profile_destroy, lib.gsw_align_profile):
         f.restype = ctypes.c_int
+    lib.gsw_fill_static.argtypes = [i32, P, P, P, P, P, P, i32, P, i32, i32, i32, u32, i32, P, P, P, P]
+    lib.gsw_fill_static.restype = ctypes.c_int
     lib.gsw_last_stats.argtypes = [P, ctypes.POINTER(GswStats)]
     lib.gsw_last_stats.restype = ctypes.c_int
     lib.gsw_strerror.argtypes = [ctypes.c_int]
@@ -158,6 +160,20 @@ def gsw_last_stats(ctx) -> dict:
     if st.timed:
         out["stage_ms"] = {n: float(st.stage_ms[k]) for k, n in enumerate(STAGE_NAMES)}
     return out
+
+
+GSW_STATIC_MAX_TARGET = 1024
+
+
+def gsw_fill_static(npairs, q, q_off, q_len, t, t_off, t_len, max_target_len, matrix, gap_open,
+                    gap_extend, flags=0, mask_len=-1, results=None, colmax=None, colmax_off=None,
+                    stream=None) -> int:
+    """Allocation-free forward fill (device pointers only); returns the status code."""
+    m = np.ascontiguousarray(matrix, dtype=np.int8)
+    return load().gsw_fill_static(npairs, _ptr(q), _ptr(q_off), _ptr(q_len), _ptr(t), _ptr(t_off),
+                                  _ptr(t_len), max_target_len, m.ctypes.data, m.shape[0], gap_open,
+                                  gap_extend, flags, mask_len, _ptr(results), _ptr(colmax),
+                                  _ptr(colmax_off), _stream_handle(stream))
 
 
 def gsw_profile_create(ctx, query, matrix, gap_open, gap_extend) -> int:
