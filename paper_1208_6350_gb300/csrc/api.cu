@@ -97,10 +97,30 @@ int ensure(gsw_ctx *ctx, DevBuf &b, size_t need) {
 }
 
 void release(gsw_ctx *ctx, DevBuf &b) {
-    if (b.p) cudaFree(b.p);
+    if (b.p) {
+        cudaDeviceSynchronize();
+        cudaFree(b.p);
+    }
     ctx->used -= b.bytes;
     b.p = nullptr;
     b.bytes = 0;
+}
+
+// Bytes of budget left if buffers a and b were released.
+size_t room(const gsw_ctx *ctx, const DevBuf &a, const DevBuf &b) {
+    const size_t used = ctx->used - a.bytes - b.bytes;
+    return ctx->budget > used ? ctx->budget - used : 0;
+}
+
+// Grows two buffers that are sized together, releasing both first when
+// either must grow, so the budget never counts an old and a new copy.
+int ensure2(gsw_ctx *ctx, DevBuf &a, size_t na, DevBuf &b, size_t nb) {
+    if (na > a.bytes || nb > b.bytes) {
+        release(ctx, a);
+        release(ctx, b);
+    }
+    int rc = ensure(ctx, a, na);
+    return rc != GSW_OK ? rc : ensure(ctx, b, nb);
 }
 
 int make_scoring(const int8_t *matrix, int32_t A, int32_t O, int32_t X, Scoring *sc) {
@@ -164,7 +184,7 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
     int max_blocks = INT32_MAX;
     {
         // keep the scratch inside half of what the budget has left
-        size_t have = ctx->budget > ctx->used ? ctx->budget - ctx->used + ctx->fill_cm.bytes + ctx->fill_bnd.bytes : 0;
+        size_t have = room(ctx, ctx->fill_cm, ctx->fill_bnd);
         size_t cap_slots = have / 2 / per_slot;
         if (slots > cap_slots) {
             // every variant has at most 2 slots per warp
@@ -172,8 +192,7 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
             slots = (size_t)max_blocks * warps_per_block * 2;
         }
     }
-    GSW_TRY(ensure(ctx, ctx->fill_cm, slots * ncap * sizeof(int32_t)));
-    GSW_TRY(ensure(ctx, ctx->fill_bnd, slots * 2 * ncap * sizeof(int2)));
+    GSW_TRY(ensure2(ctx, ctx->fill_cm, slots * ncap * sizeof(int32_t), ctx->fill_bnd, slots * 2 * ncap * sizeof(int2)));
 
     FillLaunch fl;
     fl.b = bv;
@@ -229,13 +248,19 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
         int bgrid = ctx->sms * 8;
         const int bwarps_per_block = band_block_threads() / 32;
         {
-            size_t have = ctx->budget > ctx->used ? ctx->budget - ctx->used + ctx->band_scr.bytes : 0;
+            // a quarter of what is left: the band scratch holds every row of
+            // the pairs in flight
+            size_t have = room(ctx, ctx->band_scr, ctx->band_scr) + ctx->band_scr.bytes;
             size_t per_warp = (size_t)words * sizeof(uint32_t);
-            size_t max_warps = have / 2 / per_warp;
+            size_t max_warps = have / 4 / per_warp;
             if ((size_t)bgrid * bwarps_per_block > max_warps)
                 bgrid = (int)std::max<size_t>(1, max_warps / bwarps_per_block);
         }
-        GSW_TRY(ensure(ctx, ctx->band_scr, (size_t)bgrid * bwarps_per_block * words * sizeof(uint32_t)));
+        {
+            const size_t need = (size_t)bgrid * bwarps_per_block * words * sizeof(uint32_t);
+            if (need > ctx->band_scr.bytes) release(ctx, ctx->band_scr);
+            GSW_TRY(ensure(ctx, ctx->band_scr, need));
+        }
         CUDA_TRY(launch_band(bv, sc, pb, ctx->band_scr.p, words, bgrid, st));
         ctx->launches += 3;
         ctx->stage_done[4] = 1;
@@ -251,19 +276,19 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
         CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
         const long long need_dir = (long long)hs[0], need_ops = (long long)hs[1], need_nch = (long long)hs[2];
-        if (need_nch > 0) {
-            const int tgrid = ctx->sms * 2;
+        if (need_dir > 0) {
+            const int tgrid = ctx->sms * 16;  // latency-bound per step: many warps per SM
             const int twarps = tgrid * (trace_block_threads() / 32);
             const long long dir_words = std::max<long long>(need_dir, 64);
             const long long op_words = std::max<long long>(need_ops + 64 * need_nch, 64);
             size_t per_warp = (size_t)(dir_words + op_words) * sizeof(uint32_t);
             int use_warps = twarps;
-            size_t have = ctx->budget > ctx->used ? ctx->budget - ctx->used + ctx->trace_dirs.bytes + ctx->trace_ops.bytes : 0;
-            if ((size_t)use_warps * per_warp > have) use_warps = (int)std::max<size_t>(1, have / per_warp);
+            size_t have = room(ctx, ctx->trace_dirs, ctx->trace_ops) / 2;
+            if ((size_t)use_warps * per_warp > have) use_warps = (int)std::max<size_t>(4, have / per_warp);
             int use_grid = std::max(1, use_warps / (trace_block_threads() / 32));
             use_warps = use_grid * (trace_block_threads() / 32);
-            GSW_TRY(ensure(ctx, ctx->trace_dirs, (size_t)use_warps * dir_words * sizeof(uint32_t)));
-            GSW_TRY(ensure(ctx, ctx->trace_ops, (size_t)use_warps * op_words * sizeof(uint32_t)));
+            GSW_TRY(ensure2(ctx, ctx->trace_dirs, (size_t)use_warps * dir_words * sizeof(uint32_t), ctx->trace_ops,
+                            (size_t)use_warps * op_words * sizeof(uint32_t)));
             TraceScratch ts;
             ts.dirs = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
             ts.dir_words = dir_words;
@@ -271,8 +296,9 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
             ts.op_words = op_words;
             ts.order = pb.order;
             ts.var_start = pb.var_start;
+            CUDA_TRY(launch_trace_ad(bv, sc, ts, use_grid, st));
             CUDA_TRY(launch_traceback(bv, sc, ts, use_grid, st));
-            ctx->launches += 1;
+            ctx->launches += 5;
         }
         ctx->stage_done[5] = 1;
     }

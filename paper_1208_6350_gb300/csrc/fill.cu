@@ -68,6 +68,7 @@ struct L32 {
     static constexpr bool FOLD = false;
     using cm_t = int32_t;
     using bnd_t = int2;
+    static constexpr uint32_t Z = 0u;
     static constexpr uint32_t Z2 = 0u;
     static __device__ __forceinline__ uint32_t vmax(uint32_t a, uint32_t b) {
         return (uint32_t)max((int)a, (int)b);
@@ -225,42 +226,56 @@ __device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm
         uint32_t xh = Z2, xf = NEGE, xc = Z2;  // values received from lane k-1
         int nal = (-k >= 0 && -k < n) ? min((int)job.t[0], A - 1) : 0;
         int nah = 0;
+        // lane 0 receives, in its low half, the strip's top boundary (H = 0 and
+        // F = -O on the first strip) and in its high half lane P-1's low half
+        const int sh0 = (L::FOLD && k == 0) ? 16 : 0;
+        const uint32_t bzh = k == 0 ? L::lane1(0) : 0u, bzf = k == 0 ? L::lane1(-sc.O) : 0u;
+        const uint32_t bzc = k == 0 ? (L::FOLD ? L::Z : 0u) : 0u;
+        const bool has_cms = job.cms != nullptr;
+        const bool single = nstrips == 1;
 
-#pragma unroll 1
-        for (int s = 0; s < nsteps; s++) {
+        // One step of lane k: low half at column s - k, high half P columns
+        // behind.  CHECKED steps handle columns outside [0, n) (start-up and
+        // drain of the wavefront); steady steps have every column in range.
+        auto step = [&](const int s, auto checked_tag) -> bool {
+            constexpr bool CHECKED = decltype(checked_tag)::value;
             const int jlo = s - k;
             const int jhi = L::FOLD ? jlo - P : jlo;
-            // inputs from the row above
-            uint32_t hin = xh, fin = xf, cmin = xc;
-            if (k == 0) {
-                uint32_t bh = L::lane1(0), bf = L::lane1(-sc.O);
-                if (st > 0 && jlo >= 0 && jlo < n) {
-                    if constexpr (L::FOLD) {
-                        uint32_t w = bin[jlo];
-                        bh = w & 0xFFFFu;
-                        bf = w >> 16;
-                    } else {
-                        int2 w = bin[jlo];
-                        bh = (uint32_t)w.x;
-                        bf = (uint32_t)w.y;
-                    }
-                }
+            uint32_t hin, fin, cmin;
+            if constexpr (L::FOLD) {
+                hin = (xh << sh0) | bzh;
+                fin = (xf << sh0) | bzf;
+                cmin = (xc << sh0) | bzc;
+            } else {
+                hin = k == 0 ? bzh : xh;
+                fin = k == 0 ? bzf : xf;
+                cmin = k == 0 ? bzc : xc;
+            }
+            if (st > 0 && k == 0 && (!CHECKED || (jlo >= 0 && jlo < n))) {
                 if constexpr (L::FOLD) {
-                    hin = (xh << 16) | bh;
-                    fin = (xf << 16) | bf;
-                    cmin = (xc << 16) | L::Z;
+                    const uint32_t w = bin[jlo];
+                    hin = (hin & 0xFFFF0000u) | (w & 0xFFFFu);
+                    fin = (fin & 0xFFFF0000u) | (w >> 16);
                 } else {
-                    hin = bh;
-                    fin = bf;
-                    cmin = Z2;
+                    const int2 w = bin[jlo];
+                    hin = (uint32_t)w.x;
+                    fin = (uint32_t)w.y;
                 }
             }
             // letters of this lane's columns (loaded one step ahead)
             const int al = nal, ah = nah;
             {
-                const int j1 = jlo + 1, j2 = jhi + 1;
-                nal = (j1 >= 0 && j1 < n) ? min((int)job.t[(long long)j1 * job.ts], A - 1) : 0;
-                if constexpr (L::FOLD) nah = (j2 >= 0 && j2 < n) ? min((int)job.t[(long long)j2 * job.ts], A - 1) : 0;
+                const int j1 = jlo + 1;
+                if constexpr (CHECKED) {
+                    nal = (j1 >= 0 && j1 < n) ? min((int)job.t[(long long)j1 * job.ts], A - 1) : 0;
+                    if constexpr (L::FOLD) {
+                        const int j2 = j1 - P;
+                        nah = (j2 >= 0 && j2 < n) ? min((int)job.t[(long long)j2 * job.ts], A - 1) : 0;
+                    }
+                } else {
+                    nal = min((int)job.t[(long long)j1 * job.ts], A - 1);
+                    if constexpr (L::FOLD) nah = min((int)job.t[(long long)(j1 - P) * job.ts], A - 1);
+                }
             }
             uint32_t pw[R];
             if constexpr (DNA) {
@@ -289,22 +304,25 @@ __device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm
                 m = L::vmax(m, h);
                 E[r] = L::vmax(E[r] + kX, h + kO);
             }
-            // before a half's first column its state must be the left boundary
-            if (jhi < 0) {
-                const uint32_t keep = (L::FOLD && jlo >= 0) ? 0x0000FFFFu : 0u;
+            uint32_t cme = m;
+            if constexpr (CHECKED) {
+                // before a half's first column its state must be the left boundary
+                if (jhi < 0) {
+                    const uint32_t keep = (L::FOLD && jlo >= 0) ? 0x0000FFFFu : 0u;
 #pragma unroll
-                for (int r = 0; r < R; r++) {
-                    H[r] = (H[r] & keep) | (Z2 & ~keep);
-                    E[r] = (E[r] & keep) | (NEGE & ~keep);
+                    for (int r = 0; r < R; r++) {
+                        H[r] = (H[r] & keep) | (Z2 & ~keep);
+                        E[r] = (E[r] & keep) | (NEGE & ~keep);
+                    }
+                    hdiag = (hdiag & keep) | (Z2 & ~keep);
                 }
-                hdiag = (hdiag & keep) | (Z2 & ~keep);
-            }
-            // tracker: first column where the running column max strictly improved
-            {
                 uint32_t vm = 0;
                 if (jlo >= 0 && jlo < n) vm |= L::FOLD ? 0x0000FFFFu : 0xFFFFFFFFu;
                 if (L::FOLD && jhi >= 0 && jhi < n) vm |= 0xFFFF0000u;
-                const uint32_t cme = (m & vm) | (Z2 & ~vm);
+                cme = (m & vm) | (Z2 & ~vm);
+            }
+            // tracker: first column where the running column max strictly improved
+            {
                 const uint32_t nb = L::vmax(cme, best);
                 if (nb != best) {
                     const uint32_t diff = nb ^ best;
@@ -324,29 +342,42 @@ __device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm
             }
             // the last lane holds complete columns: column max and strip boundary
             bool found = false;
-            if (k == P - 1 && jhi >= 0 && jhi < n) {
+            if (k == P - 1 && (!CHECKED || (jhi >= 0 && jhi < n))) {
                 if constexpr (L::FOLD) {
                     const uint32_t full = m >> 16;
-                    if (job.cms) {
+                    if (has_cms) {
                         if (st == 0) cms[jhi] = (uint16_t)full;
                         else cms[jhi] = (uint16_t)max((uint32_t)cms[jhi], full);
                     }
                     if (!last_strip) bout[jhi] = (H[R - 1] >> 16) | (f & 0xFFFF0000u);
-                    found = job.stop_u && full == job.stop_u;
+                    found = full == job.stop_u;
                 } else {
-                    if (job.cms) {
+                    if (has_cms) {
                         if (st == 0) cms[jhi] = (int)m;
                         else cms[jhi] = max(cms[jhi], (int)m);
                     }
                     if (!last_strip) bout[jhi] = make_int2((int)H[R - 1], (int)f);
-                    found = job.stop_u && m == job.stop_u;
+                    found = m == job.stop_u;
                 }
             }
-            if (job.stop_u && nstrips == 1 && __any_sync(gmask, found)) break;
+            if (job.stop_u && single && __any_sync(gmask, found)) return true;
             xh = __shfl_sync(gmask, H[R - 1], src);
             xf = __shfl_sync(gmask, f, src);
             xc = __shfl_sync(gmask, m, src);
-        }
+            return false;
+        };
+
+        // start-up (checked), steady (unchecked), drain (checked)
+        const int s_steady = L::FOLD ? 2 * P - 1 : P - 1;
+        const int s_drain = max(s_steady, n - 1);
+        bool stop = false;
+        int s = 0;
+#pragma unroll 1
+        for (; s < s_steady && s < nsteps && !stop; s++) stop = step(s, std::true_type{});
+#pragma unroll 1
+        for (; s < s_drain && !stop; s++) stop = step(s, std::false_type{});
+#pragma unroll 1
+        for (; s < nsteps && !stop; s++) stop = step(s, std::true_type{});
 
         // ---- strip epilogue: the strip's maximum, its first column, its first row
         const uint32_t bl = __shfl_sync(gmask, best, gbase + P - 1);

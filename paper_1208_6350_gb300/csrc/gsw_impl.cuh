@@ -223,6 +223,8 @@ cudaError_t launch_trace_need(const BatchView &b, const Scoring &sc, unsigned lo
                               cudaStream_t st);
 cudaError_t launch_traceback(const BatchView &b, const Scoring &sc, const TraceScratch &ts, int grid,
                              cudaStream_t st);
+cudaError_t launch_trace_ad(const BatchView &b, const Scoring &sc, const TraceScratch &ts, int grid,
+                            cudaStream_t st);
 
 int band_block_threads();
 cudaError_t launch_band(const BatchView &b, const Scoring &sc, const PlanBuffers &pb, void *scratch,

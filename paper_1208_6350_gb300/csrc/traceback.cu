@@ -44,16 +44,21 @@ struct Need {
 __device__ Need pair_need(const gsw_result &r, const Scoring &sc) {
     Need nd{0, 0, 0, 0, 0};
     const int la = r.read_end1 - r.read_begin1 + 1, lb = r.ref_end1 - r.ref_begin1 + 1;
-    const int w = band_halfwidth(la, lb, r.score1, sc);
-    const int delta = lb - la;
-    int dlo = min(0, delta) - w, dhi = max(0, delta) + w;
-    dlo = max(dlo, -la);
-    dhi = min(dhi, lb);
+    int dlo, dhi;
+    const int width = band_range(la, lb, r.score1, sc, &dlo, &dhi);
     nd.dlo = dlo;
     nd.dhi = dhi;
     nd.nch = (dhi - dlo + 32) / 32;
-    nd.dir = (long long)(la + 1) * nd.nch * 4;
-    nd.ops = (long long)la + lb + 2;
+    if (width <= 512) {
+        // anti-diagonal kernel: (la + lb + 1) steps x chunks of 64 x 4 planes
+        const int nch_cls = width <= 64 ? 1 : width <= 128 ? 2 : width <= 256 ? 4 : 8;
+        nd.dir = (long long)(la + lb + 1) * nch_cls * 4;
+        nd.ops = (long long)la + lb + 2;
+        nd.nch = 0;
+    } else {
+        nd.dir = (long long)(la + 1) * nd.nch * 4;
+        nd.ops = (long long)la + lb + 2;
+    }
     return nd;
 }
 
@@ -78,7 +83,7 @@ __global__ void k_trace_need(BatchView b, Scoring sc, unsigned long long *max_ne
     d = __reduce_max_sync(0xFFFFFFFFu, d);
     o = __reduce_max_sync(0xFFFFFFFFu, o);
     c = __reduce_max_sync(0xFFFFFFFFu, c);
-    if ((threadIdx.x & 31) == 0 && c > 0) {
+    if ((threadIdx.x & 31) == 0 && d > 0) {
         atomicMax(&max_need[0], (unsigned long long)d);
         atomicMax(&max_need[1], (unsigned long long)o);
         atomicMax(&max_need[2], (unsigned long long)c);
@@ -242,7 +247,7 @@ __global__ void __launch_bounds__(kTBlock) k_traceback(BatchView b, Scoring sc, 
     uint32_t *gdir = ts.dirs + (size_t)gwarp * ts.dir_words;
     uint32_t *gops = ts.ops + (size_t)gwarp * ts.op_words;  // ops, then the chunk state
     // the planned list (sorted by cost, descending) is dealt round-robin
-    const int first = ts.var_start[0], last = ts.var_start[1];
+    const int first = ts.var_start[4], last = ts.var_start[5];
     const int nwarps = gridDim.x * (kTBlock / 32);
     for (int idx = first + gwarp; idx < last; idx += nwarps) {
         const int p = ts.order[idx];
@@ -263,6 +268,217 @@ __global__ void __launch_bounds__(kTBlock) k_traceback(BatchView b, Scoring sc, 
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Anti-diagonal warp traceback for bands of up to 64*NCH diagonals.
+//
+// Lane l of chunk c owns diagonals d0 = dlo + 64c + 2l and d0 + 1.  On
+// anti-diagonal a = i + j exactly one of them holds a cell, and which one
+// ((a - dlo) even: d0) is the same for every lane, so all 32 lanes work every
+// step.  The left neighbour (i, j-1) and the upper one (i-1, j) lie on the
+// previous anti-diagonal, one diagonal away: either the lane's own other
+// diagonal or a neighbour lane's (one shuffle), and the diagonal neighbour is
+// the lane's own value from two steps back.  Decision bits: 4 ballots per
+// chunk and step.
+template <int NCH>
+__device__ void trace_ad_pair(const BatchView &b, const Scoring &sc, const int8_t *sW, int p, const gsw_result &r,
+                              int dlo, int dhi, uint32_t *dirs, uint32_t *ops, uint4 *stage, int lane) {
+    const int la = r.read_end1 - r.read_begin1 + 1, lb = r.ref_end1 - r.ref_begin1 + 1;
+    const uint8_t *qs = b.q + b.q_off[p] + r.read_begin1;
+    const uint8_t *ts = b.t + b.t_off[p] + r.ref_begin1;
+    const int O = sc.O, X = sc.X, A = sc.A;
+    int H1[NCH], E1[NCH], F1[NCH], H2[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; c++) { H1[c] = kNegT; E1[c] = kNegT; F1[c] = kNegT; H2[c] = kNegT; }
+    int final_h = kNegT;
+    const int steps = la + lb;
+    for (int a = 0; a <= steps; a++) {
+        const int par = (a - dlo) & 1;
+        // neighbour values from the previous anti-diagonal (before any update)
+        int nh[NCH], nx[NCH];  // par 0: left (H, E); par 1: up (H, F)
+#pragma unroll
+        for (int c = 0; c < NCH; c++) {
+            if (par == 0) {
+                int h = __shfl_up_sync(0xFFFFFFFFu, H1[c], 1), e = __shfl_up_sync(0xFFFFFFFFu, E1[c], 1);
+                const int ph = c > 0 ? __shfl_sync(0xFFFFFFFFu, H1[c > 0 ? c - 1 : 0], 31) : kNegT;
+                const int pe = c > 0 ? __shfl_sync(0xFFFFFFFFu, E1[c > 0 ? c - 1 : 0], 31) : kNegT;
+                nh[c] = lane == 0 ? ph : h;
+                nx[c] = lane == 0 ? pe : e;
+            } else {
+                int h = __shfl_down_sync(0xFFFFFFFFu, H1[c], 1), f = __shfl_down_sync(0xFFFFFFFFu, F1[c], 1);
+                const int uh = c + 1 < NCH ? __shfl_sync(0xFFFFFFFFu, H1[c + 1 < NCH ? c + 1 : c], 0) : kNegT;
+                const int uf = c + 1 < NCH ? __shfl_sync(0xFFFFFFFFu, F1[c + 1 < NCH ? c + 1 : c], 0) : kNegT;
+                nh[c] = lane == 31 ? uh : h;
+                nx[c] = lane == 31 ? uf : f;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NCH; c++) {
+            const int d = dlo + 64 * c + 2 * lane + par;
+            const int i = (a - d) >> 1, j = (a + d) >> 1;
+            const bool valid = d <= dhi && i >= 0 && i <= la && j >= 0 && j <= lb;
+            int hl, el, hu, fu;
+            if (par == 0) { hl = nh[c]; el = nx[c]; hu = H1[c]; fu = F1[c]; }
+            else { hl = H1[c]; el = E1[c]; hu = nh[c]; fu = nx[c]; }
+            int E = kNegT, F = kNegT, hdg = kNegT, H;
+            bool eopen = false, fopen = false;
+            if (j >= 1) {
+                const int eo = hl - O;
+                E = max(eo, el - X);
+                eopen = E == eo;
+            }
+            if (i >= 1) {
+                const int fo = hu - O;
+                F = max(fo, fu - X);
+                fopen = F == fo;
+            }
+            if (valid && i >= 1 && j >= 1) {
+                const int qa = min((int)qs[i - 1], A - 1), tb = min((int)ts[j - 1], A - 1);
+                hdg = H2[c] + sW[qa * A + tb];
+            }
+            H = max(hdg, max(E, F));
+            if (i == 0 && j == 0) H = 0;
+            if (!valid || H < kNegHalf) { H = kNegT; E = kNegT; F = kNegT; }
+            const int src = (valid && i >= 1 && j >= 1 && hdg > kNegHalf && H == hdg) ? 0 : (H == E ? 1 : 2);
+            const unsigned b0 = __ballot_sync(0xFFFFFFFFu, src & 1);
+            const unsigned b1 = __ballot_sync(0xFFFFFFFFu, src & 2);
+            const unsigned b2 = __ballot_sync(0xFFFFFFFFu, eopen);
+            const unsigned b3 = __ballot_sync(0xFFFFFFFFu, fopen);
+            if (lane < 4) dirs[((long long)a * NCH + c) * 4 + lane] = lane == 0 ? b0 : lane == 1 ? b1 : lane == 2 ? b2 : b3;
+            if (valid && i == la && j == lb) final_h = H;
+            H2[c] = H1[c];
+            H1[c] = H;
+            E1[c] = E;
+            F1[c] = F;
+        }
+    }
+    final_h = __reduce_max_sync(0xFFFFFFFFu, final_h);
+    __syncwarp();
+    gsw_result *rp = b.res + p;
+    // Walk back from (la, lb).  The anti-diagonal index i + j never increases
+    // along the walk, so the warp stages the decision planes into shared
+    // memory 32 anti-diagonals at a time (coalesced) and lane 0 walks inside
+    // the staged block; the runs go to `ops` in reverse order.
+    constexpr int KB = 32;
+    const uint4 *dirs4 = reinterpret_cast<const uint4 *>(dirs);
+    int i = la, j = lb, state = 0, cur = -1, len = 0, runs = 0;
+    bool ok = final_h == r.score1;
+    int a_hi = la + lb;
+    while (ok && (i > 0 || j > 0) && a_hi >= 0) {
+        const int a_lo = max(0, a_hi - KB + 1);
+        const int nwords = (a_hi - a_lo + 1) * NCH;
+        for (int w = lane; w < nwords; w += 32) stage[w] = dirs4[(long long)a_lo * NCH + w];
+        __syncwarp();
+        if (lane == 0) {
+            while ((i > 0 || j > 0) && i + j >= a_lo) {
+                const int off2 = j - i - dlo;
+                if (i < 0 || j < 0 || off2 < 0 || off2 >= 64 * NCH) { ok = false; break; }
+                const uint4 pl = stage[(i + j - a_lo) * NCH + (off2 >> 6)];
+                const int l = (off2 & 63) >> 1;
+                const int src = ((pl.x >> l) & 1) | (((pl.y >> l) & 1) << 1);
+                const int eo = (pl.z >> l) & 1, fo = (pl.w >> l) & 1;
+                int op;
+                if (state == 0) {
+                    if (src == 0) { op = GSW_CIGAR_M; i--; j--; }
+                    else { state = src; continue; }
+                } else if (state == 1) {
+                    op = GSW_CIGAR_D; state = eo ? 0 : 1; j--;
+                } else {
+                    op = GSW_CIGAR_I; state = fo ? 0 : 2; i--;
+                }
+                if (op == cur) {
+                    len++;
+                } else {
+                    if (len) ops[runs++] = ((uint32_t)len << 4) | (uint32_t)cur;
+                    cur = op;
+                    len = 1;
+                }
+            }
+        }
+        ok = __shfl_sync(0xFFFFFFFFu, (int)ok, 0);
+        i = __shfl_sync(0xFFFFFFFFu, i, 0);
+        j = __shfl_sync(0xFFFFFFFFu, j, 0);
+        __syncwarp();
+        a_hi = a_lo - 1;
+    }
+    if (lane == 0 && ok && (i != 0 || j != 0)) ok = false;
+    if (lane == 0 && ok && len) ops[runs++] = ((uint32_t)len << 4) | (uint32_t)cur;
+    ok = __shfl_sync(0xFFFFFFFFu, (int)ok, 0);
+    const int nr = __shfl_sync(0xFFFFFFFFu, runs, 0);
+    if (!ok) {
+        if (lane == 0) rp->flags |= kResInternal;
+        __syncwarp();
+        return;
+    }
+    unsigned long long off = 0;
+    if (lane == 0) off = atomicAdd(b.cigar_cursor, (unsigned long long)nr);
+    off = __shfl_sync(0xFFFFFFFFu, off, 0);
+    if ((long long)(off + nr) > b.cigar_cap) {
+        if (lane == 0) {
+            rp->flags |= GSW_RES_CIGAR_SPACE;
+            rp->cigar_len = -nr;
+            rp->cigar_off = -1;
+            rp->flags &= ~kResPendingTrace;
+        }
+        __syncwarp();
+        return;
+    }
+    __syncwarp();
+    for (int t = lane; t < nr; t += 32) b.cigar[off + t] = ops[nr - 1 - t];
+    if (lane == 0) {
+        rp->cigar_len = nr;
+        rp->cigar_off = (int64_t)off;
+        rp->flags &= ~kResPendingTrace;
+    }
+    __syncwarp();
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(kTBlock) k_trace_ad(BatchView b, Scoring sc, TraceScratch ts, int cls) {
+    __shared__ int8_t sW[kMaxAlpha * kMaxAlpha];
+    __shared__ uint4 stage_all[kTBlock / 32][32 * NCH];
+    for (int i = threadIdx.x; i < sc.A * sc.A; i += blockDim.x) sW[i] = sc.W[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gwarp = blockIdx.x * (kTBlock / 32) + warp;
+    const int nwarps = gridDim.x * (kTBlock / 32);
+    uint32_t *dirs = ts.dirs + (size_t)gwarp * ts.dir_words;
+    uint32_t *ops = ts.ops + (size_t)gwarp * ts.op_words;
+    const int first = ts.var_start[cls], last = ts.var_start[cls + 1];
+    for (int idx = first + gwarp; idx < last; idx += nwarps) {
+        const int p = ts.order[idx];
+        const gsw_result r = b.res[p];
+        if (!wants_trace(r)) continue;
+        const int la = r.read_end1 - r.read_begin1 + 1, lb = r.ref_end1 - r.ref_begin1 + 1;
+        int dlo, dhi;
+        band_range(la, lb, r.score1, sc, &dlo, &dhi);
+        if ((long long)(la + lb + 1) * NCH * 4 > ts.dir_words || dhi - dlo + 1 > 64 * NCH ||
+            (long long)(la + lb + 2) > ts.op_words) {
+            if (lane == 0) b.res[p].flags |= kResInternal;
+            continue;
+        }
+        trace_ad_pair<NCH>(b, sc, sW, p, r, dlo, dhi, dirs, ops, stage_all[warp], lane);
+    }
+}
+
+}  // namespace
+
+// classes of the warp traceback: 0..3 = anti-diagonal kernel with 1/2/4/8
+// chunks of 64 diagonals, 4 = the row kernel (wider bands)
+int trace_class(int width) {
+    return width <= 64 ? 0 : width <= 128 ? 1 : width <= 256 ? 2 : width <= 512 ? 3 : 4;
+}
+
+cudaError_t launch_trace_ad(const BatchView &b, const Scoring &sc, const TraceScratch &ts, int grid,
+                            cudaStream_t st) {
+    k_trace_ad<1><<<grid, kTBlock, 0, st>>>(b, sc, ts, 0);
+    k_trace_ad<2><<<grid, kTBlock, 0, st>>>(b, sc, ts, 1);
+    k_trace_ad<4><<<grid, kTBlock, 0, st>>>(b, sc, ts, 2);
+    k_trace_ad<8><<<grid, kTBlock, 0, st>>>(b, sc, ts, 3);
+    return cudaGetLastError();
+}
+
+namespace {
 }  // namespace
 
 int trace_block_threads() { return kTBlock; }
