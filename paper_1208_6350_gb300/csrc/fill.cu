@@ -41,6 +41,13 @@
 #include "gsw_impl.cuh"
 
 #include <climits>
+
+#ifndef GSW_FILL_DPX
+#define GSW_FILL_DPX 1
+#endif
+#ifndef GSW_FILL_SPLIT
+#define GSW_FILL_SPLIT 1
+#endif
 #include <type_traits>
 #include <cstring>
 #include <mutex>
@@ -62,6 +69,19 @@ struct L16 {
     static __device__ __forceinline__ uint32_t both(int v) { return lane1(v) | (lane1(v) << 16); }
     // integer that adds c to both lanes of a word
     static __device__ __forceinline__ uint32_t addk(int c) { return (uint32_t)(c * 65537); }
+#if GSW_FILL_DPX
+    // per-lane max(a + b, c) in one DPX instruction; b holds two 16-bit
+    // two's-complement halves (no borrow between them)
+    static __device__ __forceinline__ uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) {
+        return __viaddmax_u16x2(a, b, c);
+    }
+    static __device__ __forceinline__ uint32_t halves(int lo, int hi) {
+        return ((uint32_t)lo & 0xFFFFu) | (((uint32_t)hi & 0xFFFFu) << 16);
+    }
+#else
+    static __device__ __forceinline__ uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) { return vmax(a + b, c); }
+    static __device__ __forceinline__ uint32_t halves(int lo, int hi) { return (uint32_t)(lo + hi * 65536); }
+#endif
 };
 
 struct L32 {
@@ -76,11 +96,13 @@ struct L32 {
     static __device__ __forceinline__ uint32_t lane1(int v) { return (uint32_t)v; }
     static __device__ __forceinline__ uint32_t both(int v) { return (uint32_t)v; }
     static __device__ __forceinline__ uint32_t addk(int c) { return (uint32_t)c; }
+    static __device__ __forceinline__ uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) { return vmax(a + b, c); }
+    static __device__ __forceinline__ uint32_t halves(int lo, int hi) { return (uint32_t)lo; }
 };
 
 // words of one lane's profile (the warp region holds 32 lanes' worth)
 __host__ __device__ constexpr int prof_words(int R, bool fold, bool dna, int A) {
-    return dna ? (fold ? 16 * R : 4 * R) : (fold ? 2 * A * R : A * R);
+    return dna ? (fold ? (GSW_FILL_SPLIT ? 8 * R : 16 * R) : 4 * R) : (fold ? 2 * A * R : A * R);
 }
 
 // Index of profile word (table c, row r) of lane l inside the warp region:
@@ -152,7 +174,7 @@ __device__ __forceinline__ void build_profile(uint32_t *psm, const Job &job, con
             int rho_hi = st * SP + S + k * R + r - pad_top;
             qhi = rho_hi >= 0 ? min((int)job.q[(long long)rho_hi * job.qs], A - 1) : -1;
         }
-        if constexpr (DNA) {
+        if constexpr (DNA && !GSW_FILL_SPLIT) {
             if constexpr (L::FOLD) {
 #pragma unroll
                 for (int a = 0; a < 4; a++)
@@ -160,7 +182,7 @@ __device__ __forceinline__ void build_profile(uint32_t *psm, const Job &job, con
                     for (int b = 0; b < 4; b++) {
                         int wl = qlo >= 0 ? sc_w(sc, qlo, a) : 0;
                         int wh = qhi >= 0 ? sc_w(sc, qhi, b) : 0;
-                        psm[pidx<R>(a * 4 + b, r, lane)] = (uint32_t)(wl + wh * 65536);
+                        psm[pidx<R>(a * 4 + b, r, lane)] = L::halves(wl, wh);
                     }
             } else {
 #pragma unroll
@@ -168,9 +190,9 @@ __device__ __forceinline__ void build_profile(uint32_t *psm, const Job &job, con
             }
         } else {
             for (int a = 0; a < A; a++) {
-                psm[pidx<R>(a, r, lane)] = (uint32_t)(qlo >= 0 ? sc_w(sc, qlo, a) : 0);
+                psm[pidx<R>(a, r, lane)] = L::halves(qlo >= 0 ? sc_w(sc, qlo, a) : 0, 0);
                 if constexpr (L::FOLD)
-                    psm[pidx<R>(A + a, r, lane)] = (uint32_t)((qhi >= 0 ? sc_w(sc, qhi, a) : 0) * 65536);
+                    psm[pidx<R>(A + a, r, lane)] = L::halves(0, qhi >= 0 ? sc_w(sc, qhi, a) : 0);
             }
         }
     }
@@ -199,6 +221,8 @@ __device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm
     const int nstrips = (job.mrows + SP - 1) / SP;
     const int pad_top = nstrips * SP - job.mrows;
     const uint32_t kO = L::addk(-sc.O), kX = L::addk(-sc.X);
+    const uint32_t kXm = L::halves(-sc.X, -sc.X);  // operand of addmax (two 16-bit halves in DPX form)
+    (void)kX;
     const uint32_t NEGE = L::both(-sc.O);  // E and F on the boundary: exactly -O after one step
     const int A = sc.A;
     const int src = gbase + ((k + P - 1) & (P - 1));
@@ -278,7 +302,7 @@ __device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm
                 }
             }
             uint32_t pw[R];
-            if constexpr (DNA) {
+            if constexpr (DNA && !GSW_FILL_SPLIT) {
                 load_words<R>(psm, L::FOLD ? al * 4 + ah : al, lane, pw);
             } else {
                 load_words<R>(psm, al, lane, pw);
@@ -294,15 +318,15 @@ __device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm
             uint32_t f = fin, m = cmin;
 #pragma unroll
             for (int r = 0; r < R; r++) {
-                uint32_t tt = L::vmax(diag + pw[r], E[r]);
+                uint32_t tt = L::addmax(diag, pw[r], E[r]);
                 tt = L::vmax(tt, Z2);
                 const uint32_t to = tt + kO;
                 const uint32_t h = L::vmax(tt, f);
-                f = L::vmax(f + kX, to);  // = max(F - X, H - O) since O >= X
+                f = L::addmax(f, kXm, to);  // = max(F - X, H - O) since O >= X
                 diag = H[r];
                 H[r] = h;
                 m = L::vmax(m, h);
-                E[r] = L::vmax(E[r] + kX, h + kO);
+                E[r] = L::addmax(E[r], kXm, h + kO);
             }
             uint32_t cme = m;
             if constexpr (CHECKED) {
