@@ -35,11 +35,46 @@ ALGO_OPS_PER_CELL = 10  # 2-input integer ops of one Gotoh cell update (add, 3 s
 WORKLOAD = "dna_short_read_extension_1M"
 
 
-def workload_config(npairs):
-    return {"workload": WORKLOAD, "pairs": npairs, "query_nt": [100, 250], "target_nt": [300, 1000],
-            "subst": 0.01, "indel": 0.001, "decoys": 0.10, "scoring": "+2/-2, open 3, extend 1",
-            "outputs": "score1, ends, score2, ref_end2, begins, CIGAR",
-            "l2": "inputs ~0.8 GB per step, larger than the 129 MB L2 (no flush)"}
+def make_workload(name, pairs, rank):
+    """(batch, config dict) of a named workload; `pairs` overrides its size."""
+    from paper_1208_6350_gb300 import workloads as wl
+    if name == "dna_short_read_extension_1M":
+        n = pairs or 1_000_000
+        cfg = {"workload": name, "pairs": n, "query_nt": [100, 250], "target_nt": [300, 1000],
+               "subst": 0.01, "indel": 0.001, "decoys": 0.10, "scoring": "+2/-2, open 3, extend 1"}
+        return wl.config2(n, seed=1 + rank), cfg
+    if name == "dna_1k_100x1000":
+        b = wl.config1(seed=rank)
+        if pairs:
+            b = b.subset(np.arange(min(pairs, b.npairs)))
+        return b, {"workload": name, "pairs": b.npairs, "query_nt": 100, "target_nt": 1000, "subst": 0.02,
+                   "indel": 0.002, "scoring": "+2/-2, open 3, extend 1"}
+    if name == "dna_long_reads_10k":
+        n = pairs or 10_000
+        return wl.config3(n, seed=2 + rank), {
+            "workload": name, "pairs": n, "query_nt": "log-uniform 1000-20000", "target": "1.2 x query",
+            "error": "6% subst, 2% ins, 2% del", "scoring": "+2/-4, open 4, extend 2"}
+    if name == "protein_search_1kx10k":
+        ps = wl.protein_search(seed=3 + rank)
+        n = pairs or 1_000_000
+        rng = np.random.default_rng(7 + rank)
+        qi = rng.integers(0, ps.n_queries, n)
+        di = rng.integers(0, ps.n_db, n)
+        return ps.pairs(qi, di, name), {
+            "workload": name, "pairs": n, "sample_of": "1,000 queries x 10,000 database sequences",
+            "query_aa": [50, 1000], "db_aa": "clip(LogNormal(ln 300, 0.6), 20, 5000)",
+            "matrix": "seeded synthetic symmetric 20x20 (BLOSUM-like ranges)", "gap": "open 11, extend 1"}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(cfg, b):
+    out = dict(cfg)
+    out["outputs"] = "score1, ends, score2, ref_end2, begins, CIGAR"
+    nbytes = len(b.q) + len(b.t)
+    out["l2"] = (f"inputs {nbytes / 1e9:.2f} GB per step, " +
+                 ("larger than the 129 MB L2 (no flush)" if nbytes > 129e6 else "smaller than L2"))
+    out["cells"] = b.cells
+    return out
 
 
 # ----------------------------------------------------------------- clocks
@@ -96,16 +131,17 @@ def cpu_baseline(b, target_s=10.0, max_pairs=200_000):
     import oracle
     cores = len(os.sched_getaffinity(0))
     rng = np.random.default_rng(123)
-    pilot = b.subset(rng.permutation(b.npairs)[:1000])
+    pilot = b.subset(rng.permutation(b.npairs)[:min(1000, max(16, b.npairs // 50))])
     t0 = time.perf_counter()
     oracle.align_batch(pilot.q, pilot.q_off, pilot.q_len, pilot.t, pilot.t_off, pilot.t_len, pilot.W,
-                       pilot.gap_open, pilot.gap_extend, nthreads=cores, cigar_stride=1300)
+                       pilot.gap_open, pilot.gap_extend, nthreads=cores,
+                       cigar_stride=int(pilot.q_len.max() + pilot.t_len.max() + 2))
     rate = pilot.cells / max(time.perf_counter() - t0, 1e-6)
-    n = int(min(max_pairs, b.npairs, max(1000, target_s * rate / (b.cells / b.npairs))))
+    n = int(min(max_pairs, b.npairs, max(16, target_s * rate / (b.cells / b.npairs))))
     s = b.subset(rng.permutation(b.npairs)[:n])
     t0 = time.perf_counter()
     res, _, _ = oracle.align_batch(s.q, s.q_off, s.q_len, s.t, s.t_off, s.t_len, s.W, s.gap_open,
-                                   s.gap_extend, nthreads=cores, cigar_stride=1300)
+                                   s.gap_extend, nthreads=cores, cigar_stride=int(s.q_len.max() + s.t_len.max() + 2))
     dt = time.perf_counter() - t0
     return {"value": s.cells / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} random pairs of the workload ({s.cells / 1e9:.2f} G cells), full outputs, "
@@ -123,9 +159,11 @@ def _cpu_model():
     return platform.machine()
 
 
-def fill_traffic_bytes(cells):
+def fill_traffic_bytes(cells, workload):
     """DRAM bytes per forward-fill launch from the committed ncu summary, if it
-    was taken on the current fill kernel source; else None."""
+    was taken on the current fill kernel source and this workload; else None."""
+    if workload != WORKLOAD:
+        return None
     path = os.path.join(ROOT, "profiles", "fill_fwd_traffic.txt")
     src = os.path.join(ROOT, "paper_1208_6350_gb300", "csrc", "fill.cu")
     try:
@@ -153,7 +191,7 @@ def run_gsw(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    b = wl.config2(args.pairs, seed=1 + rank)
+    b, wcfg = make_workload(args.workload, args.pairs, rank)
     cells = b.cells
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     q, t = T(b.q), T(b.t)
@@ -161,7 +199,7 @@ def run_gsw(args):
     ql, tl = T(b.q_len.astype(np.int32)), T(b.t_len.astype(np.int32))
     n = b.npairs
     res = torch.zeros(n * 12, dtype=torch.int32, device=dev)
-    cap = 32 * n + 1024
+    cap = int(min(32 * n + 1024 + (b.q_len.sum() + b.t_len.sum()) // 4, 1 << 30))
     cig = torch.zeros(cap, dtype=torch.int32, device=dev)
     ctx = gsw.Context(local, args.budget_gb << 30)
     stream = torch.cuda.current_stream(dev)
@@ -218,7 +256,7 @@ def run_gsw(args):
     fill_s = float(np.mean(fill_ms)) / 1e3
     achieved = ALGO_OPS_PER_CELL * cells / fill_s / 1e9
     roof = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak_gops, 1), "unit": "Gop/s",
-            "frac": round(achieved / peak_gops, 4), "traffic": fill_traffic_bytes(cells),
+            "frac": round(achieved / peak_gops, 4), "traffic": fill_traffic_bytes(cells, args.workload),
             "kernel": "k_fill (forward, 16-bit folded ring)",
             "fill_ms": round(float(np.mean(fill_ms)), 3),
             "fill_gcups": round(cells / fill_s / 1e9, 1),
@@ -229,7 +267,7 @@ def run_gsw(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i16x2 (i32 refill)",
             "data": "synthetic (seeded; stands in for simulated short reads)",
-            "config": workload_config(args.pairs), "e2e": e2e,
+            "config": workload_config(wcfg, b), "e2e": e2e,
             "gpu_launches": launches,
             "stage_ms": {k: round(v / args.steps, 3) for k, v in stage_sum.items()},
             "checked_pairs": checked, "clocks": clocks, "roofline": roof}
@@ -248,7 +286,7 @@ def run_e2e(args, gsw, b, ctx, stream, dev, torch):
     qo, to = pin(b.q_off.astype(np.int64)), pin(b.t_off.astype(np.int64))
     ql, tl = pin(b.q_len.astype(np.int32)), pin(b.t_len.astype(np.int32))
     res = pin(np.zeros(n, gsw.RESULT_DTYPE).view(np.int32))
-    cap = 32 * n + 1024
+    cap = int(min(32 * n + 1024 + (b.q_len.sum() + b.t_len.sum()) // 4, 1 << 30))
     cig = pin(np.zeros(cap, np.uint32))
     flags = gsw.GSW_CIGAR | gsw.GSW_HOST_IO
 
@@ -274,14 +312,18 @@ def run_e2e(args, gsw, b, ctx, stream, dev, torch):
             "api": "gsw_align_batch with GSW_HOST_IO (pinned host buffers)"}
 
 
-def check_sample(b, res, cig, rank, k=300):
+def check_sample(b, res, cig, rank, k=300, max_cells=3e9):
     import oracle
     from paper_1208_6350_gb300 import gsw
     rng = np.random.default_rng(7 + rank)
     idx = rng.permutation(b.npairs)[:k]
+    # keep the oracle's share of the check bounded (long pairs)
+    cum = np.cumsum(b.q_len[idx].astype(np.int64) * b.t_len[idx])
+    idx = idx[: max(1, int(np.searchsorted(cum, max_cells)))]
+    k = len(idx)
     s = b.subset(idx)
     ores, ocg, _ = oracle.align_batch(s.q, s.q_off, s.q_len, s.t, s.t_off, s.t_len, s.W, s.gap_open,
-                                      s.gap_extend, cigar_stride=1300)
+                                      s.gap_extend, cigar_stride=int(s.q_len.max() + s.t_len.max() + 2))
     r = res.cpu().numpy().view(gsw.RESULT_DTYPE)
     c = cig.cpu().numpy().view(np.uint32)
     for j, p in enumerate(idx):
@@ -304,16 +346,16 @@ def run_reference(args):
     from paper_1208_6350_gb300 import workloads as wl
 
     cores = len(os.sched_getaffinity(0))
-    b = wl.config2(args.pairs, seed=1)
+    b, wcfg = make_workload(args.workload, args.pairs, 0)
     rng = np.random.default_rng(99)
     per_step = args.ref_pairs
     total = 0.0
     cells = 0
     for k in range(args.warmup + args.steps):
-        s = b.subset(rng.permutation(b.npairs)[:per_step])
+        s = b.subset(rng.permutation(b.npairs)[:min(per_step, b.npairs)])
         t0 = time.perf_counter()
         oracle.align_batch(s.q, s.q_off, s.q_len, s.t, s.t_off, s.t_len, s.W, s.gap_open, s.gap_extend,
-                           nthreads=cores, cigar_stride=1300)
+                           nthreads=cores, cigar_stride=int(s.q_len.max() + s.t_len.max() + 2))
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             total += dt
@@ -323,7 +365,7 @@ def run_reference(args):
             "n_gpus": int(os.environ.get("WORLD_SIZE", 1)), "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
-            "config": workload_config(args.pairs),
+            "config": workload_config(wcfg, b),
             "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} random pairs of the workload per step, full outputs",
                              "cpu": _cpu_model()},
@@ -338,7 +380,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gsw", choices=["gsw", "reference"])
-    ap.add_argument("--pairs", type=int, default=1_000_000)
+    ap.add_argument("--pairs", type=int, default=0, help="override the workload's pair count")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=["dna_short_read_extension_1M", "dna_1k_100x1000", "dna_long_reads_10k",
+                             "protein_search_1kx10k"])
     ap.add_argument("--budget-gb", type=int, default=24)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-pairs", type=int, default=4000)

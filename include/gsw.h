@@ -225,6 +225,63 @@ int gsw_fill_static(int32_t npairs, const uint8_t *q, const int64_t *q_off, cons
                     gsw_result *results, int32_t *colmax, const int64_t *colmax_off,
                     void *stream);
 
+/*
+ * Serving loop (continuous batching).  A server owns `workers` batch slots,
+ * each with its own context (scratch bounded by mem_budget_bytes / workers),
+ * stream and pinned / device staging.  Requests (one or more pairs, host
+ * memory, copied at submit) wait in a FIFO; a free worker forms its next
+ * batch from the head of the queue -- as many whole requests as fit its
+ * max_batch_pairs and max_batch_letters -- and runs the whole hot path on it
+ * while the other workers' batches are on the GPU, so requests that arrive
+ * while others are being aligned are admitted as soon as a slot frees.  Each
+ * request's results are those gsw_align_batch gives for it alone.
+ * Paper analogue: the library "called in multi-threaded way" by MOSAIK,
+ * SCISSORS and TANGRAM (Applications).
+ */
+typedef struct gsw_server gsw_server;
+typedef struct gsw_serve_config {
+    int32_t device;
+    int32_t workers;             /* batches in flight; 0 -> 3 */
+    int32_t max_batch_pairs;     /* pairs per batch; 0 -> 8192 */
+    int64_t max_batch_letters;   /* query + target letters per batch; 0 -> 16M */
+    size_t mem_budget_bytes;     /* device memory of all workers; 0 -> 8 GiB */
+    int32_t max_queue_requests;  /* queued requests beyond which submit fails (GSW_ENOMEM); 0 -> 1M */
+    uint32_t flags;              /* GSW_BEGIN and/or GSW_CIGAR */
+    int32_t mask_len;            /* as gsw_align_batch */
+    const int8_t *matrix;        /* alphabet x alphabet, copied */
+    int32_t alphabet, gap_open, gap_extend;
+} gsw_serve_config;
+
+/* Starts the workers.  Errors: GSW_EINVAL (scoring, flags), GSW_ENOMEM, GSW_ECUDA. */
+int gsw_serve_create(const gsw_serve_config *cfg, gsw_server **out);
+
+/* Stops the workers after the queued and running batches finish. */
+int gsw_serve_destroy(gsw_server *srv);
+
+/* Queues one request of npairs pairs (layout of gsw_align_batch, host memory,
+ * copied before return).  Errors: GSW_EINVAL (a request larger than one batch,
+ * bad lengths or letters are reported by its poll), GSW_ENOMEM (queue full). */
+int gsw_serve_submit(gsw_server *srv, int32_t npairs, const uint8_t *q, const int64_t *q_off,
+                     const int32_t *q_len, const uint8_t *t, const int64_t *t_off,
+                     const int32_t *t_len, uint64_t *req_id);
+
+/* Waits at most timeout_us (< 0: no limit) for request req_id; on completion
+ * copies its npairs records to `results` (host) and its CIGAR words to
+ * `cigar` (cigar_off in the records index this buffer), sets *cigar_words,
+ * and forgets the request.  Returns the request's status (GSW_OK or the error
+ * of its batch), GSW_ETIMEDOUT (still queued or running; poll again),
+ * GSW_ENOTFOUND, or GSW_ECIGAR_SPACE (cigar_capacity too small; the request
+ * is kept).  Thread-safe with submit. */
+int gsw_serve_poll(gsw_server *srv, uint64_t req_id, int32_t timeout_us, gsw_result *results,
+                   uint32_t *cigar, int64_t cigar_capacity, int64_t *cigar_words);
+
+typedef struct gsw_serve_stats {
+    uint64_t submitted, completed, batches, pairs, cells;
+    double busy_seconds;         /* sum over workers of time with a batch in flight */
+    int32_t queued, running;
+} gsw_serve_stats;
+int gsw_serve_get_stats(gsw_server *srv, gsw_serve_stats *out);
+
 /* Name of an error code (static string). */
 const char *gsw_strerror(int code);
 

@@ -52,6 +52,20 @@ class GswStats(ctypes.Structure):
                 ("stage_ms", ctypes.c_float * 8)]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("workers", ctypes.c_int32), ("max_batch_pairs", ctypes.c_int32),
+                ("max_batch_letters", ctypes.c_int64), ("mem_budget_bytes", ctypes.c_size_t),
+                ("max_queue_requests", ctypes.c_int32), ("flags", ctypes.c_uint32), ("mask_len", ctypes.c_int32),
+                ("matrix", ctypes.c_void_p), ("alphabet", ctypes.c_int32), ("gap_open", ctypes.c_int32),
+                ("gap_extend", ctypes.c_int32)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("pairs", ctypes.c_uint64), ("cells", ctypes.c_uint64), ("busy_seconds", ctypes.c_double),
+                ("queued", ctypes.c_int32), ("running", ctypes.c_int32)]
+
+
 class GswError(RuntimeError):
     def __init__(self, code, what):
         self.code = code
@@ -85,6 +99,14 @@ def load(build_if_missing: bool = True):
         f.restype = ctypes.c_int
     lib.gsw_fill_static.argtypes = [i32, P, P, P, P, P, P, i32, P, i32, i32, i32, u32, i32, P, P, P, P]
     lib.gsw_fill_static.restype = ctypes.c_int
+    lib.gsw_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(P)]
+    lib.gsw_serve_destroy.argtypes = [P]
+    lib.gsw_serve_submit.argtypes = [P, i32, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.gsw_serve_poll.argtypes = [P, ctypes.c_uint64, i32, P, P, i64, ctypes.POINTER(ctypes.c_int64)]
+    lib.gsw_serve_get_stats.argtypes = [P, ctypes.POINTER(ServeStats)]
+    for f in (lib.gsw_serve_create, lib.gsw_serve_destroy, lib.gsw_serve_submit, lib.gsw_serve_poll,
+              lib.gsw_serve_get_stats):
+        f.restype = ctypes.c_int
     lib.gsw_last_stats.argtypes = [P, ctypes.POINTER(GswStats)]
     lib.gsw_last_stats.restype = ctypes.c_int
     lib.gsw_strerror.argtypes = [ctypes.c_int]
@@ -251,3 +273,57 @@ class Context:
                              gap_extend, flags | GSW_HOST_IO, mask_len, res, cig, cigar_capacity, cm,
                              cmoff)
         return res, cig, (cm, cmoff), rc
+
+
+class Server:
+    """Continuous-batching server (gsw_serve_*); host numpy arrays in and out."""
+
+    def __init__(self, matrix, gap_open, gap_extend, flags=GSW_CIGAR, mask_len=-1, device=0, workers=3,
+                 max_batch_pairs=8192, max_batch_letters=16 << 20, mem_budget_bytes=8 << 30):
+        self._m = np.ascontiguousarray(matrix, dtype=np.int8)
+        cfg = ServeConfig(device, workers, max_batch_pairs, max_batch_letters, mem_budget_bytes, 0, flags,
+                          mask_len, self._m.ctypes.data, self._m.shape[0], gap_open, gap_extend)
+        out = ctypes.c_void_p()
+        _check(load().gsw_serve_create(ctypes.byref(cfg), ctypes.byref(out)), "gsw_serve_create")
+        self.handle = out.value
+
+    def submit(self, q, q_off, q_len, t, t_off, t_len) -> int:
+        q = np.ascontiguousarray(q, np.uint8)
+        t = np.ascontiguousarray(t, np.uint8)
+        q_off = np.ascontiguousarray(q_off, np.int64)
+        t_off = np.ascontiguousarray(t_off, np.int64)
+        q_len = np.ascontiguousarray(q_len, np.int32)
+        t_len = np.ascontiguousarray(t_len, np.int32)
+        rid = ctypes.c_uint64()
+        _check(load().gsw_serve_submit(self.handle, len(q_len), _ptr(q), _ptr(q_off), _ptr(q_len), _ptr(t),
+                                       _ptr(t_off), _ptr(t_len), ctypes.byref(rid)), "gsw_serve_submit")
+        return rid.value
+
+    def poll(self, req_id, npairs, timeout_us=-1, cigar_capacity=None):
+        """Returns (status, results, cigar words) -- results None while pending."""
+        res = np.zeros(npairs, RESULT_DTYPE)
+        cap = cigar_capacity if cigar_capacity is not None else 64 * npairs + 64
+        cig = np.zeros(max(cap, 1), np.uint32)
+        used = ctypes.c_int64()
+        rc = load().gsw_serve_poll(self.handle, req_id, timeout_us, _ptr(res), _ptr(cig), cap, ctypes.byref(used))
+        if rc == GSW_ECIGAR_SPACE:
+            return self.poll(req_id, npairs, timeout_us, int(used.value))
+        if rc == GSW_ETIMEDOUT:
+            return rc, None, None
+        return rc, res, cig[: used.value]
+
+    def stats(self) -> dict:
+        st = ServeStats()
+        _check(load().gsw_serve_get_stats(self.handle, ctypes.byref(st)), "gsw_serve_get_stats")
+        return {k: getattr(st, k) for k, _ in ServeStats._fields_}
+
+    def close(self):
+        if self.handle:
+            _check(load().gsw_serve_destroy(self.handle), "gsw_serve_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
