@@ -177,6 +177,20 @@ def fill_traffic_bytes(cells, workload):
 
 
 # ------------------------------------------------------------ GPU arm
+def combine_ranks(ms, cells, dist=None, device="cpu"):
+    """Whole-job step time and cells: the slowest rank's time, every rank's
+    cells (each rank aligns its own batch; no collective on the data path)."""
+    if dist is None:
+        return ms, cells
+    import torch
+    x = torch.tensor([ms, float(cells)], dtype=torch.float64, device=device)
+    t = x[:1].clone()
+    c = x[1:].clone()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(float(c.item())))
+
+
 def run_gsw(args):
     import torch
     import torch.distributed as dist
@@ -237,12 +251,8 @@ def run_gsw(args):
         dist.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    ms_max = ms
-    if world > 1:
-        x = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        ms_max = float(x.item())
-    value = world * cells / (ms_max / 1e3) / 1e9
+    ms_max, job_cells = combine_ranks(ms, cells, dist if world > 1 else None, dev)
+    value = job_cells / (ms_max / 1e3) / 1e9
 
     # e2e: the same call on host buffers (pinned), copies inside the timed region
     e2e = None

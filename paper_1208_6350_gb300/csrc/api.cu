@@ -145,7 +145,7 @@ int make_scoring(const int8_t *matrix, int32_t A, int32_t O, int32_t X, Scoring 
 }
 
 // device scratch layout of ctx->misc (64-bit words)
-enum MiscSlot { kMiscTraceHead = 0, kMiscCursor = 1, kMiscNeed = 2 /* 3 words */, kMiscMaxLen = 5, kMiscValid = 6, kMiscWords = 8 };
+enum MiscSlot { kMiscTraceHead = 0, kMiscCursor = 1, kMiscMaxLen = 2, kMiscValid = 3, kMiscNeed = 4 /* 9 words */, kMiscWords = 16 };
 
 // event e[k] marks the end of stage k-1 / start of stage k
 int mark(gsw_ctx *ctx, int k, cudaStream_t st) {
@@ -160,7 +160,7 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
     // ---- plan buffers
     GSW_TRY(ensure(ctx, ctx->plan_keys, sizeof(int32_t) * (size_t)std::max(npairs, 1)));
     GSW_TRY(ensure(ctx, ctx->plan_order, sizeof(int32_t) * (size_t)std::max(npairs, 1)));
-    const size_t small_words = 3 * (size_t)kPlanBins + 4 * kNumVariants + 8;
+    const size_t small_words = 3 * (size_t)kPlanBins + 4 * kNumFillClasses + 8;
     GSW_TRY(ensure(ctx, ctx->plan_small, sizeof(int32_t) * small_words));
     int32_t *ps = reinterpret_cast<int32_t *>(ctx->plan_small.p);
     PlanBuffers pb;
@@ -170,9 +170,9 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
     pb.binoff = ps + kPlanBins;
     pb.cursor = ps + 2 * kPlanBins;
     pb.var_start = ps + 3 * kPlanBins;
-    pb.task_lo = pb.var_start + kNumVariants + 1;
-    pb.task_hi = pb.task_lo + kNumVariants;
-    pb.ntasks = pb.task_hi + kNumVariants;
+    pb.task_lo = pb.var_start + kNumFillClasses + 1;
+    pb.task_hi = pb.task_lo + kNumFillClasses;
+    pb.ntasks = pb.task_hi + kNumFillClasses;
     pb.head = pb.ntasks + 1;
 
     // ---- fill launch geometry and per-slot scratch
@@ -206,7 +206,7 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
     fl.scr.colmax = ctx->fill_cm.p;
     fl.scr.boundary = ctx->fill_bnd.p;
     fl.scr.ncap = (int32_t)ncap;
-    fl.scr.slots_per_warp = 2;
+    fl.scr.nslots = (int32_t)slots;
 
     auto plan = [&](int32_t mode) -> int {
         cudaError_t e = launch_plan(bv, sc, mode, pb, st);
@@ -218,7 +218,7 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
         fl.mode = mode;
         cudaError_t e = launch_fill(fl, ctx->sms, max_blocks, st);
         if (e != cudaSuccess) return set_err(GSW_ECUDA, "fill: %s", cudaGetErrorString(e));
-        ctx->launches += kNumVariants;
+        ctx->launches += kNumFillClasses;
         return GSW_OK;
     };
     GSW_TRY(mark(ctx, 0, st));
@@ -273,32 +273,59 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
         CUDA_TRY(launch_trace_need(bv, sc, misc + kMiscNeed, st));
         ctx->launches += 1;
         unsigned long long *hs = reinterpret_cast<unsigned long long *>(ctx->host_small);
-        CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, 9 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
-        const long long need_dir = (long long)hs[0], need_ops = (long long)hs[1], need_nch = (long long)hs[2];
-        if (need_dir > 0) {
-            const int tgrid = ctx->sms * 16;  // latency-bound per step: many warps per SM
-            const int twarps = tgrid * (trace_block_threads() / 32);
-            const long long dir_words = std::max<long long>(need_dir, 64);
-            const long long op_words = std::max<long long>(need_ops + 64 * need_nch, 64);
-            size_t per_warp = (size_t)(dir_words + op_words) * sizeof(uint32_t);
-            int use_warps = twarps;
-            size_t have = room(ctx, ctx->trace_dirs, ctx->trace_ops) / 2;
-            if ((size_t)use_warps * per_warp > have) use_warps = (int)std::max<size_t>(4, have / per_warp);
-            int use_grid = std::max(1, use_warps / (trace_block_threads() / 32));
-            use_warps = use_grid * (trace_block_threads() / 32);
-            GSW_TRY(ensure2(ctx, ctx->trace_dirs, (size_t)use_warps * dir_words * sizeof(uint32_t), ctx->trace_ops,
-                            (size_t)use_warps * op_words * sizeof(uint32_t)));
-            TraceScratch ts;
-            ts.dirs = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
-            ts.dir_words = dir_words;
-            ts.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
-            ts.op_words = op_words;
-            ts.order = pb.order;
-            ts.var_start = pb.var_start;
-            CUDA_TRY(launch_trace_ad(bv, sc, ts, use_grid, st));
-            CUDA_TRY(launch_traceback(bv, sc, ts, use_grid, st));
-            ctx->launches += 5;
+        unsigned long long need[9];
+        std::memcpy(need, hs, sizeof(need));
+        // groups: 0 anti-diagonal (<= 512 diagonals), 1 wide anti-diagonal, 2 row kernel.
+        // One scratch pair serves the three launches in turn, partitioned per warp.
+        struct Grp {
+            long long dir, ops;
+            int warps, grid;
+        } g[3];
+        const size_t have = room(ctx, ctx->trace_dirs, ctx->trace_ops) / 2;
+        size_t max_dir = 0, max_ops = 0;
+        for (int k = 0; k < 3; k++) {
+            g[k].dir = std::max<long long>((long long)need[3 * k], 0);
+            g[k].ops = std::max<long long>((long long)need[3 * k + 1], 0);
+            if (k == 2) g[k].ops += 64 * (long long)need[8];
+            g[k].warps = 0;
+            g[k].grid = 0;
+            if (g[k].dir == 0) continue;
+            g[k].dir = std::max<long long>(g[k].dir, 64);
+            g[k].ops = std::max<long long>(g[k].ops, 64);
+            const size_t per_warp = (size_t)(g[k].dir + g[k].ops) * sizeof(uint32_t);
+            int want = k == 0 ? ctx->sms * 16 * (trace_block_threads() / 32) : (k == 1 ? ctx->sms * 2 : ctx->sms * 2 * (trace_block_threads() / 32));
+            int warps = (int)std::min<size_t>((size_t)want, std::max<size_t>(1, have / per_warp));
+            if (k != 1) warps = std::max(trace_block_threads() / 32, warps - warps % (trace_block_threads() / 32));
+            g[k].warps = warps;
+            g[k].grid = k == 1 ? warps : warps / (trace_block_threads() / 32);
+            max_dir = std::max<size_t>(max_dir, (size_t)warps * (size_t)g[k].dir);
+            max_ops = std::max<size_t>(max_ops, (size_t)warps * (size_t)g[k].ops);
+        }
+        if (max_dir > 0) {
+            GSW_TRY(ensure2(ctx, ctx->trace_dirs, max_dir * sizeof(uint32_t), ctx->trace_ops, max_ops * sizeof(uint32_t)));
+            for (int k = 0; k < 3; k++) {
+                if (g[k].warps == 0) continue;
+                TraceScratch ts;
+                ts.dirs = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
+                ts.dir_words = g[k].dir;
+                ts.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
+                ts.op_words = g[k].ops;
+                ts.order = pb.order;
+                ts.var_start = pb.var_start;
+                if (k == 0) {
+                    CUDA_TRY(launch_trace_ad(bv, sc, ts, g[k].grid, st));
+                    ctx->launches += 4;
+                } else if (k == 1) {
+                    const int nch_max = (int)std::min<unsigned long long>(need[5], (unsigned long long)trace_adw_max_chunks());
+                    CUDA_TRY(launch_trace_adw(bv, sc, ts, g[k].grid, nch_max, st));
+                    ctx->launches += 1;
+                } else {
+                    CUDA_TRY(launch_traceback(bv, sc, ts, g[k].grid, st));
+                    ctx->launches += 1;
+                }
+            }
         }
         ctx->stage_done[5] = 1;
     }

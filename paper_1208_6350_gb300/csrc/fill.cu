@@ -209,201 +209,278 @@ __device__ __forceinline__ int lane_hi(uint32_t w) {
     else return (int)w;
 }
 
-// The ring fill of one pair by the P lanes of a group.  All lanes of the
-// group call it with the same job and return the same result.
+// One strip of the ring fill for the P lanes of a group: the per-strip state
+// (H, E, the saved column, the trackers, the values received from the lane
+// above) and the step.  ring_fill runs the strips of a pair one after the
+// other; k_fill_long runs them on several warps of a CTA at once.
 template <int P, int R, class L, bool DNA>
-__device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm, int k, unsigned gmask,
-                                int gbase, int lane) {
-    constexpr int S = P * R;
-    constexpr int SP = L::FOLD ? 2 * S : S;
-    constexpr uint32_t Z2 = L::Z2;
-    const int n = job.ncols;
-    const int nstrips = (job.mrows + SP - 1) / SP;
-    const int pad_top = nstrips * SP - job.mrows;
-    const uint32_t kO = L::addk(-sc.O), kX = L::addk(-sc.X);
-    const uint32_t kXm = L::halves(-sc.X, -sc.X);  // operand of addmax (two 16-bit halves in DPX form)
-    (void)kX;
-    const uint32_t NEGE = L::both(-sc.O);  // E and F on the boundary: exactly -O after one step
-    const int A = sc.A;
-    const int src = gbase + ((k + P - 1) & (P - 1));
-    const int nsteps = n + (L::FOLD ? 2 * P - 1 : P - 1);
-    typename L::cm_t *cms = reinterpret_cast<typename L::cm_t *>(job.cms);
-    typename L::bnd_t *bnd = reinterpret_cast<typename L::bnd_t *>(job.bnd);
+struct StripRunner {
+    static constexpr int S = P * R;
+    static constexpr int SP = L::FOLD ? 2 * S : S;
+    static constexpr uint32_t Z2 = L::Z2;
+    using bnd_t = typename L::bnd_t;
+    using cm_t = typename L::cm_t;
+    static constexpr int CM_OFF = L::FOLD ? -(2 * P - 1) : -(P - 1);
 
-    RingResult res{0, -1, -1, pad_top};
-    int g_score = 0, g_col = -1, g_row = -1;
+    Job job;
+    uint32_t *psm;
+    int k, gbase, lane, src, n, A, nsteps, pad_top;
+    unsigned gmask;
+    uint32_t kO, kXm, NEGE;
+    int sh0;
+    uint32_t bzh, bzf, bzc;
+    cm_t *cms;
+    bool has_cms;
 
-#pragma unroll 1
-    for (int st = 0; st < nstrips; st++) {
+    // Binds the runner to a pair (job) and to lane k of the group at gbase.
+    __device__ __forceinline__ void init(const Job &job_, const Scoring &sc, uint32_t *psm_, int k_, unsigned gmask_,
+                                         int gbase_, int lane_, int pad_top_) {
+        job = job_;
+        psm = psm_;
+        k = k_;
+        gbase = gbase_;
+        lane = lane_;
+        src = gbase_ + ((k_ + P - 1) & (P - 1));
+        n = job_.ncols;
+        A = sc.A;
+        nsteps = job_.ncols + (L::FOLD ? 2 * P - 1 : P - 1);
+        pad_top = pad_top_;
+        gmask = gmask_;
+        kO = L::addk(-sc.O);
+        kXm = L::halves(-sc.X, -sc.X);
+        NEGE = L::both(-sc.O);
+        sh0 = (L::FOLD && k_ == 0) ? 16 : 0;
+        bzh = k_ == 0 ? L::lane1(0) : 0u;
+        bzf = k_ == 0 ? L::lane1(-sc.O) : 0u;
+        bzc = k_ == 0 ? (L::FOLD ? L::Z : 0u) : 0u;
+        cms = reinterpret_cast<cm_t *>(job_.cms);
+        has_cms = job_.cms != nullptr;
+    }
+
+    int st = 0;
+    bool last_strip = false;
+    const bnd_t *bin = nullptr;
+    bnd_t *bout = nullptr;
+    uint32_t H[R], E[R], SV[R];
+    uint32_t hdiag, best, xh, xf, xc;
+    int c_lo, c_hi, nal, nah;
+    bnd_t b_cur, b_nxt;
+    cm_t c_cur, c_nxt;
+
+
+    // Strips after the first read the previous strip's boundary (lane 0,
+    // column s) and accumulate the column max (lane P-1, column s-2P+1): the
+    // group loads both one block of P columns ahead and the two lanes take
+    // their word by shuffle, so no step waits on global memory.
+    __device__ __forceinline__ void prefetch(const int s0) {
+        const int jb = s0 + k, jc = s0 + CM_OFF + k;
+        b_nxt = (jb >= 0 && jb < n) ? bin[jb] : bnd_t{};
+        c_nxt = (has_cms && jc >= 0 && jc < n) ? cms[jc] : cm_t{};
+    }
+
+    // Starts strip st_ (boundary in from bin_, out to bout_).
+    __device__ void begin(const Scoring &sc, int st_, const bnd_t *bin_, bnd_t *bout_, bool last_) {
+        st = st_;
+        bin = bin_;
+        bout = bout_;
+        last_strip = last_;
         build_profile<P, R, L, DNA>(psm, job, sc, k, lane, st, pad_top);
         __syncwarp(gmask);
-        const typename L::bnd_t *bin = bnd + (size_t)((st + 1) & 1) * n;  // written by strip st-1
-        typename L::bnd_t *bout = bnd + (size_t)(st & 1) * n;             // read by strip st+1
-        const bool last_strip = st == nstrips - 1;
-
-        uint32_t H[R], E[R], SV[R];
 #pragma unroll
         for (int r = 0; r < R; r++) { H[r] = Z2; E[r] = NEGE; SV[r] = Z2; }
-        uint32_t hdiag = Z2;
-        uint32_t best = Z2;
-        int c_lo = -1, c_hi = -1;
-        uint32_t xh = Z2, xf = NEGE, xc = Z2;  // values received from lane k-1
-        int nal = (-k >= 0 && -k < n) ? min((int)job.t[0], A - 1) : 0;
-        int nah = 0;
-        // lane 0 receives, in its low half, the strip's top boundary (H = 0 and
-        // F = -O on the first strip) and in its high half lane P-1's low half
-        const int sh0 = (L::FOLD && k == 0) ? 16 : 0;
-        const uint32_t bzh = k == 0 ? L::lane1(0) : 0u, bzf = k == 0 ? L::lane1(-sc.O) : 0u;
-        const uint32_t bzc = k == 0 ? (L::FOLD ? L::Z : 0u) : 0u;
-        const bool has_cms = job.cms != nullptr;
-        const bool single = nstrips == 1;
+        hdiag = Z2;
+        best = Z2;
+        c_lo = -1;
+        c_hi = -1;
+        xh = Z2;  // values received from lane k-1
+        xf = NEGE;
+        xc = Z2;
+        nal = (-k >= 0 && -k < n) ? min((int)job.t[0], A - 1) : 0;
+        nah = 0;
+        b_cur = bnd_t{};
+        b_nxt = bnd_t{};
+        c_cur = cm_t{};
+        c_nxt = cm_t{};
+        if (st > 0) prefetch(0);
+    }
 
-        // One step of lane k: low half at column s - k, high half P columns
-        // behind.  CHECKED steps handle columns outside [0, n) (start-up and
-        // drain of the wavefront); steady steps have every column in range.
-        auto step = [&](const int s, auto checked_tag) -> bool {
-            constexpr bool CHECKED = decltype(checked_tag)::value;
-            const int jlo = s - k;
-            const int jhi = L::FOLD ? jlo - P : jlo;
-            uint32_t hin, fin, cmin;
-            if constexpr (L::FOLD) {
-                hin = (xh << sh0) | bzh;
-                fin = (xf << sh0) | bzf;
-                cmin = (xc << sh0) | bzc;
-            } else {
-                hin = k == 0 ? bzh : xh;
-                fin = k == 0 ? bzf : xf;
-                cmin = k == 0 ? bzc : xc;
+    // One step of lane k: low half at column s - k, high half P columns
+    // behind.  CHECKED steps handle columns outside [0, n) (start-up and
+    // drain of the wavefront); steady steps have every column in range.
+    // Returns true when the reverse fill found its target column.
+    template <bool CHECKED>
+    __device__ __forceinline__ bool step(const int s) {
+        const int jlo = s - k;
+        const int jhi = L::FOLD ? jlo - P : jlo;
+        uint32_t hin, fin, cmin;
+        if constexpr (L::FOLD) {
+            hin = (xh << sh0) | bzh;
+            fin = (xf << sh0) | bzf;
+            cmin = (xc << sh0) | bzc;
+        } else {
+            hin = k == 0 ? bzh : xh;
+            fin = k == 0 ? bzf : xf;
+            cmin = k == 0 ? bzc : xc;
+        }
+        cm_t cm_prev{};
+        if (st > 0) {
+            const int bi = s & (P - 1);
+            if (bi == 0) {
+                b_cur = b_nxt;
+                c_cur = c_nxt;
+                prefetch(s + P);
             }
-            if (st > 0 && k == 0 && (!CHECKED || (jlo >= 0 && jlo < n))) {
+            const int srcl = gbase + bi;
+            if constexpr (L::FOLD) cm_prev = (cm_t)__shfl_sync(gmask, (uint32_t)c_cur, srcl);
+            else cm_prev = __shfl_sync(gmask, c_cur, srcl);
+            bnd_t w;
+            if constexpr (L::FOLD) {
+                w = __shfl_sync(gmask, b_cur, srcl);
+            } else {
+                w.x = __shfl_sync(gmask, b_cur.x, srcl);
+                w.y = __shfl_sync(gmask, b_cur.y, srcl);
+            }
+            if (k == 0 && (!CHECKED || (jlo >= 0 && jlo < n))) {
                 if constexpr (L::FOLD) {
-                    const uint32_t w = bin[jlo];
                     hin = (hin & 0xFFFF0000u) | (w & 0xFFFFu);
                     fin = (fin & 0xFFFF0000u) | (w >> 16);
                 } else {
-                    const int2 w = bin[jlo];
                     hin = (uint32_t)w.x;
                     fin = (uint32_t)w.y;
                 }
             }
-            // letters of this lane's columns (loaded one step ahead)
-            const int al = nal, ah = nah;
-            {
-                const int j1 = jlo + 1;
-                if constexpr (CHECKED) {
-                    nal = (j1 >= 0 && j1 < n) ? min((int)job.t[(long long)j1 * job.ts], A - 1) : 0;
-                    if constexpr (L::FOLD) {
-                        const int j2 = j1 - P;
-                        nah = (j2 >= 0 && j2 < n) ? min((int)job.t[(long long)j2 * job.ts], A - 1) : 0;
-                    }
-                } else {
-                    nal = min((int)job.t[(long long)j1 * job.ts], A - 1);
-                    if constexpr (L::FOLD) nah = min((int)job.t[(long long)(j1 - P) * job.ts], A - 1);
-                }
-            }
-            uint32_t pw[R];
-            if constexpr (DNA && !GSW_FILL_SPLIT) {
-                load_words<R>(psm, L::FOLD ? al * 4 + ah : al, lane, pw);
-            } else {
-                load_words<R>(psm, al, lane, pw);
-                if constexpr (L::FOLD) {
-                    uint32_t ph[R];
-                    load_words<R>(psm, A + ah, lane, ph);
-#pragma unroll
-                    for (int r = 0; r < R; r++) pw[r] += ph[r];
-                }
-            }
-            uint32_t diag = hdiag;
-            hdiag = hin;
-            uint32_t f = fin, m = cmin;
-#pragma unroll
-            for (int r = 0; r < R; r++) {
-                uint32_t tt = L::addmax(diag, pw[r], E[r]);
-                tt = L::vmax(tt, Z2);
-                const uint32_t to = tt + kO;
-                const uint32_t h = L::vmax(tt, f);
-                f = L::addmax(f, kXm, to);  // = max(F - X, H - O) since O >= X
-                diag = H[r];
-                H[r] = h;
-                m = L::vmax(m, h);
-                E[r] = L::addmax(E[r], kXm, h + kO);
-            }
-            uint32_t cme = m;
+        }
+        // letters of this lane's columns (loaded one step ahead)
+        const int al = nal, ah = nah;
+        {
+            const int j1 = jlo + 1;
             if constexpr (CHECKED) {
-                // before a half's first column its state must be the left boundary
-                if (jhi < 0) {
-                    const uint32_t keep = (L::FOLD && jlo >= 0) ? 0x0000FFFFu : 0u;
-#pragma unroll
-                    for (int r = 0; r < R; r++) {
-                        H[r] = (H[r] & keep) | (Z2 & ~keep);
-                        E[r] = (E[r] & keep) | (NEGE & ~keep);
-                    }
-                    hdiag = (hdiag & keep) | (Z2 & ~keep);
-                }
-                uint32_t vm = 0;
-                if (jlo >= 0 && jlo < n) vm |= L::FOLD ? 0x0000FFFFu : 0xFFFFFFFFu;
-                if (L::FOLD && jhi >= 0 && jhi < n) vm |= 0xFFFF0000u;
-                cme = (m & vm) | (Z2 & ~vm);
-            }
-            // tracker: first column where the running column max strictly improved
-            {
-                const uint32_t nb = L::vmax(cme, best);
-                if (nb != best) {
-                    const uint32_t diff = nb ^ best;
-                    uint32_t mk;
-                    if constexpr (L::FOLD) {
-                        mk = ((diff & 0xFFFFu) ? 0x0000FFFFu : 0u) | ((diff >> 16) ? 0xFFFF0000u : 0u);
-                        if (diff & 0xFFFFu) c_lo = jlo;
-                        if (diff >> 16) c_hi = jhi;
-                    } else {
-                        mk = 0xFFFFFFFFu;
-                        c_lo = jlo;
-                    }
-                    best = nb;
-#pragma unroll
-                    for (int r = 0; r < R; r++) SV[r] = (H[r] & mk) | (SV[r] & ~mk);
-                }
-            }
-            // the last lane holds complete columns: column max and strip boundary
-            bool found = false;
-            if (k == P - 1 && (!CHECKED || (jhi >= 0 && jhi < n))) {
+                nal = (j1 >= 0 && j1 < n) ? min((int)job.t[(long long)j1 * job.ts], A - 1) : 0;
                 if constexpr (L::FOLD) {
-                    const uint32_t full = m >> 16;
-                    if (has_cms) {
-                        if (st == 0) cms[jhi] = (uint16_t)full;
-                        else cms[jhi] = (uint16_t)max((uint32_t)cms[jhi], full);
-                    }
-                    if (!last_strip) bout[jhi] = (H[R - 1] >> 16) | (f & 0xFFFF0000u);
-                    found = full == job.stop_u;
-                } else {
-                    if (has_cms) {
-                        if (st == 0) cms[jhi] = (int)m;
-                        else cms[jhi] = max(cms[jhi], (int)m);
-                    }
-                    if (!last_strip) bout[jhi] = make_int2((int)H[R - 1], (int)f);
-                    found = m == job.stop_u;
+                    const int j2 = j1 - P;
+                    nah = (j2 >= 0 && j2 < n) ? min((int)job.t[(long long)j2 * job.ts], A - 1) : 0;
                 }
+            } else {
+                nal = min((int)job.t[(long long)j1 * job.ts], A - 1);
+                if constexpr (L::FOLD) nah = min((int)job.t[(long long)(j1 - P) * job.ts], A - 1);
             }
-            if (job.stop_u && single && __any_sync(gmask, found)) return true;
-            xh = __shfl_sync(gmask, H[R - 1], src);
-            xf = __shfl_sync(gmask, f, src);
-            xc = __shfl_sync(gmask, m, src);
-            return false;
-        };
+        }
+        uint32_t pw[R];
+        if constexpr (DNA && !GSW_FILL_SPLIT) {
+            load_words<R>(psm, L::FOLD ? al * 4 + ah : al, lane, pw);
+        } else {
+            load_words<R>(psm, al, lane, pw);
+            if constexpr (L::FOLD) {
+                uint32_t ph[R];
+                load_words<R>(psm, A + ah, lane, ph);
+#pragma unroll
+                for (int r = 0; r < R; r++) pw[r] += ph[r];
+            }
+        }
+        uint32_t diag = hdiag;
+        hdiag = hin;
+        uint32_t f = fin, m = cmin;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            uint32_t tt = L::addmax(diag, pw[r], E[r]);
+            tt = L::vmax(tt, Z2);
+            const uint32_t to = tt + kO;
+            const uint32_t h = L::vmax(tt, f);
+            f = L::addmax(f, kXm, to);  // = max(F - X, H - O) since O >= X
+            diag = H[r];
+            H[r] = h;
+            m = L::vmax(m, h);
+            E[r] = L::addmax(E[r], kXm, h + kO);
+        }
+        uint32_t cme = m;
+        if constexpr (CHECKED) {
+            // before a half's first column its state must be the left boundary
+            if (jhi < 0) {
+                const uint32_t keep = (L::FOLD && jlo >= 0) ? 0x0000FFFFu : 0u;
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    H[r] = (H[r] & keep) | (Z2 & ~keep);
+                    E[r] = (E[r] & keep) | (NEGE & ~keep);
+                }
+                hdiag = (hdiag & keep) | (Z2 & ~keep);
+            }
+            uint32_t vm = 0;
+            if (jlo >= 0 && jlo < n) vm |= L::FOLD ? 0x0000FFFFu : 0xFFFFFFFFu;
+            if (L::FOLD && jhi >= 0 && jhi < n) vm |= 0xFFFF0000u;
+            cme = (m & vm) | (Z2 & ~vm);
+        }
+        // tracker: first column where the running column max strictly improved
+        {
+            const uint32_t nb = L::vmax(cme, best);
+            if (nb != best) {
+                const uint32_t diff = nb ^ best;
+                uint32_t mk;
+                if constexpr (L::FOLD) {
+                    mk = ((diff & 0xFFFFu) ? 0x0000FFFFu : 0u) | ((diff >> 16) ? 0xFFFF0000u : 0u);
+                    if (diff & 0xFFFFu) c_lo = jlo;
+                    if (diff >> 16) c_hi = jhi;
+                } else {
+                    mk = 0xFFFFFFFFu;
+                    c_lo = jlo;
+                }
+                best = nb;
+#pragma unroll
+                for (int r = 0; r < R; r++) SV[r] = (H[r] & mk) | (SV[r] & ~mk);
+            }
+        }
+        // the last lane holds complete columns: column max and strip boundary
+        bool found = false;
+        if (k == P - 1 && (!CHECKED || (jhi >= 0 && jhi < n))) {
+            if constexpr (L::FOLD) {
+                const uint32_t full = m >> 16;
+                if (has_cms) {
+                    if (st == 0) cms[jhi] = (uint16_t)full;
+                    else cms[jhi] = (uint16_t)max((uint32_t)cm_prev, full);
+                }
+                if (!last_strip) bout[jhi] = (H[R - 1] >> 16) | (f & 0xFFFF0000u);
+                found = full == job.stop_u;
+            } else {
+                if (has_cms) {
+                    if (st == 0) cms[jhi] = (int)m;
+                    else cms[jhi] = max((int)cm_prev, (int)m);
+                }
+                if (!last_strip) bout[jhi] = make_int2((int)H[R - 1], (int)f);
+                found = m == job.stop_u;
+            }
+        }
+        // Reverse fill: stop at the first column where the last strip reaches
+        // the target.  Every column up to it is complete in every strip (the
+        // earlier strips are ahead), so the first column holding the maximum
+        // is at or before it and the strip trackers hold it.
+        if (job.stop_u && last_strip && __any_sync(gmask, found)) return true;
+        xh = __shfl_sync(gmask, H[R - 1], src);
+        xf = __shfl_sync(gmask, f, src);
+        xc = __shfl_sync(gmask, m, src);
+        return false;
+    }
 
-        // start-up (checked), steady (unchecked), drain (checked)
+    // Steps [s0, s1) of the current strip: start-up (checked), steady
+    // (unchecked), drain (checked).  Returns true on an early stop.
+    __device__ bool run(int s0, int s1) {
         const int s_steady = L::FOLD ? 2 * P - 1 : P - 1;
         const int s_drain = max(s_steady, n - 1);
-        bool stop = false;
-        int s = 0;
+        s1 = min(s1, nsteps);
+        int s = s0;
 #pragma unroll 1
-        for (; s < s_steady && s < nsteps && !stop; s++) stop = step(s, std::true_type{});
+        for (; s < s1 && s < s_steady; s++)
+            if (step<true>(s)) return true;
 #pragma unroll 1
-        for (; s < s_drain && !stop; s++) stop = step(s, std::false_type{});
+        for (; s < s1 && s < s_drain; s++)
+            if (step<false>(s)) return true;
 #pragma unroll 1
-        for (; s < nsteps && !stop; s++) stop = step(s, std::true_type{});
+        for (; s < s1; s++)
+            if (step<true>(s)) return true;
+        return false;
+    }
 
-        // ---- strip epilogue: the strip's maximum, its first column, its first row
+    // Strip epilogue: the strip's maximum, its first column, and the first row
+    // (within the strip) of that column holding it; the same on every lane.
+    __device__ void end(int *v_out, int *c_out, int *row_out) {
         const uint32_t bl = __shfl_sync(gmask, best, gbase + P - 1);
         const int cl = __shfl_sync(gmask, L::FOLD ? c_hi : c_lo, gbase + P - 1);
         const int vfull = lane_hi<L>(bl);
@@ -421,13 +498,45 @@ __device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm
         }
 #pragma unroll
         for (int d = 1; d < P; d <<= 1) cand = min(cand, __shfl_xor_sync(gmask, cand, d));
-        if (vfull > g_score || (vfull == g_score && vfull > 0 && cl < g_col)) {
-            g_score = vfull;
-            g_col = cl;
-            g_row = st * SP + cand;
-        }
+        *v_out = vfull;
+        *c_out = cl;
+        *row_out = cand;
         __syncwarp(gmask);
     }
+};
+
+// Lexicographic best over strips: larger score, then smaller column, then
+// smaller row.
+__device__ __forceinline__ void best_merge(int v, int c, int row, int *bv, int *bc, int *br) {
+    if (v > *bv || (v == *bv && v > 0 && (c < *bc || (c == *bc && row < *br)))) {
+        *bv = v;
+        *bc = c;
+        *br = row;
+    }
+}
+
+// The ring fill of one pair by the P lanes of a group, strip after strip.
+// All lanes of the group call it with the same job and return the same result.
+template <int P, int R, class L, bool DNA>
+__device__ RingResult ring_fill(const Job &job, const Scoring &sc, uint32_t *psm, int k, unsigned gmask,
+                                int gbase, int lane) {
+    using SR = StripRunner<P, R, L, DNA>;
+    const int n = job.ncols;
+    const int nstrips = (job.mrows + SR::SP - 1) / SR::SP;
+    const int pad_top = nstrips * SR::SP - job.mrows;
+    typename L::bnd_t *bnd = reinterpret_cast<typename L::bnd_t *>(job.bnd);
+    SR sr;
+    sr.init(job, sc, psm, k, gmask, gbase, lane, pad_top);
+    int g_score = 0, g_col = INT_MAX, g_row = INT_MAX;
+#pragma unroll 1
+    for (int st = 0; st < nstrips; st++) {
+        sr.begin(sc, st, bnd + (size_t)((st + 1) & 1) * n, bnd + (size_t)(st & 1) * n, st == nstrips - 1);
+        sr.run(0, sr.nsteps);
+        int v, c, row;
+        sr.end(&v, &c, &row);
+        best_merge(v, c, st * SR::SP + row, &g_score, &g_col, &g_row);
+    }
+    RingResult res{0, -1, -1, pad_top};
     res.score = g_score;
     res.col = g_score > 0 ? g_col : -1;
     res.row = g_score > 0 ? g_row : -1;
@@ -464,68 +573,48 @@ __device__ void secondary(const BatchView &b, int pair, const Job &job, int end_
     *end2 = bv > 0 ? bj : -1;
 }
 
-template <int P, int R, class L, bool DNA>
-__device__ void run_task(const FillLaunch &fl, int first, int last, uint32_t *wsm, int lane, int slot_base) {
-    const int g = lane / P, k = lane % P, gbase = g * P;
-    const unsigned gmask = (P == 32) ? 0xFFFFFFFFu : (((1u << P) - 1u) << gbase);
-    const int idx = first + g;
-    if (idx >= last) return;
-    const BatchView &b = fl.b;
-    const Scoring &sc = fl.sc;
-    const int pair = fl.plan.order[idx];
-    gsw_result *rp = b.res + pair;
-    const int m = b.q_len[pair], n = b.t_len[pair];
-    const uint8_t *qp = b.q + b.q_off[pair];
-    const uint8_t *tp = b.t + b.t_off[pair];
-    const int slot = slot_base + g;
-    uint32_t *psm = wsm;  // the warp's profile region (lane-interleaved)
-    Job job;
-    const size_t ncap = (size_t)fl.scr.ncap;
-    // one stride for every variant, so slots never overlap when 16-bit and
-    // 32-bit tasks run in the same launch
-    job.cms = (char *)fl.scr.colmax + slot * ncap * sizeof(int32_t);
-    job.bnd = (char *)fl.scr.boundary + slot * 2 * ncap * sizeof(int2);
-    job.stop_u = 0;
+// Job of a reverse fill: the query reversed from the end row, the target
+// reversed from the end column over the window that must hold the begin.
+__device__ __forceinline__ void reverse_job(const BatchView &b, const Scoring &sc, int pair, Job *job) {
+    const gsw_result *rp = b.res + pair;
+    const int eq = rp->read_end1, et = rp->ref_end1;
+    job->q = b.q + b.q_off[pair] + eq;
+    job->qs = -1;
+    job->mrows = eq + 1;
+    job->t = b.t + b.t_off[pair] + et;
+    job->ts = -1;
+    job->ncols = reverse_window(eq, et, rp->score1, sc);
+    job->cms = nullptr;
+}
 
-    if (fl.mode == kFillReverse) {
-        const int s1 = rp->score1, eq = rp->read_end1, et = rp->ref_end1;
-        job.q = qp + eq;
-        job.qs = -1;
-        job.mrows = eq + 1;
-        job.t = tp + et;
-        job.ts = -1;
-        job.ncols = reverse_window(eq, et, s1, sc);
-        job.stop_u = L::lane1(s1);
-        job.cms = nullptr;
-        RingResult rr = ring_fill<P, R, L, DNA>(job, sc, psm, k, gmask, gbase, lane);
-        if (k == 0) {
-            if (rr.score == s1 && rr.col >= 0) {
-                rp->ref_begin1 = et - rr.col;
-                rp->read_begin1 = eq - (rr.row - rr.pad_top);
-            } else {
-                rp->flags |= kResInternal;  // reversed maximum differs from score1
-            }
-        }
-        return;
+__device__ __forceinline__ void forward_job(const BatchView &b, int pair, Job *job) {
+    job->q = b.q + b.q_off[pair];
+    job->qs = 1;
+    job->mrows = b.q_len[pair];
+    job->t = b.t + b.t_off[pair];
+    job->ts = 1;
+    job->ncols = b.t_len[pair];
+    job->stop_u = 0;
+}
+
+// Begins from the reversed maximum (one lane writes).
+__device__ __forceinline__ void finish_reverse(gsw_result *rp, const RingResult &rr) {
+    const int s1 = rp->score1, eq = rp->read_end1, et = rp->ref_end1;
+    if (rr.score == s1 && rr.col >= 0) {
+        rp->ref_begin1 = et - rr.col;
+        rp->read_begin1 = eq - (rr.row - rr.pad_top);
+    } else {
+        rp->flags |= kResInternal;  // reversed maximum differs from score1
     }
-    // forward (16-bit first pass, or 32-bit rerun)
-    if (m <= 0 || n <= 0) {
-        if (k == 0) {
-            rp->score1 = 0; rp->score2 = 0; rp->ref_begin1 = -1; rp->ref_end1 = -1;
-            rp->read_begin1 = -1; rp->read_end1 = -1; rp->ref_end2 = -1; rp->cigar_len = 0;
-            rp->cigar_off = -1; rp->flags = L::FOLD ? 0 : GSW_RES_S32; rp->reserved = 0;
-        }
-        if ((b.flags & GSW_COLMAX) && n > 0)
-            for (int j = k; j < n; j += P) b.colmax[b.colmax_off[pair] + j] = 0;
-        return;
-    }
-    job.q = qp;
-    job.qs = 1;
-    job.mrows = m;
-    job.t = tp;
-    job.ts = 1;
-    job.ncols = n;
-    RingResult rr = ring_fill<P, R, L, DNA>(job, sc, psm, k, gmask, gbase, lane);
+}
+
+// Forward result: score1, ends, secondary score (all P lanes of the group
+// call it; the column maxima are in job.cms).
+template <int P, class L>
+__device__ __forceinline__ void finish_forward(const BatchView &b, const Scoring &sc, int pair, const Job &job,
+                                               const RingResult &rr, int k, unsigned gmask) {
+    gsw_result *rp = b.res + pair;
+    const int m = job.mrows;
     const bool overflow = L::FOLD && rr.score > 32767 - sc.wmax;
     int s2 = 0, e2 = -1;
     const int end_t = rr.col, end_q = rr.score > 0 ? rr.row - rr.pad_top : -1;
@@ -546,6 +635,51 @@ __device__ void run_task(const FillLaunch &fl, int first, int last, uint32_t *ws
         rp->flags = overflow ? (GSW_RES_S32 | kResPendingS32) : (L::FOLD ? 0 : GSW_RES_S32);
         rp->reserved = 0;
     }
+}
+
+// Per-slot scratch of a fill launch: one stride for every variant, so slots
+// never overlap when 16-bit and 32-bit tasks run in the same launch.
+__device__ __forceinline__ void slot_scratch(const FillScratch &scr, int slot, Job *job) {
+    const size_t ncap = (size_t)scr.ncap;
+    job->cms = (char *)scr.colmax + slot * ncap * sizeof(int32_t);
+    job->bnd = (char *)scr.boundary + slot * 2 * ncap * sizeof(int2);
+}
+
+template <int P, int R, class L, bool DNA>
+__device__ void run_task(const FillLaunch &fl, int first, int last, uint32_t *wsm, int lane, int slot_base) {
+    const int g = lane / P, k = lane % P, gbase = g * P;
+    const unsigned gmask = (P == 32) ? 0xFFFFFFFFu : (((1u << P) - 1u) << gbase);
+    const int idx = first + g;
+    if (idx >= last) return;
+    const BatchView &b = fl.b;
+    const Scoring &sc = fl.sc;
+    const int pair = fl.plan.order[idx];
+    gsw_result *rp = b.res + pair;
+    uint32_t *psm = wsm;  // the warp's profile region (lane-interleaved)
+    Job job;
+    slot_scratch(fl.scr, slot_base + g, &job);
+    if (fl.mode == kFillReverse) {
+        reverse_job(b, sc, pair, &job);
+        job.stop_u = L::lane1(rp->score1);
+        RingResult rr = ring_fill<P, R, L, DNA>(job, sc, psm, k, gmask, gbase, lane);
+        if (k == 0) finish_reverse(rp, rr);
+        return;
+    }
+    // forward (16-bit first pass, or 32-bit rerun)
+    const int m = b.q_len[pair], n = b.t_len[pair];
+    if (m <= 0 || n <= 0) {
+        if (k == 0) {
+            rp->score1 = 0; rp->score2 = 0; rp->ref_begin1 = -1; rp->ref_end1 = -1;
+            rp->read_begin1 = -1; rp->read_end1 = -1; rp->ref_end2 = -1; rp->cigar_len = 0;
+            rp->cigar_off = -1; rp->flags = L::FOLD ? 0 : GSW_RES_S32; rp->reserved = 0;
+        }
+        if ((b.flags & GSW_COLMAX) && n > 0)
+            for (int j = k; j < n; j += P) b.colmax[b.colmax_off[pair] + j] = 0;
+        return;
+    }
+    forward_job(b, pair, &job);
+    RingResult rr = ring_fill<P, R, L, DNA>(job, sc, psm, k, gmask, gbase, lane);
+    finish_forward<P, L>(b, sc, pair, job, rr, k, gmask);
 }
 
 template <int VID>
@@ -582,6 +716,281 @@ __global__ void __launch_bounds__(kBlock) k_fill(FillLaunch fl, int warp_words) 
     }
 }
 
+// ---------------------------------------------------------------------------
+// CTA kernel for pairs whose query spans many strips.  Strip x reads only the
+// bottom row (H, F) and the running column maxima that strip x-1 leaves in
+// global scratch, one column at a time, so several strips of a pair can run
+// at once when each stays far enough behind the one above it.  The warps of
+// the CTA (one 32-lane folded ring each, 512 rows per strip in 16-bit lanes)
+// advance in phases of kLongChunk steps separated by a CTA barrier, which
+// also makes the previous phases' global writes visible.  Strip x+1 starts
+// long_lag() phases after strip x, so every boundary word and column maximum
+// it reads (one block of 32 columns ahead) was written in a completed phase,
+// and the ping-pong boundary buffer it writes was read a phase earlier.
+//
+// One thread schedules between the two barriers of a phase: it merges the
+// results of strips that ended, hands a finished pair to one warp (secondary
+// score or begins), hands strips to idle warps (oldest pair first, the next
+// strip of a pair no earlier than long_lag() phases after the previous one),
+// and opens the next pair of the class in a free scratch slot, so the end of
+// one pair overlaps the start of the next.
+constexpr int kLongChunk = 64;
+constexpr int kLongSlots = 4;  // pairs in flight per CTA
+
+template <class L>
+__host__ __device__ constexpr int long_lag() {
+    // strip x-1 writes column j at its step j + dw; strip x reads columns up
+    // to s + 2P - 1 at step s: (lag - 1) * C >= 2P - 1 + dw
+    constexpr int P = 32, dw = L::FOLD ? 2 * P - 1 : P - 1;
+    return 1 + (2 * P - 1 + dw + kLongChunk - 1) / kLongChunk;
+}
+
+struct LongSlot {
+    Job job;
+    int pair;  // -1: free
+    int seq;   // order in which the pairs were opened
+    int nstrips, pad_top;
+    int next;        // next strip to hand out
+    int last_start;  // phase at which the last handed-out strip started
+    int running;     // strips running
+    int stopped;     // the last strip found the reverse target
+    int fin;         // finalisation handed out
+    int bv, bc, br;  // merged maximum, its column and (padded) row
+};
+
+struct LongCmd {
+    int slot;   // -1: idle
+    int strip;  // >= 0: strip to run; -1: finalise the slot's pair
+    int start;  // phase at which the strip started
+};
+
+struct LongRep {
+    int ended;  // the strip ended (or the finalisation finished) this phase
+    int v, c, row, stop;
+};
+
+template <int NW>
+struct LongShared {
+    LongSlot slot[kLongSlots];
+    LongCmd cmd[NW];
+    LongRep rep[NW];
+    int seq, exhausted, done;
+};
+
+// Opens the next pair of class CLS in slot s; false when none is left.
+template <class L, int SP>
+__device__ bool long_open(const FillLaunch &fl, int cls, LongSlot &S, int s, int seq) {
+    const int ntasks = fl.plan.task_hi[cls] - fl.plan.task_lo[cls];
+    const int t = atomicAdd(&fl.plan.head[cls], 1);
+    if (t >= ntasks) return false;
+    const int pair = fl.plan.order[fl.plan.var_start[cls] + t];
+    Job job;
+    slot_scratch(fl.scr, blockIdx.x * kLongSlots + s, &job);
+    if (fl.mode == kFillReverse) {
+        reverse_job(fl.b, fl.sc, pair, &job);
+        job.stop_u = L::lane1(fl.b.res[pair].score1);
+    } else {
+        forward_job(fl.b, pair, &job);
+    }
+    S.job = job;
+    S.pair = pair;
+    S.seq = seq;
+    S.nstrips = (job.mrows + SP - 1) / SP;
+    S.pad_top = S.nstrips * SP - job.mrows;
+    S.next = 0;
+    S.last_start = 0;
+    S.running = 0;
+    S.stopped = 0;
+    S.fin = 0;
+    S.bv = 0;
+    S.bc = INT_MAX;
+    S.br = INT_MAX;
+    return true;
+}
+
+template <class L, int NW, int SP>
+__device__ void long_schedule(const FillLaunch &fl, int cls, LongShared<NW> &sh, int ph) {
+    constexpr int LAG = long_lag<L>();
+    // results of strips that ended, finished finalisations
+    for (int w = 0; w < NW; w++) {
+        if (!sh.rep[w].ended) continue;
+        sh.rep[w].ended = 0;
+        LongCmd &c = sh.cmd[w];
+        LongSlot &S = sh.slot[c.slot];
+        if (c.strip < 0) {
+            S.pair = -1;
+        } else {
+            best_merge(sh.rep[w].v, sh.rep[w].c, sh.rep[w].row, &S.bv, &S.bc, &S.br);
+            S.running--;
+            if (sh.rep[w].stop) S.stopped = 1;
+        }
+        c.slot = -1;
+    }
+    // idle warps: finalisations first, then strips of the oldest pair that
+    // may start one, then a new pair
+    for (int w = 0; w < NW; w++) {
+        LongCmd &c = sh.cmd[w];
+        if (c.slot >= 0) continue;
+        int pick = -1;
+        for (int s = 0; s < kLongSlots; s++) {
+            const LongSlot &S = sh.slot[s];
+            if (S.pair >= 0 && !S.fin && S.running == 0 && (S.stopped || S.next == S.nstrips)) {
+                pick = s;
+                break;
+            }
+        }
+        if (pick >= 0) {
+            sh.slot[pick].fin = 1;
+            c.slot = pick;
+            c.strip = -1;
+            c.start = ph;
+            continue;
+        }
+        int best_seq = INT_MAX;
+        for (int s = 0; s < kLongSlots; s++) {
+            const LongSlot &S = sh.slot[s];
+            if (S.pair >= 0 && !S.stopped && S.next < S.nstrips && (S.next == 0 || ph >= S.last_start + LAG) &&
+                S.seq < best_seq) {
+                best_seq = S.seq;
+                pick = s;
+            }
+        }
+        if (pick < 0 && !sh.exhausted) {
+            for (int s = 0; s < kLongSlots; s++) {
+                if (sh.slot[s].pair >= 0) continue;
+                if (long_open<L, SP>(fl, cls, sh.slot[s], s, sh.seq)) {
+                    sh.seq++;
+                    pick = s;
+                } else {
+                    sh.exhausted = 1;
+                }
+                break;
+            }
+        }
+        if (pick < 0) break;  // nothing can start in this phase
+        LongSlot &S = sh.slot[pick];
+        c.slot = pick;
+        c.strip = S.next++;
+        c.start = ph;
+        S.last_start = ph;
+        S.running++;
+    }
+    bool busy = !sh.exhausted;
+    for (int s = 0; s < kLongSlots; s++) busy |= sh.slot[s].pair >= 0;
+    sh.done = busy ? 0 : 1;
+}
+
+template <bool DNA, bool S32>
+struct LongCfg {
+    using L = std::conditional_t<S32, L32, L16>;
+    static constexpr int P = 32, R = 8;
+    static constexpr int NW = DNA ? 8 : 4;
+    static constexpr int SP = S32 ? P * R : 2 * P * R;
+    static constexpr int CLS = S32 ? kClassLong32 : kClassLong16;
+};
+
+template <bool DNA, bool S32>
+__global__ void __launch_bounds__(LongCfg<DNA, S32>::NW * 32, 1)
+    k_fill_long(FillLaunch fl, int warp_words) {
+    using C = LongCfg<DNA, S32>;
+    using L = typename C::L;
+    constexpr int NW = C::NW, SP = C::SP;
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ LongShared<NW> sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *psm = smem + (size_t)warp * warp_words;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kLongSlots; s++) sh.slot[s].pair = -1;
+        for (int w = 0; w < NW; w++) {
+            sh.cmd[w].slot = -1;
+            sh.rep[w].ended = 0;
+        }
+        sh.seq = 0;
+        sh.exhausted = 0;
+        sh.done = 0;
+    }
+    StripRunner<C::P, C::R, L, DNA> sr;
+#pragma unroll 1
+    for (int ph = 0;; ph++) {
+        __syncthreads();
+        if (threadIdx.x == 0) long_schedule<L, NW, SP>(fl, C::CLS, sh, ph);
+        __syncthreads();
+        if (sh.done) break;
+        const LongCmd cmd = sh.cmd[warp];
+        if (cmd.slot < 0) continue;
+        const LongSlot &S = sh.slot[cmd.slot];
+        if (cmd.strip < 0) {
+            RingResult rr;
+            rr.score = S.bv;
+            rr.col = S.bv > 0 ? S.bc : -1;
+            rr.row = S.bv > 0 ? S.br : -1;
+            rr.pad_top = S.pad_top;
+            if (fl.mode == kFillReverse) {
+                if (lane == 0) finish_reverse(fl.b.res + S.pair, rr);
+            } else {
+                finish_forward<32, L>(fl.b, fl.sc, S.pair, S.job, rr, lane, 0xFFFFFFFFu);
+            }
+            if (lane == 0) sh.rep[warp].ended = 1;
+            continue;
+        }
+        if (ph == cmd.start) {
+            sr.init(S.job, fl.sc, psm, lane, 0xFFFFFFFFu, 0, lane, S.pad_top);
+            typename L::bnd_t *bnd = reinterpret_cast<typename L::bnd_t *>(S.job.bnd);
+            const size_t n = (size_t)S.job.ncols;
+            sr.begin(fl.sc, cmd.strip, bnd + ((cmd.strip + 1) & 1) * n, bnd + (cmd.strip & 1) * n,
+                     cmd.strip == S.nstrips - 1);
+        }
+        bool stop = false, fin = S.stopped != 0;
+        if (!fin) {
+            const int q = ph - cmd.start;
+            stop = sr.run(q * kLongChunk, (q + 1) * kLongChunk);
+            fin = stop || (q + 1) * kLongChunk >= sr.nsteps;
+        }
+        if (fin) {
+            int v, c, row;
+            sr.end(&v, &c, &row);
+            if (lane == 0) {
+                LongRep &r = sh.rep[warp];
+                r.v = v;
+                r.c = c;
+                r.row = cmd.strip * SP + row;
+                r.stop = stop ? 1 : 0;
+                r.ended = 1;
+            }
+        }
+    }
+}
+
+template <bool DNA, bool S32>
+size_t long_smem_bytes(int A) {
+    using C = LongCfg<DNA, S32>;
+    return (size_t)prof_words(C::R, C::L::FOLD, DNA, A) * 32 * sizeof(uint32_t) * C::NW;
+}
+
+template <bool DNA, bool S32>
+int long_occupancy(int A) {
+    using C = LongCfg<DNA, S32>;
+    const size_t sm = long_smem_bytes<DNA, S32>(A);
+    cudaFuncSetAttribute(k_fill_long<DNA, S32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fill_long<DNA, S32>, C::NW * 32, sm);
+    return nb;
+}
+
+template <bool DNA, bool S32>
+cudaError_t launch_long(const FillLaunch &fl, int sms, int max_blocks, cudaStream_t st) {
+    using C = LongCfg<DNA, S32>;
+    const size_t sm = long_smem_bytes<DNA, S32>(fl.sc.A);
+    const int nb = long_occupancy<DNA, S32>(fl.sc.A);
+    if (nb < 1) return cudaErrorInvalidConfiguration;
+    int grid = sms * nb;
+    grid = std::min(grid, max_blocks);
+    grid = std::min(grid, fl.scr.nslots / kLongSlots);
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    k_fill_long<DNA, S32><<<grid, C::NW * 32, sm, st>>>(fl, (int)(sm / sizeof(uint32_t) / C::NW));
+    return cudaGetLastError();
+}
+
 template <bool DNA, int VID>
 size_t smem_bytes(int A) {
     using V = VarC<VID>;
@@ -610,8 +1019,10 @@ cudaError_t launch_one(const FillLaunch &fl, int sms, int max_blocks, cudaStream
 
 template <bool DNA>
 cudaError_t launch_all(const FillLaunch &fl, int sms, int max_blocks, cudaStream_t st) {
-    cudaError_t e = cudaSuccess;
-    // heaviest variants first
+    // heaviest classes first: the CTA kernel for queries of many strips, then
+    // the per-group variants by rows per strip
+    cudaError_t e = launch_long<DNA, true>(fl, sms, max_blocks, st);
+    if (e == cudaSuccess) e = launch_long<DNA, false>(fl, sms, max_blocks, st);
 #define GSW_LAUNCH(id, P_, R_, S_) \
     if (e == cudaSuccess) e = launch_one<DNA, kNumVariants - 1 - id>(fl, sms, max_blocks, st);
     GSW_FILL_VARIANTS(GSW_LAUNCH)

@@ -68,14 +68,32 @@ struct Variant {
 constexpr int kNumVariants = 8;
 constexpr int kVarS32 = 7;
 constexpr int kVarMaxS16 = 6;
+// Two more fill classes: pairs whose query spans many strips run on a whole
+// CTA (k_fill_long), one 32-lane warp per strip, strips pipelined across the
+// CTA's warps; 16-bit lanes (2*32*8 = 512 rows per strip) or 32-bit lanes
+// (256 rows per strip).  One pair per task.
+constexpr int kClassLong16 = kNumVariants;
+constexpr int kClassLong32 = kNumVariants + 1;
+constexpr int kNumFillClasses = kNumVariants + 2;
 __host__ __device__ inline Variant variant_at(int v) {
     switch (v) {
 #define GSW_VARIANT_CASE(id, P, R, S32) \
     case id: return Variant{P, R, S32};
         GSW_FILL_VARIANTS(GSW_VARIANT_CASE)
 #undef GSW_VARIANT_CASE
+    case kClassLong16: return Variant{32, 8, 0};
     default: return Variant{32, 8, 1};
     }
+}
+// Warps of a k_fill_long CTA: 8 for the 4-letter DNA profile, 4 for general
+// alphabets (whose 32-lane profiles take 6x the shared memory).
+__host__ __device__ inline int long_warps(bool dna) { return dna ? 8 : 4; }
+// A query goes to the CTA kernel when it spans at least 3.5 strips of 4-letter
+// DNA (a few such pairs in flight keep every warp busy), or more than 8
+// strips of a general alphabet (whose CTA holds fewer warps per SM).
+__host__ __device__ inline bool long_pair(int rows, bool s32, bool dna) {
+    const int sp = s32 ? 256 : 512;
+    return dna ? 2 * rows > 7 * sp : rows > 8 * sp;
 }
 __host__ __device__ inline int variant_rows(int v) {
     Variant x = variant_at(v);
@@ -87,10 +105,10 @@ __host__ __device__ inline int variant_rows(int v) {
 // out heaviest variant first (variant index descending).
 struct FillPlan {
     const int32_t *order;      // sorted pair indices
-    const int32_t *var_start;  // [kNumVariants+1] start of each variant's pairs in `order`
-    const int32_t *task_lo;    // [kNumVariants] first task index of each variant
-    const int32_t *task_hi;    // [kNumVariants] one past its last task index
-    int32_t *head;             // [kNumVariants] task counters (zeroed by the plan)
+    const int32_t *var_start;  // [kNumFillClasses+1] start of each class's pairs in `order`
+    const int32_t *task_lo;    // [kNumFillClasses] first task index of each class
+    const int32_t *task_hi;    // [kNumFillClasses] one past its last task index
+    int32_t *head;             // [kNumFillClasses] task counters (zeroed by the plan)
     const int32_t *ntasks;     // total tasks
 };
 
@@ -99,7 +117,7 @@ struct FillScratch {
     void *colmax;    // slots x ncap elements (uint16 biased for 16-bit, int32 for 32-bit)
     void *boundary;  // slots x 2 x ncap boundary words (uint32 for 16-bit, int2 for 32-bit)
     int32_t ncap;    // columns per slot
-    int32_t slots_per_warp;
+    int32_t nslots;  // slots allocated
 };
 
 struct FillLaunch {
@@ -122,7 +140,7 @@ constexpr int kBandMaxWidth = 32;
 constexpr int kBandMaxRows = 4096;
 
 constexpr int kPlanBinsPerVariant = 1024;
-constexpr int kPlanBins = kNumVariants * kPlanBinsPerVariant;
+constexpr int kPlanBins = kNumFillClasses * kPlanBinsPerVariant;
 
 // Width of the window the reversed fill scans, ending at the end column: an
 // optimal alignment ending at (end_q, end_t) with score1 has at most
@@ -199,11 +217,11 @@ struct PlanBuffers {
     int32_t *binoff;     // [kPlanBins]
     int32_t *cursor;     // [kPlanBins]
     int32_t *order;      // [npairs]
-    int32_t *var_start;  // [kNumVariants+1]
-    int32_t *task_lo;    // [kNumVariants]
-    int32_t *task_hi;    // [kNumVariants]
+    int32_t *var_start;  // [kNumFillClasses+1]
+    int32_t *task_lo;    // [kNumFillClasses]
+    int32_t *task_hi;    // [kNumFillClasses]
     int32_t *ntasks;     // [1]
-    int32_t *head;       // [kNumVariants]
+    int32_t *head;       // [kNumFillClasses]
 };
 cudaError_t launch_plan(const BatchView &b, const Scoring &sc, int32_t mode, const PlanBuffers &pb,
                         cudaStream_t st);
@@ -218,13 +236,18 @@ struct TraceScratch {
 };
 int trace_block_threads();
 size_t trace_smem_bytes();
-// max over the batch of [0] direction words, [1] op words, [2] chunks of 32 diagonals
+// max over the batch, per kernel group (anti-diagonal <= 512 wide, wide
+// anti-diagonal, row kernel): [3g] direction words, [3g+1] op words, [3g+2] chunks
 cudaError_t launch_trace_need(const BatchView &b, const Scoring &sc, unsigned long long *max_need,
                               cudaStream_t st);
 cudaError_t launch_traceback(const BatchView &b, const Scoring &sc, const TraceScratch &ts, int grid,
                              cudaStream_t st);
 cudaError_t launch_trace_ad(const BatchView &b, const Scoring &sc, const TraceScratch &ts, int grid,
                             cudaStream_t st);
+size_t trace_adw_smem(int nch_max);
+int trace_adw_max_chunks();
+cudaError_t launch_trace_adw(const BatchView &b, const Scoring &sc, const TraceScratch &ts, int grid, int nch_max,
+                             cudaStream_t st);
 
 int band_block_threads();
 cudaError_t launch_band(const BatchView &b, const Scoring &sc, const PlanBuffers &pb, void *scratch,

@@ -1,10 +1,10 @@
 // Work planning for the persistent fill launches, entirely on the device so
 // that a batch needs no host round trip and the stage chain can be captured
-// in a CUDA graph.  A counting sort groups pairs by fill variant (how many
-// query rows a strip covers) and, inside a variant, by estimated cost
-// (strips x steps) descending; the persistent kernel then hands out warp
-// tasks heaviest variant first, so long pairs start early and the tail is
-// made of short ones.
+// in a CUDA graph.  A counting sort groups pairs by fill class (how many
+// query rows a strip covers; queries of many strips go to the CTA kernel)
+// and, inside a class, by estimated cost (strips x steps) descending; the
+// persistent kernels then hand out tasks heaviest class first, so long pairs
+// start early and the tail is made of short ones.
 #include "gsw_impl.cuh"
 
 #include <climits>
@@ -36,11 +36,12 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
         rows = b.q_len[p];
         cols = b.t_len[p];
         v = (b.flags & GSW_FORCE_S32) ? kVarS32 : pick_s16(rows);
+        if (cols > 0 && long_pair(rows, v == kVarS32, sc.dna4)) v = v == kVarS32 ? kClassLong32 : kClassLong16;
     } else if (mode == kFillRerun) {
         if (!(b.res[p].flags & kResPendingS32)) { keys[p] = -1; return; }
         rows = b.q_len[p];
         cols = b.t_len[p];
-        v = kVarS32;
+        v = long_pair(rows, true, sc.dna4) ? kClassLong32 : kVarS32;
     } else if (mode == kFillReverse) {
         // the ring fill takes the reverse of pairs whose band is too wide or
         // too long for one thread
@@ -51,6 +52,7 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
         if (G >= 0 && 2 * G + 1 <= kBandMaxWidth && rows <= kBandMaxRows) { keys[p] = -1; return; }
         cols = reverse_window(r.read_end1, r.ref_end1, r.score1, sc);
         v = (r.flags & GSW_RES_S32) ? kVarS32 : pick_s16(rows);
+        if (long_pair(rows, v == kVarS32, sc.dna4)) v = v == kVarS32 ? kClassLong32 : kClassLong16;
     } else if (mode == kPlanTrace) {
         const gsw_result r = b.res[p];
         if (r.score1 <= 0 || !(r.flags & kResPendingTrace) || (r.flags & kResInternal) || r.read_begin1 < 0) {
@@ -60,7 +62,8 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
         const int la = r.read_end1 - r.read_begin1 + 1, lb = r.ref_end1 - r.ref_begin1 + 1;
         int dlo, dhi;
         const int width = band_range(la, lb, r.score1, sc, &dlo, &dhi);
-        const int cls = width <= 64 ? 0 : width <= 128 ? 1 : width <= 256 ? 2 : width <= 512 ? 3 : 4;
+        const int cls = width <= 64 ? 0 : width <= 128 ? 1 : width <= 256 ? 2 : width <= 512 ? 3
+                      : width <= 64 * 256 ? 4 : 5;
         const int key = cls * kPlanBinsPerVariant + cost_bin((long long)(la + lb + 1) * ((width + 31) / 32));
         keys[p] = key;
         atomicAdd(&hist[key], 1);
@@ -134,12 +137,12 @@ __global__ void __launch_bounds__(kScanThreads) k_plan_scan(const int32_t *hist,
     for (int i = 0; i < PER; i++) binoff[tid * PER + i] = base + loc[i];
     __syncthreads();
     if (tid == 0) {
-        int32_t starts[kNumVariants + 1];
-        for (int v = 0; v < kNumVariants; v++) starts[v] = binoff[v * kPlanBinsPerVariant];
-        starts[kNumVariants] = part[kScanThreads - 1];
-        for (int v = 0; v <= kNumVariants; v++) var_start[v] = starts[v];
+        int32_t starts[kNumFillClasses + 1];
+        for (int v = 0; v < kNumFillClasses; v++) starts[v] = binoff[v * kPlanBinsPerVariant];
+        starts[kNumFillClasses] = part[kScanThreads - 1];
+        for (int v = 0; v <= kNumFillClasses; v++) var_start[v] = starts[v];
         int32_t t = 0;
-        for (int v = kNumVariants - 1; v >= 0; v--) {
+        for (int v = kNumFillClasses - 1; v >= 0; v--) {
             const int per = 32 / variant_at(v).P;
             const int32_t cnt = starts[v + 1] - starts[v];
             task_lo[v] = t;
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(kScanThreads) k_plan_scan(const int32_t *hist,
             task_hi[v] = t;
         }
         *ntasks = t;
-        for (int v = 0; v < kNumVariants; v++) head[v] = 0;
+        for (int v = 0; v < kNumFillClasses; v++) head[v] = 0;
     }
 }
 

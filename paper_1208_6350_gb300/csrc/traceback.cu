@@ -24,6 +24,7 @@ namespace gsw {
 namespace {
 
 constexpr int kTBlock = 128;
+constexpr int kAdwMaxChunks = 256;  // widest band of the wide anti-diagonal kernel: 64 x 256 diagonals
 constexpr int kNegT = -(1 << 28);
 constexpr int kNegHalf = -(1 << 27);
 
@@ -48,19 +49,25 @@ __device__ Need pair_need(const gsw_result &r, const Scoring &sc) {
     const int width = band_range(la, lb, r.score1, sc, &dlo, &dhi);
     nd.dlo = dlo;
     nd.dhi = dhi;
-    nd.nch = (dhi - dlo + 32) / 32;
+    nd.nch = 0;
     if (width <= 512) {
         // anti-diagonal kernel: (la + lb + 1) steps x chunks of 64 x 4 planes
         const int nch_cls = width <= 64 ? 1 : width <= 128 ? 2 : width <= 256 ? 4 : 8;
         nd.dir = (long long)(la + lb + 1) * nch_cls * 4;
         nd.ops = (long long)la + lb + 2;
-        nd.nch = 0;
+    } else if (width <= 64 * kAdwMaxChunks) {
+        nd.nch = (width + 63) / 64;  // wide anti-diagonal kernel
+        nd.dir = (long long)(la + lb + 1) * nd.nch * 4;
+        nd.ops = (long long)la + lb + 2;
     } else {
-        nd.dir = (long long)(la + 1) * nd.nch * 4;
+        nd.nch = -((dhi - dlo + 32) / 32);  // row kernel (negative: marks the class)
+        nd.dir = (long long)(la + 1) * (-nd.nch) * 4;
         nd.ops = (long long)la + lb + 2;
     }
     return nd;
 }
+
+__device__ __forceinline__ int dhi_width_chunks(const Need &nd) { return (nd.dhi - nd.dlo + 32) / 32; }
 
 // pairs the thread-per-pair band kernel left to this kernel (band too wide)
 __device__ __forceinline__ bool wants_trace(const gsw_result &r) {
@@ -70,23 +77,21 @@ __device__ __forceinline__ bool wants_trace(const gsw_result &r) {
 
 __global__ void k_trace_need(BatchView b, Scoring sc, unsigned long long *max_need) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned d = 0, o = 0, c = 0;
+    unsigned v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (p < b.npairs) {
         const gsw_result r = b.res[p];
         if (wants_trace(r)) {
             const Need nd = pair_need(r, sc);
-            d = (unsigned)min(nd.dir, (long long)UINT_MAX);
-            o = (unsigned)min(nd.ops, (long long)UINT_MAX);
-            c = (unsigned)nd.nch;
+            const int g = nd.nch == 0 ? 0 : (nd.nch > 0 ? 3 : 6);
+            v[g] = (unsigned)min(nd.dir, (long long)UINT_MAX);
+            v[g + 1] = (unsigned)min(nd.ops, (long long)UINT_MAX);
+            v[g + 2] = (unsigned)(nd.nch < 0 ? -nd.nch : (nd.nch > 0 ? nd.nch : 1));
         }
     }
-    d = __reduce_max_sync(0xFFFFFFFFu, d);
-    o = __reduce_max_sync(0xFFFFFFFFu, o);
-    c = __reduce_max_sync(0xFFFFFFFFu, c);
-    if ((threadIdx.x & 31) == 0 && d > 0) {
-        atomicMax(&max_need[0], (unsigned long long)d);
-        atomicMax(&max_need[1], (unsigned long long)o);
-        atomicMax(&max_need[2], (unsigned long long)c);
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        const unsigned m = __reduce_max_sync(0xFFFFFFFFu, v[k]);
+        if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&max_need[k], (unsigned long long)m);
     }
 }
 
@@ -247,13 +252,14 @@ __global__ void __launch_bounds__(kTBlock) k_traceback(BatchView b, Scoring sc, 
     uint32_t *gdir = ts.dirs + (size_t)gwarp * ts.dir_words;
     uint32_t *gops = ts.ops + (size_t)gwarp * ts.op_words;  // ops, then the chunk state
     // the planned list (sorted by cost, descending) is dealt round-robin
-    const int first = ts.var_start[4], last = ts.var_start[5];
+    const int first = ts.var_start[5], last = ts.var_start[6];
     const int nwarps = gridDim.x * (kTBlock / 32);
     for (int idx = first + gwarp; idx < last; idx += nwarps) {
         const int p = ts.order[idx];
         const gsw_result r = b.res[p];
         if (!wants_trace(r)) continue;
-        const Need nd = pair_need(r, sc);
+        Need nd = pair_need(r, sc);
+        nd.nch = nd.nch < 0 ? -nd.nch : (dhi_width_chunks(nd));
         const bool small = nd.dir <= cfg.smem_dir_words && nd.ops <= cfg.smem_op_words &&
                            nd.nch <= cfg.smem_state_chunks;
         if (small) {
@@ -479,6 +485,214 @@ cudaError_t launch_trace_ad(const BatchView &b, const Scoring &sc, const TraceSc
 }
 
 namespace {
+
+// ---------------------------------------------------------------------------
+// Wide anti-diagonal traceback (bands of 513 .. 64*kAdwMaxChunks diagonals,
+// long reads): the same wavefront as k_trace_ad, with each chunk's state
+// (H, E, F of the previous anti-diagonal, H of the one before) in shared
+// memory.  Chunks are visited in descending order on even steps (each needs
+// its left neighbour chunk's old value) and ascending order on odd steps (its
+// right neighbour's), so no chunk is read after it was updated in the same
+// step.  One warp per block; the walk stages 16 anti-diagonals at a time.
+constexpr int kAdwStage = 16;
+
+__device__ void trace_adw_pair(const BatchView &b, const Scoring &sc, const int8_t *sW, int p, const gsw_result &r,
+                               int dlo, int dhi, int nch, uint32_t *dirs, uint32_t *ops, int4 *state, uint4 *stage,
+                               int lane) {
+    const int la = r.read_end1 - r.read_begin1 + 1, lb = r.ref_end1 - r.ref_begin1 + 1;
+    const uint8_t *qs = b.q + b.q_off[p] + r.read_begin1;
+    const uint8_t *ts = b.t + b.t_off[p] + r.ref_begin1;
+    const int O = sc.O, X = sc.X, A = sc.A;
+    for (int c = 0; c < nch; c++) state[c * 32 + lane] = make_int4(kNegT, kNegT, kNegT, kNegT);
+    __syncwarp();
+    int final_h = kNegT;
+    const int steps = la + lb;
+    for (int a = 0; a <= steps; a++) {
+        const int par = (a - dlo) & 1;
+        for (int t = 0; t < nch; t++) {
+            const int c = par == 0 ? nch - 1 - t : t;
+            const int4 stv = state[c * 32 + lane];  // x: H1, y: E1, z: F1, w: H2
+            int hl, el, hu, fu;
+            if (par == 0) {
+                int h = __shfl_up_sync(0xFFFFFFFFu, stv.x, 1), e = __shfl_up_sync(0xFFFFFFFFu, stv.y, 1);
+                if (lane == 0) {
+                    if (c > 0) {
+                        const int4 nb = state[(c - 1) * 32 + 31];
+                        h = nb.x;
+                        e = nb.y;
+                    } else {
+                        h = kNegT;
+                        e = kNegT;
+                    }
+                }
+                hl = h; el = e; hu = stv.x; fu = stv.z;
+            } else {
+                int h = __shfl_down_sync(0xFFFFFFFFu, stv.x, 1), f = __shfl_down_sync(0xFFFFFFFFu, stv.z, 1);
+                if (lane == 31) {
+                    if (c + 1 < nch) {
+                        const int4 nb = state[(c + 1) * 32];
+                        h = nb.x;
+                        f = nb.z;
+                    } else {
+                        h = kNegT;
+                        f = kNegT;
+                    }
+                }
+                hl = stv.x; el = stv.y; hu = h; fu = f;
+            }
+            __syncwarp();
+            const int d = dlo + 64 * c + 2 * lane + par;
+            const int i = (a - d) >> 1, j = (a + d) >> 1;
+            const bool valid = d <= dhi && i >= 0 && i <= la && j >= 0 && j <= lb;
+            int E = kNegT, F = kNegT, hdg = kNegT, H;
+            bool eopen = false, fopen = false;
+            if (j >= 1) {
+                const int eo = hl - O;
+                E = max(eo, el - X);
+                eopen = E == eo;
+            }
+            if (i >= 1) {
+                const int fo = hu - O;
+                F = max(fo, fu - X);
+                fopen = F == fo;
+            }
+            if (valid && i >= 1 && j >= 1) {
+                const int qa = min((int)qs[i - 1], A - 1), tb = min((int)ts[j - 1], A - 1);
+                hdg = stv.w + sW[qa * A + tb];
+            }
+            H = max(hdg, max(E, F));
+            if (i == 0 && j == 0) H = 0;
+            if (!valid || H < kNegHalf) { H = kNegT; E = kNegT; F = kNegT; }
+            const int src = (valid && i >= 1 && j >= 1 && hdg > kNegHalf && H == hdg) ? 0 : (H == E ? 1 : 2);
+            const unsigned b0 = __ballot_sync(0xFFFFFFFFu, src & 1);
+            const unsigned b1 = __ballot_sync(0xFFFFFFFFu, src & 2);
+            const unsigned b2 = __ballot_sync(0xFFFFFFFFu, eopen);
+            const unsigned b3 = __ballot_sync(0xFFFFFFFFu, fopen);
+            if (lane < 4) dirs[((long long)a * nch + c) * 4 + lane] = lane == 0 ? b0 : lane == 1 ? b1 : lane == 2 ? b2 : b3;
+            if (valid && i == la && j == lb) final_h = H;
+            state[c * 32 + lane] = make_int4(H, E, F, stv.x);
+            __syncwarp();
+        }
+    }
+    final_h = __reduce_max_sync(0xFFFFFFFFu, final_h);
+    __syncwarp();
+    gsw_result *rp = b.res + p;
+    const uint4 *dirs4 = reinterpret_cast<const uint4 *>(dirs);
+    int i = la, j = lb, state_w = 0, cur = -1, len = 0, runs = 0;
+    bool ok = final_h == r.score1;
+    int a_hi = la + lb;
+    while (ok && (i > 0 || j > 0) && a_hi >= 0) {
+        const int a_lo = max(0, a_hi - kAdwStage + 1);
+        const int nwords = (a_hi - a_lo + 1) * nch;
+        for (int w = lane; w < nwords; w += 32) stage[w] = dirs4[(long long)a_lo * nch + w];
+        __syncwarp();
+        if (lane == 0) {
+            while ((i > 0 || j > 0) && i + j >= a_lo) {
+                const int off2 = j - i - dlo;
+                if (i < 0 || j < 0 || off2 < 0 || off2 >= 64 * nch) { ok = false; break; }
+                const uint4 pl = stage[(i + j - a_lo) * nch + (off2 >> 6)];
+                const int l = (off2 & 63) >> 1;
+                const int src = ((pl.x >> l) & 1) | (((pl.y >> l) & 1) << 1);
+                const int eo = (pl.z >> l) & 1, fo = (pl.w >> l) & 1;
+                int op;
+                if (state_w == 0) {
+                    if (src == 0) { op = GSW_CIGAR_M; i--; j--; }
+                    else { state_w = src; continue; }
+                } else if (state_w == 1) {
+                    op = GSW_CIGAR_D; state_w = eo ? 0 : 1; j--;
+                } else {
+                    op = GSW_CIGAR_I; state_w = fo ? 0 : 2; i--;
+                }
+                if (op == cur) {
+                    len++;
+                } else {
+                    if (len) ops[runs++] = ((uint32_t)len << 4) | (uint32_t)cur;
+                    cur = op;
+                    len = 1;
+                }
+            }
+        }
+        ok = __shfl_sync(0xFFFFFFFFu, (int)ok, 0);
+        i = __shfl_sync(0xFFFFFFFFu, i, 0);
+        j = __shfl_sync(0xFFFFFFFFu, j, 0);
+        __syncwarp();
+        a_hi = a_lo - 1;
+    }
+    if (lane == 0 && ok && (i != 0 || j != 0)) ok = false;
+    if (lane == 0 && ok && len) ops[runs++] = ((uint32_t)len << 4) | (uint32_t)cur;
+    ok = __shfl_sync(0xFFFFFFFFu, (int)ok, 0);
+    const int nr = __shfl_sync(0xFFFFFFFFu, runs, 0);
+    if (!ok) {
+        if (lane == 0) rp->flags |= kResInternal;
+        __syncwarp();
+        return;
+    }
+    unsigned long long off = 0;
+    if (lane == 0) off = atomicAdd(b.cigar_cursor, (unsigned long long)nr);
+    off = __shfl_sync(0xFFFFFFFFu, off, 0);
+    if ((long long)(off + nr) > b.cigar_cap) {
+        if (lane == 0) {
+            rp->flags |= GSW_RES_CIGAR_SPACE;
+            rp->cigar_len = -nr;
+            rp->cigar_off = -1;
+            rp->flags &= ~kResPendingTrace;
+        }
+        __syncwarp();
+        return;
+    }
+    __syncwarp();
+    for (int t = lane; t < nr; t += 32) b.cigar[off + t] = ops[nr - 1 - t];
+    if (lane == 0) {
+        rp->cigar_len = nr;
+        rp->cigar_off = (int64_t)off;
+        rp->flags &= ~kResPendingTrace;
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(32) k_trace_adw(BatchView b, Scoring sc, TraceScratch ts, int cls, int nch_max) {
+    extern __shared__ __align__(16) uint8_t adw_smem[];
+    __shared__ int8_t sW[kMaxAlpha * kMaxAlpha];
+    for (int i = threadIdx.x; i < sc.A * sc.A; i += blockDim.x) sW[i] = sc.W[i];
+    __syncwarp();
+    int4 *state = reinterpret_cast<int4 *>(adw_smem);
+    uint4 *stage = reinterpret_cast<uint4 *>(adw_smem + (size_t)nch_max * 32 * sizeof(int4));
+    const int lane = threadIdx.x & 31;
+    const int gwarp = blockIdx.x;
+    const int nwarps = gridDim.x;
+    uint32_t *dirs = ts.dirs + (size_t)gwarp * ts.dir_words;
+    uint32_t *ops = ts.ops + (size_t)gwarp * ts.op_words;
+    const int first = ts.var_start[cls], last = ts.var_start[cls + 1];
+    for (int idx = first + gwarp; idx < last; idx += nwarps) {
+        const int p = ts.order[idx];
+        const gsw_result r = b.res[p];
+        if (!wants_trace(r)) continue;
+        const int la = r.read_end1 - r.read_begin1 + 1, lb = r.ref_end1 - r.ref_begin1 + 1;
+        int dlo, dhi;
+        const int width = band_range(la, lb, r.score1, sc, &dlo, &dhi);
+        const int nch = (width + 63) / 64;
+        if (nch > nch_max || (long long)(la + lb + 1) * nch * 4 > ts.dir_words || (long long)(la + lb + 2) > ts.op_words) {
+            if (lane == 0) b.res[p].flags |= kResInternal;
+            continue;
+        }
+        trace_adw_pair(b, sc, sW, p, r, dlo, dhi, nch, dirs, ops, state, stage, lane);
+    }
+}
+
+}  // namespace
+
+size_t trace_adw_smem(int nch_max) { return (size_t)nch_max * 32 * sizeof(int4) + (size_t)kAdwStage * nch_max * sizeof(uint4); }
+int trace_adw_max_chunks() { return kAdwMaxChunks; }
+
+cudaError_t launch_trace_adw(const BatchView &b, const Scoring &sc, const TraceScratch &ts, int grid, int nch_max,
+                             cudaStream_t st) {
+    const size_t smem = trace_adw_smem(nch_max);
+    cudaFuncSetAttribute(k_trace_adw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_trace_adw<<<grid, 32, smem, st>>>(b, sc, ts, 4, nch_max);
+    return cudaGetLastError();
+}
+
+namespace {
 }  // namespace
 
 int trace_block_threads() { return kTBlock; }
@@ -486,7 +700,7 @@ int trace_block_threads() { return kTBlock; }
 // Maximum needs over the batch: [0] direction words, [1] op words, [2] chunks.
 cudaError_t launch_trace_need(const BatchView &b, const Scoring &sc, unsigned long long *max_need,
                               cudaStream_t st) {
-    cudaMemsetAsync(max_need, 0, 3 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(max_need, 0, 9 * sizeof(unsigned long long), st);
     const int nb = (b.npairs + 255) / 256;
     if (nb > 0) k_trace_need<<<nb, 256, 0, st>>>(b, sc, max_need);
     return cudaGetLastError();

@@ -187,3 +187,69 @@ def test_plain_per_pair_baseline_matches(ctx):
     b = mixed_dna(15, 40, 120, 300)
     got = run_gpu_host(ctx, b, flags=gsw.GSW_CIGAR | gsw.GSW_PLAIN)
     compare(b, run_oracle(b), got)
+
+
+def test_long_reads_wide_bands(ctx):
+    # 10 % error reads of 3-6 kb: bands of several hundred to a few thousand
+    # diagonals (wide anti-diagonal traceback), queries of 12-24 strips
+    b = wl.dna_long_reads(5, 3000, 6000, seed=17)
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
+def _implanted(rng, A, qlens, flank, p_sub):
+    """Random queries over A letters, each implanted with substitutions into a
+    random target `flank` times its length."""
+    qs, ts = [], []
+    for L in qlens:
+        q = rng.integers(0, A, int(L)).astype(np.uint8)
+        cp = q.copy()
+        mut = rng.random(len(cp)) < p_sub
+        cp[mut] = rng.integers(0, A, int(mut.sum()))
+        t = rng.integers(0, A, int(flank * L)).astype(np.uint8)
+        o = int(rng.integers(0, len(t) - len(cp) + 1))
+        t[o:o + len(cp)] = cp
+        qs.append(q)
+        ts.append(t)
+    return qs, ts
+
+
+def test_cta_kernel_many_strips(ctx):
+    # queries of 3.5-18 strips of 512 rows: the CTA kernel, with more strips
+    # than warps and several pairs in flight per CTA, mixed in one batch with
+    # short pairs of the per-group variants
+    lb = wl.dna_long_reads(10, 1800, 9000, seed=21)
+    sb = mixed_dna(22, 60, 300, 900)
+    b = wl.concat([lb, wl.Batch(sb.name, sb.q, sb.q_off, sb.q_len, sb.t, sb.t_off, sb.t_len, lb.W,
+                                lb.gap_open, lb.gap_extend, "ACGT")])
+    assert (b.q_len > 1792).sum() >= 8
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
+def test_cta_kernel_32bit_lanes(ctx):
+    # forced 32-bit lanes: the 32-bit CTA class (256 rows per strip)
+    b = wl.dna_long_reads(4, 1000, 2600, seed=23)
+    got = run_gpu_host(ctx, b, flags=gsw.GSW_CIGAR | gsw.GSW_FORCE_S32)
+    assert (got[0]["flags"] & gsw.GSW_RES_S32).all()
+    compare(b, run_oracle(b), got)
+
+
+def test_cta_kernel_overflow_rerun(ctx):
+    # match 20: 2-3 kb near-identical alignments score ~40000-60000, past the
+    # 16-bit bound, so the 16-bit CTA fill flags them and the 32-bit CTA
+    # fill redoes them
+    rng = np.random.default_rng(24)
+    qs, ts = _implanted(rng, 4, [2000, 2400, 3000], 1.2, 0.02)
+    b = _batch(qs, ts, wl.dna_matrix(20, -20), 30, 10, "overflow-long")
+    got = run_gpu_host(ctx, b)
+    assert (got[0]["flags"] & gsw.GSW_RES_S32).all()
+    compare(b, run_oracle(b), got)
+
+
+def test_cta_kernel_general_alphabet(ctx):
+    # a 20-letter matrix with queries of more than 8 strips (general-alphabet
+    # CTA kernel) beside short ones
+    rng = np.random.default_rng(25)
+    qs, ts = _implanted(rng, 20, [4200, 4700, 300, 150], 1.1, 0.3)
+    b = _batch(qs, ts, wl.synthetic_protein_matrix(), 11, 1, "protein-long",
+               "ARNDCQEGHILKMFPSTWYV")
+    compare(b, run_oracle(b), run_gpu_host(ctx, b))
