@@ -283,8 +283,14 @@ def run_gsw(args):
             "checked_pairs": checked, "clocks": clocks, "roofline": roof}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(b, args.cpu_seconds)
+    if world == 1 and not args.no_serve:
+        ctx.close()
+        ctx = None
+        torch.cuda.empty_cache()
+        line["serving"] = run_serving([10000.0], 300, 40, gsw)[0]
     print(json.dumps(line), flush=True)
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -346,6 +352,151 @@ def check_sample(b, res, cig, rank, k=300, max_cells=3e9):
     return k
 
 
+# ------------------------------------------------------------ serving
+SERVE_SCORING = (2, -4, 4, 2)  # one scoring for the whole stream: the long reads'
+
+
+def serving_requests(rate, n_requests, seed=5):
+    """The mixed request stream (70 % 100x1000 reads, 20 % short-read
+    extensions, 10 % long reads; 1-64 pairs each; Poisson arrivals), every
+    request scored with SERVE_SCORING."""
+    from paper_1208_6350_gb300 import workloads as wl
+    tr = wl.serving_trace(rate, n_requests, seed=seed)
+    return [(r.arrival_s, r.kind, r.batch) for r in tr]
+
+
+def _latency_summary(lat_s, queue_s=None):
+    lat = np.asarray(lat_s) * 1e3
+    out = {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+           "mean_ms": round(float(lat.mean()), 3), "max_ms": round(float(lat.max()), 3)}
+    if queue_s is not None:
+        out["mean_queue_ms"] = round(float(np.mean(queue_s)) * 1e3, 3)
+    return out
+
+
+def serve_trace(gsw, reqs, W, O, X, workers=4, check=None):
+    """Submits each request at its arrival time (one client thread) and
+    collects results with the server's timestamps (another thread).  Latency
+    = completion on the host - scheduled arrival."""
+    import threading
+    srv = gsw.Server(W, O, X, gsw.GSW_CIGAR, workers=workers, max_batch_pairs=8192,
+                     max_batch_letters=24 << 20, mem_budget_bytes=48 << 30)
+    # warm-up: one request of each kind, not timed
+    seen = set()
+    for a, k, b in reqs:
+        if k not in seen:
+            seen.add(k)
+            rid = srv.submit(b.q, b.q_off, b.q_len, b.t, b.t_off, b.t_len)
+            srv.poll(rid, b.npairs)
+    n = len(reqs)
+    ids = [None] * n
+    out = [None] * n
+    ready = threading.Semaphore(0)
+    t_client0 = time.perf_counter()
+    t_srv0 = srv.now()
+
+    def submitter():
+        for i, (a, k, b) in enumerate(reqs):
+            d = t_client0 + a - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            ids[i] = srv.submit(b.q, b.q_off, b.q_len, b.t, b.t_off, b.t_len)
+            ready.release()
+
+    def poller():
+        for i, (a, k, b) in enumerate(reqs):
+            ready.acquire()
+            rc, res, cig, tm = srv.poll(ids[i], b.npairs, times=True)
+            out[i] = (rc, res, cig, tm)
+
+    th = [threading.Thread(target=submitter), threading.Thread(target=poller)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    st = srv.stats()
+    srv.close()
+    lat, qd = [], []
+    for (a, k, b), (rc, res, cig, tm) in zip(reqs, out):
+        if rc != gsw.GSW_OK:
+            raise SystemExit(f"serving: request failed with {rc}")
+        lat.append(tm[2] - t_srv0 - a)
+        qd.append(tm[1] - tm[0])
+    span = max(tm[2] for *_, tm in out) - t_srv0
+    cells = sum(b.cells for _, _, b in reqs)
+    return lat, qd, span, cells, out, st
+
+
+def plain_trace(gsw, reqs, W, O, X):
+    """The baseline: requests in arrival order, FIFO, each pair its own
+    launch sequence (fill, reverse, banded traceback) on one stream."""
+    ctx = gsw.Context(0, 24 << 30)
+    try:
+        seen = set()
+        for a, k, b in reqs:  # warm-up per kind
+            if k not in seen:
+                seen.add(k)
+                ctx.align_host(b.q, b.q_off, b.q_len, b.t, b.t_off, b.t_len, W, O, X,
+                               gsw.GSW_CIGAR | gsw.GSW_PLAIN, -1, int(b.q_len.sum() + b.t_len.sum() + 64))
+        t0 = time.perf_counter()
+        lat, outs = [], []
+        for a, k, b in reqs:
+            d = t0 + a - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            res, cig, _, rc = ctx.align_host(b.q, b.q_off, b.q_len, b.t, b.t_off, b.t_len, W, O, X,
+                                             gsw.GSW_CIGAR | gsw.GSW_PLAIN, -1,
+                                             int(b.q_len.sum() + b.t_len.sum() + 64))
+            if rc != gsw.GSW_OK:
+                raise SystemExit(f"plain baseline failed with {rc}")
+            lat.append(time.perf_counter() - t0 - a)
+            outs.append((res, cig))
+        return lat, outs
+    finally:
+        ctx.close()
+
+
+def _same_results(gsw, srv_out, plain_out):
+    fields = ("score1", "score2", "ref_begin1", "ref_end1", "read_begin1", "read_end1", "ref_end2")
+    for (rc, res, cig, _), (pres, pcig) in zip(srv_out, plain_out):
+        for f in fields:
+            if not np.array_equal(res[f], pres[f]):
+                return False
+        for p in range(len(res)):
+            a = cig[res["cigar_off"][p]: res["cigar_off"][p] + res["cigar_len"][p]] if res["cigar_len"][p] > 0 else []
+            c = pcig[pres["cigar_off"][p]: pres["cigar_off"][p] + pres["cigar_len"][p]] if pres["cigar_len"][p] > 0 else []
+            if list(a) != list(c):
+                return False
+    return True
+
+
+def run_serving(rates, n_requests, head, gsw, dev_name=""):
+    """Per arrival rate: the server over the whole stream, and server vs the
+    plain per-pair baseline over the stream's first `head` requests."""
+    from paper_1208_6350_gb300 import workloads as wl
+    W = wl.dna_matrix(SERVE_SCORING[0], SERVE_SCORING[1])
+    O, X = SERVE_SCORING[2], SERVE_SCORING[3]
+    rows = []
+    for rate in rates:
+        reqs = serving_requests(rate, n_requests)
+        arr_span = reqs[-1][0] if reqs else 0.0
+        lat, qd, span, cells, out, st = serve_trace(gsw, reqs, W, O, X)
+        row = {"rate_req_s": rate, "requests": len(reqs),
+               "offered_gcups": round(cells / max(arr_span, 1e-9) / 1e9, 1),
+               "achieved_gcups": round(cells / span / 1e9, 1), "server": _latency_summary(lat, qd),
+               "batches": int(st["batches"])}
+        if head:
+            hr = reqs[:head]
+            hlat, _, _, _, hout, _ = serve_trace(gsw, hr, W, O, X)
+            plat, pout = plain_trace(gsw, hr, W, O, X)
+            row["head"] = {"requests": len(hr), "server": _latency_summary(hlat),
+                           "plain_per_pair": _latency_summary(plat),
+                           "same_results": _same_results(gsw, hout, pout)}
+        rows.append(row)
+        print(json.dumps({"progress": row}), file=sys.stderr, flush=True)
+    return rows
+
+
 # ------------------------------------------------------ reference arm
 def run_reference(args):
     """The oracle (this method's plain CPU definition) as the reference arm."""
@@ -384,6 +535,34 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving_line(args):
+    """--workload serving_stream: one line, value = the server's p99 latency at
+    the first rate; every rate's figures under "serving"."""
+    import torch
+    from paper_1208_6350_gb300 import gsw
+    if int(os.environ.get("RANK", 0)) != 0:
+        return  # one GPU's server; other ranks idle
+    torch.cuda.set_device(0)
+    rates = [float(x) for x in args.rates.split(",") if x]
+    sampler = ClockSampler(0)
+    sampler.start()
+    rows = run_serving(rates, args.requests, args.head, gsw)
+    clocks = sampler.stop()
+    first = rows[0]
+    line = {"metric": "served latency p99 (arrival to result on the host), mixed request stream",
+            "value": first["server"]["p99_ms"], "unit": "ms", "n_gpus": 1, "steps": len(rows),
+            "warmup": 3, "higher_is_better": False, "scaling": "none", "vs_baseline": None,
+            "dtype": "i16x2 (i32 refill)", "data": "synthetic (seeded request stream)",
+            "config": {"workload": "serving_stream", "rates_req_s": rates, "requests_per_rate": args.requests,
+                       "mix": "70% 1-64 x (100 vs 1000 nt), 20% 1-64 short-read extensions, "
+                              "10% 1-64 long reads (1-20 kb, 1.2x targets)",
+                       "scoring": "+2/-4, open 4, extend 2 for every request",
+                       "server": "4 workers (2 heavy at 7/8 of the SMs), batches <= 8192 pairs / 24M letters",
+                       "baseline": "plain: FIFO, one launch sequence per pair, one stream"},
+            "serving": rows, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,7 +572,13 @@ def main():
     ap.add_argument("--pairs", type=int, default=0, help="override the workload's pair count")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["dna_short_read_extension_1M", "dna_1k_100x1000", "dna_long_reads_10k",
-                             "protein_search_1kx10k"])
+                             "protein_search_1kx10k", "serving_stream"])
+    ap.add_argument("--rates", default="1000,10000,100000,500000",
+                    help="serving_stream: Poisson arrival rates (requests/s)")
+    ap.add_argument("--requests", type=int, default=2000, help="serving_stream: requests per rate")
+    ap.add_argument("--head", type=int, default=100,
+                    help="serving_stream: leading requests also run by the plain per-pair baseline")
+    ap.add_argument("--no-serve", action="store_true", help="skip the short serving run of the default line")
     ap.add_argument("--budget-gb", type=int, default=24)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-pairs", type=int, default=4000)
@@ -405,6 +590,8 @@ def main():
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving_stream":
+        run_serving_line(args)
     else:
         run_gsw(args)
 

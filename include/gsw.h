@@ -111,6 +111,11 @@ int gsw_context_create(int device, size_t mem_budget_bytes, gsw_ctx **out);
 /* Releases everything the context owns.  Waits for its work to finish. */
 int gsw_context_destroy(gsw_ctx *ctx);
 
+/* Sizes the context's persistent launches for at most `sms` SMs (0: all), so
+ * that work of other streams finds free SMs while this context's kernels
+ * run.  Results do not depend on it.  Errors: GSW_EINVAL (sms < 0). */
+int gsw_context_set_sm_limit(gsw_ctx *ctx, int sms);
+
 /*
  * Aligns npairs pairs: query p is q[q_off[p] .. q_off[p]+q_len[p]), target p
  * is t[t_off[p] .. t_off[p]+t_len[p]).  Lengths may be 0 (score1 = 0).
@@ -241,7 +246,7 @@ int gsw_fill_static(int32_t npairs, const uint8_t *q, const int64_t *q_off, cons
 typedef struct gsw_server gsw_server;
 typedef struct gsw_serve_config {
     int32_t device;
-    int32_t workers;             /* batches in flight; 0 -> 3 */
+    int32_t workers;             /* batches in flight; 0 -> 4 */
     int32_t max_batch_pairs;     /* pairs per batch; 0 -> 8192 */
     int64_t max_batch_letters;   /* query + target letters per batch; 0 -> 16M */
     size_t mem_budget_bytes;     /* device memory of all workers; 0 -> 8 GiB */
@@ -250,6 +255,15 @@ typedef struct gsw_serve_config {
     int32_t mask_len;            /* as gsw_align_batch */
     const int8_t *matrix;        /* alphabet x alphabet, copied */
     int32_t alphabet, gap_open, gap_extend;
+    /* Requests of at least heavy_cells cells (sum of m*n) queue apart and go
+     * to the first heavy_workers workers, whose launches are sized for
+     * heavy_sm_limit SMs; the other workers take only light requests, so a
+     * short request never waits behind a long one.  heavy_workers 0 -> half
+     * the workers (none if there is one), < 0 -> none; heavy_cells 0 -> 2^25,
+     * heavy_sm_limit 0 -> 7/8 of the SMs, < 0 -> all. */
+    int32_t heavy_workers;
+    int64_t heavy_cells;
+    int32_t heavy_sm_limit;
 } gsw_serve_config;
 
 /* Starts the workers.  Errors: GSW_EINVAL (scoring, flags), GSW_ENOMEM, GSW_ECUDA. */
@@ -274,6 +288,22 @@ int gsw_serve_submit(gsw_server *srv, int32_t npairs, const uint8_t *q, const in
  * is kept).  Thread-safe with submit. */
 int gsw_serve_poll(gsw_server *srv, uint64_t req_id, int32_t timeout_us, gsw_result *results,
                    uint32_t *cigar, int64_t cigar_capacity, int64_t *cigar_words);
+
+/* Times of one request on the server's monotonic clock (seconds since
+ * gsw_serve_create): queued by submit, taken into a batch by a worker, and
+ * its batch's results on the host. */
+typedef struct gsw_serve_times {
+    double submitted, started, done;
+} gsw_serve_times;
+
+/* gsw_serve_poll that also fills *times (may be NULL) when the request is
+ * complete. */
+int gsw_serve_poll_timed(gsw_server *srv, uint64_t req_id, int32_t timeout_us, gsw_result *results,
+                         uint32_t *cigar, int64_t cigar_capacity, int64_t *cigar_words,
+                         gsw_serve_times *times);
+
+/* The server's clock now (seconds since gsw_serve_create); -1 for NULL. */
+double gsw_serve_now(gsw_server *srv);
 
 typedef struct gsw_serve_stats {
     uint64_t submitted, completed, batches, pairs, cells;

@@ -48,7 +48,8 @@ struct gsw_ctx {
     int device = 0;
     size_t budget = 0;
     size_t used = 0;
-    int sms = 0;
+    int sms = 0;      // SMs the launches are sized for
+    int sms_all = 0;  // SMs of the device
     DevBuf plan_keys, plan_order, plan_small;
     DevBuf fill_cm, fill_bnd;
     DevBuf trace_dirs, trace_ops, band_scr;
@@ -543,13 +544,20 @@ int gsw_context_create(int device, size_t mem_budget_bytes, gsw_ctx **out) {
     if (!c) return set_err(GSW_ENOMEM, "host allocation");
     c->device = device;
     c->budget = mem_budget_bytes ? mem_budget_bytes : ((size_t)4 << 30);
-    cudaError_t e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e = cudaDeviceGetAttribute(&c->sms_all, cudaDevAttrMultiProcessorCount, device);
+    c->sms = c->sms_all;
     if (e == cudaSuccess) e = cudaMallocHost(&c->host_small, 4096);
     if (e != cudaSuccess) {
         delete c;
         return set_err(GSW_ECUDA, "context setup: %s", cudaGetErrorString(e));
     }
     *out = c;
+    return GSW_OK;
+}
+
+int gsw_context_set_sm_limit(gsw_ctx *c, int sms) {
+    if (!c || sms < 0) return set_err(GSW_EINVAL, "context or SM limit");
+    c->sms = (sms == 0 || sms > c->sms_all) ? c->sms_all : sms;
     return GSW_OK;
 }
 

@@ -1,5 +1,9 @@
 // Serving loop behind gsw_serve_* (include/gsw.h): continuous batching of
-// alignment requests over several batch slots ("workers").
+// alignment requests over several batch slots ("workers").  Requests of many
+// cells (long reads) queue apart from the others and go to the heavy workers,
+// whose persistent launches leave a few SMs free, so the light requests'
+// batches start at once beside them instead of waiting behind seconds of
+// long-read work.
 //
 // Each worker owns a context (its own scratch, a share of the memory budget),
 // a stream and pinned host / device staging sized for one batch.  Submitted
@@ -39,9 +43,12 @@ struct Req {
     std::vector<uint32_t> cigar;
     int status = GSW_OK;
     bool done = false;
+    bool heavy = false;
+    double t_submit = 0, t_start = 0, t_done = 0;  // server clock, seconds
 };
 
 struct Worker {
+    bool heavy = false;  // takes heavy requests first (light ones when none is queued)
     gsw_ctx *ctx = nullptr;
     cudaStream_t st = nullptr;
     int32_t cap_pairs = 0;
@@ -61,12 +68,14 @@ struct gsw_server {
     std::vector<int8_t> matrix;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<Req *> queue;
+    std::deque<Req *> queue, heavy_queue;
     std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
     uint64_t next_id = 1;
     bool stop = false;
     std::vector<std::unique_ptr<Worker>> workers;
     gsw_serve_stats stats;
+    Clock::time_point t0 = Clock::now();
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
 
 namespace {
@@ -163,35 +172,48 @@ int run_batch(gsw_server *srv, Worker *w, std::vector<Req *> &batch) {
     return GSW_OK;
 }
 
+// Takes as many whole requests from the head of `q` as fit one batch.
+void take(std::deque<Req *> &q, const Worker *w, std::vector<Req *> &batch) {
+    int32_t pairs = 0;
+    int64_t letters = 0;
+    while (!q.empty()) {
+        Req *r = q.front();
+        if (!batch.empty() && (pairs + r->npairs > w->cap_pairs || letters + r->letters > w->cap_letters)) break;
+        q.pop_front();
+        batch.push_back(r);
+        pairs += r->npairs;
+        letters += r->letters;
+    }
+}
+
 void worker_loop(gsw_server *srv, Worker *w) {
     cudaSetDevice(srv->cfg.device);
     for (;;) {
         std::vector<Req *> batch;
         {
             std::unique_lock<std::mutex> lk(srv->mu);
-            srv->cv_work.wait(lk, [&] { return srv->stop || !srv->queue.empty(); });
-            if (srv->queue.empty()) return;  // stopping and drained
-            int32_t pairs = 0;
-            int64_t letters = 0;
-            while (!srv->queue.empty()) {
-                Req *r = srv->queue.front();
-                if (!batch.empty() && (pairs + r->npairs > w->cap_pairs || letters + r->letters > w->cap_letters)) break;
-                srv->queue.pop_front();
-                batch.push_back(r);
-                pairs += r->npairs;
-                letters += r->letters;
-            }
-            srv->stats.queued = (int32_t)srv->queue.size();
+            // a heavy worker takes heavy requests, else light ones; a light
+            // worker only light ones
+            auto has_work = [&] { return !srv->queue.empty() || (w->heavy && !srv->heavy_queue.empty()); };
+            srv->cv_work.wait(lk, [&] { return srv->stop || has_work(); });
+            if (!has_work()) return;  // stopping and drained
+            if (w->heavy && !srv->heavy_queue.empty()) take(srv->heavy_queue, w, batch);
+            else take(srv->queue, w, batch);
+            srv->stats.queued = (int32_t)(srv->queue.size() + srv->heavy_queue.size());
             srv->stats.running++;
+            const double ts = srv->now();
+            for (Req *r : batch) r->t_start = ts;
         }
         const auto t0 = Clock::now();
         const int rc = run_batch(srv, w, batch);
         const double secs = std::chrono::duration<double>(Clock::now() - t0).count();
         {
             std::lock_guard<std::mutex> lk(srv->mu);
+            const double td = srv->now();
             for (Req *r : batch) {
                 r->status = rc;
                 r->done = true;
+                r->t_done = td;
                 srv->stats.completed++;
                 srv->stats.pairs += r->npairs;
                 srv->stats.cells += r->cells;
@@ -212,11 +234,15 @@ int gsw_serve_create(const gsw_serve_config *cfg_in, gsw_server **out) {
     if (!cfg_in || !out) return GSW_EINVAL;
     *out = nullptr;
     gsw_serve_config c = *cfg_in;
-    if (c.workers <= 0) c.workers = 3;
+    if (c.workers <= 0) c.workers = 4;
     if (c.max_batch_pairs <= 0) c.max_batch_pairs = 8192;
     if (c.max_batch_letters <= 0) c.max_batch_letters = 16 << 20;
     if (c.mem_budget_bytes == 0) c.mem_budget_bytes = (size_t)8 << 30;
     if (c.max_queue_requests <= 0) c.max_queue_requests = 1 << 20;
+    if (c.heavy_workers == 0) c.heavy_workers = c.workers / 2;
+    if (c.heavy_workers < 0) c.heavy_workers = 0;
+    if (c.heavy_workers > c.workers) c.heavy_workers = c.workers;
+    if (c.heavy_cells <= 0) c.heavy_cells = (int64_t)1 << 25;
     if (c.flags & ~(uint32_t)(GSW_BEGIN | GSW_CIGAR)) return GSW_EINVAL;
     if (!c.matrix || c.alphabet < 1 || c.alphabet > gsw::kMaxAlpha || c.gap_extend < 0 || c.gap_open < c.gap_extend ||
         c.gap_open > 255 || c.workers > 64)
@@ -231,7 +257,13 @@ int gsw_serve_create(const gsw_serve_config *cfg_in, gsw_server **out) {
     const size_t share = c.mem_budget_bytes / (size_t)c.workers;
     for (int k = 0; k < c.workers; k++) {
         std::unique_ptr<Worker> w(new Worker());
+        w->heavy = k < c.heavy_workers;
         int rc = alloc_worker(w.get(), c, share);
+        if (rc == GSW_OK && w->heavy && c.heavy_sm_limit >= 0) {
+            int sms = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);
+            rc = gsw_context_set_sm_limit(w->ctx, c.heavy_sm_limit > 0 ? c.heavy_sm_limit : std::max(1, sms * 7 / 8));
+        }
         if (rc != GSW_OK) {
             free_worker(w.get());
             for (auto &x : srv->workers) free_worker(x.get());
@@ -300,20 +332,23 @@ int gsw_serve_submit(gsw_server *srv, int32_t npairs, const uint8_t *q, const in
     r->letters = qn + tn;
     {
         std::lock_guard<std::mutex> lk(srv->mu);
-        if ((int32_t)srv->queue.size() >= srv->cfg.max_queue_requests) return GSW_ENOMEM;
+        if ((int32_t)(srv->queue.size() + srv->heavy_queue.size()) >= srv->cfg.max_queue_requests) return GSW_ENOMEM;
         r->id = srv->next_id++;
+        r->t_submit = srv->now();
         *req_id = r->id;
-        srv->queue.push_back(r.get());
+        // with no heavy worker every request is light
+        r->heavy = srv->cfg.heavy_workers > 0 && r->cells >= srv->cfg.heavy_cells;
+        (r->heavy ? srv->heavy_queue : srv->queue).push_back(r.get());
         srv->stats.submitted++;
-        srv->stats.queued = (int32_t)srv->queue.size();
+        srv->stats.queued = (int32_t)(srv->queue.size() + srv->heavy_queue.size());
         srv->reqs.emplace(r->id, std::move(r));
     }
-    srv->cv_work.notify_one();
+    srv->cv_work.notify_all();  // the request may need a worker of its kind
     return GSW_OK;
 }
 
-int gsw_serve_poll(gsw_server *srv, uint64_t req_id, int32_t timeout_us, gsw_result *results, uint32_t *cigar,
-                   int64_t cigar_capacity, int64_t *cigar_words) {
+int gsw_serve_poll_timed(gsw_server *srv, uint64_t req_id, int32_t timeout_us, gsw_result *results, uint32_t *cigar,
+                         int64_t cigar_capacity, int64_t *cigar_words, gsw_serve_times *times) {
     if (!srv || !results) return GSW_EINVAL;
     std::unique_lock<std::mutex> lk(srv->mu);
     auto it = srv->reqs.find(req_id);
@@ -327,6 +362,11 @@ int gsw_serve_poll(gsw_server *srv, uint64_t req_id, int32_t timeout_us, gsw_res
         return GSW_ECIGAR_SPACE;
     }
     const int status = r->status;
+    if (times) {
+        times->submitted = r->t_submit;
+        times->started = r->t_start;
+        times->done = r->t_done;
+    }
     if (status == GSW_OK) {
         std::memcpy(results, r->res.data(), sizeof(gsw_result) * (size_t)r->npairs);
         if (!r->cigar.empty()) std::memcpy(cigar, r->cigar.data(), 4 * r->cigar.size());
@@ -336,11 +376,18 @@ int gsw_serve_poll(gsw_server *srv, uint64_t req_id, int32_t timeout_us, gsw_res
     return status;
 }
 
+int gsw_serve_poll(gsw_server *srv, uint64_t req_id, int32_t timeout_us, gsw_result *results, uint32_t *cigar,
+                   int64_t cigar_capacity, int64_t *cigar_words) {
+    return gsw_serve_poll_timed(srv, req_id, timeout_us, results, cigar, cigar_capacity, cigar_words, nullptr);
+}
+
+double gsw_serve_now(gsw_server *srv) { return srv ? srv->now() : -1.0; }
+
 int gsw_serve_get_stats(gsw_server *srv, gsw_serve_stats *out) {
     if (!srv || !out) return GSW_EINVAL;
     std::lock_guard<std::mutex> lk(srv->mu);
     *out = srv->stats;
-    out->queued = (int32_t)srv->queue.size();
+    out->queued = (int32_t)(srv->queue.size() + srv->heavy_queue.size());
     return GSW_OK;
 }
 

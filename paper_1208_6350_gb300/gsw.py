@@ -57,7 +57,12 @@ class ServeConfig(ctypes.Structure):
                 ("max_batch_letters", ctypes.c_int64), ("mem_budget_bytes", ctypes.c_size_t),
                 ("max_queue_requests", ctypes.c_int32), ("flags", ctypes.c_uint32), ("mask_len", ctypes.c_int32),
                 ("matrix", ctypes.c_void_p), ("alphabet", ctypes.c_int32), ("gap_open", ctypes.c_int32),
-                ("gap_extend", ctypes.c_int32)]
+                ("gap_extend", ctypes.c_int32), ("heavy_workers", ctypes.c_int32), ("heavy_cells", ctypes.c_int64),
+                ("heavy_sm_limit", ctypes.c_int32)]
+
+
+class ServeTimes(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_double), ("started", ctypes.c_double), ("done", ctypes.c_double)]
 
 
 class ServeStats(ctypes.Structure):
@@ -89,6 +94,8 @@ def load(build_if_missing: bool = True):
     P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
     lib.gsw_context_create.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(P)]
     lib.gsw_context_destroy.argtypes = [P]
+    lib.gsw_context_set_sm_limit.argtypes = [P, ctypes.c_int]
+    lib.gsw_context_set_sm_limit.restype = ctypes.c_int
     lib.gsw_align_batch.argtypes = [P, i32, P, P, P, P, P, P, P, i32, i32, i32, u32, i32, P, P, i64, P,
                                     P, P]
     lib.gsw_profile_create.argtypes = [P, P, i32, P, i32, i32, i32, ctypes.POINTER(P)]
@@ -103,10 +110,14 @@ def load(build_if_missing: bool = True):
     lib.gsw_serve_destroy.argtypes = [P]
     lib.gsw_serve_submit.argtypes = [P, i32, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_uint64)]
     lib.gsw_serve_poll.argtypes = [P, ctypes.c_uint64, i32, P, P, i64, ctypes.POINTER(ctypes.c_int64)]
+    lib.gsw_serve_poll_timed.argtypes = [P, ctypes.c_uint64, i32, P, P, i64, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ServeTimes)]
     lib.gsw_serve_get_stats.argtypes = [P, ctypes.POINTER(ServeStats)]
     for f in (lib.gsw_serve_create, lib.gsw_serve_destroy, lib.gsw_serve_submit, lib.gsw_serve_poll,
-              lib.gsw_serve_get_stats):
+              lib.gsw_serve_poll_timed, lib.gsw_serve_get_stats):
         f.restype = ctypes.c_int
+    lib.gsw_serve_now.argtypes = [P]
+    lib.gsw_serve_now.restype = ctypes.c_double
     lib.gsw_last_stats.argtypes = [P, ctypes.POINTER(GswStats)]
     lib.gsw_last_stats.restype = ctypes.c_int
     lib.gsw_strerror.argtypes = [ctypes.c_int]
@@ -278,11 +289,13 @@ class Context:
 class Server:
     """Continuous-batching server (gsw_serve_*); host numpy arrays in and out."""
 
-    def __init__(self, matrix, gap_open, gap_extend, flags=GSW_CIGAR, mask_len=-1, device=0, workers=3,
-                 max_batch_pairs=8192, max_batch_letters=16 << 20, mem_budget_bytes=8 << 30):
+    def __init__(self, matrix, gap_open, gap_extend, flags=GSW_CIGAR, mask_len=-1, device=0, workers=4,
+                 max_batch_pairs=8192, max_batch_letters=16 << 20, mem_budget_bytes=8 << 30, heavy_workers=0,
+                 heavy_cells=0, heavy_sm_limit=0):
         self._m = np.ascontiguousarray(matrix, dtype=np.int8)
         cfg = ServeConfig(device, workers, max_batch_pairs, max_batch_letters, mem_budget_bytes, 0, flags,
-                          mask_len, self._m.ctypes.data, self._m.shape[0], gap_open, gap_extend)
+                          mask_len, self._m.ctypes.data, self._m.shape[0], gap_open, gap_extend, heavy_workers,
+                          heavy_cells, heavy_sm_limit)
         out = ctypes.c_void_p()
         _check(load().gsw_serve_create(ctypes.byref(cfg), ctypes.byref(out)), "gsw_serve_create")
         self.handle = out.value
@@ -299,18 +312,27 @@ class Server:
                                        _ptr(t_off), _ptr(t_len), ctypes.byref(rid)), "gsw_serve_submit")
         return rid.value
 
-    def poll(self, req_id, npairs, timeout_us=-1, cigar_capacity=None):
-        """Returns (status, results, cigar words) -- results None while pending."""
+    def poll(self, req_id, npairs, timeout_us=-1, cigar_capacity=None, times=False):
+        """Returns (status, results, cigar words) -- results None while pending;
+        with times=True a fourth item: (submitted, started, done) seconds on
+        the server clock."""
         res = np.zeros(npairs, RESULT_DTYPE)
         cap = cigar_capacity if cigar_capacity is not None else 64 * npairs + 64
         cig = np.zeros(max(cap, 1), np.uint32)
         used = ctypes.c_int64()
-        rc = load().gsw_serve_poll(self.handle, req_id, timeout_us, _ptr(res), _ptr(cig), cap, ctypes.byref(used))
+        tm = ServeTimes()
+        rc = load().gsw_serve_poll_timed(self.handle, req_id, timeout_us, _ptr(res), _ptr(cig), cap,
+                                         ctypes.byref(used), ctypes.byref(tm))
         if rc == GSW_ECIGAR_SPACE:
-            return self.poll(req_id, npairs, timeout_us, int(used.value))
+            return self.poll(req_id, npairs, timeout_us, int(used.value), times)
         if rc == GSW_ETIMEDOUT:
-            return rc, None, None
-        return rc, res, cig[: used.value]
+            return (rc, None, None, None) if times else (rc, None, None)
+        out = (rc, res, cig[: used.value])
+        return out + ((tm.submitted, tm.started, tm.done),) if times else out
+
+    def now(self) -> float:
+        """The server clock (seconds since creation)."""
+        return load().gsw_serve_now(self.handle)
 
     def stats(self) -> dict:
         st = ServeStats()

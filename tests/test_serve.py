@@ -41,11 +41,14 @@ def _decode(res, cig, p):
     return oracle.decode_cigar(cig[o:o + n]) if n > 0 else []
 
 
-def test_mixed_stream_equals_alone_and_oracle():
+@pytest.mark.parametrize("heavy_cells", [0, 1 << 20])
+def test_mixed_stream_equals_alone_and_oracle(heavy_cells):
+    # heavy_cells 2^20: the long-read requests queue apart for the heavy
+    # workers (launches capped at 7/8 of the SMs)
     reqs = _requests(60, 3)
     W = wl.dna_matrix(2, -2)
     srv = gsw.Server(W, 3, 1, gsw.GSW_CIGAR, workers=3, max_batch_pairs=256, max_batch_letters=1 << 20,
-                     mem_budget_bytes=3 << 30)
+                     mem_budget_bytes=3 << 30, heavy_cells=heavy_cells)
     ids = [None] * len(reqs)
 
     def submit(lo, hi):
@@ -60,8 +63,9 @@ def test_mixed_stream_equals_alone_and_oracle():
         x.join()
     got = []
     for k, b in enumerate(reqs):
-        rc, res, cig = srv.poll(ids[k], b.npairs)
+        rc, res, cig, tm = srv.poll(ids[k], b.npairs, times=True)
         assert rc == gsw.GSW_OK
+        assert 0 <= tm[0] <= tm[1] <= tm[2] <= srv.now()
         got.append((res, cig))
     st = srv.stats()
     srv.close()
