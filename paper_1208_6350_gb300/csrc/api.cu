@@ -52,7 +52,7 @@ struct gsw_ctx {
     int sms_all = 0;  // SMs of the device
     DevBuf plan_keys, plan_order, plan_small;
     DevBuf fill_cm, fill_bnd;
-    DevBuf trace_dirs, trace_ops, band_scr;
+    DevBuf trace_dirs, trace_ops, band_scr, ring_meta;
     DevBuf misc;  // counters: trace head, cigar cursor, trace need, max lengths
     DevBuf io_q, io_t, io_qoff, io_toff, io_qlen, io_tlen, io_res, io_cigar, io_colmax, io_cmoff;
     DevBuf prof_qoff, prof_qlen;
@@ -146,7 +146,15 @@ int make_scoring(const int8_t *matrix, int32_t A, int32_t O, int32_t X, Scoring 
 }
 
 // device scratch layout of ctx->misc (64-bit words)
-enum MiscSlot { kMiscTraceHead = 0, kMiscCursor = 1, kMiscMaxLen = 2, kMiscValid = 3, kMiscNeed = 4 /* 9 words */, kMiscWords = 16 };
+enum MiscSlot {
+    kMiscTraceHead = 0,
+    kMiscCursor = 1,
+    kMiscMaxLen = 2,
+    kMiscValid = 3,
+    kMiscNeed = 4,   // 9 words: anti-diagonal traceback needs
+    kMiscRing = 13,  // 3 words: wide-band traceback (total words, max words of a pair, max op words)
+    kMiscWords = 16
+};
 
 // event e[k] marks the end of stage k-1 / start of stage k
 int mark(gsw_ctx *ctx, int k, cudaStream_t st) {
@@ -272,11 +280,19 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
         // warp traceback for the pairs the band kernel left (band wider than 32)
         GSW_TRY(plan(kPlanTrace));
         CUDA_TRY(launch_trace_need(bv, sc, misc + kMiscNeed, st));
-        ctx->launches += 1;
+        // wide bands: direction words per pair, prefix over the class
+        const size_t meta_bytes = sizeof(long long) * ((size_t)npairs + 1) + sizeof(int) * ((size_t)npairs + 4);
+        GSW_TRY(ensure(ctx, ctx->ring_meta, meta_bytes));
+        long long *ring_prefix = reinterpret_cast<long long *>(ctx->ring_meta.p);
+        int *ring_final = reinterpret_cast<int *>(ring_prefix + npairs + 1);
+        int *ring_group = ring_final + npairs;
+        CUDA_TRY(launch_ring_needs(bv, sc, pb.order, pb.var_start, ring_prefix, misc + kMiscRing, st));
+        CUDA_TRY(cudaMemsetAsync(ring_group, 0, 3 * sizeof(int), st));
+        ctx->launches += 2;
         unsigned long long *hs = reinterpret_cast<unsigned long long *>(ctx->host_small);
-        CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, 9 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, 12 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
-        unsigned long long need[9];
+        unsigned long long need[12];
         std::memcpy(need, hs, sizeof(need));
         // groups: 0 anti-diagonal (<= 512 diagonals), 1 wide anti-diagonal, 2 row kernel.
         // One scratch pair serves the three launches in turn, partitioned per warp.
@@ -304,6 +320,19 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
             max_dir = std::max<size_t>(max_dir, (size_t)warps * (size_t)g[k].dir);
             max_ops = std::max<size_t>(max_ops, (size_t)warps * (size_t)g[k].ops);
         }
+        // wide bands: the pool of direction words, groups of pairs that fit it
+        const unsigned long long ring_total = need[9], ring_max = need[10], ring_ops = need[11];
+        size_t ring_pool = 0, ring_walk_warps = 0;
+        if (ring_total > 0) {
+            ring_walk_warps = (size_t)ctx->sms * 16;
+            const size_t have_all = room(ctx, ctx->trace_dirs, ctx->trace_ops);
+            const size_t ops_bytes = ring_walk_warps * (size_t)ring_ops * sizeof(uint32_t);
+            size_t cap = have_all > ops_bytes ? (have_all - ops_bytes) / 2 / sizeof(uint32_t) : 0;
+            ring_pool = (size_t)std::min<unsigned long long>(ring_total, cap);
+            if (ring_pool < ring_max) return set_err(GSW_ENOMEM, "wide-band traceback of one pair needs %llu words", ring_max);
+            max_dir = std::max(max_dir, ring_pool);
+            max_ops = std::max(max_ops, ring_walk_warps * (size_t)ring_ops);
+        }
         if (max_dir > 0) {
             GSW_TRY(ensure2(ctx, ctx->trace_dirs, max_dir * sizeof(uint32_t), ctx->trace_ops, max_ops * sizeof(uint32_t)));
             for (int k = 0; k < 3; k++) {
@@ -325,6 +354,31 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
                 } else {
                     CUDA_TRY(launch_traceback(bv, sc, ts, g[k].grid, st));
                     ctx->launches += 1;
+                }
+            }
+            if (ring_total > 0) {
+                RingLaunchArgs ra;
+                ra.b = bv;
+                ra.sc = sc;
+                ra.order = pb.order;
+                ra.var_start = pb.var_start;
+                ra.prefix = ring_prefix;
+                ra.final_h = ring_final;
+                ra.group = ring_group;
+                ra.pool = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
+                ra.pool_words = (long long)ring_pool;
+                ra.bnd = reinterpret_cast<int2 *>(ctx->fill_bnd.p);
+                ra.bnd_stride = 2 * (long long)ncap;
+                ra.slots = (int)slots;
+                ra.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
+                ra.op_words = (long long)ring_ops;
+                ra.walk_warps = (int)ring_walk_warps;
+                // every group but the last fills more than pool - max_pair
+                const unsigned long long per = ring_pool > ring_max ? ring_pool - ring_max : 1;
+                const unsigned long long groups = ring_total <= ring_pool ? 1 : (ring_total + per - 1) / per + 1;
+                for (unsigned long long gi = 0; gi < groups; gi++) {
+                    CUDA_TRY(launch_ring_group(ra, ctx->sms, st));
+                    ctx->launches += 4;
                 }
             }
         }
@@ -568,7 +622,7 @@ int gsw_context_destroy(gsw_ctx *c) {
     DevBuf *all[] = {&c->plan_keys, &c->plan_order, &c->plan_small, &c->fill_cm, &c->fill_bnd, &c->trace_dirs,
                      &c->trace_ops, &c->band_scr, &c->misc, &c->io_q, &c->io_t, &c->io_qoff, &c->io_toff, &c->io_qlen,
                      &c->io_tlen, &c->io_res, &c->io_cigar, &c->io_colmax, &c->io_cmoff, &c->prof_qoff,
-                     &c->prof_qlen};
+                     &c->prof_qlen, &c->ring_meta};
     for (DevBuf *b : all) release(c, *b);
     if (c->host_small) cudaFreeHost(c->host_small);
     for (int k = 0; k <= GSW_NSTAGES; k++)

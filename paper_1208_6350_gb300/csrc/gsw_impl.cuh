@@ -226,6 +226,33 @@ struct PlanBuffers {
 cudaError_t launch_plan(const BatchView &b, const Scoring &sc, int32_t mode, const PlanBuffers &pb,
                         cudaStream_t st);
 
+// Wide-band traceback (trace_ring.cu): banded global fill with direction
+// bits on the CTA strip pipeline, then a warp walk per pair, group by group
+// of pairs whose direction words fit the pool.
+struct RingLaunchArgs {
+    BatchView b;
+    Scoring sc;
+    const int32_t *order;     // plan order
+    const int32_t *var_start; // class boundaries in `order`
+    const long long *prefix;  // [n + 1] from launch_ring_needs
+    int *final_h;             // [n]
+    int *group;               // 3 ints: g0 (zeroed by the caller before the first group), g1, head
+    uint32_t *pool;
+    long long pool_words;
+    int2 *bnd;                // boundary buffers: slots x bnd_stride int2
+    long long bnd_stride;
+    int slots;
+    uint32_t *ops;            // walk: walk_warps x op_words
+    long long op_words;
+    int walk_warps;
+};
+int ring_trace_class();
+int ring_slots_per_cta();
+// prefix sums of the class's direction words; out[0] total, [1] max words of a pair, [2] max op words
+cudaError_t launch_ring_needs(const BatchView &b, const Scoring &sc, const int32_t *order, const int32_t *var_start,
+                              long long *prefix, unsigned long long *out, cudaStream_t st);
+cudaError_t launch_ring_group(const RingLaunchArgs &a, int sms, cudaStream_t st);
+
 struct TraceScratch {
     uint32_t *dirs;         // per warp: dir_words words (global direction bit-planes)
     int64_t dir_words;      // per warp

@@ -1,0 +1,621 @@
+// Banded global Gotoh with the traceback that emits the CIGAR, for bands too
+// wide for the anti-diagonal warp kernels ("Algorithm and implementation",
+// item (1): the banded SW between the beginning and ending positions
+// generates the detailed alignment).
+//
+// Region.  Rows i in [1, la] (query), columns j in [1, lb] (target), row and
+// column 0 the global boundary.  The provable band is the diagonals
+// dlo <= j - i <= dhi (band_range).  Strip x holds rows
+// [1 + 256x, 256(x+1)] and the columns [c0(x), c1(x)] that the band reaches
+// in those rows, so the region computed is a staircase that contains the
+// band.  Any region between the band and the full rectangle gives the
+// canonical traceback: an optimal path lies in the band, so its cells keep
+// their full-rectangle values, and a predecessor that ties on the full
+// rectangle is itself on an optimal path; cells outside the region are -inf.
+//
+// Fill.  One warp per strip, 32 lanes x 8 rows, 32-bit lanes, one target
+// column per lane and step as in the local fill (lane k at step s works on
+// column c0 + s - k, receives H and F of the row above from lane k-1 by
+// shuffle; lane 0 reads the previous strip's bottom row from global memory,
+// one block of 32 columns ahead).  The strips of a pair run on the warps of a
+// CTA in phases separated by a barrier, each strip far enough behind the one
+// above (ring_lag) that every boundary word it reads was written in a
+// completed phase; several pairs are in flight per CTA.  Per cell 4 bits go
+// to global memory: the source of H (0 diagonal, 1 E, 2 F), whether E opened
+// here and whether F opened here; lane k's 8 rows of one step form one word,
+// so a warp writes 128 contiguous bytes per step.
+//
+// Walk.  One warp per pair stages 64 steps x 32 lanes of direction words in
+// shared memory and lane 0 walks from (la, lb) in state H with the fixed
+// preference (diagonal, then E, then F; open before extend), emitting runs
+// (len << 4) | op in reverse, then the warp writes them forward.
+#include "gsw_impl.cuh"
+
+#include <climits>
+
+namespace gsw {
+
+int ring_trace_class() { return 4; }
+
+namespace {
+
+constexpr int kRP = 32;          // lanes per strip
+constexpr int kRR = 8;           // rows per lane
+constexpr int kRS = kRP * kRR;   // rows per strip
+constexpr int kRW = 8;           // warps per CTA
+constexpr int kRC = 64;          // steps per phase
+constexpr int kRSlots = 4;       // pairs in flight per CTA
+constexpr int kRNeg = -(1 << 28);
+constexpr int kRTile = 64;       // steps of direction words the walk stages
+
+// Geometry of one pair's banded DP.
+struct RingGeom {
+    int la, lb, dlo, dhi, nstrips, stride;
+    __device__ int c0(int x) const { return max(1, 1 + x * kRS + dlo); }
+    __device__ int c1(int x) const { return min(lb, min((x + 1) * kRS, la) + dhi); }
+    __device__ long long words() const { return (long long)nstrips * stride * kRP; }
+};
+
+__device__ __forceinline__ bool ring_geom(const gsw_result &r, const Scoring &sc, RingGeom *g) {
+    g->la = r.read_end1 - r.read_begin1 + 1;
+    g->lb = r.ref_end1 - r.ref_begin1 + 1;
+    int dlo, dhi;
+    band_range(g->la, g->lb, r.score1, sc, &dlo, &dhi);
+    g->dlo = dlo;
+    g->dhi = dhi;
+    g->nstrips = (g->la + kRS - 1) / kRS;
+    // steps of the widest strip: its columns plus the 31-step wavefront skew
+    g->stride = min(g->lb, kRS + dhi - dlo) + kRP;
+    return g->la >= 1 && g->lb >= 1 && dlo <= 0 && dhi >= g->lb - g->la;
+}
+
+// Phases strip x+1 trails strip x: strip x writes column j at its step
+// j - c0(x) + 31, strip x+1 reads columns up to c0(x+1) + s + 63 at its step
+// s, and c0(x+1) - c0(x) <= 256, so (lag - 1) * 64 >= 256 + 63 + 31.
+constexpr int kRingLag = 1 + (kRS + 2 * kRP - 1 + kRP - 1 + kRC - 1) / kRC;
+
+// Profile index of (letter a, row r, lane l): lane-minor groups of 4 rows.
+__device__ __forceinline__ int ridx(int a, int r, int l) { return ((a * (kRR / 4) + r / 4) * 32 + l) * 4 + (r & 3); }
+
+struct RingJob {
+    const uint8_t *q, *t;  // q[i - 1], t[j - 1] for grid row i, column j
+    RingGeom g;
+    uint32_t *dirs;        // nstrips x stride x 32 words
+    int2 *bnd;             // 2 x lb boundary words (H, F of a strip's bottom row)
+    int *final_h;          // H(la, lb)
+};
+
+// One strip of the banded fill for lane k of a warp.
+struct BandStrip {
+    RingJob job;
+    const int8_t *W;
+    int A, O, X;
+    uint32_t *psm;
+    int k, x, c0, c1, c1a, nsteps, i0;
+    bool first, last;
+    const int2 *bin;
+    int2 *bout;
+    uint32_t *dout;
+    int H[kRR], E[kRR];
+    int hdiag, xh, xf;
+    int2 b_cur, b_nxt;
+    int nt;  // target letter of the next step
+
+    __device__ void begin(const RingJob &jb, const Scoring &sc, const int8_t *sW, uint32_t *psm_, int lane, int x_) {
+        job = jb;
+        W = sW;
+        A = sc.A;
+        O = sc.O;
+        X = sc.X;
+        psm = psm_;
+        k = lane;
+        x = x_;
+        const RingGeom &g = job.g;
+        c0 = g.c0(x);
+        c1 = g.c1(x);
+        c1a = x > 0 ? g.c1(x - 1) : 0;
+        nsteps = c1 - c0 + 1 + kRP - 1;
+        i0 = 1 + x * kRS + k * kRR;
+        first = x == 0;
+        last = x == g.nstrips - 1;
+        // boundary word of column j at [j - 1]
+        bin = job.bnd + (size_t)((x + 1) & 1) * g.lb;
+        bout = job.bnd + (size_t)(x & 1) * g.lb;
+        dout = job.dirs + (size_t)x * g.stride * kRP;
+        // profile: W(q_i, a) of this lane's rows (0 below the last row)
+        for (int r = 0; r < kRR; r++) {
+            const int i = i0 + r;
+            const int qa = i <= g.la ? min((int)job.q[i - 1], A - 1) : -1;
+            for (int a = 0; a < A; a++) psm[ridx(a, r, k)] = (uint32_t)(qa >= 0 ? (int)W[qa * A + a] : 0);
+        }
+        __syncwarp();
+        // left boundary: column c0 - 1 is column 0 (H = -O - (i-1)X) or outside (-inf)
+#pragma unroll
+        for (int r = 0; r < kRR; r++) {
+            H[r] = c0 == 1 ? -O - (i0 + r - 1) * X : kRNeg;
+            E[r] = c0 == 1 ? H[r] - O : kRNeg;  // E(i, c0)
+        }
+        // H(i0 - 1, c0 - 1), the first diagonal input of lane 0
+        const int ia = i0 - 1, ja = c0 - 1;
+        if (ja == 0) hdiag = ia == 0 ? 0 : -O - (ia - 1) * X;
+        else if (first) hdiag = -O - (ja - 1) * X;
+        else hdiag = ja <= c1a ? bin[ja - 1].x : kRNeg;
+        // H of the row above this lane's first row, at column c0 - 1: lane k
+        // takes it as the diagonal input of its first column
+        xh = c0 == 1 ? (i0 == 1 ? 0 : -O - (i0 - 2) * X) : kRNeg;
+        xf = kRNeg;
+        b_cur = make_int2(kRNeg, kRNeg);
+        b_nxt = b_cur;
+        if (!first) prefetch(0);
+        nt = (c0 - k >= 1 && c0 - k <= c1) ? min((int)job.t[c0 - k - 1], A - 1) : 0;
+    }
+
+    // lane k loads the boundary word of column c0 + s0 + k (columns the strip
+    // above did not reach are -inf)
+    __device__ __forceinline__ void prefetch(int s0) {
+        const int j = c0 + s0 + k;
+        b_nxt = (j <= c1a) ? bin[j - 1] : make_int2(kRNeg, kRNeg);
+    }
+
+    __device__ __forceinline__ void step(int s) {
+        const int j = c0 + s - k;
+        int hin = xh, fin = xf;
+        if (first) {
+            if (k == 0) {
+                hin = -O - (j - 1) * X;  // H(0, j)
+                fin = hin - O;           // F(1, j): F(0, j) = -inf
+            }
+        } else {
+            const int bi = s & (kRP - 1);
+            if (bi == 0) {
+                b_cur = b_nxt;
+                prefetch(s + kRP);
+            }
+            const int hb = __shfl_sync(0xFFFFFFFFu, b_cur.x, bi);
+            const int fb = __shfl_sync(0xFFFFFFFFu, b_cur.y, bi);
+            if (k == 0) {
+                hin = hb;
+                fin = fb;
+            }
+        }
+        const int a = nt;
+        {
+            const int j1 = j + 1;
+            nt = (j1 >= 1 && j1 <= c1) ? min((int)job.t[j1 - 1], A - 1) : 0;
+        }
+        int diag = hdiag;
+        hdiag = hin;
+        int hup = hin, f = fin;
+        uint32_t bits = 0;
+        if (j >= c0 && j <= c1) {
+            int w[kRR];
+#pragma unroll
+            for (int r = 0; r < kRR; r += 4) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(psm + ridx(a, r, k));
+                w[r] = (int)v.x; w[r + 1] = (int)v.y; w[r + 2] = (int)v.z; w[r + 3] = (int)v.w;
+            }
+#pragma unroll
+            for (int r = 0; r < kRR; r++) {
+                const int hleft = H[r];
+                const int e = E[r];
+                const bool eo = e == hleft - O;
+                const bool fo = f == hup - O;
+                const int dw = diag + w[r];
+                const int h = max(max(dw, e), f);
+                const uint32_t src = h == dw ? 0u : (h == e ? 1u : 2u);
+                bits |= (src | (eo ? 4u : 0u) | (fo ? 8u : 0u)) << (4 * r);
+                const int ho = h - O;
+                E[r] = max(ho, e - X);
+                f = max(ho, f - X);
+                diag = hleft;
+                hup = h;
+                H[r] = h;
+            }
+            if (i0 <= job.g.la && job.g.la < i0 + kRR && j == job.g.lb) {
+#pragma unroll
+                for (int r = 0; r < kRR; r++)
+                    if (i0 + r == job.g.la) *job.final_h = H[r];
+            }
+            if (k == kRP - 1 && !last) bout[j - 1] = make_int2(H[kRR - 1], f);
+        }
+        dout[(size_t)s * kRP + k] = bits;
+        xh = __shfl_up_sync(0xFFFFFFFFu, H[kRR - 1], 1);
+        xf = __shfl_up_sync(0xFFFFFFFFu, f, 1);
+    }
+
+    // steps [s0, s1); true when the strip is complete
+    __device__ bool run(int s0, int s1) {
+        s1 = min(s1, nsteps);
+#pragma unroll 1
+        for (int s = s0; s < s1; s++) step(s);
+        return s1 >= nsteps;
+    }
+};
+
+struct RingSlot {
+    RingJob job;
+    int pair;        // -1: free
+    int seq;
+    int next;        // next strip to hand out
+    int last_start;  // phase the last handed-out strip started
+    int running;
+};
+
+struct RingCmd {
+    int slot, strip, start;
+};
+
+struct RingShared {
+    RingSlot slot[kRSlots];
+    RingCmd cmd[kRW];
+    int ended[kRW];
+    int seq, exhausted, done;
+};
+// (kRW warps per CTA, or kRW / 2 when a large alphabet's profiles would not
+// fit the shared memory of 8 warps)
+
+// Pairs of the ring class in plan order: t in [g0, g1) of the group; the
+// pair's direction words start at prefix[t] - prefix[g0] in the pool.
+struct RingLaunch {
+    BatchView b;
+    Scoring sc;
+    const int32_t *order;     // sorted pair indices (the class starts at var_start[cls])
+    const int32_t *var_start;
+    int cls;
+    const long long *prefix;  // [n + 1] direction words before each pair of the class
+    int *final_h;             // [n]
+    int *group;               // [0] g0, [1] g1, [2] head
+    uint32_t *pool;
+    long long pool_words;
+    int2 *bnd;                // per slot 2 x ncap
+    long long bnd_stride;     // int2 per slot
+    uint32_t *ops;            // walk: per warp op_words
+    long long op_words;
+};
+
+__device__ bool ring_open(const RingLaunch &rl, RingSlot &S, int s, int seq) {
+    const int g0 = rl.group[0], g1 = rl.group[1];
+    const int t = g0 + atomicAdd(&rl.group[2], 1);
+    if (t >= g1) return false;
+    const int pair = rl.order[rl.var_start[rl.cls] + t];
+    const gsw_result r = rl.b.res[pair];
+    RingJob jb;
+    if (!ring_geom(r, rl.sc, &jb.g) || jb.g.words() > rl.pool_words || 2LL * jb.g.lb > rl.bnd_stride) {
+        rl.b.res[pair].flags |= kResInternal;
+        rl.final_h[t] = INT_MIN;
+        S.pair = -1;
+        return true;  // taken (and rejected); try the next one
+    }
+    jb.q = rl.b.q + rl.b.q_off[pair] + r.read_begin1;
+    jb.t = rl.b.t + rl.b.t_off[pair] + r.ref_begin1;
+    jb.dirs = rl.pool + (rl.prefix[t] - rl.prefix[g0]);
+    jb.bnd = rl.bnd + (size_t)(blockIdx.x * kRSlots + s) * rl.bnd_stride;
+    jb.final_h = rl.final_h + t;
+    rl.final_h[t] = INT_MIN;
+    S.job = jb;
+    S.pair = pair;
+    S.seq = seq;
+    S.next = 0;
+    S.last_start = 0;
+    S.running = 0;
+    return true;
+}
+
+__device__ void ring_schedule(const RingLaunch &rl, RingShared &sh, int ph, int nw) {
+    for (int w = 0; w < nw; w++) {
+        if (!sh.ended[w]) continue;
+        sh.ended[w] = 0;
+        RingSlot &S = sh.slot[sh.cmd[w].slot];
+        S.running--;
+        if (S.running == 0 && S.next == S.job.g.nstrips) S.pair = -1;
+        sh.cmd[w].slot = -1;
+    }
+    for (int w = 0; w < nw; w++) {
+        RingCmd &c = sh.cmd[w];
+        if (c.slot >= 0) continue;
+        int pick = -1, best = INT_MAX;
+        for (int s = 0; s < kRSlots; s++) {
+            const RingSlot &S = sh.slot[s];
+            if (S.pair >= 0 && S.next < S.job.g.nstrips && (S.next == 0 || ph >= S.last_start + kRingLag) &&
+                S.seq < best) {
+                best = S.seq;
+                pick = s;
+            }
+        }
+        while (pick < 0 && !sh.exhausted) {
+            int fs = -1;
+            for (int s = 0; s < kRSlots; s++)
+                if (sh.slot[s].pair < 0) { fs = s; break; }
+            if (fs < 0) break;
+            if (!ring_open(rl, sh.slot[fs], fs, sh.seq)) {
+                sh.exhausted = 1;
+                break;
+            }
+            if (sh.slot[fs].pair >= 0) {
+                sh.seq++;
+                pick = fs;
+            }
+        }
+        if (pick < 0) break;
+        RingSlot &S = sh.slot[pick];
+        c.slot = pick;
+        c.strip = S.next++;
+        c.start = ph;
+        S.last_start = ph;
+        S.running++;
+    }
+    bool busy = !sh.exhausted;
+    for (int s = 0; s < kRSlots; s++) busy |= sh.slot[s].pair >= 0;
+    sh.done = busy ? 0 : 1;
+}
+
+template <bool DNA>
+__global__ void __launch_bounds__(kRW * 32, 1) k_trace_ring(RingLaunch rl) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ RingShared sh;
+    __shared__ int8_t sW[kMaxAlpha * kMaxAlpha];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int A = DNA ? 4 : rl.sc.A;
+    for (int i = threadIdx.x; i < rl.sc.A * rl.sc.A; i += blockDim.x) sW[i] = rl.sc.W[i];
+    uint32_t *psm = smem + (size_t)warp * A * kRR * 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kRSlots; s++) sh.slot[s].pair = -1;
+        for (int w = 0; w < kRW; w++) {
+            sh.cmd[w].slot = -1;
+            sh.ended[w] = 0;
+        }
+        sh.seq = 0;
+        sh.exhausted = 0;
+        sh.done = 0;
+    }
+    BandStrip bs;
+#pragma unroll 1
+    for (int ph = 0;; ph++) {
+        __syncthreads();
+        if (threadIdx.x == 0) ring_schedule(rl, sh, ph, nw);
+        __syncthreads();
+        if (sh.done) break;
+        const RingCmd cmd = sh.cmd[warp];
+        if (cmd.slot < 0) continue;
+        if (ph == cmd.start) bs.begin(sh.slot[cmd.slot].job, rl.sc, sW, psm, lane, cmd.strip);
+        const int q = ph - cmd.start;
+        if (bs.run(q * kRC, (q + 1) * kRC) && lane == 0) sh.ended[warp] = 1;
+    }
+}
+
+// Group t in [g0, g1): the pairs whose direction words fit the pool.
+__global__ void k_ring_group(const long long *prefix, const int32_t *var_start, int cls, long long pool_words,
+                             int *group) {
+    const int n = var_start[cls + 1] - var_start[cls];
+    const int g0 = group[0];
+    int lo = g0, hi = n;  // largest g1 with prefix[g1] - prefix[g0] <= pool
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] - prefix[g0] <= pool_words) lo = mid;
+        else hi = mid - 1;
+    }
+    group[1] = (lo == g0 && g0 < n) ? g0 + 1 : lo;  // a pair beyond the pool is rejected alone
+    group[2] = 0;
+}
+
+__global__ void k_ring_advance(int *group) { group[0] = group[1]; }
+
+// Direction words (and walk op words) of each pair of the class, then the
+// exclusive prefix over the class in plan order (one block).
+__global__ void __launch_bounds__(1024) k_ring_needs(BatchView b, Scoring sc, const int32_t *order,
+                                                     const int32_t *var_start, int cls, long long *prefix,
+                                                     unsigned long long *out) {
+    const int cls_start = var_start[cls], n = var_start[cls + 1] - cls_start;
+    __shared__ long long part[1024];
+    __shared__ long long carry;
+    __shared__ unsigned long long mx_words, mx_ops;
+    if (threadIdx.x == 0) {
+        carry = 0;
+        mx_words = 0;
+        mx_ops = 0;
+    }
+    __syncthreads();
+    for (int base = 0; base < n; base += 1024) {
+        const int t = base + threadIdx.x;
+        long long w = 0;
+        if (t < n) {
+            const gsw_result r = b.res[order[cls_start + t]];
+            RingGeom g;
+            if (ring_geom(r, sc, &g)) {
+                w = g.words();
+                atomicMax(&mx_words, (unsigned long long)w);
+                atomicMax(&mx_ops, (unsigned long long)(g.la + g.lb + 2));
+            }
+        }
+        part[threadIdx.x] = w;
+        __syncthreads();
+        for (int d = 1; d < 1024; d <<= 1) {
+            const long long v = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+            __syncthreads();
+            part[threadIdx.x] += v;
+            __syncthreads();
+        }
+        if (t < n) prefix[t] = carry + part[threadIdx.x] - w;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += part[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        prefix[n] = carry;
+        out[0] = (unsigned long long)carry;
+        out[1] = mx_words;
+        out[2] = mx_ops;
+    }
+}
+
+// Walk of one pair by one warp (see the file comment).
+__global__ void __launch_bounds__(128) k_ring_walk(RingLaunch rl) {
+    __shared__ uint32_t tile[4][kRTile * kRP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gwarp = blockIdx.x * 4 + warp, nwarps = gridDim.x * 4;
+    uint32_t *stage = tile[warp];
+    uint32_t *ops = rl.ops + (size_t)gwarp * rl.op_words;
+    const int g0 = rl.group[0], g1 = rl.group[1];
+    for (int t = g0 + gwarp; t < g1; t += nwarps) {
+        const int pair = rl.order[rl.var_start[rl.cls] + t];
+        gsw_result *rp = rl.b.res + pair;
+        const gsw_result r = *rp;
+        RingGeom g;
+        bool ok = ring_geom(r, rl.sc, &g) && rl.final_h[t] == r.score1 && g.la + g.lb + 2 <= rl.op_words;
+        if (!ok) {
+            if (lane == 0 && !(r.flags & kResInternal)) rp->flags |= kResInternal;
+            continue;
+        }
+        const uint32_t *dirs = rl.pool + (rl.prefix[t] - rl.prefix[g0]);
+        int i = g.la, j = g.lb, st = 0, cur = -1, len = 0, runs = 0;
+        int tx = -1, ts_hi = -1;  // staged tile: strip, top step
+        while (ok && i > 0 && j > 0) {
+            const int x = (i - 1) / kRS;
+            const int k = ((i - 1) % kRS) / kRR;
+            if (j < g.c0(x) || j > g.c1(x)) {  // left the region (never for an optimal path)
+                ok = false;
+                break;
+            }
+            const int s = j - g.c0(x) + k;
+            if (x != tx || s > ts_hi || s <= ts_hi - kRTile) {
+                tx = x;
+                ts_hi = s;
+                const int lo = max(0, s - kRTile + 1);
+                const uint32_t *src = dirs + ((size_t)x * g.stride + lo) * kRP;
+                for (int w = lane; w < (s - lo + 1) * kRP; w += 32) stage[w + (kRTile - 1 - (s - lo)) * kRP] = src[w];
+                __syncwarp();
+            }
+            if (lane == 0) {
+                // walk inside the staged tile
+                for (;;) {
+                    if (i <= 0 || j <= 0) break;
+                    const int x2 = (i - 1) / kRS;
+                    if (x2 != tx) break;
+                    if (j < g.c0(x2) || j > g.c1(x2)) { ok = false; break; }  // left the region
+                    const int k2 = ((i - 1) % kRS) / kRR, r2 = (i - 1) % kRR;
+                    const int s2 = j - g.c0(x2) + k2;
+                    if (s2 > ts_hi || s2 <= ts_hi - kRTile) break;
+                    const uint32_t wd = stage[(kRTile - 1 - (ts_hi - s2)) * kRP + k2] >> (4 * r2);
+                    int op;
+                    if (st == 0) {
+                        const int src = wd & 3;
+                        if (src == 0) { op = GSW_CIGAR_M; i--; j--; }
+                        else { st = src; continue; }
+                    } else if (st == 1) {
+                        op = GSW_CIGAR_D; st = (wd & 4) ? 0 : 1; j--;
+                    } else {
+                        op = GSW_CIGAR_I; st = (wd & 8) ? 0 : 2; i--;
+                    }
+                    if (op == cur) {
+                        len++;
+                    } else {
+                        if (len) ops[runs++] = ((uint32_t)len << 4) | (uint32_t)cur;
+                        cur = op;
+                        len = 1;
+                    }
+                }
+            }
+            ok = __shfl_sync(0xFFFFFFFFu, (int)ok, 0);
+            i = __shfl_sync(0xFFFFFFFFu, i, 0);
+            j = __shfl_sync(0xFFFFFFFFu, j, 0);
+            __syncwarp();
+        }
+        if (lane == 0 && ok) {
+            // row 0 or column 0: the rest is one gap (D along row 0, I along column 0)
+            const int rest_op = i == 0 ? GSW_CIGAR_D : GSW_CIGAR_I;
+            const int rest = i == 0 ? j : i;
+            if (rest > 0) {
+                if (rest_op == cur) {
+                    len += rest;
+                } else {
+                    if (len) ops[runs++] = ((uint32_t)len << 4) | (uint32_t)cur;
+                    cur = rest_op;
+                    len = rest;
+                }
+            }
+            if (len) ops[runs++] = ((uint32_t)len << 4) | (uint32_t)cur;
+        }
+        const int nr = __shfl_sync(0xFFFFFFFFu, runs, 0);
+        if (!ok) {
+            if (lane == 0) rp->flags |= kResInternal;
+            __syncwarp();
+            continue;
+        }
+        unsigned long long off = 0;
+        if (lane == 0) off = atomicAdd(rl.b.cigar_cursor, (unsigned long long)nr);
+        off = __shfl_sync(0xFFFFFFFFu, off, 0);
+        if ((long long)(off + nr) > rl.b.cigar_cap) {
+            if (lane == 0) {
+                rp->flags |= GSW_RES_CIGAR_SPACE;
+                rp->cigar_len = -nr;
+                rp->cigar_off = -1;
+                rp->flags &= ~kResPendingTrace;
+            }
+            __syncwarp();
+            continue;
+        }
+        __syncwarp();
+        for (int q = lane; q < nr; q += 32) rl.b.cigar[off + q] = ops[nr - 1 - q];
+        if (lane == 0) {
+            rp->cigar_len = nr;
+            rp->cigar_off = (int64_t)off;
+            rp->flags &= ~kResPendingTrace;
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_ring_needs(const BatchView &b, const Scoring &sc, const int32_t *order, const int32_t *var_start,
+                              long long *prefix, unsigned long long *out, cudaStream_t st) {
+    k_ring_needs<<<1, 1024, 0, st>>>(b, sc, order, var_start, ring_trace_class(), prefix, out);
+    return cudaGetLastError();
+}
+
+// One group: bounds, banded fill, walk, advance.  `rl` holds the pool, the
+// slot boundary buffers and the walk's op buffers.
+cudaError_t launch_ring_group(const RingLaunchArgs &a, int sms, cudaStream_t st) {
+    RingLaunch rl;
+    rl.b = a.b;
+    rl.sc = a.sc;
+    rl.order = a.order;
+    rl.var_start = a.var_start;
+    rl.cls = ring_trace_class();
+    rl.prefix = a.prefix;
+    rl.final_h = a.final_h;
+    rl.group = a.group;
+    rl.pool = a.pool;
+    rl.pool_words = a.pool_words;
+    rl.bnd = a.bnd;
+    rl.bnd_stride = a.bnd_stride;
+    rl.ops = a.ops;
+    rl.op_words = a.op_words;
+    k_ring_group<<<1, 1, 0, st>>>(a.prefix, a.var_start, rl.cls, a.pool_words, a.group);
+    const bool dna = a.sc.dna4 != 0;
+    const int A = dna ? 4 : a.sc.A;
+    const size_t per_warp = (size_t)A * kRR * 32 * sizeof(uint32_t);
+    const int nw = per_warp * kRW <= 200 * 1024 ? kRW : kRW / 2;
+    const size_t smem = per_warp * nw;
+    int nb = 0;
+    if (dna) {
+        cudaFuncSetAttribute(k_trace_ring<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace_ring<true>, nw * 32, smem);
+    } else {
+        cudaFuncSetAttribute(k_trace_ring<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace_ring<false>, nw * 32, smem);
+    }
+    if (nb < 1) return cudaErrorInvalidConfiguration;
+    const int grid = std::min(sms * nb, a.slots / kRSlots);
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    if (dna) k_trace_ring<true><<<grid, nw * 32, smem, st>>>(rl);
+    else k_trace_ring<false><<<grid, nw * 32, smem, st>>>(rl);
+    const int wgrid = std::max(1, a.walk_warps / 4);
+    k_ring_walk<<<wgrid, 128, 0, st>>>(rl);
+    k_ring_advance<<<1, 1, 0, st>>>(a.group);
+    return cudaGetLastError();
+}
+
+int ring_slots_per_cta() { return kRSlots; }
+
+}  // namespace gsw

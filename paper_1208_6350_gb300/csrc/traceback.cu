@@ -80,9 +80,9 @@ __global__ void k_trace_need(BatchView b, Scoring sc, unsigned long long *max_ne
     unsigned v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (p < b.npairs) {
         const gsw_result r = b.res[p];
-        if (wants_trace(r)) {
-            const Need nd = pair_need(r, sc);
-            const int g = nd.nch == 0 ? 0 : (nd.nch > 0 ? 3 : 6);
+        const Need nd = wants_trace(r) ? pair_need(r, sc) : Need{0, 0, 1, 0, 0};
+        if (nd.nch == 0) {  // at most 512 diagonals (wider bands: trace_ring.cu)
+            const int g = 0;
             v[g] = (unsigned)min(nd.dir, (long long)UINT_MAX);
             v[g + 1] = (unsigned)min(nd.ops, (long long)UINT_MAX);
             v[g + 2] = (unsigned)(nd.nch < 0 ? -nd.nch : (nd.nch > 0 ? nd.nch : 1));
