@@ -151,8 +151,8 @@ enum MiscSlot {
     kMiscCursor = 1,
     kMiscMaxLen = 2,
     kMiscValid = 3,
-    kMiscNeed = 4,   // 9 words: anti-diagonal traceback needs
-    kMiscRing = 13,  // 3 words: wide-band traceback (total words, max words of a pair, max op words)
+    kMiscNeed = 4,   // 2 words: anti-diagonal traceback (direction words, op words per pair)
+    kMiscRing = 6,   // 3 words: wide-band traceback (total words, max words of a pair, max op words)
     kMiscWords = 16
 };
 
@@ -277,7 +277,9 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
     GSW_TRY(mark(ctx, 5, st));
 
     if (bv.flags & GSW_CIGAR) {
-        // warp traceback for the pairs the band kernel left (band wider than 32)
+        // tracebacks for the pairs the band kernel left (band wider than 32 or
+        // more than 4096 rows): anti-diagonal warp kernel up to 512 diagonals,
+        // CTA strip kernel beyond
         GSW_TRY(plan(kPlanTrace));
         CUDA_TRY(launch_trace_need(bv, sc, misc + kMiscNeed, st));
         // wide bands: direction words per pair, prefix over the class
@@ -290,38 +292,26 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
         CUDA_TRY(cudaMemsetAsync(ring_group, 0, 3 * sizeof(int), st));
         ctx->launches += 2;
         unsigned long long *hs = reinterpret_cast<unsigned long long *>(ctx->host_small);
-        CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, 12 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
-        unsigned long long need[12];
+        unsigned long long need[5];
         std::memcpy(need, hs, sizeof(need));
-        // groups: 0 anti-diagonal (<= 512 diagonals), 1 wide anti-diagonal, 2 row kernel.
-        // One scratch pair serves the three launches in turn, partitioned per warp.
-        struct Grp {
-            long long dir, ops;
-            int warps, grid;
-        } g[3];
-        const size_t have = room(ctx, ctx->trace_dirs, ctx->trace_ops) / 2;
+        // anti-diagonal kernel (<= 512 diagonals): direction and op words per warp
+        const long long ad_dir = (long long)need[0], ad_ops = std::max<long long>((long long)need[1], 64);
+        int ad_grid = 0;
         size_t max_dir = 0, max_ops = 0;
-        for (int k = 0; k < 3; k++) {
-            g[k].dir = std::max<long long>((long long)need[3 * k], 0);
-            g[k].ops = std::max<long long>((long long)need[3 * k + 1], 0);
-            if (k == 2) g[k].ops += 64 * (long long)need[8];
-            g[k].warps = 0;
-            g[k].grid = 0;
-            if (g[k].dir == 0) continue;
-            g[k].dir = std::max<long long>(g[k].dir, 64);
-            g[k].ops = std::max<long long>(g[k].ops, 64);
-            const size_t per_warp = (size_t)(g[k].dir + g[k].ops) * sizeof(uint32_t);
-            int want = k == 0 ? ctx->sms * 16 * (trace_block_threads() / 32) : (k == 1 ? ctx->sms * 2 : ctx->sms * 2 * (trace_block_threads() / 32));
-            int warps = (int)std::min<size_t>((size_t)want, std::max<size_t>(1, have / per_warp));
-            if (k != 1) warps = std::max(trace_block_threads() / 32, warps - warps % (trace_block_threads() / 32));
-            g[k].warps = warps;
-            g[k].grid = k == 1 ? warps : warps / (trace_block_threads() / 32);
-            max_dir = std::max<size_t>(max_dir, (size_t)warps * (size_t)g[k].dir);
-            max_ops = std::max<size_t>(max_ops, (size_t)warps * (size_t)g[k].ops);
+        const int wpb = trace_block_threads() / 32;
+        if (ad_dir > 0) {
+            const size_t have = room(ctx, ctx->trace_dirs, ctx->trace_ops) / 2;
+            const size_t per_warp = (size_t)(ad_dir + ad_ops) * sizeof(uint32_t);
+            int warps = (int)std::min<size_t>((size_t)ctx->sms * 16 * wpb, std::max<size_t>(1, have / per_warp));
+            warps = std::max(wpb, warps - warps % wpb);
+            ad_grid = warps / wpb;
+            max_dir = (size_t)warps * (size_t)ad_dir;
+            max_ops = (size_t)warps * (size_t)ad_ops;
         }
         // wide bands: the pool of direction words, groups of pairs that fit it
-        const unsigned long long ring_total = need[9], ring_max = need[10], ring_ops = need[11];
+        const unsigned long long ring_total = need[2], ring_max = need[3], ring_ops = need[4];
         size_t ring_pool = 0, ring_walk_warps = 0;
         if (ring_total > 0) {
             ring_walk_warps = (size_t)ctx->sms * 16;
@@ -335,26 +325,16 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
         }
         if (max_dir > 0) {
             GSW_TRY(ensure2(ctx, ctx->trace_dirs, max_dir * sizeof(uint32_t), ctx->trace_ops, max_ops * sizeof(uint32_t)));
-            for (int k = 0; k < 3; k++) {
-                if (g[k].warps == 0) continue;
+            if (ad_grid > 0) {
                 TraceScratch ts;
                 ts.dirs = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
-                ts.dir_words = g[k].dir;
+                ts.dir_words = ad_dir;
                 ts.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
-                ts.op_words = g[k].ops;
+                ts.op_words = ad_ops;
                 ts.order = pb.order;
                 ts.var_start = pb.var_start;
-                if (k == 0) {
-                    CUDA_TRY(launch_trace_ad(bv, sc, ts, g[k].grid, st));
-                    ctx->launches += 4;
-                } else if (k == 1) {
-                    const int nch_max = (int)std::min<unsigned long long>(need[5], (unsigned long long)trace_adw_max_chunks());
-                    CUDA_TRY(launch_trace_adw(bv, sc, ts, g[k].grid, nch_max, st));
-                    ctx->launches += 1;
-                } else {
-                    CUDA_TRY(launch_traceback(bv, sc, ts, g[k].grid, st));
-                    ctx->launches += 1;
-                }
+                CUDA_TRY(launch_trace_ad(bv, sc, ts, ad_grid, st));
+                ctx->launches += 4;
             }
             if (ring_total > 0) {
                 RingLaunchArgs ra;

@@ -262,19 +262,11 @@ struct TraceScratch {
     const int32_t *var_start;
 };
 int trace_block_threads();
-size_t trace_smem_bytes();
-// max over the batch, per kernel group (anti-diagonal <= 512 wide, wide
-// anti-diagonal, row kernel): [3g] direction words, [3g+1] op words, [3g+2] chunks
+// largest needs of a pair of the anti-diagonal classes: [0] direction words, [1] op words
 cudaError_t launch_trace_need(const BatchView &b, const Scoring &sc, unsigned long long *max_need,
                               cudaStream_t st);
-cudaError_t launch_traceback(const BatchView &b, const Scoring &sc, const TraceScratch &ts, int grid,
-                             cudaStream_t st);
 cudaError_t launch_trace_ad(const BatchView &b, const Scoring &sc, const TraceScratch &ts, int grid,
                             cudaStream_t st);
-size_t trace_adw_smem(int nch_max);
-int trace_adw_max_chunks();
-cudaError_t launch_trace_adw(const BatchView &b, const Scoring &sc, const TraceScratch &ts, int grid, int nch_max,
-                             cudaStream_t st);
 
 int band_block_threads();
 cudaError_t launch_band(const BatchView &b, const Scoring &sc, const PlanBuffers &pb, void *scratch,

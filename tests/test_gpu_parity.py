@@ -253,3 +253,33 @@ def test_cta_kernel_general_alphabet(ctx):
     b = _batch(qs, ts, wl.synthetic_protein_matrix(), 11, 1, "protein-long",
                "ARNDCQEGHILKMFPSTWYV")
     compare(b, run_oracle(b), run_gpu_host(ctx, b))
+
+
+def _indel_pairs(rng, specs, p_sub=0.05):
+    """Queries from a random source with one inserted block and/or one deleted
+    block (bands clipped by either end of the alignment), targets = random
+    flanks + the source."""
+    qs, ts = [], []
+    for L, ins, dele in specs:
+        s = rng.integers(0, 4, L).astype(np.uint8)
+        q = np.concatenate([s[: L // 3], rng.integers(0, 4, ins).astype(np.uint8), s[L // 3:]])
+        if dele:
+            c = 2 * len(q) // 3
+            q = np.concatenate([q[:c], q[c + dele:]])
+        mut = rng.random(len(q)) < p_sub
+        q[mut] = rng.integers(0, 4, int(mut.sum()))
+        t = np.concatenate([rng.integers(0, 4, 200), s, rng.integers(0, 4, 150)]).astype(np.uint8)
+        qs.append(q)
+        ts.append(t)
+    return qs, ts
+
+
+@pytest.mark.parametrize("O,X", [(4, 2), (3, 3), (5, 0)])
+def test_wide_band_traceback_indels_and_gap_costs(ctx, O, X):
+    # bands of 600 to all diagonals (extend 0: every diagonal) through the CTA
+    # strip traceback: a 300-letter insertion, a 300-letter deletion, both,
+    # and open == extend (the open bit of every gap cell)
+    rng = np.random.default_rng(31 + O + X)
+    qs, ts = _indel_pairs(rng, [(2500, 300, 0), (2500, 0, 300), (3000, 150, 150), (1800, 0, 0)])
+    b = _batch(qs, ts, wl.dna_matrix(2, -4), O, X, "indels")
+    compare(b, run_oracle(b), run_gpu_host(ctx, b))
