@@ -481,10 +481,15 @@ def run_serving(rates, n_requests, head, gsw, dev_name=""):
         reqs = serving_requests(rate, n_requests)
         arr_span = reqs[-1][0] if reqs else 0.0
         lat, qd, span, cells, out, st = serve_trace(gsw, reqs, W, O, X)
+        kinds = np.array([k for _, k, _ in reqs])
+        lat_a, qd_a = np.asarray(lat), np.asarray(qd)
+        by_kind = {name: _latency_summary(lat_a[kinds == k], qd_a[kinds == k])
+                   for k, name in ((1, "short_100x1000"), (2, "short_read_extension"), (3, "long_reads"))
+                   if (kinds == k).any()}
         row = {"rate_req_s": rate, "requests": len(reqs),
                "offered_gcups": round(cells / max(arr_span, 1e-9) / 1e9, 1),
                "achieved_gcups": round(cells / span / 1e9, 1), "server": _latency_summary(lat, qd),
-               "batches": int(st["batches"])}
+               "server_by_kind": by_kind, "batches": int(st["batches"])}
         if head:
             hr = reqs[:head]
             hlat, _, _, _, hout, _ = serve_trace(gsw, hr, W, O, X)

@@ -50,6 +50,8 @@ struct gsw_ctx {
     size_t used = 0;
     int sms = 0;      // SMs the launches are sized for
     int sms_all = 0;  // SMs of the device
+    cudaMemPool_t pool = nullptr;  // stream-ordered scratch allocations
+    cudaStream_t st = nullptr;     // stream of the call in progress
     DevBuf plan_keys, plan_order, plan_small;
     DevBuf fill_cm, fill_bnd;
     DevBuf trace_dirs, trace_ops, band_scr, ring_meta;
@@ -72,14 +74,15 @@ struct gsw_profile {
 
 namespace {
 
-// Grows `b` to at least `need` bytes (never shrinks).  Synchronizes the device
-// before releasing an old allocation that queued work may still use.
+// Grows `b` to at least `need` bytes (never shrinks).  Allocation and release
+// are stream-ordered on the call's stream (the context's own memory pool), so
+// growing a buffer waits for no other stream's work: work queued on this
+// stream that uses the old buffer runs before it is released.
 int ensure(gsw_ctx *ctx, DevBuf &b, size_t need) {
     if (need <= b.bytes) return GSW_OK;
     need = std::max<size_t>(need, 256);
     if (b.p) {
-        CUDA_TRY(cudaDeviceSynchronize());
-        CUDA_TRY(cudaFree(b.p));
+        CUDA_TRY(cudaFreeAsync(b.p, ctx->st));
         ctx->used -= b.bytes;
         b.p = nullptr;
         b.bytes = 0;
@@ -87,10 +90,10 @@ int ensure(gsw_ctx *ctx, DevBuf &b, size_t need) {
     if (ctx->used + need > ctx->budget)
         return set_err(GSW_ENOMEM, "scratch of %zu bytes exceeds the context budget (%zu used of %zu)", need,
                        ctx->used, ctx->budget);
-    cudaError_t e = cudaMalloc(&b.p, need);
+    cudaError_t e = cudaMallocFromPoolAsync(&b.p, need, ctx->pool, ctx->st);
     if (e != cudaSuccess) {
         b.p = nullptr;
-        return set_err(GSW_ENOMEM, "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+        return set_err(GSW_ENOMEM, "scratch allocation of %zu bytes: %s", need, cudaGetErrorString(e));
     }
     b.bytes = need;
     ctx->used += need;
@@ -98,10 +101,7 @@ int ensure(gsw_ctx *ctx, DevBuf &b, size_t need) {
 }
 
 void release(gsw_ctx *ctx, DevBuf &b) {
-    if (b.p) {
-        cudaDeviceSynchronize();
-        cudaFree(b.p);
-    }
+    if (b.p) cudaFreeAsync(b.p, ctx->st);
     ctx->used -= b.bytes;
     b.p = nullptr;
     b.bytes = 0;
@@ -390,6 +390,7 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
     if ((flags & GSW_COLMAX) && (!colmax || !colmax_off)) return set_err(GSW_EINVAL, "colmax output missing");
     if (mask_len > (1 << 30)) return set_err(GSW_EINVAL, "mask_len too large");
     CUDA_TRY(cudaSetDevice(ctx->device));
+    ctx->st = st;
     GSW_TRY(ensure(ctx, ctx->misc, kMiscWords * sizeof(unsigned long long)));
     ctx->launches = 0;
     for (int k = 0; k < GSW_NSTAGES; k++) ctx->stage_done[k] = 0;
@@ -580,6 +581,20 @@ int gsw_context_create(int device, size_t mem_budget_bytes, gsw_ctx **out) {
     c->budget = mem_budget_bytes ? mem_budget_bytes : ((size_t)4 << 30);
     cudaError_t e = cudaDeviceGetAttribute(&c->sms_all, cudaDevAttrMultiProcessorCount, device);
     c->sms = c->sms_all;
+    if (e == cudaSuccess) {
+        // the context's own pool keeps its memory between calls (no release
+        // at synchronisation), so scratch stays resident
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        e = cudaMemPoolCreate(&c->pool, &props);
+        if (e == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
     if (e == cudaSuccess) e = cudaMallocHost(&c->host_small, 4096);
     if (e != cudaSuccess) {
         delete c;
@@ -603,7 +618,10 @@ int gsw_context_destroy(gsw_ctx *c) {
                      &c->trace_ops, &c->band_scr, &c->misc, &c->io_q, &c->io_t, &c->io_qoff, &c->io_toff, &c->io_qlen,
                      &c->io_tlen, &c->io_res, &c->io_cigar, &c->io_colmax, &c->io_cmoff, &c->prof_qoff,
                      &c->prof_qlen, &c->ring_meta};
+    c->st = nullptr;
     for (DevBuf *b : all) release(c, *b);
+    cudaDeviceSynchronize();
+    if (c->pool) cudaMemPoolDestroy(c->pool);
     if (c->host_small) cudaFreeHost(c->host_small);
     for (int k = 0; k <= GSW_NSTAGES; k++)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
@@ -677,6 +695,7 @@ int gsw_align_profile(gsw_ctx *ctx, const gsw_profile *prof, int32_t ntargets, c
         return batch_impl(ctx, ntargets, qh.data(), qo.data(), ql.data(), t, t_off, t_len, prof->sc, flags,
                           mask_len, results, cigar, cigar_capacity, colmax, colmax_off, st);
     }
+    ctx->st = st;
     GSW_TRY(ensure(ctx, ctx->prof_qoff, sizeof(int64_t) * ntargets));
     GSW_TRY(ensure(ctx, ctx->prof_qlen, sizeof(int32_t) * ntargets));
     CUDA_TRY(launch_fill_const64((int64_t *)ctx->prof_qoff.p, 0, ntargets, st));
