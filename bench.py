@@ -216,6 +216,17 @@ def run_gsw(args):
     cap = int(min(32 * n + 1024 + (b.q_len.sum() + b.t_len.sum()) // 4, 1 << 30))
     cig = torch.zeros(cap, dtype=torch.int32, device=dev)
     ctx = gsw.Context(local, args.budget_gb << 30)
+    tune = None
+    if not args.no_tune:
+        # fill class per query-length bucket, measured on this GPU for this
+        # scoring and the workload's mean target length (results unchanged)
+        t0 = time.perf_counter()
+        tune = ctx.autotune(b.W, b.gap_open, b.gap_extend, target_len=max(1, int(b.t_len.mean())))
+        tune["seconds"] = round(time.perf_counter() - t0, 2)
+        nb = max(1, min(gsw.TUNE_BUCKETS, int(np.ceil(b.q_len.max() / gsw.TUNE_ROWS))))
+        tune = {"buckets_of_rows": gsw.TUNE_ROWS, "fill_class": tune["fill_class"][:nb],
+                "gcups": tune["gcups"][:nb], "gcups_default_rule": tune["gcups_default"][:nb],
+                "seconds": tune["seconds"]}
     stream = torch.cuda.current_stream(dev)
     flags = gsw.GSW_CIGAR | gsw.GSW_TIMING
 
@@ -280,7 +291,7 @@ def run_gsw(args):
             "config": workload_config(wcfg, b), "e2e": e2e,
             "gpu_launches": launches,
             "stage_ms": {k: round(v / args.steps, 3) for k, v in stage_sum.items()},
-            "checked_pairs": checked, "clocks": clocks, "roofline": roof}
+            "checked_pairs": checked, "clocks": clocks, "roofline": roof, "autotune": tune}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(b, args.cpu_seconds)
     if world == 1 and not args.no_serve:
@@ -584,6 +595,7 @@ def main():
     ap.add_argument("--head", type=int, default=100,
                     help="serving_stream: leading requests also run by the plain per-pair baseline")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving run of the default line")
+    ap.add_argument("--no-tune", action="store_true", help="default fill classes instead of the autotuner's")
     ap.add_argument("--budget-gb", type=int, default=24)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-pairs", type=int, default=4000)

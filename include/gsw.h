@@ -111,6 +111,36 @@ int gsw_context_create(int device, size_t mem_budget_bytes, gsw_ctx **out);
 /* Releases everything the context owns.  Waits for its work to finish. */
 int gsw_context_destroy(gsw_ctx *ctx);
 
+/*
+ * Autotuner for the forward and reversed fills (16-bit lanes).  Queries are
+ * bucketed by length in GSW_TUNE_ROWS-row buckets; for each bucket a fill class
+ * is chosen: 0..6 = one pair per 16-lane group with 2..8 row words per lane
+ * (64..256 query rows per strip; longer queries run several strips), 8 = one
+ * pair per CTA (512-row strips pipelined across the warps), -1 = the default
+ * rule (the smallest one-strip class, the CTA class from 1792 rows).  The
+ * choice changes speed only: every class gives the same results.
+ */
+#define GSW_TUNE_BUCKETS 32
+#define GSW_TUNE_ROWS 32
+typedef struct gsw_tune {
+    int8_t fill_class[GSW_TUNE_BUCKETS]; /* bucket b: queries of 32b+1 .. 32(b+1) rows */
+    float gcups[GSW_TUNE_BUCKETS];       /* measured forward-fill rate of the chosen class */
+    float gcups_default[GSW_TUNE_BUCKETS]; /* ... of the default rule's class */
+} gsw_tune;
+
+/* Measures every candidate class of every bucket on seeded random pairs
+ * (queries of the bucket's largest length against targets of target_len
+ * letters, the given scoring, score-only batches of about 2 G cells, best of 3
+ * runs), installs the fastest in the context and copies the table to *out (may
+ * be NULL).  Takes a few seconds; allocates its own temporary device buffers.
+ * Errors: GSW_EINVAL, GSW_ENOMEM, GSW_ECUDA. */
+int gsw_autotune(gsw_ctx *ctx, const int8_t *matrix, int32_t alphabet, int32_t gap_open, int32_t gap_extend,
+                 int32_t target_len, gsw_tune *out);
+
+/* Installs a table (e.g. one saved from gsw_autotune); NULL restores the
+ * default rule.  Errors: GSW_EINVAL (a class outside -1..6, 8). */
+int gsw_context_set_tune(gsw_ctx *ctx, const gsw_tune *tune);
+
 /* Sizes the context's persistent launches for at most `sms` SMs (0: all), so
  * that work of other streams finds free SMs while this context's kernels
  * run.  Results do not depend on it.  Errors: GSW_EINVAL (sms < 0). */

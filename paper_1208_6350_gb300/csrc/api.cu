@@ -51,6 +51,7 @@ struct gsw_ctx {
     int sms = 0;      // SMs the launches are sized for
     int sms_all = 0;  // SMs of the device
     cudaMemPool_t pool = nullptr;  // stream-ordered scratch allocations
+    int8_t tune[GSW_TUNE_BUCKETS];  // fill class per query-row bucket (gsw_autotune), -1: default rule
     cudaStream_t st = nullptr;     // stream of the call in progress
     DevBuf plan_keys, plan_order, plan_small;
     DevBuf fill_cm, fill_bnd;
@@ -142,6 +143,7 @@ int make_scoring(const int8_t *matrix, int32_t A, int32_t O, int32_t X, Scoring 
     sc->wmax = wmax;
     sc->wmin = wmin;
     sc->dna4 = A == 4;
+    std::memset(sc->fill_class, -1, sizeof(sc->fill_class));
     return GSW_OK;
 }
 
@@ -377,10 +379,12 @@ int check_common(gsw_ctx *ctx, int32_t npairs, uint32_t flags) {
 }
 
 int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_off, const int32_t *q_len,
-               const uint8_t *t, const int64_t *t_off, const int32_t *t_len, const Scoring &sc, uint32_t flags,
+               const uint8_t *t, const int64_t *t_off, const int32_t *t_len, const Scoring &sc_in, uint32_t flags,
                int32_t mask_len, gsw_result *results, uint32_t *cigar, int64_t cigar_capacity, int32_t *colmax,
                const int64_t *colmax_off, cudaStream_t st) {
     GSW_TRY(check_common(ctx, npairs, flags));
+    Scoring sc = sc_in;
+    std::memcpy(sc.fill_class, ctx->tune, sizeof(sc.fill_class));
     if (flags & GSW_CIGAR) flags |= GSW_BEGIN;
     if (npairs == 0) return GSW_OK;
     if (!q || !q_off || !q_len || !t || !t_off || !t_len || !results)
@@ -579,6 +583,7 @@ int gsw_context_create(int device, size_t mem_budget_bytes, gsw_ctx **out) {
     if (!c) return set_err(GSW_ENOMEM, "host allocation");
     c->device = device;
     c->budget = mem_budget_bytes ? mem_budget_bytes : ((size_t)4 << 30);
+    std::memset(c->tune, -1, sizeof(c->tune));
     cudaError_t e = cudaDeviceGetAttribute(&c->sms_all, cudaDevAttrMultiProcessorCount, device);
     c->sms = c->sms_all;
     if (e == cudaSuccess) {
@@ -601,6 +606,27 @@ int gsw_context_create(int device, size_t mem_budget_bytes, gsw_ctx **out) {
         return set_err(GSW_ECUDA, "context setup: %s", cudaGetErrorString(e));
     }
     *out = c;
+    return GSW_OK;
+}
+
+}  // extern "C"
+
+namespace gsw {
+int context_device(const gsw_ctx *ctx) { return ctx->device; }
+}  // namespace gsw
+
+extern "C" {
+
+int gsw_context_set_tune(gsw_ctx *c, const gsw_tune *t) {
+    if (!c) return set_err(GSW_EINVAL, "context is NULL");
+    if (!t) {
+        std::memset(c->tune, -1, sizeof(c->tune));
+        return GSW_OK;
+    }
+    for (int b = 0; b < GSW_TUNE_BUCKETS; b++)
+        if (t->fill_class[b] < -1 || t->fill_class[b] > 8 || t->fill_class[b] == 7)
+            return set_err(GSW_EINVAL, "fill class %d of bucket %d", t->fill_class[b], b);
+    std::memcpy(c->tune, t->fill_class, sizeof(c->tune));
     return GSW_OK;
 }
 

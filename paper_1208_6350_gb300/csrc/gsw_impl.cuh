@@ -20,6 +20,7 @@ struct Scoring {
     int32_t wmin;   // min matrix entry
     int32_t dna4;   // 1 when A == 4: the fill uses the letter-pair profile
     int8_t W[kMaxAlpha * kMaxAlpha];  // W[a * A + b]: query letter a vs target letter b
+    int8_t fill_class[GSW_TUNE_BUCKETS];  // tuned 16-bit fill class per query-row bucket, -1: default rule
 };
 
 // Batch view (device pointers) shared by every stage.
@@ -247,6 +248,7 @@ struct RingLaunchArgs {
     int walk_warps;
 };
 int ring_trace_class();
+int context_device(const gsw_ctx *ctx);
 int ring_slots_per_cta();
 // prefix sums of the class's direction words; out[0] total, [1] max words of a pair, [2] max op words
 cudaError_t launch_ring_needs(const BatchView &b, const Scoring &sc, const int32_t *order, const int32_t *var_start,

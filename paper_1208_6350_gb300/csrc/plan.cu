@@ -20,6 +20,15 @@ __device__ __forceinline__ int pick_s16(int rows) {
     return kVarMaxS16;  // several strips
 }
 
+// 16-bit fill class of a query of `rows`: the tuned class of its bucket, else
+// the smallest one-strip variant, or the CTA class for queries of many strips.
+__device__ __forceinline__ int pick_class16(int rows, const Scoring &sc) {
+    const int b = (rows - 1) / GSW_TUNE_ROWS;
+    if (rows >= 1 && b < GSW_TUNE_BUCKETS && sc.fill_class[b] >= 0)
+        return sc.fill_class[b] == 8 ? kClassLong16 : sc.fill_class[b];
+    return long_pair(rows, false, sc.dna4) ? kClassLong16 : pick_s16(rows);
+}
+
 __device__ __forceinline__ int cost_bin(long long cost) {
     // 32 bins per doubling of cost, descending order inside a variant
     float lg = log2f((float)(cost < 1 ? 1 : cost));
@@ -35,8 +44,8 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
     if (mode == kFillForward) {
         rows = b.q_len[p];
         cols = b.t_len[p];
-        v = (b.flags & GSW_FORCE_S32) ? kVarS32 : pick_s16(rows);
-        if (cols > 0 && long_pair(rows, v == kVarS32, sc.dna4)) v = v == kVarS32 ? kClassLong32 : kClassLong16;
+        if (b.flags & GSW_FORCE_S32) v = (cols > 0 && long_pair(rows, true, sc.dna4)) ? kClassLong32 : kVarS32;
+        else v = cols > 0 ? pick_class16(rows, sc) : pick_s16(rows);
     } else if (mode == kFillRerun) {
         if (!(b.res[p].flags & kResPendingS32)) { keys[p] = -1; return; }
         rows = b.q_len[p];
@@ -51,8 +60,8 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
         const int G = reverse_gap_bound(r.read_end1, r.score1, sc);
         if (G >= 0 && 2 * G + 1 <= kBandMaxWidth && rows <= kBandMaxRows) { keys[p] = -1; return; }
         cols = reverse_window(r.read_end1, r.ref_end1, r.score1, sc);
-        v = (r.flags & GSW_RES_S32) ? kVarS32 : pick_s16(rows);
-        if (long_pair(rows, v == kVarS32, sc.dna4)) v = v == kVarS32 ? kClassLong32 : kClassLong16;
+        if (r.flags & GSW_RES_S32) v = long_pair(rows, true, sc.dna4) ? kClassLong32 : kVarS32;
+        else v = pick_class16(rows, sc);
     } else if (mode == kPlanTrace) {
         const gsw_result r = b.res[p];
         if (r.score1 <= 0 || !(r.flags & kResPendingTrace) || (r.flags & kResInternal) || r.read_begin1 < 0) {

@@ -52,6 +52,15 @@ class GswStats(ctypes.Structure):
                 ("stage_ms", ctypes.c_float * 8)]
 
 
+TUNE_BUCKETS = 32
+TUNE_ROWS = 32
+
+
+class GswTune(ctypes.Structure):
+    _fields_ = [("fill_class", ctypes.c_int8 * TUNE_BUCKETS), ("gcups", ctypes.c_float * TUNE_BUCKETS),
+                ("gcups_default", ctypes.c_float * TUNE_BUCKETS)]
+
+
 class ServeConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("workers", ctypes.c_int32), ("max_batch_pairs", ctypes.c_int32),
                 ("max_batch_letters", ctypes.c_int64), ("mem_budget_bytes", ctypes.c_size_t),
@@ -96,6 +105,10 @@ def load(build_if_missing: bool = True):
     lib.gsw_context_destroy.argtypes = [P]
     lib.gsw_context_set_sm_limit.argtypes = [P, ctypes.c_int]
     lib.gsw_context_set_sm_limit.restype = ctypes.c_int
+    lib.gsw_autotune.argtypes = [P, P, i32, i32, i32, i32, ctypes.POINTER(GswTune)]
+    lib.gsw_autotune.restype = ctypes.c_int
+    lib.gsw_context_set_tune.argtypes = [P, ctypes.POINTER(GswTune)]
+    lib.gsw_context_set_tune.restype = ctypes.c_int
     lib.gsw_align_batch.argtypes = [P, i32, P, P, P, P, P, P, P, i32, i32, i32, u32, i32, P, P, i64, P,
                                     P, P]
     lib.gsw_profile_create.argtypes = [P, P, i32, P, i32, i32, i32, ctypes.POINTER(P)]
@@ -258,6 +271,27 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def autotune(self, matrix, gap_open, gap_extend, target_len=1000) -> dict:
+        """Measures the fill class per query-length bucket (gsw_autotune) and
+        installs the fastest; returns {"fill_class", "gcups", "gcups_default"}."""
+        m = np.ascontiguousarray(matrix, dtype=np.int8)
+        t = GswTune()
+        _check(load().gsw_autotune(self.handle, m.ctypes.data, m.shape[0], gap_open, gap_extend, target_len,
+                                   ctypes.byref(t)), "gsw_autotune")
+        return {"fill_class": list(t.fill_class), "gcups": [round(x, 1) for x in t.gcups],
+                "gcups_default": [round(x, 1) for x in t.gcups_default]}
+
+    def set_tune(self, fill_class=None):
+        """Installs a class per bucket (-1 default rule, 0..6 group variants, 8
+        the CTA kernel); None restores the default rule."""
+        if fill_class is None:
+            _check(load().gsw_context_set_tune(self.handle, None), "gsw_context_set_tune")
+            return
+        t = GswTune()
+        for b, c in enumerate(fill_class):
+            t.fill_class[b] = int(c)
+        _check(load().gsw_context_set_tune(self.handle, ctypes.byref(t)), "gsw_context_set_tune")
 
     def align_host(self, q, q_off, q_len, t, t_off, t_len, matrix, gap_open, gap_extend,
                    flags=GSW_CIGAR, mask_len=-1, cigar_capacity=None, colmax=False):

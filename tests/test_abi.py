@@ -58,3 +58,9 @@ def test_bad_scoring_rejected_without_gpu():
     rc = lib.gsw_align_batch(None, 1, None, None, None, None, None, None, W.ctypes.data, 40, 3, 1,
                              0, -1, None, None, 0, None, None, None)
     assert rc == gsw.GSW_EINVAL
+
+
+def test_tuning_calls_reject_null_context_without_gpu():
+    lib = gsw.load()
+    assert lib.gsw_context_set_tune(None, None) == gsw.GSW_EINVAL
+    assert lib.gsw_autotune(None, None, 4, 3, 1, 1000, None) == gsw.GSW_EINVAL

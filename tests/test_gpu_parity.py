@@ -283,3 +283,33 @@ def test_wide_band_traceback_indels_and_gap_costs(ctx, O, X):
     qs, ts = _indel_pairs(rng, [(2500, 300, 0), (2500, 0, 300), (3000, 150, 150), (1800, 0, 0)])
     b = _batch(qs, ts, wl.dna_matrix(2, -4), O, X, "indels")
     compare(b, run_oracle(b), run_gpu_host(ctx, b))
+
+
+@pytest.mark.parametrize("seed", [40, 41, 42])
+def test_any_fill_class_table_gives_the_same_results(ctx, seed):
+    # the autotuner may give any query length any class: per-group variants
+    # with one or several strips, or the CTA kernel; forward and reversed
+    # fills must stay exact under each
+    rng = np.random.default_rng(seed)
+    table = [int(rng.choice([0, 1, 2, 3, 4, 5, 6, 8])) for _ in range(gsw.TUNE_BUCKETS)]
+    b = mixed_dna(seed, 160, 1024, 1400)
+    ora = run_oracle(b)
+    ctx.set_tune(table)
+    try:
+        compare(b, ora, run_gpu_device(ctx, b))
+    finally:
+        ctx.set_tune(None)
+
+
+def test_autotune_table_is_valid_and_exact():
+    c = gsw.Context(0, 4 << 30)
+    try:
+        W = wl.dna_matrix(2, -2)
+        t = c.autotune(W, 3, 1, target_len=600)
+        assert len(t["fill_class"]) == gsw.TUNE_BUCKETS
+        assert all(x in (0, 1, 2, 3, 4, 5, 6, 8) for x in t["fill_class"])
+        assert all(g > 0 for g in t["gcups"]) and all(g >= d for g, d in zip(t["gcups"], t["gcups_default"]))
+        b = mixed_dna(43, 200, 900, 1200)
+        compare(b, run_oracle(b), run_gpu_host(c, b))
+    finally:
+        c.close()
