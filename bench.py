@@ -227,7 +227,10 @@ def run_gsw(args):
         tune = {"buckets_of_rows": gsw.TUNE_ROWS, "fill_class": tune["fill_class"][:nb],
                 "gcups": tune["gcups"][:nb], "gcups_default_rule": tune["gcups_default"][:nb],
                 "seconds": tune["seconds"]}
-    stream = torch.cuda.current_stream(dev)
+    # a stream of its own: the library captures the repeated step's launch
+    # sequence in CUDA graphs (the legacy default stream cannot be captured)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize(dev)
     flags = gsw.GSW_CIGAR | gsw.GSW_TIMING
 
     def step():
@@ -245,13 +248,14 @@ def run_gsw(args):
     sampler = ClockSampler(local)
     sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    fill_ms, pipe_ms, launches = [], [], 0
+    fill_ms, pipe_ms, launches, graph_segments = [], [], 0, 0
     stage_sum = {}
     e0.record(stream)
     for _ in range(args.steps):
         step()
         st = gsw.gsw_last_stats(ctx.handle)
         launches += st["kernel_launches"]
+        graph_segments += st["graph_segments"]
         fill_ms.append(st["stage_ms"]["fill_fwd"])
         pipe_ms.append(st["stage_ms"]["pipeline"])
         for k, v in st["stage_ms"].items():
@@ -290,6 +294,7 @@ def run_gsw(args):
             "data": "synthetic (seeded; stands in for simulated short reads)",
             "config": workload_config(wcfg, b), "e2e": e2e,
             "gpu_launches": launches,
+            "graph_segments_replayed": graph_segments,
             "stage_ms": {k: round(v / args.steps, 3) for k, v in stage_sum.items()},
             "checked_pairs": checked, "clocks": clocks, "roofline": roof, "autotune": tune}
     if world == 1 and not args.no_cpu:

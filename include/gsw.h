@@ -214,13 +214,18 @@ int gsw_align_profile(gsw_ctx *ctx, const gsw_profile *prof, int32_t ntargets,
  *   [5] warp traceback of pairs whose traceback band is wider than 32
  *   [6] whole device pipeline ([0] .. [5])
  * Stages that did not run read 0.  The call has already waited for its work,
- * so reading the stats does not block.  Errors: GSW_EINVAL (NULL).
+ * so reading the stats does not block.  graph_segments: how many of the two
+ * pipeline segments (before / after the traceback readback) ran as a replay
+ * of a captured CUDA graph: a call repeated with the same buffers, sizes,
+ * flags and scoring on a non-default stream is captured on its second run and
+ * replayed from the third.  Errors: GSW_EINVAL (NULL).
  */
 #define GSW_NSTAGES 7
 typedef struct gsw_stats {
     int32_t kernel_launches;
     int32_t timed;
     float stage_ms[8];
+    int32_t graph_segments;
 } gsw_stats;
 int gsw_last_stats(const gsw_ctx *ctx, gsw_stats *out);
 

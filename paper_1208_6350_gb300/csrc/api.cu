@@ -44,6 +44,29 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Host-side state of one pipeline run that the stages after the trace
+// readback need (also saved with a captured graph).
+struct PipeState {
+    gsw::PlanBuffers pb;
+    gsw::FillLaunch fl;
+    size_t slots = 0, ncap = 0;
+    int max_blocks = 0;
+    long long *ring_prefix = nullptr;
+    int *ring_final = nullptr, *ring_group = nullptr;
+    int launches = 0;
+    int stage_done[GSW_NSTAGES] = {};
+};
+
+// One captured segment of the pipeline: replayed while the call repeats with
+// the same key (pointers, sizes, flags, scoring, scratch), captured on the
+// second identical call.
+struct GraphSeg {
+    std::vector<uint8_t> key;
+    bool seen = false;
+    cudaGraphExec_t exec = nullptr;
+    PipeState state;
+};
+
 struct gsw_ctx {
     int device = 0;
     size_t budget = 0;
@@ -52,6 +75,8 @@ struct gsw_ctx {
     int sms_all = 0;  // SMs of the device
     cudaMemPool_t pool = nullptr;  // stream-ordered scratch allocations
     int8_t tune[GSW_TUNE_BUCKETS];  // fill class per query-row bucket (gsw_autotune), -1: default rule
+    GraphSeg seg[2];                // before and after the traceback readback
+    bool capturing = false;         // a segment is being captured: no allocation
     cudaStream_t st = nullptr;     // stream of the call in progress
     DevBuf plan_keys, plan_order, plan_small;
     DevBuf fill_cm, fill_bnd;
@@ -64,6 +89,7 @@ struct gsw_ctx {
     bool timing = false;
     int launches = 0;
     int stage_done[GSW_NSTAGES] = {};
+    int graph_segments = 0;  // segments of the last call replayed from a graph
 };
 
 struct gsw_profile {
@@ -81,6 +107,7 @@ namespace {
 // stream that uses the old buffer runs before it is released.
 int ensure(gsw_ctx *ctx, DevBuf &b, size_t need) {
     if (need <= b.bytes) return GSW_OK;
+    if (ctx->capturing) return GSW_ESTATE;  // the segment runs without a graph
     need = std::max<size_t>(need, 256);
     if (b.p) {
         CUDA_TRY(cudaFreeAsync(b.p, ctx->st));
@@ -102,6 +129,7 @@ int ensure(gsw_ctx *ctx, DevBuf &b, size_t need) {
 }
 
 void release(gsw_ctx *ctx, DevBuf &b) {
+    if (ctx->capturing) return;  // ensure() then reports GSW_ESTATE
     if (b.p) cudaFreeAsync(b.p, ctx->st);
     ctx->used -= b.bytes;
     b.p = nullptr;
@@ -118,6 +146,7 @@ size_t room(const gsw_ctx *ctx, const DevBuf &a, const DevBuf &b) {
 // either must grow, so the budget never counts an old and a new copy.
 int ensure2(gsw_ctx *ctx, DevBuf &a, size_t na, DevBuf &b, size_t nb) {
     if (na > a.bytes || nb > b.bytes) {
+        if (ctx->capturing) return GSW_ESTATE;
         release(ctx, a);
         release(ctx, b);
     }
@@ -161,212 +190,316 @@ enum MiscSlot {
 // event e[k] marks the end of stage k-1 / start of stage k
 int mark(gsw_ctx *ctx, int k, cudaStream_t st) {
     if (!ctx->timing) return GSW_OK;
-    CUDA_TRY(cudaEventRecord(ctx->ev[k], st));
+    // while a segment is captured, an external record makes the graph record
+    // the event each time it runs (a plain record would only order the capture)
+    if (ctx->capturing) CUDA_TRY(cudaEventRecordWithFlags(ctx->ev[k], st, cudaEventRecordExternal));
+    else CUDA_TRY(cudaEventRecord(ctx->ev[k], st));
     return GSW_OK;
+}
+
+template <class T>
+void key_add(std::vector<uint8_t> &k, const T &v) {
+    const uint8_t *p = reinterpret_cast<const uint8_t *>(&v);
+    k.insert(k.end(), p, p + sizeof(T));
+}
+
+void key_buf(std::vector<uint8_t> &k, const DevBuf &b) {
+    key_add(k, b.p);
+    key_add(k, b.bytes);
+}
+
+// Runs body() on the stream, or replays it as a CUDA graph: a segment is
+// captured on the second call with the same key (the first call sized every
+// buffer, so the capture allocates nothing) and replayed while the key repeats.
+// A segment that would have to grow a buffer while captured runs eagerly.
+template <class F>
+int run_segment(gsw_ctx *ctx, GraphSeg &g, const std::vector<uint8_t> &key, cudaStream_t st, PipeState &state,
+                F body) {
+    if (g.exec && g.key == key) {
+        CUDA_TRY(cudaGraphLaunch(g.exec, st));
+        state = g.state;
+        ctx->graph_segments++;
+        return GSW_OK;
+    }
+    const bool capture = st != nullptr && g.seen && g.key == key;
+    if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+    }
+    g.key = key;
+    g.seen = true;
+    if (!capture) return body();
+    const PipeState before = state;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return body();
+    }
+    ctx->capturing = true;
+    const int rc = body();
+    ctx->capturing = false;
+    cudaGraph_t gr = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &gr);
+    cudaGraphExec_t ex = nullptr;
+    if (rc == GSW_OK && e == cudaSuccess && gr && cudaGraphInstantiate(&ex, gr, 0) == cudaSuccess) {
+        cudaGraphDestroy(gr);
+        g.exec = ex;
+        g.state = state;
+        CUDA_TRY(cudaGraphLaunch(ex, st));
+        return GSW_OK;
+    }
+    if (gr) cudaGraphDestroy(gr);
+    cudaGetLastError();
+    g.seen = false;
+    state = before;
+    return body();
 }
 
 int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st, int maxm, int maxn) {
     const int npairs = bv.npairs;
     unsigned long long *misc = reinterpret_cast<unsigned long long *>(ctx->misc.p);
-    // ---- plan buffers
-    GSW_TRY(ensure(ctx, ctx->plan_keys, sizeof(int32_t) * (size_t)std::max(npairs, 1)));
-    GSW_TRY(ensure(ctx, ctx->plan_order, sizeof(int32_t) * (size_t)std::max(npairs, 1)));
-    const size_t small_words = 3 * (size_t)kPlanBins + 4 * kNumFillClasses + 8;
-    GSW_TRY(ensure(ctx, ctx->plan_small, sizeof(int32_t) * small_words));
-    int32_t *ps = reinterpret_cast<int32_t *>(ctx->plan_small.p);
-    PlanBuffers pb;
-    pb.keys = reinterpret_cast<int32_t *>(ctx->plan_keys.p);
-    pb.order = reinterpret_cast<int32_t *>(ctx->plan_order.p);
-    pb.hist = ps;
-    pb.binoff = ps + kPlanBins;
-    pb.cursor = ps + 2 * kPlanBins;
-    pb.var_start = ps + 3 * kPlanBins;
-    pb.task_lo = pb.var_start + kNumFillClasses + 1;
-    pb.task_hi = pb.task_lo + kNumFillClasses;
-    pb.ntasks = pb.task_hi + kNumFillClasses;
-    pb.head = pb.ntasks + 1;
+    unsigned long long *hs = reinterpret_cast<unsigned long long *>(ctx->host_small);
+    PipeState S;
+    std::vector<uint8_t> key;
+    key.reserve(2048);
+    key_add(key, bv);
+    key_add(key, sc);
+    key_add(key, maxm);
+    key_add(key, maxn);
+    key_add(key, st);
+    key_add(key, ctx->sms);
+    key_add(key, ctx->budget);
+    key_add(key, ctx->used);
+    key_add(key, ctx->timing);
+    key_add(key, ctx->ev);
+    for (const DevBuf *d : {&ctx->plan_keys, &ctx->plan_order, &ctx->plan_small, &ctx->fill_cm, &ctx->fill_bnd,
+                            &ctx->band_scr, &ctx->ring_meta, &ctx->trace_dirs, &ctx->trace_ops, &ctx->misc})
+        key_buf(key, *d);
 
-    // ---- fill launch geometry and per-slot scratch
-    const int warps_per_block = fill_block_threads() / 32;
-    const size_t ncap = (size_t)std::max(maxn, 1);
-    const size_t per_slot = ncap * sizeof(int32_t) + 2 * ncap * sizeof(int2);
-    size_t slots = (size_t)fill_slots(sc, ctx->sms);
-    if (slots == 0) return set_err(GSW_ECUDA, "fill kernels cannot be resident");
-    int max_blocks = INT32_MAX;
-    {
-        // keep the scratch inside half of what the budget has left
-        size_t have = room(ctx, ctx->fill_cm, ctx->fill_bnd);
-        size_t cap_slots = have / 2 / per_slot;
-        if (slots > cap_slots) {
-            // every variant has at most 2 slots per warp
-            max_blocks = (int)std::max<size_t>(1, cap_slots / (2 * warps_per_block));
-            slots = (size_t)max_blocks * warps_per_block * 2;
+    // ---- segment 1: fills, reverse, band kernel, traceback plan and needs
+    auto seg1 = [&]() -> int {
+        GSW_TRY(ensure(ctx, ctx->plan_keys, sizeof(int32_t) * (size_t)std::max(npairs, 1)));
+        GSW_TRY(ensure(ctx, ctx->plan_order, sizeof(int32_t) * (size_t)std::max(npairs, 1)));
+        const size_t small_words = 3 * (size_t)kPlanBins + 4 * kNumFillClasses + 8;
+        GSW_TRY(ensure(ctx, ctx->plan_small, sizeof(int32_t) * small_words));
+        int32_t *ps = reinterpret_cast<int32_t *>(ctx->plan_small.p);
+        PlanBuffers &pb = S.pb;
+        pb.keys = reinterpret_cast<int32_t *>(ctx->plan_keys.p);
+        pb.order = reinterpret_cast<int32_t *>(ctx->plan_order.p);
+        pb.hist = ps;
+        pb.binoff = ps + kPlanBins;
+        pb.cursor = ps + 2 * kPlanBins;
+        pb.var_start = ps + 3 * kPlanBins;
+        pb.task_lo = pb.var_start + kNumFillClasses + 1;
+        pb.task_hi = pb.task_lo + kNumFillClasses;
+        pb.ntasks = pb.task_hi + kNumFillClasses;
+        pb.head = pb.ntasks + 1;
+
+        // fill launch geometry and per-slot scratch
+        const int warps_per_block = fill_block_threads() / 32;
+        S.ncap = (size_t)std::max(maxn, 1);
+        const size_t per_slot = S.ncap * sizeof(int32_t) + 2 * S.ncap * sizeof(int2);
+        S.slots = (size_t)fill_slots(sc, ctx->sms);
+        if (S.slots == 0) return set_err(GSW_ECUDA, "fill kernels cannot be resident");
+        S.max_blocks = INT32_MAX;
+        {
+            // keep the scratch inside half of what the budget has left
+            size_t have = room(ctx, ctx->fill_cm, ctx->fill_bnd);
+            size_t cap_slots = have / 2 / per_slot;
+            if (S.slots > cap_slots) {
+                // every variant has at most 2 slots per warp
+                S.max_blocks = (int)std::max<size_t>(1, cap_slots / (2 * warps_per_block));
+                S.slots = (size_t)S.max_blocks * warps_per_block * 2;
+            }
         }
-    }
-    GSW_TRY(ensure2(ctx, ctx->fill_cm, slots * ncap * sizeof(int32_t), ctx->fill_bnd, slots * 2 * ncap * sizeof(int2)));
+        GSW_TRY(ensure2(ctx, ctx->fill_cm, S.slots * S.ncap * sizeof(int32_t), ctx->fill_bnd,
+                        S.slots * 2 * S.ncap * sizeof(int2)));
 
-    FillLaunch fl;
-    fl.b = bv;
-    fl.sc = sc;
-    fl.plan.order = pb.order;
-    fl.plan.var_start = pb.var_start;
-    fl.plan.task_lo = pb.task_lo;
-    fl.plan.task_hi = pb.task_hi;
-    fl.plan.head = pb.head;
-    fl.plan.ntasks = pb.ntasks;
-    fl.scr.colmax = ctx->fill_cm.p;
-    fl.scr.boundary = ctx->fill_bnd.p;
-    fl.scr.ncap = (int32_t)ncap;
-    fl.scr.nslots = (int32_t)slots;
+        FillLaunch &fl = S.fl;
+        fl.b = bv;
+        fl.sc = sc;
+        fl.plan.order = pb.order;
+        fl.plan.var_start = pb.var_start;
+        fl.plan.task_lo = pb.task_lo;
+        fl.plan.task_hi = pb.task_hi;
+        fl.plan.head = pb.head;
+        fl.plan.ntasks = pb.ntasks;
+        fl.scr.colmax = ctx->fill_cm.p;
+        fl.scr.boundary = ctx->fill_bnd.p;
+        fl.scr.ncap = (int32_t)S.ncap;
+        fl.scr.nslots = (int32_t)S.slots;
 
-    auto plan = [&](int32_t mode) -> int {
-        cudaError_t e = launch_plan(bv, sc, mode, pb, st);
-        if (e != cudaSuccess) return set_err(GSW_ECUDA, "plan: %s", cudaGetErrorString(e));
-        ctx->launches += 3;
+        auto plan = [&](int32_t mode) -> int {
+            cudaError_t e = launch_plan(bv, sc, mode, pb, st);
+            if (e != cudaSuccess) return set_err(GSW_ECUDA, "plan: %s", cudaGetErrorString(e));
+            S.launches += 3;
+            return GSW_OK;
+        };
+        auto fill = [&](int32_t mode) -> int {
+            fl.mode = mode;
+            cudaError_t e = launch_fill(fl, ctx->sms, S.max_blocks, st);
+            if (e != cudaSuccess) return set_err(GSW_ECUDA, "fill: %s", cudaGetErrorString(e));
+            S.launches += kNumFillClasses;
+            return GSW_OK;
+        };
+        GSW_TRY(mark(ctx, 0, st));
+        GSW_TRY(plan(kFillForward));
+        GSW_TRY(mark(ctx, 1, st));
+        GSW_TRY(fill(kFillForward));
+        GSW_TRY(mark(ctx, 2, st));
+        S.stage_done[0] = S.stage_done[1] = 1;
+        if (!(bv.flags & GSW_FORCE_S32)) {
+            GSW_TRY(plan(kFillRerun));
+            GSW_TRY(fill(kFillRerun));
+            S.stage_done[2] = 1;
+        }
+        GSW_TRY(mark(ctx, 3, st));
+        if (bv.flags & (GSW_BEGIN | GSW_CIGAR)) {
+            // reversed fill in the ring kernels for pairs whose reverse band is wide
+            GSW_TRY(plan(kFillReverse));
+            GSW_TRY(fill(kFillReverse));
+            S.stage_done[3] = 1;
+        }
+        GSW_TRY(mark(ctx, 4, st));
+        if (bv.flags & (GSW_BEGIN | GSW_CIGAR)) {
+            // thread-per-pair banded reverse and traceback for narrow bands
+            GSW_TRY(plan(kPlanBand));
+            const int rows_cap = std::min(std::max(maxm, 1), kBandMaxRows);
+            const int64_t words = (int64_t)(rows_cap + 1) * 32 * 4;  // widest class: 4 words per lane and row
+            int bgrid = ctx->sms * 8;
+            const int bwarps_per_block = band_block_threads() / 32;
+            {
+                // a quarter of what is left: the band scratch holds every row of
+                // the pairs in flight
+                size_t have = room(ctx, ctx->band_scr, ctx->band_scr) + ctx->band_scr.bytes;
+                size_t per_warp = (size_t)words * sizeof(uint32_t);
+                size_t max_warps = have / 4 / per_warp;
+                if ((size_t)bgrid * bwarps_per_block > max_warps)
+                    bgrid = (int)std::max<size_t>(1, max_warps / bwarps_per_block);
+            }
+            {
+                const size_t need = (size_t)bgrid * bwarps_per_block * words * sizeof(uint32_t);
+                if (need > ctx->band_scr.bytes) release(ctx, ctx->band_scr);
+                GSW_TRY(ensure(ctx, ctx->band_scr, need));
+            }
+            CUDA_TRY(launch_band(bv, sc, pb, ctx->band_scr.p, words, bgrid, st));
+            S.launches += 3;
+            S.stage_done[4] = 1;
+        }
+        GSW_TRY(mark(ctx, 5, st));
+        if (bv.flags & GSW_CIGAR) {
+            // tracebacks for the pairs the band kernel left (band wider than 32
+            // or more than 4096 rows): anti-diagonal warp kernel up to 512
+            // diagonals, CTA strip kernel beyond; their scratch is sized from
+            // the needs read back after this segment
+            GSW_TRY(plan(kPlanTrace));
+            CUDA_TRY(launch_trace_need(bv, sc, misc + kMiscNeed, st));
+            const size_t meta_bytes = sizeof(long long) * ((size_t)npairs + 1) + sizeof(int) * ((size_t)npairs + 4);
+            GSW_TRY(ensure(ctx, ctx->ring_meta, meta_bytes));
+            S.ring_prefix = reinterpret_cast<long long *>(ctx->ring_meta.p);
+            S.ring_final = reinterpret_cast<int *>(S.ring_prefix + npairs + 1);
+            S.ring_group = S.ring_final + npairs;
+            CUDA_TRY(launch_ring_needs(bv, sc, pb.order, pb.var_start, S.ring_prefix, misc + kMiscRing, st));
+            CUDA_TRY(cudaMemsetAsync(S.ring_group, 0, 3 * sizeof(int), st));
+            S.launches += 2;
+            CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                     st));
+        }
         return GSW_OK;
     };
-    auto fill = [&](int32_t mode) -> int {
-        fl.mode = mode;
-        cudaError_t e = launch_fill(fl, ctx->sms, max_blocks, st);
-        if (e != cudaSuccess) return set_err(GSW_ECUDA, "fill: %s", cudaGetErrorString(e));
-        ctx->launches += kNumFillClasses;
-        return GSW_OK;
-    };
-    GSW_TRY(mark(ctx, 0, st));
-    GSW_TRY(plan(kFillForward));
-    GSW_TRY(mark(ctx, 1, st));
-    GSW_TRY(fill(kFillForward));
-    GSW_TRY(mark(ctx, 2, st));
-    ctx->stage_done[0] = ctx->stage_done[1] = 1;
-    if (!(bv.flags & GSW_FORCE_S32)) {
-        GSW_TRY(plan(kFillRerun));
-        GSW_TRY(fill(kFillRerun));
-        ctx->stage_done[2] = 1;
-    }
-    GSW_TRY(mark(ctx, 3, st));
-    if (bv.flags & (GSW_BEGIN | GSW_CIGAR)) {
-        // reversed fill in the ring kernel for pairs whose reverse band is wide
-        GSW_TRY(plan(kFillReverse));
-        GSW_TRY(fill(kFillReverse));
-        ctx->stage_done[3] = 1;
-    }
-    GSW_TRY(mark(ctx, 4, st));
-    if (bv.flags & (GSW_BEGIN | GSW_CIGAR)) {
-        // thread-per-pair banded reverse and traceback for narrow bands
-        GSW_TRY(plan(kPlanBand));
-        const int rows_cap = std::min(std::max(maxm, 1), kBandMaxRows);
-        const int64_t words = (int64_t)(rows_cap + 1) * 32 * 4;  // widest class: 4 words per lane and row
-        int bgrid = ctx->sms * 8;
-        const int bwarps_per_block = band_block_threads() / 32;
-        {
-            // a quarter of what is left: the band scratch holds every row of
-            // the pairs in flight
-            size_t have = room(ctx, ctx->band_scr, ctx->band_scr) + ctx->band_scr.bytes;
-            size_t per_warp = (size_t)words * sizeof(uint32_t);
-            size_t max_warps = have / 4 / per_warp;
-            if ((size_t)bgrid * bwarps_per_block > max_warps)
-                bgrid = (int)std::max<size_t>(1, max_warps / bwarps_per_block);
-        }
-        {
-            const size_t need = (size_t)bgrid * bwarps_per_block * words * sizeof(uint32_t);
-            if (need > ctx->band_scr.bytes) release(ctx, ctx->band_scr);
-            GSW_TRY(ensure(ctx, ctx->band_scr, need));
-        }
-        CUDA_TRY(launch_band(bv, sc, pb, ctx->band_scr.p, words, bgrid, st));
-        ctx->launches += 3;
-        ctx->stage_done[4] = 1;
-    }
-    GSW_TRY(mark(ctx, 5, st));
+    GSW_TRY(run_segment(ctx, ctx->seg[0], key, st, S, seg1));
 
     if (bv.flags & GSW_CIGAR) {
-        // tracebacks for the pairs the band kernel left (band wider than 32 or
-        // more than 4096 rows): anti-diagonal warp kernel up to 512 diagonals,
-        // CTA strip kernel beyond
-        GSW_TRY(plan(kPlanTrace));
-        CUDA_TRY(launch_trace_need(bv, sc, misc + kMiscNeed, st));
-        // wide bands: direction words per pair, prefix over the class
-        const size_t meta_bytes = sizeof(long long) * ((size_t)npairs + 1) + sizeof(int) * ((size_t)npairs + 4);
-        GSW_TRY(ensure(ctx, ctx->ring_meta, meta_bytes));
-        long long *ring_prefix = reinterpret_cast<long long *>(ctx->ring_meta.p);
-        int *ring_final = reinterpret_cast<int *>(ring_prefix + npairs + 1);
-        int *ring_group = ring_final + npairs;
-        CUDA_TRY(launch_ring_needs(bv, sc, pb.order, pb.var_start, ring_prefix, misc + kMiscRing, st));
-        CUDA_TRY(cudaMemsetAsync(ring_group, 0, 3 * sizeof(int), st));
-        ctx->launches += 2;
-        unsigned long long *hs = reinterpret_cast<unsigned long long *>(ctx->host_small);
-        CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
         unsigned long long need[5];
         std::memcpy(need, hs, sizeof(need));
-        // anti-diagonal kernel (<= 512 diagonals): direction and op words per warp
-        const long long ad_dir = (long long)need[0], ad_ops = std::max<long long>((long long)need[1], 64);
-        int ad_grid = 0;
-        size_t max_dir = 0, max_ops = 0;
-        const int wpb = trace_block_threads() / 32;
-        if (ad_dir > 0) {
-            const size_t have = room(ctx, ctx->trace_dirs, ctx->trace_ops) / 2;
-            const size_t per_warp = (size_t)(ad_dir + ad_ops) * sizeof(uint32_t);
-            int warps = (int)std::min<size_t>((size_t)ctx->sms * 16 * wpb, std::max<size_t>(1, have / per_warp));
-            warps = std::max(wpb, warps - warps % wpb);
-            ad_grid = warps / wpb;
-            max_dir = (size_t)warps * (size_t)ad_dir;
-            max_ops = (size_t)warps * (size_t)ad_ops;
-        }
-        // wide bands: the pool of direction words, groups of pairs that fit it
-        const unsigned long long ring_total = need[2], ring_max = need[3], ring_ops = need[4];
-        size_t ring_pool = 0, ring_walk_warps = 0;
-        if (ring_total > 0) {
-            ring_walk_warps = (size_t)ctx->sms * 16;
-            const size_t have_all = room(ctx, ctx->trace_dirs, ctx->trace_ops);
-            const size_t ops_bytes = ring_walk_warps * (size_t)ring_ops * sizeof(uint32_t);
-            size_t cap = have_all > ops_bytes ? (have_all - ops_bytes) / 2 / sizeof(uint32_t) : 0;
-            ring_pool = (size_t)std::min<unsigned long long>(ring_total, cap);
-            if (ring_pool < ring_max) return set_err(GSW_ENOMEM, "wide-band traceback of one pair needs %llu words", ring_max);
-            max_dir = std::max(max_dir, ring_pool);
-            max_ops = std::max(max_ops, ring_walk_warps * (size_t)ring_ops);
-        }
-        if (max_dir > 0) {
-            GSW_TRY(ensure2(ctx, ctx->trace_dirs, max_dir * sizeof(uint32_t), ctx->trace_ops, max_ops * sizeof(uint32_t)));
-            if (ad_grid > 0) {
-                TraceScratch ts;
-                ts.dirs = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
-                ts.dir_words = ad_dir;
-                ts.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
-                ts.op_words = ad_ops;
-                ts.order = pb.order;
-                ts.var_start = pb.var_start;
-                CUDA_TRY(launch_trace_ad(bv, sc, ts, ad_grid, st));
-                ctx->launches += 4;
+        std::vector<uint8_t> key2 = key;
+        key_add(key2, need);
+        for (const DevBuf *d : {&ctx->fill_bnd, &ctx->trace_dirs, &ctx->trace_ops, &ctx->ring_meta})
+            key_buf(key2, *d);
+        key_add(key2, ctx->used);
+
+        // ---- segment 2: the tracebacks, sized from the needs
+        auto seg2 = [&]() -> int {
+            const PlanBuffers &pb = S.pb;
+            // anti-diagonal kernel (<= 512 diagonals): direction and op words per warp
+            const long long ad_dir = (long long)need[0], ad_ops = std::max<long long>((long long)need[1], 64);
+            int ad_grid = 0;
+            size_t max_dir = 0, max_ops = 0;
+            const int wpb = trace_block_threads() / 32;
+            if (ad_dir > 0) {
+                const size_t have = room(ctx, ctx->trace_dirs, ctx->trace_ops) / 2;
+                const size_t per_warp = (size_t)(ad_dir + ad_ops) * sizeof(uint32_t);
+                int warps = (int)std::min<size_t>((size_t)ctx->sms * 16 * wpb, std::max<size_t>(1, have / per_warp));
+                warps = std::max(wpb, warps - warps % wpb);
+                ad_grid = warps / wpb;
+                max_dir = (size_t)warps * (size_t)ad_dir;
+                max_ops = (size_t)warps * (size_t)ad_ops;
             }
+            // wide bands: the pool of direction words, groups of pairs that fit it
+            const unsigned long long ring_total = need[2], ring_max = need[3], ring_ops = need[4];
+            size_t ring_pool = 0, ring_walk_warps = 0;
             if (ring_total > 0) {
-                RingLaunchArgs ra;
-                ra.b = bv;
-                ra.sc = sc;
-                ra.order = pb.order;
-                ra.var_start = pb.var_start;
-                ra.prefix = ring_prefix;
-                ra.final_h = ring_final;
-                ra.group = ring_group;
-                ra.pool = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
-                ra.pool_words = (long long)ring_pool;
-                ra.bnd = reinterpret_cast<int2 *>(ctx->fill_bnd.p);
-                ra.bnd_stride = 2 * (long long)ncap;
-                ra.slots = (int)slots;
-                ra.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
-                ra.op_words = (long long)ring_ops;
-                ra.walk_warps = (int)ring_walk_warps;
-                // every group but the last fills more than pool - max_pair
-                const unsigned long long per = ring_pool > ring_max ? ring_pool - ring_max : 1;
-                const unsigned long long groups = ring_total <= ring_pool ? 1 : (ring_total + per - 1) / per + 1;
-                for (unsigned long long gi = 0; gi < groups; gi++) {
-                    CUDA_TRY(launch_ring_group(ra, ctx->sms, st));
-                    ctx->launches += 4;
+                ring_walk_warps = (size_t)ctx->sms * 16;
+                const size_t have_all = room(ctx, ctx->trace_dirs, ctx->trace_ops);
+                const size_t ops_bytes = ring_walk_warps * (size_t)ring_ops * sizeof(uint32_t);
+                size_t cap = have_all > ops_bytes ? (have_all - ops_bytes) / 2 / sizeof(uint32_t) : 0;
+                ring_pool = (size_t)std::min<unsigned long long>(ring_total, cap);
+                if (ring_pool < ring_max)
+                    return set_err(GSW_ENOMEM, "wide-band traceback of one pair needs %llu words", ring_max);
+                max_dir = std::max(max_dir, ring_pool);
+                max_ops = std::max(max_ops, ring_walk_warps * (size_t)ring_ops);
+            }
+            if (max_dir > 0) {
+                GSW_TRY(ensure2(ctx, ctx->trace_dirs, max_dir * sizeof(uint32_t), ctx->trace_ops,
+                                max_ops * sizeof(uint32_t)));
+                if (ad_grid > 0) {
+                    TraceScratch ts;
+                    ts.dirs = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
+                    ts.dir_words = ad_dir;
+                    ts.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
+                    ts.op_words = ad_ops;
+                    ts.order = pb.order;
+                    ts.var_start = pb.var_start;
+                    CUDA_TRY(launch_trace_ad(bv, sc, ts, ad_grid, st));
+                    S.launches += 4;
+                }
+                if (ring_total > 0) {
+                    RingLaunchArgs ra;
+                    ra.b = bv;
+                    ra.sc = sc;
+                    ra.order = pb.order;
+                    ra.var_start = pb.var_start;
+                    ra.prefix = S.ring_prefix;
+                    ra.final_h = S.ring_final;
+                    ra.group = S.ring_group;
+                    ra.pool = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
+                    ra.pool_words = (long long)ring_pool;
+                    ra.bnd = reinterpret_cast<int2 *>(ctx->fill_bnd.p);
+                    ra.bnd_stride = 2 * (long long)S.ncap;
+                    ra.slots = (int)S.slots;
+                    ra.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
+                    ra.op_words = (long long)ring_ops;
+                    ra.walk_warps = (int)ring_walk_warps;
+                    // every group but the last fills more than pool - max_pair
+                    const unsigned long long per = ring_pool > ring_max ? ring_pool - ring_max : 1;
+                    const unsigned long long groups =
+                        ring_total <= ring_pool ? 1 : (ring_total + per - 1) / per + 1;
+                    for (unsigned long long gi = 0; gi < groups; gi++) {
+                        CUDA_TRY(launch_ring_group(ra, ctx->sms, st));
+                        S.launches += 4;
+                    }
                 }
             }
-        }
-        ctx->stage_done[5] = 1;
+            S.stage_done[5] = 1;
+            GSW_TRY(mark(ctx, 6, st));
+            return GSW_OK;
+        };
+        GSW_TRY(run_segment(ctx, ctx->seg[1], key2, st, S, seg2));
+    } else {
+        GSW_TRY(mark(ctx, 6, st));
     }
-    GSW_TRY(mark(ctx, 6, st));
+    ctx->launches += S.launches;
+    for (int k = 0; k < GSW_NSTAGES; k++) ctx->stage_done[k] |= S.stage_done[k];
     return GSW_OK;
 }
 
@@ -397,6 +530,7 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
     ctx->st = st;
     GSW_TRY(ensure(ctx, ctx->misc, kMiscWords * sizeof(unsigned long long)));
     ctx->launches = 0;
+    ctx->graph_segments = 0;
     for (int k = 0; k < GSW_NSTAGES; k++) ctx->stage_done[k] = 0;
     ctx->timing = (flags & GSW_TIMING) != 0;
     if (ctx->timing && !ctx->ev[0])
@@ -558,17 +692,23 @@ int gsw_last_stats(const gsw_ctx *ctx, gsw_stats *out) {
     if (!ctx || !out) return set_err(GSW_EINVAL, "NULL argument");
     std::memset(out, 0, sizeof(*out));
     out->kernel_launches = ctx->launches;
+    out->graph_segments = ctx->graph_segments;
     if (!ctx->timing || !ctx->ev[0]) return GSW_OK;
     out->timed = 1;
     // stage k spans events k..k+1, except: [0] = e0..e1, [1] = e1..e2, [2] = e2..e3,
     // [3] = e3..e4, [4] = e4..e5, [5] = e5..e6, [6] = e0..e6
-    for (int k = 0; k < 6; k++) {
+    // a failed query must not leave its error for the next call's launch checks
+    auto elapsed = [](cudaEvent_t a, cudaEvent_t b) -> float {
         float ms = 0.f;
-        if (ctx->stage_done[k] && cudaEventElapsedTime(&ms, ctx->ev[k], ctx->ev[k + 1]) == cudaSuccess)
-            out->stage_ms[k] = ms;
-    }
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[6]) == cudaSuccess) out->stage_ms[6] = ms;
+        if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+            cudaGetLastError();
+            return 0.f;
+        }
+        return ms;
+    };
+    for (int k = 0; k < 6; k++)
+        if (ctx->stage_done[k]) out->stage_ms[k] = elapsed(ctx->ev[k], ctx->ev[k + 1]);
+    out->stage_ms[6] = elapsed(ctx->ev[0], ctx->ev[6]);
     return GSW_OK;
 }
 
@@ -645,6 +785,9 @@ int gsw_context_destroy(gsw_ctx *c) {
                      &c->io_tlen, &c->io_res, &c->io_cigar, &c->io_colmax, &c->io_cmoff, &c->prof_qoff,
                      &c->prof_qlen, &c->ring_meta};
     c->st = nullptr;
+    c->capturing = false;
+    for (GraphSeg &g : c->seg)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     for (DevBuf *b : all) release(c, *b);
     cudaDeviceSynchronize();
     if (c->pool) cudaMemPoolDestroy(c->pool);

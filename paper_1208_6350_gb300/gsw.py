@@ -49,7 +49,7 @@ _lib = None
 
 class GswStats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int32), ("timed", ctypes.c_int32),
-                ("stage_ms", ctypes.c_float * 8)]
+                ("stage_ms", ctypes.c_float * 8), ("graph_segments", ctypes.c_int32)]
 
 
 TUNE_BUCKETS = 32
@@ -202,7 +202,7 @@ def gsw_align_batch(ctx, npairs, q, q_off, q_len, t, t_off, t_len, matrix, gap_o
 def gsw_last_stats(ctx) -> dict:
     st = GswStats()
     _check(load().gsw_last_stats(ctx, ctypes.byref(st)), "gsw_last_stats")
-    out = {"kernel_launches": st.kernel_launches, "timed": bool(st.timed)}
+    out = {"kernel_launches": st.kernel_launches, "timed": bool(st.timed), "graph_segments": st.graph_segments}
     if st.timed:
         out["stage_ms"] = {n: float(st.stage_ms[k]) for k, n in enumerate(STAGE_NAMES)}
     return out
