@@ -7,6 +7,7 @@
 #include <climits>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -109,6 +110,9 @@ int ensure(gsw_ctx *ctx, DevBuf &b, size_t need) {
     if (need <= b.bytes) return GSW_OK;
     if (ctx->capturing) return GSW_ESTATE;  // the segment runs without a graph
     need = std::max<size_t>(need, 256);
+    if (std::getenv("GSW_DEBUG_GRAPHS"))
+        std::fprintf(stderr, "gsw: buffer at +%td grows %zu -> %zu\n",
+                     reinterpret_cast<const char *>(&b) - reinterpret_cast<const char *>(ctx), b.bytes, need);
     if (b.p) {
         CUDA_TRY(cudaFreeAsync(b.p, ctx->st));
         ctx->used -= b.bytes;
@@ -222,6 +226,11 @@ int run_segment(gsw_ctx *ctx, GraphSeg &g, const std::vector<uint8_t> &key, cuda
         return GSW_OK;
     }
     const bool capture = st != nullptr && g.seen && g.key == key;
+    if (!capture && g.seen && std::getenv("GSW_DEBUG_GRAPHS")) {
+        size_t at = 0;
+        while (at < key.size() && at < g.key.size() && key[at] == g.key[at]) at++;
+        std::fprintf(stderr, "gsw: segment key changed at byte %zu of %zu\n", at, key.size());
+    }
     if (g.exec) {
         cudaGraphExecDestroy(g.exec);
         g.exec = nullptr;
@@ -248,7 +257,10 @@ int run_segment(gsw_ctx *ctx, GraphSeg &g, const std::vector<uint8_t> &key, cuda
         return GSW_OK;
     }
     if (gr) cudaGraphDestroy(gr);
-    cudaGetLastError();
+    const cudaError_t le = cudaGetLastError();
+    if (std::getenv("GSW_DEBUG_GRAPHS"))
+        std::fprintf(stderr, "gsw: segment not captured (body %d, end capture %s, last %s)\n", rc,
+                     cudaGetErrorString(e), cudaGetErrorString(le));
     g.seen = false;
     state = before;
     return body();
@@ -370,7 +382,7 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
             {
                 // a quarter of what is left: the band scratch holds every row of
                 // the pairs in flight
-                size_t have = room(ctx, ctx->band_scr, ctx->band_scr) + ctx->band_scr.bytes;
+                size_t have = room(ctx, ctx->band_scr, ctx->misc) + ctx->misc.bytes;  // budget left without band_scr
                 size_t per_warp = (size_t)words * sizeof(uint32_t);
                 size_t max_warps = have / 4 / per_warp;
                 if ((size_t)bgrid * bwarps_per_block > max_warps)

@@ -78,9 +78,16 @@ struct L16 {
     static __device__ __forceinline__ uint32_t halves(int lo, int hi) {
         return ((uint32_t)lo & 0xFFFFu) | (((uint32_t)hi & 0xFFFFu) << 16);
     }
+    // low half of a, high half of b (words made by halves)
+    static __device__ __forceinline__ uint32_t merge(uint32_t a, uint32_t b) {
+        return (a & 0x0000FFFFu) | (b & 0xFFFF0000u);
+    }
 #else
     static __device__ __forceinline__ uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) { return vmax(a + b, c); }
     static __device__ __forceinline__ uint32_t halves(int lo, int hi) { return (uint32_t)(lo + hi * 65536); }
+    static __device__ __forceinline__ uint32_t merge(uint32_t a, uint32_t b) {
+        return b - (uint32_t)(int)(int16_t)(b & 0xFFFFu) + (uint32_t)(int)(int16_t)(a & 0xFFFFu);
+    }
 #endif
 };
 
@@ -98,11 +105,12 @@ struct L32 {
     static __device__ __forceinline__ uint32_t addk(int c) { return (uint32_t)c; }
     static __device__ __forceinline__ uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) { return vmax(a + b, c); }
     static __device__ __forceinline__ uint32_t halves(int lo, int hi) { return (uint32_t)lo; }
+    static __device__ __forceinline__ uint32_t merge(uint32_t a, uint32_t b) { return a; }
 };
 
 // words of one lane's profile (the warp region holds 32 lanes' worth)
 __host__ __device__ constexpr int prof_words(int R, bool fold, bool dna, int A) {
-    return dna ? (fold ? (GSW_FILL_SPLIT ? 8 * R : 16 * R) : 4 * R) : (fold ? 2 * A * R : A * R);
+    return dna ? (fold ? (GSW_FILL_SPLIT ? 8 * R : 16 * R) : 4 * R) : A * R;
 }
 
 // Index of profile word (table c, row r) of lane l inside the warp region:
@@ -188,12 +196,20 @@ __device__ __forceinline__ void build_profile(uint32_t *psm, const Job &job, con
 #pragma unroll
                 for (int a = 0; a < 4; a++) psm[pidx<R>(a, r, lane)] = (uint32_t)(qlo >= 0 ? sc_w(sc, qlo, a) : 0);
             }
-        } else {
+        } else if constexpr (DNA) {
             for (int a = 0; a < A; a++) {
                 psm[pidx<R>(a, r, lane)] = L::halves(qlo >= 0 ? sc_w(sc, qlo, a) : 0, 0);
                 if constexpr (L::FOLD)
                     psm[pidx<R>(A + a, r, lane)] = L::halves(0, qhi >= 0 ? sc_w(sc, qhi, a) : 0);
             }
+        } else {
+            // general alphabets: one table, both halves' scores in one word
+            // (the step takes the low half from the low letter's word and the
+            // high half from the high letter's), half the shared memory of
+            // two tables
+            for (int a = 0; a < A; a++)
+                psm[pidx<R>(a, r, lane)] =
+                    L::halves(qlo >= 0 ? sc_w(sc, qlo, a) : 0, L::FOLD && qhi >= 0 ? sc_w(sc, qhi, a) : 0);
         }
     }
 }
@@ -368,13 +384,21 @@ struct StripRunner {
         uint32_t pw[R];
         if constexpr (DNA && !GSW_FILL_SPLIT) {
             load_words<R>(psm, L::FOLD ? al * 4 + ah : al, lane, pw);
-        } else {
+        } else if constexpr (DNA) {
             load_words<R>(psm, al, lane, pw);
             if constexpr (L::FOLD) {
                 uint32_t ph[R];
                 load_words<R>(psm, A + ah, lane, ph);
 #pragma unroll
                 for (int r = 0; r < R; r++) pw[r] += ph[r];
+            }
+        } else {
+            load_words<R>(psm, al, lane, pw);
+            if constexpr (L::FOLD) {
+                uint32_t ph[R];
+                load_words<R>(psm, ah, lane, ph);
+#pragma unroll
+                for (int r = 0; r < R; r++) pw[r] = L::merge(pw[r], ph[r]);
             }
         }
         uint32_t diag = hdiag;

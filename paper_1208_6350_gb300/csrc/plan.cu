@@ -29,6 +29,12 @@ __device__ __forceinline__ int pick_class16(int rows, const Scoring &sc) {
     return long_pair(rows, false, sc.dna4) ? kClassLong16 : pick_s16(rows);
 }
 
+// Below this many pairs the thread-per-pair band kernel would occupy a few
+// percent of the GPU's threads: the begins then come from the ring reverse
+// fill and the CIGARs from the warp traceback (one pair per 16 or 32 lanes).
+constexpr int kSmallBatch = 1 << 14;
+__device__ __forceinline__ bool small_batch(const BatchView &b) { return b.npairs < kSmallBatch; }
+
 __device__ __forceinline__ int cost_bin(long long cost) {
     // 32 bins per doubling of cost, descending order inside a variant
     float lg = log2f((float)(cost < 1 ? 1 : cost));
@@ -58,10 +64,21 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
         if (r.score1 <= 0 || (r.flags & kResInternal)) { keys[p] = -1; return; }
         rows = r.read_end1 + 1;
         const int G = reverse_gap_bound(r.read_end1, r.score1, sc);
-        if (G >= 0 && 2 * G + 1 <= kBandMaxWidth && rows <= kBandMaxRows) { keys[p] = -1; return; }
+        if (!small_batch(b) && G >= 0 && 2 * G + 1 <= kBandMaxWidth && rows <= kBandMaxRows) {
+            keys[p] = -1;
+            return;
+        }
         cols = reverse_window(r.read_end1, r.ref_end1, r.score1, sc);
         if (r.flags & GSW_RES_S32) v = long_pair(rows, true, sc.dna4) ? kClassLong32 : kVarS32;
         else v = pick_class16(rows, sc);
+        // a query of several strips reverses in the CTA kernel: its strips run
+        // concurrently, so the stop at the first column reaching score1 (often
+        // a few dozen columns into a window of thousands) ends every strip,
+        // where a group would finish the upper strips over the whole window
+        // before the last one starts
+        // (4-letter DNA: a general alphabet's CTA holds 4 warps per SM)
+        if (sc.dna4 && v != kClassLong16 && v != kClassLong32 && rows > variant_rows(v))
+            v = v == kVarS32 ? kClassLong32 : kClassLong16;
     } else if (mode == kPlanTrace) {
         const gsw_result r = b.res[p];
         if (r.score1 <= 0 || !(r.flags & kResPendingTrace) || (r.flags & kResInternal) || r.read_begin1 < 0) {
@@ -98,7 +115,7 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
             int dlo, dhi;
             width = band_range(la, lb, r.score1, sc, &dlo, &dhi);
             rows = la;
-            if (width > kBandMaxWidth || rows > kBandMaxRows) {
+            if (small_batch(b) || width > kBandMaxWidth || rows > kBandMaxRows) {
                 b.res[p].flags |= kResPendingTrace;
                 keys[p] = -1;
                 return;

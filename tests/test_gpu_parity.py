@@ -359,3 +359,12 @@ def test_repeated_call_replays_captured_graphs(ctx):
     got, g = call()
     assert g >= 1  # the first segment replays; the second depends on the new traceback needs
     compare(b2, run_oracle(b2, colmax=False), got, check_colmax=False)
+
+
+def test_large_batch_uses_the_band_kernel(ctx):
+    # from 2^14 pairs on, narrow bands go to the thread-per-pair band kernel
+    # (reverse + traceback in one thread); smaller batches take the warp
+    # kernels.  Every pair of a 20,000-pair short-read batch is compared.
+    b = wl.config2(20000, seed=12)
+    assert b.npairs >= 1 << 14
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
