@@ -116,9 +116,11 @@ int gsw_context_destroy(gsw_ctx *ctx);
  * bucketed by length in GSW_TUNE_ROWS-row buckets; for each bucket a fill class
  * is chosen: 0..6 = one pair per 16-lane group with 2..8 row words per lane
  * (64..256 query rows per strip; longer queries run several strips), 8 = one
- * pair per CTA (512-row strips pipelined across the warps), -1 = the default
- * rule (the smallest one-strip class, the CTA class from 1792 rows).  The
- * choice changes speed only: every class gives the same results.
+ * pair per CTA (512-row strips pipelined across the warps), 9..13 = one pair
+ * per 8-lane group with 8, 10, 12, 14, 16 row words per lane (128..256 rows
+ * per strip), -1 = the default rule (the smallest one-strip class of 0..6, the
+ * CTA class from 1792 rows).  The choice changes speed only: every class
+ * gives the same results.
  */
 #define GSW_TUNE_BUCKETS 32
 #define GSW_TUNE_ROWS 32
@@ -138,7 +140,7 @@ int gsw_autotune(gsw_ctx *ctx, const int8_t *matrix, int32_t alphabet, int32_t g
                  int32_t target_len, gsw_tune *out);
 
 /* Installs a table (e.g. one saved from gsw_autotune); NULL restores the
- * default rule.  Errors: GSW_EINVAL (a class outside -1..6, 8). */
+ * default rule.  Errors: GSW_EINVAL (a class outside -1..6, 8..13). */
 int gsw_context_set_tune(gsw_ctx *ctx, const gsw_tune *tune);
 
 /* Sizes the context's persistent launches for at most `sms` SMs (0: all), so

@@ -776,7 +776,7 @@ int gsw_context_set_tune(gsw_ctx *c, const gsw_tune *t) {
         return GSW_OK;
     }
     for (int b = 0; b < GSW_TUNE_BUCKETS; b++)
-        if (t->fill_class[b] < -1 || t->fill_class[b] > 8 || t->fill_class[b] == 7)
+        if (t->fill_class[b] < -1 || t->fill_class[b] > 13 || t->fill_class[b] == 7)
             return set_err(GSW_EINVAL, "fill class %d of bucket %d", t->fill_class[b], b);
     std::memcpy(c->tune, t->fill_class, sizeof(c->tune));
     return GSW_OK;

@@ -62,13 +62,23 @@ enum FillMode : int32_t {
     X(4, 16, 6, 0)           \
     X(5, 16, 7, 0)           \
     X(6, 16, 8, 0)           \
-    X(7, 32, 8, 1)
+    X(7, 32, 8, 1)           \
+    X(8, 8, 8, 0)            \
+    X(9, 8, 10, 0)           \
+    X(10, 8, 12, 0)          \
+    X(11, 8, 14, 0)          \
+    X(12, 8, 16, 0)
 struct Variant {
     int P, R, s32;
 };
-constexpr int kNumVariants = 8;
+constexpr int kNumVariants = 13;
 constexpr int kVarS32 = 7;
-constexpr int kVarMaxS16 = 6;
+constexpr int kVarMaxS16 = 6;  // the default rule picks among 0..6
+// 8..12: one pair per 8 lanes with 8..16 row words per lane (128..256 rows per
+// strip): twice the cells per lane and step of the 16-lane variants, so the
+// per-step costs (shuffles, letter loads, trackers) weigh half as much; chosen
+// per query length by the autotuner
+constexpr int kVarP8First = 8;
 // Two more fill classes: pairs whose query spans many strips run on a whole
 // CTA (k_fill_long), one 32-lane warp per strip, strips pipelined across the
 // CTA's warps; 16-bit lanes (2*32*8 = 512 rows per strip) or 32-bit lanes

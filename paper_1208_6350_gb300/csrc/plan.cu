@@ -24,8 +24,10 @@ __device__ __forceinline__ int pick_s16(int rows) {
 // the smallest one-strip variant, or the CTA class for queries of many strips.
 __device__ __forceinline__ int pick_class16(int rows, const Scoring &sc) {
     const int b = (rows - 1) / GSW_TUNE_ROWS;
-    if (rows >= 1 && b < GSW_TUNE_BUCKETS && sc.fill_class[b] >= 0)
-        return sc.fill_class[b] == 8 ? kClassLong16 : sc.fill_class[b];
+    if (rows >= 1 && b < GSW_TUNE_BUCKETS && sc.fill_class[b] >= 0) {
+        const int c = sc.fill_class[b];  // public codes: 0..6, 8 CTA, 9..13 8-lane variants
+        return c == 8 ? kClassLong16 : (c >= 9 ? kVarP8First + (c - 9) : c);
+    }
     return long_pair(rows, false, sc.dna4) ? kClassLong16 : pick_s16(rows);
 }
 

@@ -100,11 +100,17 @@ extern "C" int gsw_autotune(gsw_ctx *ctx, const int8_t *matrix, int32_t alphabet
             break;
         }
         const int def = default_class(rows, dna);
-        std::vector<int> cand;
+        std::vector<int> cand;  // public codes (include/gsw.h)
         if (rows <= variant_rows(kVarMaxS16)) {
             cand = {def, std::min(def + 1, (int)kVarMaxS16), kVarMaxS16, 8};
+            // 8-lane variants: the smallest holding the query in one strip, and the next
+            for (int i = 0, got = 0; i <= kNumVariants - 1 - kVarP8First && got < 2; i++)
+                if (variant_rows(kVarP8First + i) >= rows) {
+                    cand.push_back(9 + i);
+                    got++;
+                }
         } else {
-            cand = {4, 5, kVarMaxS16, 8};  // several strips per group, or the CTA kernel
+            cand = {4, 5, kVarMaxS16, 8, 9 + (kNumVariants - 1 - kVarP8First)};  // several strips, or the CTA kernel
             cand.push_back(def);
         }
         std::sort(cand.begin(), cand.end());
