@@ -217,7 +217,12 @@ def run_gsw(args):
     cig = torch.zeros(cap, dtype=torch.int32, device=dev)
     ctx = gsw.Context(local, args.budget_gb << 30)
     tune = None
-    if not args.no_tune:
+    if args.tune_table:
+        # a saved table instead of measuring (e.g. to profile one variant)
+        table = [int(x) for x in args.tune_table.split(",")]
+        ctx.set_tune(table + [-1] * (gsw.TUNE_BUCKETS - len(table)))
+        tune = {"buckets_of_rows": gsw.TUNE_ROWS, "fill_class": table, "source": "--tune-table"}
+    elif not args.no_tune:
         # fill class per query-length bucket, measured on this GPU for this
         # scoring and the workload's mean target length (results unchanged)
         t0 = time.perf_counter()
@@ -601,6 +606,7 @@ def main():
                     help="serving_stream: leading requests also run by the plain per-pair baseline")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving run of the default line")
     ap.add_argument("--no-tune", action="store_true", help="default fill classes instead of the autotuner's")
+    ap.add_argument("--tune-table", default="", help="fill class per 32-row bucket, comma-separated (no tuning)")
     ap.add_argument("--budget-gb", type=int, default=24)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-pairs", type=int, default=4000)

@@ -48,6 +48,12 @@
 #ifndef GSW_FILL_SPLIT
 #define GSW_FILL_SPLIT 1
 #endif
+// 1: F' = max(F - X, T - O) with T = max(H(i-1,j-1) + W, E, 0), off the F
+// chain but an extra add per cell; 0: F' = max(F - X, H - O) sharing H - O
+// with E (one add fewer, longer chain)
+#ifndef GSW_FILL_TTRICK
+#define GSW_FILL_TTRICK 0
+#endif
 #include <type_traits>
 #include <cstring>
 #include <mutex>
@@ -408,13 +414,20 @@ struct StripRunner {
         for (int r = 0; r < R; r++) {
             uint32_t tt = L::addmax(diag, pw[r], E[r]);
             tt = L::vmax(tt, Z2);
-            const uint32_t to = tt + kO;
             const uint32_t h = L::vmax(tt, f);
-            f = L::addmax(f, kXm, to);  // = max(F - X, H - O) since O >= X
+#if GSW_FILL_TTRICK
+            f = L::addmax(f, kXm, tt + kO);  // = max(F - X, H - O) since O >= X
+            E[r] = L::addmax(E[r], kXm, h + kO);
+#else
+            // one H - O for both gap states; the F chain then runs through
+            // h (3 dependent instructions per row), hidden by the other warps
+            const uint32_t ho = h + kO;
+            f = L::addmax(f, kXm, ho);
+            E[r] = L::addmax(E[r], kXm, ho);
+#endif
             diag = H[r];
             H[r] = h;
             m = L::vmax(m, h);
-            E[r] = L::addmax(E[r], kXm, h + kO);
         }
         uint32_t cme = m;
         if constexpr (CHECKED) {
