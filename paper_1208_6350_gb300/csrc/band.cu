@@ -122,6 +122,40 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
         typename DirWord<W>::T dw;
         zero<W>(dw);
         int row_hit = -1;
+        // rows whose band cells all lie inside the rectangle (most of them):
+        // no boundary tests per cell; cells past the band width stay -inf
+        const bool interior = i >= 1 && i + dlo >= 1 && i + dlo + wb - 1 <= s.cols;
+        if (interior) {
+#pragma unroll
+            for (int k = 0; k < W; k++) {
+                const int hup = k + 1 < W ? Hp[k + 1] : kNegB;
+                const int fup = k + 1 < W ? Fp[k + 1] : kNegB;
+                const int fo = hup - O, eo = hleft - O;
+                int F = max(fo, fup - X);
+                int E = max(eo, eleft - X);
+                int w;
+                if constexpr (DNA) w = (int)(int8_t)(uint8_t)(wpack >> (8 * tw[k]));
+                else w = wrow[tw[k]];
+                const int hdg = Hp[k] + w;
+                int H = max(hdg, max(E, F));
+                if (k >= wb) {
+                    H = kNegB;
+                    E = kNegB;
+                    F = kNegB;
+                }
+                if constexpr (REV) {
+                    if (H == target && row_hit < 0) row_hit = i + dlo + k;
+                } else {
+                    const uint32_t src = H == hdg ? 0u : (H == E ? 1u : 2u);
+                    put_nib<W>(dw, k, src | (E == eo ? 4u : 0u) | (F == fo ? 8u : 0u));
+                    if (i == s.rows && i + dlo + k == s.cols) fin = H;
+                }
+                Hp[k] = H;
+                Fp[k] = F;
+                hleft = H;
+                eleft = E;
+            }
+        } else {
 #pragma unroll
         for (int k = 0; k < W; k++) {
             const int j = i + dlo + k;
@@ -165,6 +199,7 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
             Fp[k] = F;
             hleft = H;
             eleft = E;
+        }
         }
         if constexpr (REV) {
             if (row_hit >= 0 && row_hit < best_j) {
