@@ -368,3 +368,19 @@ def test_large_batch_uses_the_band_kernel(ctx):
     b = wl.config2(20000, seed=12)
     assert b.npairs >= 1 << 14
     compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
+def test_empty_batch_and_all_empty_pairs(ctx):
+    # zero pairs is a no-op; pairs with an empty query or target give score
+    # 0, positions -1 and no CIGAR (the oracle's empty alignment)
+    res, cig, _, rc = ctx.align_host(np.zeros(0, np.uint8), np.zeros(0, np.int64), np.zeros(0, np.int32),
+                                     np.zeros(0, np.uint8), np.zeros(0, np.int64), np.zeros(0, np.int32),
+                                     wl.dna_matrix(2, -2), 3, 1)
+    assert rc == gsw.GSW_OK and len(res) == 0
+    qs = [np.zeros(0, np.uint8), np.array([1, 2], np.uint8), np.zeros(0, np.uint8)]
+    ts = [np.array([0, 1, 2], np.uint8), np.zeros(0, np.uint8), np.zeros(0, np.uint8)]
+    b = _batch(qs, ts, wl.dna_matrix(2, -2), 3, 1, "empty")
+    got = run_gpu_host(ctx, b)
+    compare(b, run_oracle(b), got)
+    assert (got[0]["score1"] == 0).all() and (got[0]["cigar_len"] == 0).all()
+    assert (got[0]["ref_end1"] == -1).all() and (got[0]["read_begin1"] == -1).all()
