@@ -71,6 +71,8 @@ def workload_config(cfg, b):
     out = dict(cfg)
     out["outputs"] = "score1, ends, score2, ref_end2, begins, CIGAR"
     nbytes = len(b.q) + len(b.t)
+    if str(cfg.get("input", "")).startswith("2-bit"):
+        nbytes = (len(b.q) + 3) // 4 + (len(b.t) + 3) // 4
     out["l2"] = (f"inputs {nbytes / 1e9:.2f} GB per step, " +
                  ("larger than the 129 MB L2 (no flush)" if nbytes > 129e6 else "smaller than L2"))
     out["cells"] = b.cells
@@ -208,7 +210,12 @@ def run_gsw(args):
     b, wcfg = make_workload(args.workload, args.pairs, rank)
     cells = b.cells
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    q, t = T(b.q), T(b.t)
+    # DNA arenas stay 2-bit packed (4 letters per byte) in memory; the call
+    # expands them on the device
+    packed = b.alphabet == "ACGT" and not args.no_pack
+    pk = (lambda a: gsw.pack2(a)) if packed else (lambda a: a)
+    wcfg = dict(wcfg, input="2-bit packed DNA arenas (GSW_PACKED2)" if packed else "one byte per letter")
+    q, t = T(pk(b.q)), T(pk(b.t))
     qo, to = T(b.q_off.astype(np.int64)), T(b.t_off.astype(np.int64))
     ql, tl = T(b.q_len.astype(np.int32)), T(b.t_len.astype(np.int32))
     n = b.npairs
@@ -236,7 +243,7 @@ def run_gsw(args):
     # sequence in CUDA graphs (the legacy default stream cannot be captured)
     stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize(dev)
-    flags = gsw.GSW_CIGAR | gsw.GSW_TIMING
+    flags = gsw.GSW_CIGAR | gsw.GSW_TIMING | (gsw.GSW_PACKED2 if packed else 0)
 
     def step():
         gsw.gsw_align_batch(ctx.handle, n, q, qo, ql, t, to, tl, b.W, b.gap_open, b.gap_extend, flags,
@@ -277,7 +284,7 @@ def run_gsw(args):
     # e2e: the same call on host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, gsw, b, ctx, stream, dev, torch)
+        e2e = run_e2e(args, gsw, b, ctx, stream, dev, torch, packed)
 
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -316,16 +323,16 @@ def run_gsw(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, gsw, b, ctx, stream, dev, torch):
+def run_e2e(args, gsw, b, ctx, stream, dev, torch, packed=False):
     n = b.npairs
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-    q, t = pin(b.q), pin(b.t)
+    q, t = (pin(gsw.pack2(b.q)), pin(gsw.pack2(b.t))) if packed else (pin(b.q), pin(b.t))
     qo, to = pin(b.q_off.astype(np.int64)), pin(b.t_off.astype(np.int64))
     ql, tl = pin(b.q_len.astype(np.int32)), pin(b.t_len.astype(np.int32))
     res = pin(np.zeros(n, gsw.RESULT_DTYPE).view(np.int32))
     cap = int(min(32 * n + 1024 + (b.q_len.sum() + b.t_len.sum()) // 4, 1 << 30))
     cig = pin(np.zeros(cap, np.uint32))
-    flags = gsw.GSW_CIGAR | gsw.GSW_HOST_IO
+    flags = gsw.GSW_CIGAR | gsw.GSW_HOST_IO | (gsw.GSW_PACKED2 if packed else 0)
 
     def step():
         gsw.gsw_align_batch(ctx.handle, n, q, qo, ql, t, to, tl, b.W, b.gap_open, b.gap_extend, flags,
@@ -607,6 +614,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving run of the default line")
     ap.add_argument("--no-tune", action="store_true", help="default fill classes instead of the autotuner's")
     ap.add_argument("--tune-table", default="", help="fill class per 32-row bucket, comma-separated (no tuning)")
+    ap.add_argument("--no-pack", action="store_true", help="DNA arenas one byte per letter instead of 2-bit packed")
     ap.add_argument("--budget-gb", type=int, default=24)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-pairs", type=int, default=4000)

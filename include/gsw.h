@@ -62,6 +62,11 @@ extern "C" {
                                sequence per pair, no batching */
 #define GSW_TIMING 0x40u    /* record CUDA events around each stage of the call
                                (read them with gsw_last_stats) */
+#define GSW_PACKED2 0x80u   /* q and t are 2-bit packed DNA arenas: letter x (codes
+                               0..3) in bits 2(x%4)..2(x%4)+1 of byte x/4; offsets
+                               and lengths count letters; alphabet must be 4.  The
+                               call expands them on the device (one kernel); not
+                               with GSW_PLAIN or gsw_align_profile */
 
 /* CIGAR words: (run_length << 4) | op, op 0 = M (match or mismatch column),
  * 1 = I (query letter against a gap), 2 = D (target letter against a gap). */

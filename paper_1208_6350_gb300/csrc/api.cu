@@ -84,6 +84,7 @@ struct gsw_ctx {
     DevBuf trace_dirs, trace_ops, band_scr, ring_meta;
     DevBuf misc;  // counters: trace head, cigar cursor, trace need, max lengths
     DevBuf io_q, io_t, io_qoff, io_toff, io_qlen, io_tlen, io_res, io_cigar, io_colmax, io_cmoff;
+    DevBuf io_qp, io_tp;  // packed input staging (GSW_PACKED2 with GSW_HOST_IO)
     DevBuf prof_qoff, prof_qlen;
     void *host_small = nullptr;  // pinned readback area
     cudaEvent_t ev[GSW_NSTAGES + 1] = {};
@@ -188,6 +189,7 @@ enum MiscSlot {
     kMiscValid = 3,
     kMiscNeed = 4,   // 2 words: anti-diagonal traceback (direction words, op words per pair)
     kMiscRing = 6,   // 3 words: wide-band traceback (total words, max words of a pair, max op words)
+    kMiscExt = 9,    // 2 words: arena extents in letters (packed input)
     kMiscWords = 16
 };
 
@@ -518,8 +520,10 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
 int check_common(gsw_ctx *ctx, int32_t npairs, uint32_t flags) {
     if (!ctx) return set_err(GSW_EINVAL, "context is NULL");
     if (npairs < 0) return set_err(GSW_EINVAL, "npairs < 0");
-    if (flags & ~(GSW_BEGIN | GSW_CIGAR | GSW_COLMAX | GSW_HOST_IO | GSW_FORCE_S32 | GSW_PLAIN | GSW_TIMING))
+    if (flags & ~(GSW_BEGIN | GSW_CIGAR | GSW_COLMAX | GSW_HOST_IO | GSW_FORCE_S32 | GSW_PLAIN | GSW_TIMING |
+                  GSW_PACKED2))
         return set_err(GSW_EINVAL, "unknown flag bits 0x%x", flags);
+    if ((flags & GSW_PACKED2) && (flags & GSW_PLAIN)) return set_err(GSW_EINVAL, "GSW_PACKED2 with GSW_PLAIN");
     return GSW_OK;
 }
 
@@ -581,8 +585,20 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
             GSW_TRY(ensure(ctx, ctx->io_colmax, sizeof(int32_t) * (size_t)std::max<int64_t>(cmext, 1)));
             GSW_TRY(ensure(ctx, ctx->io_cmoff, sizeof(int64_t) * npairs));
         }
-        CUDA_TRY(cudaMemcpyAsync(ctx->io_q.p, q, qext, cudaMemcpyHostToDevice, st));
-        CUDA_TRY(cudaMemcpyAsync(ctx->io_t.p, t, text, cudaMemcpyHostToDevice, st));
+        if (flags & GSW_PACKED2) {
+            // packed bytes in, one byte per letter on the device
+            const size_t qb = (size_t)(qext + 3) / 4, tb = (size_t)(text + 3) / 4;
+            GSW_TRY(ensure(ctx, ctx->io_qp, std::max<size_t>(qb, 1)));
+            GSW_TRY(ensure(ctx, ctx->io_tp, std::max<size_t>(tb, 1)));
+            CUDA_TRY(cudaMemcpyAsync(ctx->io_qp.p, q, qb, cudaMemcpyHostToDevice, st));
+            CUDA_TRY(cudaMemcpyAsync(ctx->io_tp.p, t, tb, cudaMemcpyHostToDevice, st));
+            CUDA_TRY(launch_unpack2((const uint8_t *)ctx->io_qp.p, (uint8_t *)ctx->io_q.p, qext, st));
+            CUDA_TRY(launch_unpack2((const uint8_t *)ctx->io_tp.p, (uint8_t *)ctx->io_t.p, text, st));
+            ctx->launches += 2;
+        } else {
+            CUDA_TRY(cudaMemcpyAsync(ctx->io_q.p, q, qext, cudaMemcpyHostToDevice, st));
+            CUDA_TRY(cudaMemcpyAsync(ctx->io_t.p, t, text, cudaMemcpyHostToDevice, st));
+        }
         CUDA_TRY(cudaMemcpyAsync(ctx->io_qoff.p, q_off, sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, st));
         CUDA_TRY(cudaMemcpyAsync(ctx->io_toff.p, t_off, sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, st));
         CUDA_TRY(cudaMemcpyAsync(ctx->io_qlen.p, q_len, sizeof(int32_t) * npairs, cudaMemcpyHostToDevice, st));
@@ -613,12 +629,31 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
         int32_t *ml = reinterpret_cast<int32_t *>(misc + kMiscMaxLen);
         CUDA_TRY(launch_max_lengths(q_len, t_len, npairs, ml, st));
         ctx->launches += 1;
+        if (flags & GSW_PACKED2) {
+            CUDA_TRY(launch_extents(q_off, q_len, t_off, t_len, npairs, misc + kMiscExt, st));
+            ctx->launches += 1;
+        }
         int32_t *hs = reinterpret_cast<int32_t *>(ctx->host_small);
         CUDA_TRY(cudaMemcpyAsync(hs, ml, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        if (flags & GSW_PACKED2)
+            CUDA_TRY(cudaMemcpyAsync(hs + 4, misc + kMiscExt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                     st));
         CUDA_TRY(cudaStreamSynchronize(st));
         maxm = hs[0];
         maxn = hs[1];
         if (maxm >= (1 << 24) || maxn >= (1 << 24)) return set_err(GSW_EINVAL, "a length is >= 2^24");
+        if (flags & GSW_PACKED2) {
+            // expand the caller's packed arenas into context scratch
+            unsigned long long ext[2];
+            std::memcpy(ext, hs + 4, sizeof(ext));
+            GSW_TRY(ensure(ctx, ctx->io_q, (size_t)std::max<unsigned long long>(ext[0], 1)));
+            GSW_TRY(ensure(ctx, ctx->io_t, (size_t)std::max<unsigned long long>(ext[1], 1)));
+            CUDA_TRY(launch_unpack2(q, (uint8_t *)ctx->io_q.p, (long long)ext[0], st));
+            CUDA_TRY(launch_unpack2(t, (uint8_t *)ctx->io_t.p, (long long)ext[1], st));
+            ctx->launches += 2;
+            bv.q = (const uint8_t *)ctx->io_q.p;
+            bv.t = (const uint8_t *)ctx->io_t.p;
+        }
     }
     CUDA_TRY(cudaMemsetAsync(misc + kMiscCursor, 0, sizeof(unsigned long long), st));
     CUDA_TRY(launch_validate(bv, sc, reinterpret_cast<int32_t *>(misc + kMiscValid), st));
@@ -795,7 +830,7 @@ int gsw_context_destroy(gsw_ctx *c) {
     DevBuf *all[] = {&c->plan_keys, &c->plan_order, &c->plan_small, &c->fill_cm, &c->fill_bnd, &c->trace_dirs,
                      &c->trace_ops, &c->band_scr, &c->misc, &c->io_q, &c->io_t, &c->io_qoff, &c->io_toff, &c->io_qlen,
                      &c->io_tlen, &c->io_res, &c->io_cigar, &c->io_colmax, &c->io_cmoff, &c->prof_qoff,
-                     &c->prof_qlen, &c->ring_meta};
+                     &c->prof_qlen, &c->ring_meta, &c->io_qp, &c->io_tp};
     c->st = nullptr;
     c->capturing = false;
     for (GraphSeg &g : c->seg)
@@ -817,6 +852,7 @@ int gsw_align_batch(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_
                     const int64_t *colmax_off, void *stream) {
     Scoring sc;
     GSW_TRY(make_scoring(matrix, alphabet, gap_open, gap_extend, &sc));
+    if ((flags & GSW_PACKED2) && alphabet != 4) return set_err(GSW_EINVAL, "GSW_PACKED2 needs the 4-letter alphabet");
     if (flags & GSW_PLAIN) return plain_impl(ctx, npairs, q, q_off, q_len, t, t_off, t_len, sc, flags,
                                                   mask_len, results, cigar, cigar_capacity, colmax, colmax_off,
                                                   (cudaStream_t)stream);
@@ -865,6 +901,7 @@ int gsw_align_profile(gsw_ctx *ctx, const gsw_profile *prof, int32_t ntargets, c
                       const int64_t *colmax_off, void *stream) {
     if (!ctx || !prof || prof->ctx != ctx) return set_err(GSW_EINVAL, "bad profile or context");
     GSW_TRY(check_common(ctx, ntargets, flags));
+    if (flags & GSW_PACKED2) return set_err(GSW_EINVAL, "GSW_PACKED2 is for gsw_align_batch");
     if (ntargets == 0) return GSW_OK;
     cudaStream_t st = (cudaStream_t)stream;
     CUDA_TRY(cudaSetDevice(ctx->device));

@@ -287,6 +287,11 @@ cudaError_t launch_band(const BatchView &b, const Scoring &sc, const PlanBuffers
 // small helpers (misc.cu)
 cudaError_t launch_max_lengths(const int32_t *q_len, const int32_t *t_len, int32_t n, int32_t *out2,
                                cudaStream_t st);
+// largest offset + length of the query and target arenas (letters)
+cudaError_t launch_extents(const int64_t *q_off, const int32_t *q_len, const int64_t *t_off, const int32_t *t_len,
+                           int32_t n, unsigned long long *out2, cudaStream_t st);
+// 2-bit packed DNA letters to one byte per letter
+cudaError_t launch_unpack2(const uint8_t *in, uint8_t *out, long long nletters, cudaStream_t st);
 cudaError_t launch_validate(const BatchView &b, const Scoring &sc, int32_t *bad, cudaStream_t st);
 cudaError_t launch_fill_const(int32_t *dst, int32_t v, int32_t n, cudaStream_t st);
 cudaError_t launch_fill_const64(int64_t *dst, int64_t v, int32_t n, cudaStream_t st);

@@ -41,7 +41,76 @@ __global__ void k_validate(BatchView b, int32_t A, int32_t *bad) {
     if (__any_sync(0xFFFFFFFFu, found) && lane == 0) atomicOr(bad, 1);
 }
 
+// largest extent (offset + length) of each arena, in letters
+__global__ void k_extents(const int64_t *q_off, const int32_t *q_len, const int64_t *t_off, const int32_t *t_len,
+                          int32_t n, unsigned long long *out2) {
+    unsigned long long eq = 0, et = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        eq = max(eq, (unsigned long long)(q_off[i] + q_len[i]));
+        et = max(et, (unsigned long long)(t_off[i] + t_len[i]));
+    }
+    eq = max(eq, __shfl_xor_sync(0xFFFFFFFFu, eq, 16));
+    eq = max(eq, __shfl_xor_sync(0xFFFFFFFFu, eq, 8));
+    eq = max(eq, __shfl_xor_sync(0xFFFFFFFFu, eq, 4));
+    eq = max(eq, __shfl_xor_sync(0xFFFFFFFFu, eq, 2));
+    eq = max(eq, __shfl_xor_sync(0xFFFFFFFFu, eq, 1));
+    et = max(et, __shfl_xor_sync(0xFFFFFFFFu, et, 16));
+    et = max(et, __shfl_xor_sync(0xFFFFFFFFu, et, 8));
+    et = max(et, __shfl_xor_sync(0xFFFFFFFFu, et, 4));
+    et = max(et, __shfl_xor_sync(0xFFFFFFFFu, et, 2));
+    et = max(et, __shfl_xor_sync(0xFFFFFFFFu, et, 1));
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&out2[0], eq);
+        atomicMax(&out2[1], et);
+    }
+}
+
+// 2-bit packed letters to one byte each: a thread expands 16 letters (4 bytes
+// in, one 16-byte store out)
+__global__ void k_unpack2(const uint8_t *in, uint8_t *out, long long nletters) {
+    const long long groups = (nletters + 15) / 16;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < groups;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long nbytes = (nletters + 3) / 4;
+        uint32_t w = 0;
+        for (int b = 0; b < 4; b++) {
+            const long long at = g * 4 + b;
+            if (at < nbytes) w |= (uint32_t)in[at] << (8 * b);
+        }
+        uint32_t o[4];
+        for (int k = 0; k < 4; k++) {
+            uint32_t v = 0;
+            for (int x = 0; x < 4; x++) v |= ((w >> (2 * (4 * k + x))) & 3u) << (8 * x);
+            o[k] = v;
+        }
+        if ((g + 1) * 16 <= nletters) {
+            *reinterpret_cast<uint4 *>(out + g * 16) = make_uint4(o[0], o[1], o[2], o[3]);
+        } else {
+            for (long long x = g * 16; x < nletters; x++) out[x] = (uint8_t)((o[(x - g * 16) / 4] >> (8 * ((x - g * 16) % 4))) & 3u);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_extents(const int64_t *q_off, const int32_t *q_len, const int64_t *t_off, const int32_t *t_len,
+                           int32_t n, unsigned long long *out2, cudaStream_t st) {
+    cudaMemsetAsync(out2, 0, 2 * sizeof(unsigned long long), st);
+    if (n > 0) {
+        int blocks = (n + 255) / 256;
+        blocks = blocks > 1024 ? 1024 : blocks;
+        k_extents<<<blocks, 256, 0, st>>>(q_off, q_len, t_off, t_len, n, out2);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack2(const uint8_t *in, uint8_t *out, long long nletters, cudaStream_t st) {
+    if (nletters > 0) {
+        long long blocks = ((nletters + 15) / 16 + 255) / 256;
+        k_unpack2<<<(int)(blocks > 8192 ? 8192 : blocks), 256, 0, st>>>(in, out, nletters);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_validate(const BatchView &b, const Scoring &sc, int32_t *bad, cudaStream_t st) {
     cudaMemsetAsync(bad, 0, sizeof(int32_t), st);

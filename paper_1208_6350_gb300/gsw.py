@@ -31,6 +31,7 @@ GSW_HOST_IO = 0x8
 GSW_FORCE_S32 = 0x10
 GSW_PLAIN = 0x20
 GSW_TIMING = 0x40
+GSW_PACKED2 = 0x80
 GSW_NSTAGES = 7
 STAGE_NAMES = ("plan_fwd", "fill_fwd", "refill_s32", "reverse_wide", "band", "trace_wide", "pipeline")
 
@@ -252,6 +253,17 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream  # torch.cuda.Stream
+
+
+def pack2(codes) -> np.ndarray:
+    """DNA codes 0..3 packed 4 to a byte (letter x in bits 2(x%4) of byte x/4),
+    the GSW_PACKED2 layout; offsets and lengths stay in letters."""
+    c = np.ascontiguousarray(codes, np.uint8)
+    n = len(c)
+    pad = np.zeros((n + 3) // 4 * 4, np.uint8)
+    pad[:n] = c & 3
+    p = pad.reshape(-1, 4)
+    return (p[:, 0] | (p[:, 1] << 2) | (p[:, 2] << 4) | (p[:, 3] << 6)).astype(np.uint8)
 
 
 class Context:

@@ -64,3 +64,19 @@ def test_tuning_calls_reject_null_context_without_gpu():
     lib = gsw.load()
     assert lib.gsw_context_set_tune(None, None) == gsw.GSW_EINVAL
     assert lib.gsw_autotune(None, None, 4, 3, 1, 1000, None) == gsw.GSW_EINVAL
+
+
+def test_pack2_layout_and_packed_flag_checks_without_gpu():
+    import numpy as np
+    rng = np.random.default_rng(3)
+    c = rng.integers(0, 4, 1003).astype(np.uint8)
+    p = gsw.pack2(c)
+    assert len(p) == 251
+    back = np.array([(p[x // 4] >> (2 * (x % 4))) & 3 for x in range(len(c))], np.uint8)
+    assert (back == c).all()
+    W = np.eye(20, dtype=np.int8)
+    lib = gsw.load()
+    # packed input needs the 4-letter alphabet: rejected before any device work
+    rc = lib.gsw_align_batch(None, 1, None, None, None, None, None, None, W.ctypes.data, 20, 3, 1,
+                             gsw.GSW_PACKED2, -1, None, None, 0, None, None, None)
+    assert rc == gsw.GSW_EINVAL

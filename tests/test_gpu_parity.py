@@ -384,3 +384,18 @@ def test_empty_batch_and_all_empty_pairs(ctx):
     compare(b, run_oracle(b), got)
     assert (got[0]["score1"] == 0).all() and (got[0]["cigar_len"] == 0).all()
     assert (got[0]["ref_end1"] == -1).all() and (got[0]["read_begin1"] == -1).all()
+
+
+@pytest.mark.parametrize("host_io", [True, False])
+def test_packed_2bit_inputs(ctx, host_io):
+    # GSW_PACKED2: both arenas 4 letters to a byte, offsets in letters (not
+    # multiples of 4), expanded on the device; results equal the oracle's on
+    # the unpacked letters
+    b = mixed_dna(60, 300, 260, 700)
+    ora = run_oracle(b)
+    qp, tp = gsw.pack2(b.q), gsw.pack2(b.t)
+    packed = wl.Batch(b.name, qp, b.q_off, b.q_len, tp, b.t_off, b.t_len, b.W, b.gap_open, b.gap_extend,
+                      b.alphabet)
+    flags = gsw.GSW_CIGAR | gsw.GSW_PACKED2
+    got = run_gpu_host(ctx, packed, flags=flags) if host_io else run_gpu_device(ctx, packed, flags=flags)
+    compare(b, ora, got)
