@@ -148,6 +148,28 @@ int gsw_autotune(gsw_ctx *ctx, const int8_t *matrix, int32_t alphabet, int32_t g
  * default rule.  Errors: GSW_EINVAL (a class outside -1..6, 8..13). */
 int gsw_context_set_tune(gsw_ctx *ctx, const gsw_tune *tune);
 
+/*
+ * Reads against one long reference (whole viral, bacterial or chromosome
+ * sequences; the paper's genome alignments, Results).  Every read gets the
+ * record gsw_align_batch would give for the pair (read, whole reference):
+ * score1, ends, score2 / ref_end2 over the whole reference's max array,
+ * begins and CIGAR (flags GSW_BEGIN, GSW_CIGAR), bit-exact.  The reference is
+ * cut into windows owning `window` columns (0: the default, at least 65,536)
+ * that start earlier by the longest reference span of a positive-scoring
+ * local alignment of the longest read, so the work is one batch of
+ * reads x windows plus two small passes.  Pointers follow gsw_align_batch's
+ * rules (GSW_HOST_IO: all host); ref_len < 2^31; the reads' lengths < 2^24.
+ * Errors: GSW_EINVAL (arguments, or `window` smaller than 2 x mask + overlap),
+ * GSW_ENOMEM, GSW_ECUDA, GSW_ECIGAR_SPACE (records complete, CIGARs that do
+ * not fit have cigar_len = -needed).
+ */
+int gsw_align_to_reference(gsw_ctx *ctx, int32_t nreads, const uint8_t *q, const int64_t *q_off,
+                           const int32_t *q_len, const uint8_t *ref, int64_t ref_len,
+                           const int8_t *matrix, int32_t alphabet, int32_t gap_open,
+                           int32_t gap_extend, uint32_t flags, int32_t mask_len, int64_t window,
+                           gsw_result *results, uint32_t *cigar, int64_t cigar_capacity,
+                           void *stream);
+
 /* Sizes the context's persistent launches for at most `sms` SMs (0: all), so
  * that work of other streams finds free SMs while this context's kernels
  * run.  Results do not depend on it.  Errors: GSW_EINVAL (sms < 0). */

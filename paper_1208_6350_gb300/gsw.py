@@ -106,6 +106,8 @@ def load(build_if_missing: bool = True):
     lib.gsw_context_destroy.argtypes = [P]
     lib.gsw_context_set_sm_limit.argtypes = [P, ctypes.c_int]
     lib.gsw_context_set_sm_limit.restype = ctypes.c_int
+    lib.gsw_align_to_reference.argtypes = [P, i32, P, P, P, P, i64, P, i32, i32, i32, u32, i32, i64, P, P, i64, P]
+    lib.gsw_align_to_reference.restype = ctypes.c_int
     lib.gsw_autotune.argtypes = [P, P, i32, i32, i32, i32, ctypes.POINTER(GswTune)]
     lib.gsw_autotune.restype = ctypes.c_int
     lib.gsw_context_set_tune.argtypes = [P, ctypes.POINTER(GswTune)]
@@ -304,6 +306,25 @@ class Context:
         for b, c in enumerate(fill_class):
             t.fill_class[b] = int(c)
         _check(load().gsw_context_set_tune(self.handle, ctypes.byref(t)), "gsw_context_set_tune")
+
+    def align_to_reference(self, q, q_off, q_len, ref, matrix, gap_open, gap_extend, flags=GSW_CIGAR,
+                           mask_len=-1, window=0, cigar_capacity=None):
+        """Reads (host arrays) against one long reference (gsw_align_to_reference,
+        GSW_HOST_IO); returns (records, cigar words, status)."""
+        q = np.ascontiguousarray(q, np.uint8)
+        ref = np.ascontiguousarray(ref, np.uint8)
+        q_off = np.ascontiguousarray(q_off, np.int64)
+        q_len = np.ascontiguousarray(q_len, np.int32)
+        m = np.ascontiguousarray(matrix, dtype=np.int8)
+        n = len(q_len)
+        res = np.zeros(n, RESULT_DTYPE)
+        if cigar_capacity is None:
+            cigar_capacity = int(2 * q_len.sum() + 64 * n + 64) if flags & GSW_CIGAR else 0
+        cig = np.zeros(max(cigar_capacity, 1), np.uint32)
+        rc = load().gsw_align_to_reference(self.handle, n, _ptr(q), _ptr(q_off), _ptr(q_len), _ptr(ref), len(ref),
+                                           m.ctypes.data, m.shape[0], gap_open, gap_extend, flags | GSW_HOST_IO,
+                                           mask_len, window, _ptr(res), _ptr(cig), cigar_capacity, None)
+        return res, cig, rc
 
     def align_host(self, q, q_off, q_len, t, t_off, t_len, matrix, gap_open, gap_extend,
                    flags=GSW_CIGAR, mask_len=-1, cigar_capacity=None, colmax=False):
