@@ -568,6 +568,112 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reads_vs_reference(args):
+    """--workload reads_vs_reference_10M: 1,000 simulated 100-nt reads against
+    one 10 Mb reference (gsw_align_to_reference), every read against the whole
+    reference; GCUPS = sum of read length x reference length per second."""
+    import torch
+    from paper_1208_6350_gb300 import gsw, workloads as wl
+    import oracle
+    if int(os.environ.get("RANK", 0)) != 0:
+        return
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    n_reads = args.pairs or 1000
+    reads, ref = wl.reads_vs_reference(n_reads, 100, args.ref_len, seed=6)
+    cells = int(reads.q_len.astype(np.int64).sum()) * len(ref)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    q, qo, ql, R = T(reads.q), T(reads.q_off), T(reads.q_len), T(ref)
+    res = torch.zeros(n_reads * 12, dtype=torch.int32, device=dev)
+    cap = int(reads.q_len.sum()) * 2 + 64 * n_reads
+    cig = torch.zeros(cap, dtype=torch.int32, device=dev)
+    ctx = gsw.Context(0, args.budget_gb << 30)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+    W, O, X = reads.W, reads.gap_open, reads.gap_extend
+
+    def step():
+        gsw.gsw_align_to_reference(ctx.handle, n_reads, q, qo, ql, R, len(ref), W, O, X, gsw.GSW_CIGAR, -1, 0,
+                                   res, cig, cap, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness of what is timed: a few reads against the whole reference, oracle
+    checked = 0
+    if not args.no_check:
+        k = min(8, n_reads)
+        ores, ocg, _ = oracle.align_batch(reads.q, reads.q_off[:k], reads.q_len[:k], ref, np.zeros(k, np.int64),
+                                          np.full(k, len(ref), np.int32), W, O, X,
+                                          cigar_stride=int(reads.q_len.max() + 2 * 100 + 64))
+        r = res.cpu().numpy().view(gsw.RESULT_DTYPE)
+        c = cig.cpu().numpy().view(np.uint32)
+        for p in range(k):
+            for f in ("score1", "score2", "ref_begin1", "ref_end1", "read_begin1", "read_end1", "ref_end2"):
+                if int(r[f][p]) != int(ores[f][p]):
+                    raise SystemExit(f"bench check failed: read {p} field {f}")
+            o, n_ = int(r["cigar_off"][p]), int(r["cigar_len"][p])
+            if list(c[o:o + n_]) != list(ocg[p, : ores["cigar_len"][p]]):
+                raise SystemExit(f"bench check failed: read {p} CIGAR")
+        checked = k
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    value = cells / (ms / 1e3) / 1e9
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        hq, hqo, hql, href = pin(reads.q), pin(reads.q_off), pin(reads.q_len), pin(ref)
+        hres = pin(np.zeros(n_reads, gsw.RESULT_DTYPE).view(np.int32))
+        hcig = pin(np.zeros(cap, np.uint32))
+
+        def hstep():
+            gsw.gsw_align_to_reference(ctx.handle, n_reads, hq, hqo, hql, href, len(ref), W, O, X,
+                                       gsw.GSW_CIGAR | gsw.GSW_HOST_IO, -1, 0, hres, hcig, cap, stream=stream)
+
+        hstep()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hstep()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": round(cells / dt / 1e9, 2), "unit": UNIT,
+               "h2d_bytes_per_step": int(hq.nbytes + hqo.nbytes + hql.nbytes + href.nbytes),
+               "d2h_bytes_per_step": int(hres.nbytes + hcig.nbytes), "ms_per_step": round(dt * 1e3, 3),
+               "api": "gsw_align_to_reference with GSW_HOST_IO (pinned host buffers)"}
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "i16x2 (i32 refill)",
+            "data": "synthetic (seeded; stands in for 1,000 simulated 100 bp reads of a chromosome region)",
+            "config": {"workload": "reads_vs_reference", "reads": n_reads, "read_nt": 100, "reference_nt": len(ref),
+                       "errors": "1% substitutions, 0.1% 1-3 nt indels", "scoring": "+2/-2, open 3, extend 1",
+                       "outputs": "score1, ends, score2, ref_end2, begins, CIGAR against the whole reference",
+                       "cells": cells},
+            "e2e": e2e, "checked_reads": checked, "clocks": clocks}
+    if not args.no_cpu:
+        cores = len(os.sched_getaffinity(0))
+        k = min(cores, n_reads)
+        t0 = time.perf_counter()
+        oracle.align_batch(reads.q, reads.q_off[:k], reads.q_len[:k], ref, np.zeros(k, np.int64),
+                           np.full(k, len(ref), np.int32), W, O, X, nthreads=cores,
+                           cigar_stride=int(reads.q_len.max() + 264))
+        dt = time.perf_counter() - t0
+        kc = int(reads.q_len[:k].astype(np.int64).sum()) * len(ref)
+        line["cpu_baseline"] = {"value": round(kc / dt / 1e9, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{k} reads against the whole reference ({kc / 1e9:.1f} G cells, "
+                                          f"{dt:.1f} s)", "cpu": _cpu_model()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_serving_line(args):
     """--workload serving_stream: one line, value = the server's p99 latency at
     the first rate; every rate's figures under "serving"."""
@@ -605,7 +711,8 @@ def main():
     ap.add_argument("--pairs", type=int, default=0, help="override the workload's pair count")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["dna_short_read_extension_1M", "dna_1k_100x1000", "dna_long_reads_10k",
-                             "protein_search_1kx10k", "serving_stream"])
+                             "protein_search_1kx10k", "serving_stream", "reads_vs_reference"])
+    ap.add_argument("--ref-len", type=int, default=10_000_000, help="reads_vs_reference: reference letters")
     ap.add_argument("--rates", default="1000,10000,100000,500000",
                     help="serving_stream: Poisson arrival rates (requests/s)")
     ap.add_argument("--requests", type=int, default=2000, help="serving_stream: requests per rate")
@@ -628,6 +735,8 @@ def main():
         run_reference(args)
     elif args.workload == "serving_stream":
         run_serving_line(args)
+    elif args.workload == "reads_vs_reference":
+        run_reads_vs_reference(args)
     else:
         run_gsw(args)
 

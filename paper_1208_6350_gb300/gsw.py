@@ -186,6 +186,19 @@ def gsw_context_destroy(ctx: int) -> None:
     _check(load().gsw_context_destroy(ctx), "gsw_context_destroy")
 
 
+def gsw_align_to_reference(ctx, nreads, q, q_off, q_len, ref, ref_len, matrix, gap_open, gap_extend,
+                           flags=GSW_CIGAR, mask_len=-1, window=0, results=None, cigar=None, cigar_capacity=0,
+                           stream=None, check=True) -> int:
+    """Direct call of gsw_align_to_reference; pointer arguments may be tensors/arrays."""
+    m = np.ascontiguousarray(matrix, dtype=np.int8)
+    rc = load().gsw_align_to_reference(ctx, nreads, _ptr(q), _ptr(q_off), _ptr(q_len), _ptr(ref), ref_len,
+                                       m.ctypes.data, m.shape[0], gap_open, gap_extend, flags, mask_len, window,
+                                       _ptr(results), _ptr(cigar), cigar_capacity, _stream_handle(stream))
+    if check and rc != GSW_ECIGAR_SPACE:
+        _check(rc, "gsw_align_to_reference")
+    return rc
+
+
 def gsw_align_batch(ctx, npairs, q, q_off, q_len, t, t_off, t_len, matrix, gap_open, gap_extend,
                     flags=0, mask_len=-1, results=None, cigar=None, cigar_capacity=0, colmax=None,
                     colmax_off=None, stream=None, check=True) -> int:

@@ -321,6 +321,25 @@ def serving_trace(rate_per_s: float, n_requests=20_000, mix=(0.7, 0.2, 0.1), max
     return reqs
 
 
+def reads_vs_reference(n_reads=1000, read_len=100, ref_len=10_000_000, p_sub=0.01, p_indel=0.001, seed=6):
+    """One random reference of ref_len letters and n_reads reads of read_len
+    sampled from it at uniform positions with substitutions and 1-3 nt indels
+    (stands in for simulated Illumina reads of a chromosome region).  Returns
+    (reads, ref): reads a Batch whose targets are unused (t of one letter)."""
+    rng = np.random.default_rng(np.random.SeedSequence(seed))
+    ref = rng.integers(0, 4, ref_len).astype(np.uint8)
+    starts = rng.integers(0, max(1, ref_len - read_len - 8), n_reads)
+    src = np.concatenate([ref[s:s + read_len + 8] for s in starts])
+    so = np.arange(n_reads, dtype=np.int64) * (read_len + 8)
+    sl = np.full(n_reads, read_len + 8, np.int32)
+    q, qo, ql = mutate(rng, src, so, sl, p_sub, p_indel / 2, p_indel / 2, 3)
+    ql = np.minimum(ql, read_len).astype(np.int32)
+    z = np.zeros(1, np.uint8)
+    reads = Batch("reads", q, qo, ql, z, np.zeros(n_reads, np.int64), np.zeros(n_reads, np.int32),
+                  dna_matrix(2, -2), 3, 1, DNA, {"starts": starts})
+    return reads, ref
+
+
 def concat(batches, name="concat") -> Batch:
     """Concatenates batches that share scoring."""
     b0 = batches[0]
