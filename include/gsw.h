@@ -170,6 +170,22 @@ int gsw_align_to_reference(gsw_ctx *ctx, int32_t nreads, const uint8_t *q, const
                            gsw_result *results, uint32_t *cigar, int64_t cigar_capacity,
                            void *stream);
 
+/*
+ * All-vs-all: every pair (i, j), i < j, of n sequences (the paper's read
+ * overlaps, Applications), query = sequence i, target = sequence j; record k
+ * is the pair of row-major triangle order, k = i*n - i*(i+1)/2 + (j - i - 1),
+ * so results has n(n-1)/2 records (n <= 65,536).  Flags: GSW_BEGIN, GSW_CIGAR,
+ * GSW_HOST_IO, GSW_PACKED2 as for gsw_align_batch; 0 = score only (score1,
+ * ends, score2).  The pairs are generated on the device and run in chunks of
+ * `chunk` pairs (0: 2^22) through the batched path; CIGAR offsets refer to the
+ * whole `cigar` buffer.  Errors as gsw_align_batch.
+ */
+int gsw_align_all_pairs(gsw_ctx *ctx, int32_t n, const uint8_t *seq, const int64_t *off,
+                        const int32_t *len, const int8_t *matrix, int32_t alphabet,
+                        int32_t gap_open, int32_t gap_extend, uint32_t flags, int32_t mask_len,
+                        int64_t chunk, gsw_result *results, uint32_t *cigar,
+                        int64_t cigar_capacity, void *stream);
+
 /* Sizes the context's persistent launches for at most `sms` SMs (0: all), so
  * that work of other streams finds free SMs while this context's kernels
  * run.  Results do not depend on it.  Errors: GSW_EINVAL (sms < 0). */
@@ -255,6 +271,7 @@ typedef struct gsw_stats {
     int32_t timed;
     float stage_ms[8];
     int32_t graph_segments;
+    int64_t cigar_words;  /* CIGAR words the call needed (all pairs) */
 } gsw_stats;
 int gsw_last_stats(const gsw_ctx *ctx, gsw_stats *out);
 

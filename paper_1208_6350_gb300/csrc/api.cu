@@ -92,6 +92,7 @@ struct gsw_ctx {
     int launches = 0;
     int stage_done[GSW_NSTAGES] = {};
     int graph_segments = 0;  // segments of the last call replayed from a graph
+    long long cigar_words = 0;  // CIGAR words the last call needed
 };
 
 struct gsw_profile {
@@ -547,6 +548,7 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
     GSW_TRY(ensure(ctx, ctx->misc, kMiscWords * sizeof(unsigned long long)));
     ctx->launches = 0;
     ctx->graph_segments = 0;
+    ctx->cigar_words = 0;
     for (int k = 0; k < GSW_NSTAGES; k++) ctx->stage_done[k] = 0;
     ctx->timing = (flags & GSW_TIMING) != 0;
     if (ctx->timing && !ctx->ev[0])
@@ -675,6 +677,7 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
     CUDA_TRY(cudaStreamSynchronize(st));
     const unsigned long long used_words = hs[0];
     const int bad_letters = (int)(hs[1] & 0xFFFFFFFFu);
+    ctx->cigar_words = (flags & GSW_CIGAR) ? (long long)used_words : 0;
     if (hio && (flags & GSW_CIGAR) && cigar_capacity > 0) {
         const size_t n = (size_t)std::min<unsigned long long>(used_words, (unsigned long long)cigar_capacity);
         if (n) CUDA_TRY(cudaMemcpy(cigar, bv.cigar, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
@@ -740,6 +743,7 @@ int gsw_last_stats(const gsw_ctx *ctx, gsw_stats *out) {
     std::memset(out, 0, sizeof(*out));
     out->kernel_launches = ctx->launches;
     out->graph_segments = ctx->graph_segments;
+    out->cigar_words = ctx->cigar_words;
     if (!ctx->timing || !ctx->ev[0]) return GSW_OK;
     out->timed = 1;
     // stage k spans events k..k+1, except: [0] = e0..e1, [1] = e1..e2, [2] = e2..e3,

@@ -50,7 +50,8 @@ _lib = None
 
 class GswStats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int32), ("timed", ctypes.c_int32),
-                ("stage_ms", ctypes.c_float * 8), ("graph_segments", ctypes.c_int32)]
+                ("stage_ms", ctypes.c_float * 8), ("graph_segments", ctypes.c_int32),
+                ("cigar_words", ctypes.c_int64)]
 
 
 TUNE_BUCKETS = 32
@@ -108,6 +109,8 @@ def load(build_if_missing: bool = True):
     lib.gsw_context_set_sm_limit.restype = ctypes.c_int
     lib.gsw_align_to_reference.argtypes = [P, i32, P, P, P, P, i64, P, i32, i32, i32, u32, i32, i64, P, P, i64, P]
     lib.gsw_align_to_reference.restype = ctypes.c_int
+    lib.gsw_align_all_pairs.argtypes = [P, i32, P, P, P, P, i32, i32, i32, u32, i32, i64, P, P, i64, P]
+    lib.gsw_align_all_pairs.restype = ctypes.c_int
     lib.gsw_autotune.argtypes = [P, P, i32, i32, i32, i32, ctypes.POINTER(GswTune)]
     lib.gsw_autotune.restype = ctypes.c_int
     lib.gsw_context_set_tune.argtypes = [P, ctypes.POINTER(GswTune)]
@@ -218,7 +221,8 @@ def gsw_align_batch(ctx, npairs, q, q_off, q_len, t, t_off, t_len, matrix, gap_o
 def gsw_last_stats(ctx) -> dict:
     st = GswStats()
     _check(load().gsw_last_stats(ctx, ctypes.byref(st)), "gsw_last_stats")
-    out = {"kernel_launches": st.kernel_launches, "timed": bool(st.timed), "graph_segments": st.graph_segments}
+    out = {"kernel_launches": st.kernel_launches, "timed": bool(st.timed), "graph_segments": st.graph_segments,
+           "cigar_words": st.cigar_words}
     if st.timed:
         out["stage_ms"] = {n: float(st.stage_ms[k]) for k, n in enumerate(STAGE_NAMES)}
     return out
@@ -319,6 +323,25 @@ class Context:
         for b, c in enumerate(fill_class):
             t.fill_class[b] = int(c)
         _check(load().gsw_context_set_tune(self.handle, ctypes.byref(t)), "gsw_context_set_tune")
+
+    def align_all_pairs(self, seq, off, length, matrix, gap_open, gap_extend, flags=0, mask_len=-1, chunk=0,
+                        cigar_capacity=None):
+        """Every pair i < j of one sequence set (host arrays; gsw_align_all_pairs
+        with GSW_HOST_IO); records in row-major triangle order."""
+        seq = np.ascontiguousarray(seq, np.uint8)
+        off = np.ascontiguousarray(off, np.int64)
+        length = np.ascontiguousarray(length, np.int32)
+        m = np.ascontiguousarray(matrix, dtype=np.int8)
+        n = len(length)
+        npairs = n * (n - 1) // 2
+        res = np.zeros(npairs, RESULT_DTYPE)
+        if cigar_capacity is None:
+            cigar_capacity = int(npairs * (2 * int(length.max(initial=0)) + 2)) if flags & GSW_CIGAR else 0
+        cig = np.zeros(max(cigar_capacity, 1), np.uint32)
+        rc = load().gsw_align_all_pairs(self.handle, n, _ptr(seq), _ptr(off), _ptr(length), m.ctypes.data,
+                                        m.shape[0], gap_open, gap_extend, flags | GSW_HOST_IO, mask_len, chunk,
+                                        _ptr(res), _ptr(cig), cigar_capacity, None)
+        return res, cig, rc
 
     def align_to_reference(self, q, q_off, q_len, ref, matrix, gap_open, gap_extend, flags=GSW_CIGAR,
                            mask_len=-1, window=0, cigar_capacity=None):
