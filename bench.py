@@ -674,6 +674,92 @@ def run_reads_vs_reference(args):
     ctx.close()
 
 
+def run_overlap_all_vs_all(args):
+    """--workload overlap_all_vs_all: every pair of 22,543 reads of 70 nt
+    (gsw_align_all_pairs, score only: score1, ends, secondary), the read-overlap
+    computation; GCUPS = sum over pairs of m * n per second."""
+    import torch
+    from paper_1208_6350_gb300 import gsw, workloads as wl
+    import oracle
+    if int(os.environ.get("RANK", 0)) != 0:
+        return
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    n = args.pairs or 22543
+    seq, off, ln = wl.overlap_reads(n, 70, seed=7)
+    npairs = n * (n - 1) // 2
+    cells = int(((ln.astype(np.int64).sum()) ** 2 - (ln.astype(np.int64) ** 2).sum()) // 2)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    S, O_, L_ = T(gsw.pack2(seq)), T(off), T(ln)
+    res = torch.zeros(npairs * 12, dtype=torch.int32, device=dev)
+    ctx = gsw.Context(0, args.budget_gb << 30)
+    W = wl.dna_matrix(2, -3)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+
+    def step():
+        rc = load_all_pairs(gsw)(ctx.handle, n, gsw._ptr(S), gsw._ptr(O_), gsw._ptr(L_), W.ctypes.data, 4, 5, 2,
+                                 gsw.GSW_PACKED2, -1, 0, gsw._ptr(res), None, 0, stream.cuda_stream)
+        if rc != gsw.GSW_OK:
+            raise SystemExit(f"gsw_align_all_pairs failed: {rc}")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    checked = 0
+    if not args.no_check:
+        rng = np.random.default_rng(5)
+        ks = np.sort(rng.choice(npairs, 2000, replace=False))
+        # row-major triangle: pair k -> (i, j)
+        starts = np.arange(n, dtype=np.int64) * n - np.arange(n, dtype=np.int64) * (np.arange(n) + 1) // 2
+        ii = np.searchsorted(starts, ks, side="right") - 1
+        jj = ks - starts[ii] + ii + 1
+        ores, _, _ = oracle.align_batch(seq, off[ii], ln[ii], seq, off[jj], ln[jj], W, 5, 2,
+                                        cigar_stride=2 * 70 + 2)
+        r = res.cpu().numpy().view(gsw.RESULT_DTYPE)[ks]
+        for f in ("score1", "score2", "ref_end1", "read_end1", "ref_end2"):
+            if not (r[f] == ores[f]).all():
+                raise SystemExit(f"bench check failed: field {f}")
+        checked = len(ks)
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {"metric": METRIC, "value": round(cells / (ms / 1e3) / 1e9, 2), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i16x2 (i32 refill)",
+            "data": "synthetic (seeded; stands in for a 22,543 x 70 bp read set)",
+            "config": {"workload": "overlap_all_vs_all", "reads": n, "read_nt": 70, "pairs": npairs,
+                       "genome_coverage": 10, "scoring": "+2/-3, open 5, extend 2",
+                       "outputs": "score1, ends, score2, ref_end2 for every pair (score only)", "cells": cells,
+                       "input": "2-bit packed DNA arena (GSW_PACKED2)"},
+            "checked_pairs": checked, "clocks": clocks}
+    if not args.no_cpu:
+        cores = len(os.sched_getaffinity(0))
+        k = 400000
+        t0 = time.perf_counter()
+        ii = np.random.default_rng(9).integers(0, n, k)
+        jj = (ii + 1 + np.random.default_rng(10).integers(0, n - 1, k)) % n
+        oracle.align_batch(seq, off[ii], ln[ii], seq, off[jj], ln[jj], W, 5, 2, nthreads=cores,
+                           cigar_stride=2 * 70 + 2)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": round(k * 70 * 70 / dt / 1e9, 3), "unit": UNIT, "cores": cores,
+                                "kind": "oracle", "sample": f"{k} random pairs of the read set, full outputs, "
+                                                            f"{dt:.1f} s", "cpu": _cpu_model()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def load_all_pairs(gsw):
+    return gsw.load().gsw_align_all_pairs
+
+
 def run_serving_line(args):
     """--workload serving_stream: one line, value = the server's p99 latency at
     the first rate; every rate's figures under "serving"."""
@@ -711,7 +797,8 @@ def main():
     ap.add_argument("--pairs", type=int, default=0, help="override the workload's pair count")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["dna_short_read_extension_1M", "dna_1k_100x1000", "dna_long_reads_10k",
-                             "protein_search_1kx10k", "serving_stream", "reads_vs_reference"])
+                             "protein_search_1kx10k", "serving_stream", "reads_vs_reference",
+                             "overlap_all_vs_all"])
     ap.add_argument("--ref-len", type=int, default=10_000_000, help="reads_vs_reference: reference letters")
     ap.add_argument("--rates", default="1000,10000,100000,500000",
                     help="serving_stream: Poisson arrival rates (requests/s)")
@@ -737,6 +824,8 @@ def main():
         run_serving_line(args)
     elif args.workload == "reads_vs_reference":
         run_reads_vs_reference(args)
+    elif args.workload == "overlap_all_vs_all":
+        run_overlap_all_vs_all(args)
     else:
         run_gsw(args)
 

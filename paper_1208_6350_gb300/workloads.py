@@ -340,6 +340,23 @@ def reads_vs_reference(n_reads=1000, read_len=100, ref_len=10_000_000, p_sub=0.0
     return reads, ref
 
 
+def overlap_reads(n_reads=22543, read_len=70, coverage=10.0, p_sub=0.01, seed=7):
+    """Reads of read_len sampled at uniform positions of one random genome
+    (length n_reads * read_len / coverage) with substitutions: the input of an
+    all-vs-all read-overlap computation (stands in for a 22,543 x 70 bp read
+    set).  Returns (seq arena, offsets, lengths)."""
+    rng = np.random.default_rng(np.random.SeedSequence(seed))
+    g_len = max(read_len + 1, int(n_reads * read_len / coverage))
+    genome = rng.integers(0, 4, g_len).astype(np.uint8)
+    starts = rng.integers(0, g_len - read_len, n_reads)
+    idx = starts[:, None] + np.arange(read_len)[None, :]
+    seq = genome[idx].reshape(-1).copy()
+    mut = rng.random(len(seq)) < p_sub
+    seq[mut] = (seq[mut] + rng.integers(1, 4, int(mut.sum()))) % 4
+    off = np.arange(n_reads, dtype=np.int64) * read_len
+    return seq.astype(np.uint8), off, np.full(n_reads, read_len, np.int32)
+
+
 def concat(batches, name="concat") -> Batch:
     """Concatenates batches that share scoring."""
     b0 = batches[0]
