@@ -45,6 +45,11 @@
 #ifndef GSW_FILL_DPX
 #define GSW_FILL_DPX 1
 #endif
+// DNA score tables per lane: 0 = one per (low letter, high letter) pair;
+// 1 = a low-letter and a high-letter table, added; 2 = one table holding both
+// halves' scores, merged by a mask (the general-alphabet layout: half the
+// shared memory of 1, but 4 % slower on the short-read fill: the merge's
+// logic op issues at a lower rate than the add)
 #ifndef GSW_FILL_SPLIT
 #define GSW_FILL_SPLIT 1
 #endif
@@ -116,7 +121,7 @@ struct L32 {
 
 // words of one lane's profile (the warp region holds 32 lanes' worth)
 __host__ __device__ constexpr int prof_words(int R, bool fold, bool dna, int A) {
-    return dna ? (fold ? (GSW_FILL_SPLIT ? 8 * R : 16 * R) : 4 * R) : A * R;
+    return dna ? (fold ? (GSW_FILL_SPLIT == 0 ? 16 * R : GSW_FILL_SPLIT == 1 ? 8 * R : 4 * R) : 4 * R) : A * R;
 }
 
 // Index of profile word (table c, row r) of lane l inside the warp region:
@@ -188,7 +193,7 @@ __device__ __forceinline__ void build_profile(uint32_t *psm, const Job &job, con
             int rho_hi = st * SP + S + k * R + r - pad_top;
             qhi = rho_hi >= 0 ? min((int)job.q[(long long)rho_hi * job.qs], A - 1) : -1;
         }
-        if constexpr (DNA && !GSW_FILL_SPLIT) {
+        if constexpr (DNA && GSW_FILL_SPLIT == 0) {
             if constexpr (L::FOLD) {
 #pragma unroll
                 for (int a = 0; a < 4; a++)
@@ -202,7 +207,7 @@ __device__ __forceinline__ void build_profile(uint32_t *psm, const Job &job, con
 #pragma unroll
                 for (int a = 0; a < 4; a++) psm[pidx<R>(a, r, lane)] = (uint32_t)(qlo >= 0 ? sc_w(sc, qlo, a) : 0);
             }
-        } else if constexpr (DNA) {
+        } else if constexpr (DNA && GSW_FILL_SPLIT == 1) {
             for (int a = 0; a < A; a++) {
                 psm[pidx<R>(a, r, lane)] = L::halves(qlo >= 0 ? sc_w(sc, qlo, a) : 0, 0);
                 if constexpr (L::FOLD)
@@ -388,9 +393,9 @@ struct StripRunner {
             }
         }
         uint32_t pw[R];
-        if constexpr (DNA && !GSW_FILL_SPLIT) {
+        if constexpr (DNA && GSW_FILL_SPLIT == 0) {
             load_words<R>(psm, L::FOLD ? al * 4 + ah : al, lane, pw);
-        } else if constexpr (DNA) {
+        } else if constexpr (DNA && GSW_FILL_SPLIT == 1) {
             load_words<R>(psm, al, lane, pw);
             if constexpr (L::FOLD) {
                 uint32_t ph[R];
