@@ -191,6 +191,7 @@ enum MiscSlot {
     kMiscNeed = 4,   // 2 words: anti-diagonal traceback (direction words, op words per pair)
     kMiscRing = 6,   // 3 words: wide-band traceback (total words, max words of a pair, max op words)
     kMiscExt = 9,    // 2 words: arena extents in letters (packed input)
+    kMiscNeed16 = 11,  // 1 word: 16-bit rectangle traceback (direction words per group)
     kMiscWords = 16
 };
 
@@ -407,7 +408,7 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
             // diagonals, CTA strip kernel beyond; their scratch is sized from
             // the needs read back after this segment
             GSW_TRY(plan(kPlanTrace));
-            CUDA_TRY(launch_trace_need(bv, sc, misc + kMiscNeed, st));
+            CUDA_TRY(launch_trace_need(bv, sc, misc + kMiscNeed, misc + kMiscNeed16, st));
             const size_t meta_bytes = sizeof(long long) * ((size_t)npairs + 1) + sizeof(int) * ((size_t)npairs + 4);
             GSW_TRY(ensure(ctx, ctx->ring_meta, meta_bytes));
             S.ring_prefix = reinterpret_cast<long long *>(ctx->ring_meta.p);
@@ -416,7 +417,7 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
             CUDA_TRY(launch_ring_needs(bv, sc, pb.order, pb.var_start, S.ring_prefix, misc + kMiscRing, st));
             CUDA_TRY(cudaMemsetAsync(S.ring_group, 0, 3 * sizeof(int), st));
             S.launches += 2;
-            CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+            CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                      st));
         }
         return GSW_OK;
@@ -425,8 +426,10 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
 
     if (bv.flags & GSW_CIGAR) {
         CUDA_TRY(cudaStreamSynchronize(st));
-        unsigned long long need[5];
+        // [0, 1] anti-diagonal, [2, 4] ring, [7] 16-bit rectangle ([5, 6]: extents, unused here)
+        unsigned long long need[8];
         std::memcpy(need, hs, sizeof(need));
+        need[5] = need[6] = 0;
         std::vector<uint8_t> key2 = key;
         key_add(key2, need);
         for (const DevBuf *d : {&ctx->fill_bnd, &ctx->trace_dirs, &ctx->trace_ops, &ctx->ring_meta})
@@ -450,6 +453,17 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
                 max_dir = (size_t)warps * (size_t)ad_dir;
                 max_ops = (size_t)warps * (size_t)ad_ops;
             }
+            // 16-bit rectangle kernel: 4 groups per warp, direction and op words per group
+            const long long t16_dir = (long long)need[7];
+            int t16_warps = 0;
+            if (t16_dir > 0) {
+                const size_t have = room(ctx, ctx->trace_dirs, ctx->trace_ops) / 2;
+                const size_t per_warp = 4 * (size_t)(t16_dir + ad_ops) * sizeof(uint32_t);
+                t16_warps = (int)std::min<size_t>((size_t)t16_max_warps(sc, ctx->sms),
+                                                  std::max<size_t>(1, have / per_warp));
+                max_dir = std::max(max_dir, (size_t)t16_warps * 4 * (size_t)t16_dir);
+                max_ops = std::max(max_ops, (size_t)t16_warps * 4 * (size_t)ad_ops);
+            }
             // wide bands: the pool of direction words, groups of pairs that fit it
             const unsigned long long ring_total = need[2], ring_max = need[3], ring_ops = need[4];
             size_t ring_pool = 0, ring_walk_warps = 0;
@@ -467,6 +481,18 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
             if (max_dir > 0) {
                 GSW_TRY(ensure2(ctx, ctx->trace_dirs, max_dir * sizeof(uint32_t), ctx->trace_ops,
                                 max_ops * sizeof(uint32_t)));
+                if (t16_warps > 0) {
+                    T16Scratch t;
+                    t.dirs = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
+                    t.dir_words = t16_dir;
+                    t.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
+                    t.op_words = ad_ops;
+                    t.order = pb.order;
+                    t.var_start = pb.var_start;
+                    t.head = pb.head;
+                    CUDA_TRY(launch_trace16(bv, sc, t, t16_warps, ctx->sms, st));
+                    S.launches += sc.dna4 ? 4 : 2;
+                }
                 if (ad_grid > 0) {
                     TraceScratch ts;
                     ts.dirs = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);

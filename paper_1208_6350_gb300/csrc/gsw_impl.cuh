@@ -215,6 +215,47 @@ __host__ __device__ inline int band_range(int la, int lb, int score1, const Scor
     return hi - lo + 1;
 }
 
+// Traceback classes of the pairs the band kernel leaves (bands wider than 32
+// diagonals, or small batches): 0-3 anti-diagonal warp kernel (bands of at
+// most 64/128/256/512 diagonals), 4 the CTA strip kernel (wider bands), 5-8
+// the 16-bit full-rectangle kernel (regions of at most 64/128/192/256 query
+// rows: 8 lanes x R = 4/8/12/16 words x 2 halves).
+constexpr int kTraceRingClass = 4;
+constexpr int kTraceT16First = 5;
+constexpr int kTraceT16Classes = 4;
+constexpr int kT16P = 8;                // lanes per pair
+constexpr int kT16MaxCols = 1024;       // longest target region of the 16-bit kernel
+__host__ __device__ inline int t16_R(int v) { return 4 * (v + 1); }
+// direction words of one pair: steps x R/4 words x 8 lanes
+__host__ __device__ inline long long t16_dir_words(int lb, int v) {
+    return (long long)(lb + 2 * kT16P - 1) * (t16_R(v) / 4) * kT16P;
+}
+__host__ __device__ inline int trace_class(int la, int lb, int score1, const Scoring &sc, int *dlo, int *dhi) {
+    const int width = band_range(la, lb, score1, sc, dlo, dhi);
+    const int ad = width <= 64 ? 0 : width <= 128 ? 1 : width <= 256 ? 2 : width <= 512 ? 3 : kTraceRingClass;
+    if (la >= 1 && la <= 256 && lb >= 1 && lb <= kT16MaxCols) {
+        const int v = (la - 1) / 64;
+        // general alphabets keep A x R profile words per lane: up to 128 rows
+        if (sc.dna4 || v <= 1) {
+            // every value of the DP over the padded rectangle (256 rows, lb +
+            // 16 columns) lies in [-(3O + X(rows + cols) + |wmin|), wmax *
+            // min(rows, cols) + wmax]: it must fit a biased 16-bit lane
+            const int cols = lb + 2 * kT16P;
+            const long long lo = 3LL * sc.O + (long long)sc.X * (256 + cols + 2) - (sc.wmin < 0 ? sc.wmin : 0);
+            const long long hi = (long long)sc.wmax * ((cols < 256 ? cols : 256) + 1);
+            if (lo <= 30000 && hi <= 30000) {
+                // cell updates: the padded rectangle against the band's
+                // anti-diagonal slots; a 16-bit pair of cells costs about
+                // the instructions of one 32-bit anti-diagonal cell
+                const long long rect = 64LL * (v + 1) * (lb + 2 * kT16P - 1);
+                const long long band = ad < kTraceRingClass ? (32LL << ad) * (la + lb + 1) : (1LL << 62);
+                if (rect <= 3 * band) return kTraceT16First + v;
+            }
+        }
+    }
+    return ad;
+}
+
 // stage launchers (host side, enqueue on `st`)
 int fill_block_threads();
 // largest number of slots (pairs in flight) of any variant's launch
@@ -274,11 +315,28 @@ struct TraceScratch {
     const int32_t *var_start;
 };
 int trace_block_threads();
-// largest needs of a pair of the anti-diagonal classes: [0] direction words, [1] op words
+// largest needs of a pair: [0] direction words of the anti-diagonal classes,
+// [1] op words of the warp classes; need16: direction words of the 16-bit classes
 cudaError_t launch_trace_need(const BatchView &b, const Scoring &sc, unsigned long long *max_need,
-                              cudaStream_t st);
+                              unsigned long long *need16, cudaStream_t st);
 cudaError_t launch_trace_ad(const BatchView &b, const Scoring &sc, const TraceScratch &ts, int grid,
                             cudaStream_t st);
+
+// 16-bit full-rectangle traceback (trace16.cu): per group of 8 lanes
+// dir_words direction words and op_words op words
+struct T16Scratch {
+    uint32_t *dirs;
+    int64_t dir_words;  // per group
+    uint32_t *ops;
+    int64_t op_words;   // per group
+    const int32_t *order;
+    const int32_t *var_start;
+    int32_t *head;      // per-class task counters (zeroed by the plan)
+};
+// most warps any of the launches keeps resident (4 groups each)
+int t16_max_warps(const Scoring &sc, int sms);
+cudaError_t launch_trace16(const BatchView &b, const Scoring &sc, const T16Scratch &ts, int max_warps, int sms,
+                           cudaStream_t st);
 
 int band_block_threads();
 cudaError_t launch_band(const BatchView &b, const Scoring &sc, const PlanBuffers &pb, void *scratch,

@@ -89,11 +89,13 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
         }
         const int la = r.read_end1 - r.read_begin1 + 1, lb = r.ref_end1 - r.ref_begin1 + 1;
         int dlo, dhi;
-        const int width = band_range(la, lb, r.score1, sc, &dlo, &dhi);
         // 0-3: anti-diagonal warp kernel (<= 64/128/256/512 diagonals); 4:
-        // wider bands, the CTA strip kernel
-        const int cls = width <= 64 ? 0 : width <= 128 ? 1 : width <= 256 ? 2 : width <= 512 ? 3 : 4;
-        const int key = cls * kPlanBinsPerVariant + cost_bin((long long)(la + lb + 1) * ((width + 31) / 32));
+        // wider bands, the CTA strip kernel; 5-8: the 16-bit rectangle
+        const int cls = trace_class(la, lb, r.score1, sc, &dlo, &dhi);
+        const int width = dhi - dlo + 1;
+        const long long cost = cls >= kTraceT16First ? (long long)lb + 2 * kT16P
+                                                     : (long long)(la + lb + 1) * ((width + 31) / 32);
+        const int key = cls * kPlanBinsPerVariant + cost_bin(cost);
         keys[p] = key;
         atomicAdd(&hist[key], 1);
         return;

@@ -399,3 +399,51 @@ def test_packed_2bit_inputs(ctx, host_io):
     flags = gsw.GSW_CIGAR | gsw.GSW_PACKED2
     got = run_gpu_host(ctx, packed, flags=flags) if host_io else run_gpu_device(ctx, packed, flags=flags)
     compare(b, ora, got)
+
+
+def _weak_pairs(rng, lens, ident=0.75, p_indel=0.02, flank=(0, 120), A=4):
+    """Query of each length, target = flanks + a copy at `ident` identity with
+    scattered 1-3 letter indels: the local alignment spans about the whole
+    query with a low score, so the provable band covers most of the region."""
+    qs, ts = [], []
+    for L in lens:
+        q = rng.integers(0, A, L).astype(np.uint8)
+        c = []
+        for x in q:
+            u = rng.random()
+            if u < p_indel / 2:
+                continue
+            if u < p_indel:
+                c.extend(rng.integers(0, A, int(rng.integers(1, 4))).tolist())
+            c.append(int(x) if rng.random() < ident else int(rng.integers(0, A)))
+        left, right = (int(rng.integers(flank[0], flank[1] + 1)) for _ in range(2))
+        t = np.concatenate([rng.integers(0, A, left), np.array(c, np.int64), rng.integers(0, A, right)])
+        qs.append(q)
+        ts.append(t.astype(np.uint8))
+    return qs, ts
+
+
+@pytest.mark.parametrize("O,X", [(3, 1), (2, 2), (6, 0)])
+def test_rect16_traceback_region_classes(ctx, O, X):
+    # weak similarities whose regions fall on both sides of every row class of
+    # the 16-bit rectangle traceback (64/128/192/256 rows) and up to its
+    # 1024-column limit; open == extend and extend 0 exercise the tie rules
+    rng = np.random.default_rng(70 + O * 10 + X)
+    lens = [1, 2, 15, 40, 63, 64, 65, 100, 127, 128, 129, 160, 191, 192, 193, 230, 255, 256, 257, 300]
+    qs, ts = _weak_pairs(rng, lens * 3)
+    q2, t2 = _weak_pairs(rng, [200, 240, 256], flank=(700, 760))  # targets near 1,024 letters
+    b = _batch(qs + q2, ts + t2, wl.dna_matrix(2, -2), O, X, "weak")
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
+def test_rect16_traceback_general_alphabet(ctx):
+    # a 20-letter alphabet with a BLOSUM-like matrix: regions up to 128 rows
+    # take the 16-bit rectangle (one score table per lane)
+    rng = np.random.default_rng(77)
+    A = 20
+    M = rng.integers(-4, 3, (A, A))
+    M = ((M + M.T) // 2).astype(np.int8)
+    np.fill_diagonal(M, rng.integers(4, 12, A))
+    qs, ts = _weak_pairs(rng, [10, 50, 64, 65, 90, 127, 128, 129, 150] * 4, ident=0.6, A=A)
+    b = _batch(qs, ts, M, 11, 1, "weak_protein", alphabet="ARNDCQEGHILKMFPSTWYV")
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
