@@ -218,39 +218,51 @@ __host__ __device__ inline int band_range(int la, int lb, int score1, const Scor
 // Traceback classes of the pairs the band kernel leaves (bands wider than 32
 // diagonals, or small batches): 0-3 anti-diagonal warp kernel (bands of at
 // most 64/128/256/512 diagonals), 4 the CTA strip kernel (wider bands), 5-8
-// the 16-bit full-rectangle kernel (regions of at most 64/128/192/256 query
-// rows: 8 lanes x R = 4/8/12/16 words x 2 halves).
+// the 16-bit full-rectangle kernel with strips of 64/128/192/256 query rows
+// (8 lanes x R = 4/8/12/16 words x 2 halves; regions taller than the class's
+// strip run several strips: 256-row strips for DNA, 128 for other alphabets).
 constexpr int kTraceRingClass = 4;
 constexpr int kTraceT16First = 5;
 constexpr int kTraceT16Classes = 4;
-constexpr int kT16P = 8;                // lanes per pair
-constexpr int kT16MaxCols = 1024;       // longest target region of the 16-bit kernel
+constexpr int kT16P = 8;                   // lanes per pair
+constexpr int kT16MaxCols = 4096;          // longest target region of the 16-bit kernel
+constexpr long long kT16MaxWords = 1 << 17;  // scratch words of one pair (512 KB)
 __host__ __device__ inline int t16_R(int v) { return 4 * (v + 1); }
-// direction words of one pair: steps x R/4 words x 8 lanes
-__host__ __device__ inline long long t16_dir_words(int lb, int v) {
-    return (long long)(lb + 2 * kT16P - 1) * (t16_R(v) / 4) * kT16P;
+__host__ __device__ inline int t16_strip_rows(int v) { return 2 * kT16P * t16_R(v); }
+__host__ __device__ inline int t16_strips(int la, int v) { return (la + t16_strip_rows(v) - 1) / t16_strip_rows(v); }
+__host__ __device__ inline int t16_steps(int lb) { return lb + 2 * kT16P - 1; }
+// direction words of one pair (strips x steps x R/4 words x 8 lanes)
+__host__ __device__ inline long long t16_dir_words(int la, int lb, int v) {
+    return (long long)t16_strips(la, v) * t16_steps(lb) * (t16_R(v) / 4) * kT16P;
+}
+// scratch words of one pair: direction words, then two boundary rows (one
+// word per column) when it has several strips
+__host__ __device__ inline long long t16_need_words(int la, int lb, int v) {
+    const long long d = t16_dir_words(la, lb, v);
+    return t16_strips(la, v) > 1 ? d + 2LL * ((lb + 3) & ~3) : d;
 }
 __host__ __device__ inline int trace_class(int la, int lb, int score1, const Scoring &sc, int *dlo, int *dhi) {
     const int width = band_range(la, lb, score1, sc, dlo, dhi);
     const int ad = width <= 64 ? 0 : width <= 128 ? 1 : width <= 256 ? 2 : width <= 512 ? 3 : kTraceRingClass;
-    if (la >= 1 && la <= 256 && lb >= 1 && lb <= kT16MaxCols) {
-        const int v = (la - 1) / 64;
-        // general alphabets keep A x R profile words per lane: up to 128 rows
-        if (sc.dna4 || v <= 1) {
-            // every value of the DP over the padded rectangle (256 rows, lb +
-            // 16 columns) lies in [-(3O + X(rows + cols) + |wmin|), wmax *
-            // min(rows, cols) + wmax]: it must fit a biased 16-bit lane
-            const int cols = lb + 2 * kT16P;
-            const long long lo = 3LL * sc.O + (long long)sc.X * (256 + cols + 2) - (sc.wmin < 0 ? sc.wmin : 0);
-            const long long hi = (long long)sc.wmax * ((cols < 256 ? cols : 256) + 1);
-            if (lo <= 30000 && hi <= 30000) {
-                // cell updates: the padded rectangle against the band's
-                // anti-diagonal slots; a 16-bit pair of cells costs about
-                // the instructions of one 32-bit anti-diagonal cell
-                const long long rect = 64LL * (v + 1) * (lb + 2 * kT16P - 1);
-                const long long band = ad < kTraceRingClass ? (32LL << ad) * (la + lb + 1) : (1LL << 62);
-                if (rect <= 3 * band) return kTraceT16First + v;
-            }
+    if (la >= 1 && lb >= 1 && lb <= kT16MaxCols) {
+        // general alphabets keep A x R profile words per lane: strips of up to 128 rows
+        const int vmax = sc.dna4 ? kTraceT16Classes - 1 : 1;
+        const int v0 = (la - 1) / 64;
+        const int v = v0 < vmax ? v0 : vmax;
+        const long long rows = (long long)t16_strips(la, v) * t16_strip_rows(v);
+        const long long cols = lb + 2 * kT16P;
+        // every value of the DP over the padded rectangle lies in
+        // [-(3O + X(rows + cols) + |wmin|), wmax * min(rows, cols) + wmax]:
+        // it must fit a biased 16-bit lane
+        const long long lo = 3LL * sc.O + (long long)sc.X * (rows + cols + 2) - (sc.wmin < 0 ? sc.wmin : 0);
+        const long long hi = (long long)sc.wmax * ((cols < rows ? cols : rows) + 1);
+        if (lo <= 30000 && hi <= 30000 && t16_need_words(la, lb, v) <= kT16MaxWords) {
+            // cell updates: the padded rectangle against the band's
+            // anti-diagonal slots; a 16-bit pair of cells costs about the
+            // instructions of one 32-bit anti-diagonal cell
+            const long long rect = rows * t16_steps(lb);
+            const long long band = ad < kTraceRingClass ? (32LL << ad) * (la + lb + 1) : (1LL << 62);
+            if (rect <= 3 * band) return kTraceT16First + v;
         }
     }
     return ad;

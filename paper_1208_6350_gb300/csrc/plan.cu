@@ -93,7 +93,7 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
         // wider bands, the CTA strip kernel; 5-8: the 16-bit rectangle
         const int cls = trace_class(la, lb, r.score1, sc, &dlo, &dhi);
         const int width = dhi - dlo + 1;
-        const long long cost = cls >= kTraceT16First ? (long long)lb + 2 * kT16P
+        const long long cost = cls >= kTraceT16First ? (long long)t16_strips(la, cls - kTraceT16First) * t16_steps(lb)
                                                      : (long long)(la + lb + 1) * ((width + 31) / 32);
         const int key = cls * kPlanBinsPerVariant + cost_bin(cost);
         keys[p] = key;

@@ -77,24 +77,30 @@ __device__ __forceinline__ uint32_t t16_edge(int i, int O, int X) {
 template <int R, bool DNA>
 struct T16Runner {
     static constexpr int S = kP * R;
+    static constexpr int SS = 2 * S;  // rows of a strip
     static constexpr int Q = R / 4;
 
+    const uint8_t *qs;  // query region, row i (0-based) at qs[i]
     const uint8_t *ts;  // target region, column j (0-based) at ts[j]
-    int lb, A, O, X, k, src;
+    int la, lb, A, O, X, k, src, gbase, st;
     unsigned gmask;
     uint32_t *psm, *dirs, *fin_words;
+    const uint32_t *bin;  // previous strip's last row: H | F(next row) << 16 per column
+    uint32_t *bout;
     int lane;
     uint32_t kO, kXm, hb0, stepX;
     uint32_t H[R], E[R];
-    uint32_t xh, xf, hdiag;
+    uint32_t xh, xf, hdiag, b_cur, b_nxt;
     int nal, nah;
-    // the cell (la, lb): step, lane, word and half holding it
-    int s_fin, k_fin, r_fin, h_fin;
+    // the cell (la, lb): strip, step, lane, word and half holding it
+    int st_fin, s_fin, k_fin, r_fin, h_fin;
     int fh;
 
-    __device__ __forceinline__ void init(const uint8_t *qs, int la, const uint8_t *ts_, int lb_, const Scoring &sc,
-                                         uint32_t *psm_, uint32_t *dirs_, uint32_t *fin_words_, int k_, int lane_,
-                                         unsigned gmask_, int gbase) {
+    __device__ __forceinline__ void init(const uint8_t *qs_, int la_, const uint8_t *ts_, int lb_, const Scoring &sc,
+                                         uint32_t *psm_, uint32_t *fin_words_, int k_, int lane_, unsigned gmask_,
+                                         int gbase_) {
+        qs = qs_;
+        la = la_;
         ts = ts_;
         lb = lb_;
         A = sc.A;
@@ -103,17 +109,39 @@ struct T16Runner {
         k = k_;
         lane = lane_;
         gmask = gmask_;
-        src = gbase + ((k_ + kP - 1) & (kP - 1));
+        gbase = gbase_;
+        src = gbase_ + ((k_ + kP - 1) & (kP - 1));
         psm = psm_;
-        dirs = dirs_;
         fin_words = fin_words_;
         kO = (uint32_t)(-O * 65537);
         kXm = ((uint32_t)(-X) & 0xFFFFu) * 0x10001u;
         stepX = (uint32_t)X * 0x10001u;
+        st_fin = (la - 1) / SS;
+        const int ri = la - 1 - st_fin * SS, hh = ri >= S ? 1 : 0, rr = ri - hh * S;
+        k_fin = rr / R;
+        r_fin = rr - k_fin * R;
+        h_fin = hh;
+        s_fin = lb - 1 + k_fin + hh * kP;
+        fh = INT_MIN;
+        // every lane has read its old op words (the walk of the group's
+        // previous pair) before the lane holding (la, lb) overwrites them
+        __syncwarp(gmask);
+    }
+
+    // Starts strip st_ (rows st_*SS ..): its profile, the left boundary of
+    // its rows, and the row above it (the top boundary for strip 0, else the
+    // previous strip's last row from bin_).
+    __device__ __forceinline__ void begin(const Scoring &sc, int st_, uint32_t *dirs_, const uint32_t *bin_,
+                                          uint32_t *bout_) {
+        st = st_;
+        dirs = dirs_;
+        bin = bin_;
+        bout = bout_;
+        const int i0 = st * SS;
         // profile of the lane's rows (rows past la score 0)
 #pragma unroll 1
         for (int r = 0; r < R; r++) {
-            const int ilo = k * R + r, ihi = S + k * R + r;
+            const int ilo = i0 + k * R + r, ihi = i0 + S + k * R + r;
             const int qlo = ilo < la ? min((int)qs[ilo], A - 1) : -1;
             const int qhi = ihi < la ? min((int)qs[ihi], A - 1) : -1;
             if constexpr (DNA) {
@@ -133,7 +161,7 @@ struct T16Runner {
             }
         }
         // left boundary: H(i, 0) and E(i, 1) = H(i, 0) - O of the lane's rows
-        hb0 = t16_edge(k * R + 1, O, X) | (t16_edge(S + k * R + 1, O, X) << 16);
+        hb0 = t16_edge(i0 + k * R + 1, O, X) | (t16_edge(i0 + S + k * R + 1, O, X) << 16);
 #pragma unroll
         for (int r = 0; r < R; r++) {
             H[r] = hb0 - (uint32_t)r * stepX;
@@ -141,30 +169,45 @@ struct T16Runner {
         }
         // the row above the lane's first rows at column 0 (the diagonal of
         // lane 1's first column; later lanes get it down the ring)
-        xh = t16_edge(k * R, O, X) | (t16_edge(S + k * R, O, X) << 16);
+        xh = t16_edge(i0 + k * R, O, X) | (t16_edge(i0 + S + k * R, O, X) << 16);
         xf = 0;
-        hdiag = 0x80008000u;  // lane 0: H(0,0) is the diagonal of its first cell
+        hdiag = t16_edge(i0, O, X) * 0x10001u;  // lane 0: H(i0, 0), the diagonal of its first cell
         nal = (k == 0) ? min((int)ts[0], A - 1) : 0;
         nah = 0;
-        const int ri = la - 1, hh = ri >= S ? 1 : 0, rr = ri - hh * S;
-        k_fin = rr / R;
-        r_fin = rr - k_fin * R;
-        h_fin = hh;
-        s_fin = lb - 1 + k_fin + hh * kP;
-        fh = INT_MIN;
-        // every lane has read its old op words (the walk of the group's
-        // previous pair) before the lane holding (la, lb) overwrites them
-        __syncwarp(gmask);
+        b_cur = 0;
+        b_nxt = 0;
+        if (st > 0) prefetch(0);
+    }
+
+    // The previous strip's row for columns [s0, s0 + 8): lane k loads column
+    // s0 + k, lane 0 takes each by a shuffle in its step
+    __device__ __forceinline__ void prefetch(int s0) {
+        const int j = s0 + k;
+        b_nxt = j < lb ? bin[j] : 0u;
     }
 
     template <bool CHECKED>
     __device__ __forceinline__ void step(const int s) {
         const int jlo = s - k;
         const int jhi = jlo - kP;
-        // lane 0: low half from the top boundary row, high half from lane 7's low half
-        const uint32_t top = (uint32_t)(0x8000 - O - s * X) & 0xFFFFu;  // H(0, s+1)
-        const uint32_t hin = k == 0 ? ((xh << 16) | top) : xh;
-        const uint32_t fin = k == 0 ? ((xf << 16) | ((top - (uint32_t)O) & 0xFFFFu)) : xf;
+        // lane 0's low half: the row above the strip at column s (the top
+        // boundary H(0, s+1) for strip 0 and past the last column)
+        uint32_t tlo = (uint32_t)(0x8000 - O - s * X) & 0xFFFFu;
+        uint32_t flo = (tlo - (uint32_t)O) & 0xFFFFu;
+        if (st > 0) {
+            if ((s & (kP - 1)) == 0) {
+                b_cur = b_nxt;
+                prefetch(s + kP);
+            }
+            const uint32_t w = __shfl_sync(gmask, b_cur, gbase + (s & (kP - 1)));
+            if (s < lb) {
+                tlo = w & 0xFFFFu;
+                flo = w >> 16;
+            }
+        }
+        // lane 0's high half continues lane 7's low half
+        const uint32_t hin = k == 0 ? ((xh << 16) | tlo) : xh;
+        const uint32_t fin = k == 0 ? ((xf << 16) | flo) : xf;
         const int al = nal, ah = nah;
         {
             const int j1 = jlo + 1;
@@ -213,6 +256,8 @@ struct T16Runner {
         uint32_t *dst = dirs + (size_t)s * (Q * kP) + k;
 #pragma unroll
         for (int q = 0; q < Q; q++) dst[q * kP] = acc[q];
+        // lane 7 holds the strip's last row: the next strip's top
+        if (bout && k == kP - 1 && jhi >= 0 && jhi < lb) bout[jhi] = (H[R - 1] >> 16) | (f & 0xFFFF0000u);
         if constexpr (CHECKED) {
             // before a half's first column its rows hold the left boundary
             if (jhi < 0) {
@@ -227,7 +272,7 @@ struct T16Runner {
         }
         // the lane holding (la, lb) parks its words (a select by a run-time
         // row would put H in local memory)
-        if (s == s_fin && k == k_fin) {
+        if (st == st_fin && s == s_fin && k == k_fin) {
 #pragma unroll
             for (int r = 0; r < R; r++) fin_words[r] = H[r];
         }
@@ -235,10 +280,10 @@ struct T16Runner {
         xf = __shfl_sync(gmask, f, src);
     }
 
-    // the whole rectangle: start-up (some half before its first column),
-    // steady (every column in range), drain (columns past lb)
+    // the strip over every column: start-up (some half before its first
+    // column), steady (every column in range), drain (columns past lb)
     __device__ __forceinline__ void run() {
-        const int nsteps = lb + 2 * kP - 1;
+        const int nsteps = t16_steps(lb);
         const int s_steady = 2 * kP - 1;
         const int s_drain = max(s_steady, lb - 1);
         int s = 0;
@@ -248,8 +293,13 @@ struct T16Runner {
         for (; s < s_drain; s++) step<false>(s);
 #pragma unroll 1
         for (; s < nsteps; s++) step<true>(s);
+        // the next strip reads this one's boundary row, the walk its words
         __syncwarp(gmask);
-        fh = (int)((fin_words[r_fin] >> (16 * h_fin)) & 0xFFFFu) - 0x8000;
+    }
+
+    // H(la, lb), once its strip has run
+    __device__ __forceinline__ int final_h() const {
+        return (int)((fin_words[r_fin] >> (16 * h_fin)) & 0xFFFFu) - 0x8000;
     }
 };
 
@@ -272,21 +322,25 @@ __device__ __forceinline__ void t16_emit(int op, int n, int &cur, int &len, int 
 // or -1 if the walk left the rectangle (never for consistent words).
 template <int R>
 __device__ __forceinline__ int t16_walk(const uint32_t *dirs, uint32_t *stage, int tile_steps, int la, int lb, int k,
-                        unsigned gmask, uint32_t *ops) {
+                                        unsigned gmask, uint32_t *ops) {
     constexpr int S = kP * R;
+    constexpr int SS = 2 * S;
     constexpr int Q = R / 4;
+    const int nsteps = t16_steps(lb);
     int i = la, j = lb, mode = 0, cur = -1, len = 0, runs = 0;
     int tile_lo = INT_MAX;
     const bool writer = k == 0;
     int guard = la + lb + 2;
     while (i > 0 && j > 0 && guard-- > 0) {
-        const int ri = i - 1;
+        const int st = (i - 1) / SS;
+        const int ri = i - 1 - st * SS;
         const int hh = ri >= S ? 1 : 0;
         const int rr = ri - hh * S;
         const int kk = rr / R, rs = rr - kk * R;
-        const int s = j - 1 + kk + hh * kP;
+        // step index over the strips laid end to end: it never increases
+        // along the walk, so the group stages the tile ending at it
+        const int s = st * nsteps + j - 1 + kk + hh * kP;
         if (s < tile_lo) {
-            // steps never increase along the walk: stage the tile ending at s
             __syncwarp(gmask);
             tile_lo = max(0, s - tile_steps + 1);
             const int n = (s - tile_lo + 1) * (Q * kP);
@@ -368,8 +422,8 @@ __global__ void __launch_bounds__(kT16Block) k_trace16(BatchView b, Scoring sc, 
             la = rr.read_end1 - qb + 1;
             lb = rr.ref_end1 - tb + 1;
             const bool fits = score1 > 0 && (flags & kResPendingTrace) && !(flags & kResInternal) && qb >= 0 &&
-                              tb >= 0 && la >= 1 && la <= 2 * kP * R && lb >= 1 &&
-                              t16_dir_words(lb, v) <= ts.dir_words && (long long)la + lb + 2 <= ts.op_words;
+                              tb >= 0 && la >= 1 && lb >= 1 && lb <= kT16MaxCols &&
+                              t16_need_words(la, lb, v) <= ts.dir_words && (long long)la + lb + 2 <= ts.op_words;
             if (!fits) {
                 if (k == 0 && score1 > 0 && (flags & kResPendingTrace)) b.res[p].flags |= kResInternal;
                 p = -1;
@@ -380,9 +434,18 @@ __global__ void __launch_bounds__(kT16Block) k_trace16(BatchView b, Scoring sc, 
             // each lane builds and reads only its own profile words
             T16Runner<R, DNA> run;
             run.init(b.q + b.q_off[p] + b.res[p].read_begin1, la, b.t + b.t_off[p] + b.res[p].ref_begin1, lb, sc,
-                     psm, dirs, ops, k, lane, gmask, gbase);
-            run.run();
-            fh = run.fh;
+                     psm, ops, k, lane, gmask, gbase);
+            const int nst = t16_strips(la, v);
+            const size_t strip_words = (size_t)t16_steps(lb) * (R / 4) * kP;
+            uint32_t *bnd0 = dirs + strip_words * nst, *bnd1 = bnd0 + ((lb + 3) & ~3);
+#pragma unroll 1
+            for (int st = 0; st < nst; st++) {
+                const uint32_t *bin = st == 0 ? nullptr : ((st & 1) ? bnd0 : bnd1);
+                uint32_t *bout = st + 1 < nst ? ((st & 1) ? bnd1 : bnd0) : nullptr;
+                run.begin(sc, st, dirs + strip_words * st, bin, bout);
+                run.run();
+            }
+            fh = run.final_h();
         }
         __syncwarp();  // every group's fill is done: the profile region is free
         int nr = -1;

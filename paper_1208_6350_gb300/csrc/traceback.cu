@@ -57,7 +57,7 @@ __global__ void k_trace_need(BatchView b, Scoring sc, unsigned long long *max_ne
                 v[0] = (unsigned)min(ad_dir_words(la, lb, 1 << cls), (long long)UINT_MAX);
                 v[1] = (unsigned)min((long long)la + lb + 2, (long long)UINT_MAX);
             } else if (cls >= kTraceT16First) {
-                v[2] = (unsigned)min(t16_dir_words(lb, cls - kTraceT16First), (long long)UINT_MAX);
+                v[2] = (unsigned)min(t16_need_words(la, lb, cls - kTraceT16First), (long long)UINT_MAX);
                 v[1] = (unsigned)min((long long)la + lb + 2, (long long)UINT_MAX);
             }
         }

@@ -447,3 +447,34 @@ def test_rect16_traceback_general_alphabet(ctx):
     qs, ts = _weak_pairs(rng, [10, 50, 64, 65, 90, 127, 128, 129, 150] * 4, ident=0.6, A=A)
     b = _batch(qs, ts, M, 11, 1, "weak_protein", alphabet="ARNDCQEGHILKMFPSTWYV")
     compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
+@pytest.mark.parametrize("O,X", [(3, 1), (2, 2), (5, 0)])
+def test_rect16_traceback_several_strips(ctx, O, X):
+    # regions taller than one strip (256 rows for DNA) run strip after strip
+    # with the boundary row in scratch; rows on both sides of each strip edge
+    rng = np.random.default_rng(80 + O * 10 + X)
+    qs, ts = _weak_pairs(rng, [257, 300, 383, 511, 512, 513, 600, 700, 767, 768, 769] * 2, flank=(0, 300))
+    b = _batch(qs, ts, wl.dna_matrix(2, -2), O, X, "weak_strips")
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
+def test_rect16_traceback_general_alphabet_strips(ctx):
+    # 128-row strips for a 20-letter alphabet: regions of 1-4 strips
+    rng = np.random.default_rng(81)
+    A = 20
+    M = rng.integers(-4, 3, (A, A))
+    M = ((M + M.T) // 2).astype(np.int8)
+    np.fill_diagonal(M, rng.integers(4, 12, A))
+    qs, ts = _weak_pairs(rng, [129, 200, 255, 256, 257, 383, 384, 385, 500] * 2, ident=0.6, A=A)
+    b = _batch(qs, ts, M, 11, 1, "weak_protein_strips", alphabet="ARNDCQEGHILKMFPSTWYV")
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
+def test_protein_search_sample(ctx):
+    # random query x database pairs of the protein search workload: long,
+    # low-scoring local alignments with bands of hundreds of diagonals
+    ps = wl.protein_search(n_queries=200, n_db=400, seed=9)
+    rng = np.random.default_rng(9)
+    b = ps.pairs(rng.integers(0, 200, 300), rng.integers(0, 400, 300))
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
