@@ -454,7 +454,7 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
                 max_ops = (size_t)warps * (size_t)ad_ops;
             }
             // 16-bit rectangle kernel: 4 groups per warp, direction and op words per group
-            const long long t16_dir = (long long)need[7];
+            const long long t16_dir = ((long long)need[7] + 3) & ~3LL;  // 16-byte aligned group areas
             int t16_warps = 0;
             if (t16_dir > 0) {
                 const size_t have = room(ctx, ctx->trace_dirs, ctx->trace_ops) / 2;

@@ -150,6 +150,12 @@ constexpr int32_t kResPendingTrace = 0x100;  // band too wide for one thread: wa
 constexpr int kBandMaxWidth = 32;
 constexpr int kBandMaxRows = 4096;
 
+// Below this many pairs the thread-per-pair band kernel would occupy a few
+// percent of the GPU's threads: the begins then come from the ring reverse
+// fill and the CIGARs from the warp tracebacks.
+constexpr int kSmallBatch = 1 << 14;
+__host__ __device__ inline bool small_batch(const BatchView &b) { return b.npairs < kSmallBatch; }
+
 constexpr int kPlanBinsPerVariant = 1024;
 constexpr int kPlanBins = kNumFillClasses * kPlanBinsPerVariant;
 
@@ -241,7 +247,11 @@ __host__ __device__ inline long long t16_need_words(int la, int lb, int v) {
     const long long d = t16_dir_words(la, lb, v);
     return t16_strips(la, v) > 1 ? d + 2LL * ((lb + 3) & ~3) : d;
 }
-__host__ __device__ inline int trace_class(int la, int lb, int score1, const Scoring &sc, int *dlo, int *dhi) {
+// small: a batch of fewer than 2^14 pairs (the rectangle needs a wider margin
+// there, where the anti-diagonal kernel's one pair per warp keeps more pairs
+// in flight)
+__host__ __device__ inline int trace_class(int la, int lb, int score1, const Scoring &sc, bool small, int *dlo,
+                                           int *dhi) {
     const int width = band_range(la, lb, score1, sc, dlo, dhi);
     const int ad = width <= 64 ? 0 : width <= 128 ? 1 : width <= 256 ? 2 : width <= 512 ? 3 : kTraceRingClass;
     if (la >= 1 && lb >= 1 && lb <= kT16MaxCols) {
@@ -262,7 +272,7 @@ __host__ __device__ inline int trace_class(int la, int lb, int score1, const Sco
             // instructions of one 32-bit anti-diagonal cell
             const long long rect = rows * t16_steps(lb);
             const long long band = ad < kTraceRingClass ? (32LL << ad) * (la + lb + 1) : (1LL << 62);
-            if (rect <= 3 * band) return kTraceT16First + v;
+            if (rect <= (small ? 2 : 3) * band) return kTraceT16First + v;
         }
     }
     return ad;

@@ -31,11 +31,6 @@ __device__ __forceinline__ int pick_class16(int rows, const Scoring &sc) {
     return long_pair(rows, false, sc.dna4) ? kClassLong16 : pick_s16(rows);
 }
 
-// Below this many pairs the thread-per-pair band kernel would occupy a few
-// percent of the GPU's threads: the begins then come from the ring reverse
-// fill and the CIGARs from the warp traceback (one pair per 16 or 32 lanes).
-constexpr int kSmallBatch = 1 << 14;
-__device__ __forceinline__ bool small_batch(const BatchView &b) { return b.npairs < kSmallBatch; }
 
 __device__ __forceinline__ int cost_bin(long long cost) {
     // 32 bins per doubling of cost, descending order inside a variant
@@ -91,7 +86,7 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
         int dlo, dhi;
         // 0-3: anti-diagonal warp kernel (<= 64/128/256/512 diagonals); 4:
         // wider bands, the CTA strip kernel; 5-8: the 16-bit rectangle
-        const int cls = trace_class(la, lb, r.score1, sc, &dlo, &dhi);
+        const int cls = trace_class(la, lb, r.score1, sc, small_batch(b), &dlo, &dhi);
         const int width = dhi - dlo + 1;
         const long long cost = cls >= kTraceT16First ? (long long)t16_strips(la, cls - kTraceT16First) * t16_steps(lb)
                                                      : (long long)(la + lb + 1) * ((width + 31) / 32);

@@ -341,11 +341,17 @@ __device__ __forceinline__ int t16_walk(const uint32_t *dirs, uint32_t *stage, i
         // along the walk, so the group stages the tile ending at it
         const int s = st * nsteps + j - 1 + kk + hh * kP;
         if (s < tile_lo) {
+            // 16-byte asynchronous copies, all in flight at once (the words
+            // were just written: L2), then one wait
             __syncwarp(gmask);
             tile_lo = max(0, s - tile_steps + 1);
-            const int n = (s - tile_lo + 1) * (Q * kP);
-            const uint32_t *from = dirs + (size_t)tile_lo * (Q * kP);
-            for (int w = k; w < n; w += kP) stage[w] = from[w];
+            const int n4 = (s - tile_lo + 1) * (Q * kP) / 4;
+            const uint4 *from = reinterpret_cast<const uint4 *>(dirs + (size_t)tile_lo * (Q * kP));
+            for (int w = k; w < n4; w += kP) {
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(stage + 4 * w);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(from + w) : "memory");
+            }
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncwarp(gmask);
         }
         const uint32_t nib = (stage[((s - tile_lo) * Q + (rs >> 2)) * kP + kk] >> (16 * hh + 4 * (rs & 3))) & 15u;

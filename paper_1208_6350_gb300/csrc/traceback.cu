@@ -52,7 +52,7 @@ __global__ void k_trace_need(BatchView b, Scoring sc, unsigned long long *max_ne
         if (wants_trace(r)) {
             const int la = r.read_end1 - r.read_begin1 + 1, lb = r.ref_end1 - r.ref_begin1 + 1;
             int dlo, dhi;
-            const int cls = trace_class(la, lb, r.score1, sc, &dlo, &dhi);
+            const int cls = trace_class(la, lb, r.score1, sc, small_batch(b), &dlo, &dhi);
             if (cls < kTraceRingClass) {
                 v[0] = (unsigned)min(ad_dir_words(la, lb, 1 << cls), (long long)UINT_MAX);
                 v[1] = (unsigned)min((long long)la + lb + 2, (long long)UINT_MAX);
