@@ -106,8 +106,15 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
     }
     int best_j = INT_MAX, best_i = -1;
     int fin = kNegB;
+    // the letters of row i+1 are loaded during row i
+    auto qletter = [&](int i) { return i >= 1 && i <= s.rows ? min((int)s.q[(long long)(i - 1) * s.qs], A - 1) : 0; };
+    auto tletter = [&](int i) {
+        const int jj = i + dlo + W - 2;
+        return (jj >= 0 && jj < s.cols) ? min((int)s.t[(long long)jj * s.ts], A - 1) : 0;
+    };
+    int qa_next = qletter(1), tn_next = tletter(1);
     for (int i = 0; i <= s.rows; i++) {
-        const int qa = i >= 1 ? min((int)s.q[(long long)(i - 1) * s.qs], A - 1) : 0;
+        const int qa = i >= 1 ? qa_next : 0;
         uint32_t wpack = 0;  // DNA: the 4 scores of the query letter, one byte each
         const int8_t *wrow = sW + qa * A;
         if constexpr (DNA) wpack = *reinterpret_cast<const uint32_t *>(wrow);
@@ -115,8 +122,9 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
             // the window moves one column right per row
 #pragma unroll
             for (int k = 0; k < W - 1; k++) tw[k] = tw[k + 1];
-            const int jj = i + dlo + W - 2;
-            tw[W - 1] = (jj >= 0 && jj < s.cols) ? min((int)s.t[(long long)jj * s.ts], A - 1) : 0;
+            tw[W - 1] = tn_next;
+            qa_next = qletter(i + 1);
+            tn_next = tletter(i + 1);
         }
         int hleft = kNegB, eleft = kNegB;
         typename DirWord<W>::T dw;
@@ -227,10 +235,21 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
 template <int W, bool WRITE>
 __device__ int band_walk(const typename DirWord<W>::T *dirs, int la, int lb, int dlo, int wb, uint32_t *out, int nr) {
     int i = la, j = lb, state = 0, cur = -1, len = 0, runs = 0, guard = 2 * (la + lb) + 4;
+    // the walk moves up at most one row per step: it holds the current row's
+    // word and the one above, loaded when the row before it was entered
+    typename DirWord<W>::T word = dirs[(long long)la * 32], above;
+    if (la > 0) above = dirs[(long long)(la - 1) * 32];
+    else zero<W>(above);
+    int row = la;
     while ((i > 0 || j > 0) && guard-- > 0) {
         const int k = j - i - dlo;
         if (i < 0 || j < 0 || k < 0 || k >= wb) return -1;
-        const uint32_t nib = get_nib<W>(dirs[(long long)i * 32], k);
+        if (i != row) {
+            word = above;
+            row = i;
+            if (i > 0) above = dirs[(long long)(i - 1) * 32];
+        }
+        const uint32_t nib = get_nib<W>(word, k);
         int op;
         if (state == 0) {
             const int src = nib & 3;
@@ -280,8 +299,41 @@ struct BandLaunch {
     int64_t scratch_words;     // per warp, in 32-bit words
 };
 
+// Banded global DP, walk and CIGAR output of one pair in the narrowest
+// template that holds its band (WT cells per row); the decision words of
+// the warp's lanes are interleaved row by row.
+template <int WT>
+__device__ void band_trace(const BatchView &b, const Scoring &sc, gsw_result *rp, const BandSeq &s, int dlo, int wb,
+                           int s1, const int8_t *sW, uint32_t *warp_scratch, int lane) {
+    using DW = typename DirWord<WT>::T;
+    DW *dirs = reinterpret_cast<DW *>(warp_scratch) + lane;
+    const int la = s.rows, lb = s.cols;
+    int fin = 0, di, dj;
+    if (sc.dna4) band_dp<WT, false, true>(s, dlo, wb, sW, sc.A, sc.O, sc.X, 0, dirs, &di, &dj, &fin);
+    else band_dp<WT, false, false>(s, dlo, wb, sW, sc.A, sc.O, sc.X, 0, dirs, &di, &dj, &fin);
+    if (fin != s1) {
+        rp->flags |= kResInternal;
+        return;
+    }
+    const int nr = band_walk<WT, false>(dirs, la, lb, dlo, wb, nullptr, 0);
+    if (nr < 0) {
+        rp->flags |= kResInternal;
+        return;
+    }
+    const unsigned long long off = atomicAdd(b.cigar_cursor, (unsigned long long)nr);
+    if ((long long)(off + nr) > b.cigar_cap) {
+        rp->flags |= GSW_RES_CIGAR_SPACE;
+        rp->cigar_len = -nr;
+        rp->cigar_off = -1;
+        return;
+    }
+    band_walk<WT, true>(dirs, la, lb, dlo, wb, b.cigar + off, nr);
+    rp->cigar_len = nr;
+    rp->cigar_off = (int64_t)off;
+}
+
 template <int W>
-__device__ void band_pair(const BandLaunch &L, int p, const int8_t *sW, typename DirWord<W>::T *dirs) {
+__device__ void band_pair(const BandLaunch &L, int p, const int8_t *sW, uint32_t *warp_scratch, int lane) {
     const BatchView &b = L.b;
     const Scoring &sc = L.sc;
     gsw_result *rp = b.res + p;
@@ -290,11 +342,15 @@ __device__ void band_pair(const BandLaunch &L, int p, const int8_t *sW, typename
     const uint8_t *tp = b.t + b.t_off[p];
     int bq = rp->read_begin1, bt = rp->ref_begin1;
     if (bq < 0 || bt < 0) {
+        // reverse band: G diagonals above the main one (target letters
+        // against gaps), Gn below (query letters against gaps)
         const int G = reverse_gap_bound(eq, s1, sc);
+        const int Gn = reverse_gap_bound_rows(eq, s1, sc);
         BandSeq s{qp + eq, -1, eq + 1, tp + et, -1, reverse_window(eq, et, s1, sc)};
         int bi, bj, dummy;
-        const bool ok = sc.dna4 ? band_dp<W, true, true>(s, -G, 2 * G + 1, sW, sc.A, sc.O, sc.X, s1, nullptr, &bi, &bj, &dummy)
-                                : band_dp<W, true, false>(s, -G, 2 * G + 1, sW, sc.A, sc.O, sc.X, s1, nullptr, &bi, &bj, &dummy);
+        const bool ok =
+            sc.dna4 ? band_dp<W, true, true>(s, -Gn, G + Gn + 1, sW, sc.A, sc.O, sc.X, s1, nullptr, &bi, &bj, &dummy)
+                    : band_dp<W, true, false>(s, -Gn, G + Gn + 1, sW, sc.A, sc.O, sc.X, s1, nullptr, &bi, &bj, &dummy);
         if (!ok) {
             rp->flags |= kResInternal;
             return;
@@ -314,29 +370,14 @@ __device__ void band_pair(const BandLaunch &L, int p, const int8_t *sW, typename
         rp->flags |= kResPendingTrace;  // the warp traceback takes it
         return;
     }
-    BandSeq s{qp + bq, 1, la, tp + bt, 1, lb};
-    int fin = 0, di, dj;
-    if (sc.dna4) band_dp<W, false, true>(s, dlo, wb, sW, sc.A, sc.O, sc.X, 0, dirs, &di, &dj, &fin);
-    else band_dp<W, false, false>(s, dlo, wb, sW, sc.A, sc.O, sc.X, 0, dirs, &di, &dj, &fin);
-    if (fin != s1) {
-        rp->flags |= kResInternal;
-        return;
+    // the traceback band is usually much narrower than the reverse band that
+    // put the pair in this class
+    const BandSeq s{qp + bq, 1, la, tp + bt, 1, lb};
+    if (wb <= 8) band_trace<8>(b, sc, rp, s, dlo, wb, s1, sW, warp_scratch, lane);
+    else if constexpr (W >= 16) {
+        if (wb <= 16) band_trace<16>(b, sc, rp, s, dlo, wb, s1, sW, warp_scratch, lane);
+        else if constexpr (W >= 32) band_trace<32>(b, sc, rp, s, dlo, wb, s1, sW, warp_scratch, lane);
     }
-    const int nr = band_walk<W, false>(dirs, la, lb, dlo, wb, nullptr, 0);
-    if (nr < 0) {
-        rp->flags |= kResInternal;
-        return;
-    }
-    const unsigned long long off = atomicAdd(b.cigar_cursor, (unsigned long long)nr);
-    if ((long long)(off + nr) > b.cigar_cap) {
-        rp->flags |= GSW_RES_CIGAR_SPACE;
-        rp->cigar_len = -nr;
-        rp->cigar_off = -1;
-        return;
-    }
-    band_walk<W, true>(dirs, la, lb, dlo, wb, b.cigar + off, nr);
-    rp->cigar_len = nr;
-    rp->cigar_off = (int64_t)off;
 }
 
 template <int W, int CLS>
@@ -346,8 +387,7 @@ __global__ void __launch_bounds__(kBBlock) k_band(BandLaunch L) {
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gwarp = blockIdx.x * (kBBlock / 32) + warp;
-    using DW = typename DirWord<W>::T;
-    DW *dirs = reinterpret_cast<DW *>(reinterpret_cast<uint32_t *>(L.scratch) + (size_t)gwarp * L.scratch_words) + lane;
+    uint32_t *warp_scratch = reinterpret_cast<uint32_t *>(L.scratch) + (size_t)gwarp * L.scratch_words;
     const int first = L.var_start[CLS], last = L.var_start[CLS + 1];
     for (;;) {
         int t = 0;
@@ -355,7 +395,7 @@ __global__ void __launch_bounds__(kBBlock) k_band(BandLaunch L) {
         t = __shfl_sync(0xFFFFFFFFu, t, 0);
         const int idx = first + t * 32 + lane;
         if (first + t * 32 >= last) break;
-        if (idx < last) band_pair<W>(L, L.order[idx], sW, dirs);
+        if (idx < last) band_pair<W>(L, L.order[idx], sW, warp_scratch, lane);
         __syncwarp();
     }
 }

@@ -184,6 +184,27 @@ __host__ __device__ inline int reverse_gap_bound(int end_q, int score1, const Sc
     return g > (1 << 30) ? (1 << 30) : (int)g;
 }
 
+// Largest number of query letters against gaps it can hold: each also takes
+// a row from the at most end_q+1 that could be aligned pairs, so g of them
+// satisfy (end_q+1-g)*wmax - O - (g-1)X >= score1.  On the reversed
+// sequences these are the steps below the main diagonal: the reverse band is
+// [-reverse_gap_bound_rows, reverse_gap_bound], much narrower below.
+__host__ __device__ inline int reverse_gap_bound_rows(int end_q, int score1, const Scoring &sc) {
+    const long long num = (long long)(end_q + 1) * sc.wmax - score1 - sc.O + sc.X;
+    const long long den = (long long)sc.wmax + sc.X;
+    if (num < 0 || den <= 0) return 0;
+    const long long g = num / den;
+    return g > end_q + 1 ? end_q + 1 : (int)g;
+}
+
+// Diagonals of the reverse band: G above, reverse_gap_bound_rows below; -1
+// when unbounded (extend 0)
+__host__ __device__ inline int reverse_band_width(int end_q, int score1, const Scoring &sc) {
+    const int G = reverse_gap_bound(end_q, score1, sc);
+    if (G < 0) return -1;
+    return G + reverse_gap_bound_rows(end_q, score1, sc) + 1;
+}
+
 // Half-width of the band of the global alignment between begin and end
 // (la x lb letters, optimum score1): a path through diagonal d has at least
 // g = |d| + |lb - la - d| gap letters and (la + lb - g)/2 aligned pairs, so

@@ -60,8 +60,8 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
         const gsw_result r = b.res[p];
         if (r.score1 <= 0 || (r.flags & kResInternal)) { keys[p] = -1; return; }
         rows = r.read_end1 + 1;
-        const int G = reverse_gap_bound(r.read_end1, r.score1, sc);
-        if (!small_batch(b) && G >= 0 && 2 * G + 1 <= kBandMaxWidth && rows <= kBandMaxRows) {
+        const int wrev = reverse_band_width(r.read_end1, r.score1, sc);
+        if (!small_batch(b) && wrev >= 0 && wrev <= kBandMaxWidth && rows <= kBandMaxRows) {
             keys[p] = -1;
             return;
         }
@@ -100,9 +100,9 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
         if (r.score1 <= 0 || (r.flags & kResInternal)) { keys[p] = -1; return; }
         int width;
         if (r.read_begin1 < 0) {
-            const int G = reverse_gap_bound(r.read_end1, r.score1, sc);
+            const int wrev = reverse_band_width(r.read_end1, r.score1, sc);
             rows = r.read_end1 + 1;
-            width = G < 0 ? INT_MAX : 2 * G + 1;
+            width = wrev < 0 ? INT_MAX : wrev;
             if (width > kBandMaxWidth || rows > kBandMaxRows) {
                 b.res[p].flags |= kResInternal;  // the ring reverse should have taken it
                 keys[p] = -1;

@@ -478,3 +478,32 @@ def test_protein_search_sample(ctx):
     rng = np.random.default_rng(9)
     b = ps.pairs(rng.integers(0, 200, 300), rng.integers(0, 400, 300))
     compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
+def test_reverse_band_edges_in_the_band_kernel(ctx):
+    # 17,000 pairs (the thread-per-pair band kernel takes batches from 2^14):
+    # reads with a run of 1-4 inserted (or deleted) letters a few letters
+    # from their start end the reversed path below (or above) the main
+    # diagonal, up to the reverse band's bounds on each side
+    rng = np.random.default_rng(91)
+    qs, ts = [], []
+    for p in range(17000):
+        L = int(rng.integers(60, 220))
+        s = rng.integers(0, 4, L).astype(np.uint8)
+        at = int(rng.integers(1, 12))
+        k = int(rng.integers(1, 5))
+        if p % 2:
+            q = np.concatenate([s[:at], rng.integers(0, 4, k).astype(np.uint8), s[at:]])
+        else:
+            q = np.concatenate([s[:at], s[at + k:]])
+        nsub = int(rng.integers(0, 3))
+        if nsub:
+            pos = rng.integers(0, len(q), nsub)
+            q[pos] = (q[pos] + rng.integers(1, 4, nsub)) % 4
+        t = np.concatenate([rng.integers(0, 4, int(rng.integers(0, 60))), s,
+                            rng.integers(0, 4, int(rng.integers(0, 60)))]).astype(np.uint8)
+        qs.append(q.astype(np.uint8))
+        ts.append(t)
+    b = _batch(qs, ts, wl.dna_matrix(2, -2), 3, 1, "edge_indels")
+    assert b.npairs >= 1 << 14
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
