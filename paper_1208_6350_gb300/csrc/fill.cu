@@ -334,8 +334,10 @@ struct StripRunner {
     // One step of lane k: low half at column s - k, high half P columns
     // behind.  CHECKED steps handle columns outside [0, n) (start-up and
     // drain of the wavefront); steady steps have every column in range.
-    // Returns true when the reverse fill found its target column.
-    template <bool CHECKED>
+    // FAST steps are those of a forward fill of one strip with a max array
+    // (no boundary rows, no reverse stop).  Returns true when the reverse
+    // fill found its target column.
+    template <bool CHECKED, bool FAST = false>
     __device__ __forceinline__ bool step(const int s) {
         const int jlo = s - k;
         const int jhi = L::FOLD ? jlo - P : jlo;
@@ -350,7 +352,7 @@ struct StripRunner {
             cmin = k == 0 ? bzc : xc;
         }
         cm_t cm_prev{};
-        if (st > 0) {
+        if (!FAST && st > 0) {
             const int bi = s & (P - 1);
             if (bi == 0) {
                 b_cur = b_nxt;
@@ -472,7 +474,10 @@ struct StripRunner {
         }
         // the last lane holds complete columns: column max and strip boundary
         bool found = false;
-        if (k == P - 1 && (!CHECKED || (jhi >= 0 && jhi < n))) {
+        if (FAST && k == P - 1) {
+            if constexpr (L::FOLD) cms[jhi] = (uint16_t)(m >> 16);
+            else cms[jhi] = (int)m;
+        } else if (!FAST && k == P - 1 && (!CHECKED || (jhi >= 0 && jhi < n))) {
             if constexpr (L::FOLD) {
                 const uint32_t full = m >> 16;
                 if (has_cms) {
@@ -494,7 +499,7 @@ struct StripRunner {
         // the target.  Every column up to it is complete in every strip (the
         // earlier strips are ahead), so the first column holding the maximum
         // is at or before it and the strip trackers hold it.
-        if (job.stop_u && last_strip && __any_sync(gmask, found)) return true;
+        if (!FAST && job.stop_u && last_strip && __any_sync(gmask, found)) return true;
         xh = __shfl_sync(gmask, H[R - 1], src);
         xf = __shfl_sync(gmask, f, src);
         xc = __shfl_sync(gmask, m, src);
@@ -502,7 +507,10 @@ struct StripRunner {
     }
 
     // Steps [s0, s1) of the current strip: start-up (checked), steady
-    // (unchecked), drain (checked).  Returns true on an early stop.
+    // (unchecked), drain (checked).  Returns true on an early stop.  With
+    // MAYBE_FAST the steady steps of a one-strip forward fill take the FAST
+    // form (the CTA kernel's strips never do).
+    template <bool MAYBE_FAST = true>
     __device__ bool run(int s0, int s1) {
         const int s_steady = L::FOLD ? 2 * P - 1 : P - 1;
         const int s_drain = max(s_steady, n - 1);
@@ -511,9 +519,14 @@ struct StripRunner {
 #pragma unroll 1
         for (; s < s1 && s < s_steady; s++)
             if (step<true>(s)) return true;
+        if (MAYBE_FAST && st == 0 && last_strip && !job.stop_u && has_cms) {
 #pragma unroll 1
-        for (; s < s1 && s < s_drain; s++)
-            if (step<false>(s)) return true;
+            for (; s < s1 && s < s_drain; s++) step<false, true>(s);
+        } else {
+#pragma unroll 1
+            for (; s < s1 && s < s_drain; s++)
+                if (step<false>(s)) return true;
+        }
 #pragma unroll 1
         for (; s < s1; s++)
             if (step<true>(s)) return true;
@@ -985,7 +998,7 @@ __global__ void __launch_bounds__(LongCfg<DNA, S32>::NW * 32, 1)
         bool stop = false, fin = S.stopped != 0;
         if (!fin) {
             const int q = ph - cmd.start;
-            stop = sr.run(q * kLongChunk, (q + 1) * kLongChunk);
+            stop = sr.template run<false>(q * kLongChunk, (q + 1) * kLongChunk);
             fin = stop || (q + 1) * kLongChunk >= sr.nsteps;
         }
         if (fin) {
