@@ -59,6 +59,13 @@
 #ifndef GSW_FILL_TTRICK
 #define GSW_FILL_TTRICK 0
 #endif
+// unroll factors of the steady loops: one-strip forward fills (FAST), other strips
+#ifndef GSW_FILL_UNROLL_FAST
+#define GSW_FILL_UNROLL_FAST 4
+#endif
+#ifndef GSW_FILL_UNROLL_GEN
+#define GSW_FILL_UNROLL_GEN 2
+#endif
 #include <type_traits>
 #include <cstring>
 #include <mutex>
@@ -67,6 +74,8 @@ namespace gsw {
 namespace {
 
 constexpr int kBlock = 128;
+constexpr int kUnrollFast = GSW_FILL_UNROLL_FAST;
+constexpr int kUnrollGen = GSW_FILL_UNROLL_GEN;
 
 // ---------------------------------------------------------------- lanes
 struct L16 {
@@ -254,8 +263,8 @@ struct StripRunner {
     int k, gbase, lane, src, n, A, nsteps, pad_top;
     unsigned gmask;
     uint32_t kO, kXm, NEGE;
-    int sh0;
     uint32_t bzh, bzf, bzc;
+    uint32_t mulh;  // received word -> this lane's input: lane 0 shifts it to the high half (x 65536)
     cm_t *cms;
     bool has_cms;
 
@@ -276,10 +285,10 @@ struct StripRunner {
         kO = L::addk(-sc.O);
         kXm = L::halves(-sc.X, -sc.X);
         NEGE = L::both(-sc.O);
-        sh0 = (L::FOLD && k_ == 0) ? 16 : 0;
         bzh = k_ == 0 ? L::lane1(0) : 0u;
         bzf = k_ == 0 ? L::lane1(-sc.O) : 0u;
         bzc = k_ == 0 ? (L::FOLD ? L::Z : 0u) : 0u;
+        mulh = k_ == 0 ? (L::FOLD ? 65536u : 0u) : 1u;
         cms = reinterpret_cast<cm_t *>(job_.cms);
         has_cms = job_.cms != nullptr;
     }
@@ -342,15 +351,12 @@ struct StripRunner {
         const int jlo = s - k;
         const int jhi = L::FOLD ? jlo - P : jlo;
         uint32_t hin, fin, cmin;
-        if constexpr (L::FOLD) {
-            hin = (xh << sh0) | bzh;
-            fin = (xf << sh0) | bzf;
-            cmin = (xc << sh0) | bzc;
-        } else {
-            hin = k == 0 ? bzh : xh;
-            fin = k == 0 ? bzf : xf;
-            cmin = k == 0 ? bzc : xc;
-        }
+        // lane 0 shifts the received word to its high half (the fold) and
+        // puts its boundary in the low half: one multiply-add each, on the
+        // FMA pipe that the cell arithmetic leaves mostly idle
+        hin = xh * mulh + bzh;
+        fin = xf * mulh + bzf;
+        cmin = xc * mulh + bzc;
         cm_t cm_prev{};
         if (!FAST && st > 0) {
             const int bi = s & (P - 1);
@@ -519,11 +525,11 @@ struct StripRunner {
 #pragma unroll 1
         for (; s < s1 && s < s_steady; s++)
             if (step<true>(s)) return true;
-        if (MAYBE_FAST && st == 0 && last_strip && !job.stop_u && has_cms) {
-#pragma unroll 1
+        if (MAYBE_FAST && st == 0 && last_strip && !job.stop_u && has_cms && job.ts == 1) {
+#pragma unroll kUnrollFast
             for (; s < s1 && s < s_drain; s++) step<false, true>(s);
         } else {
-#pragma unroll 1
+#pragma unroll kUnrollGen
             for (; s < s1 && s < s_drain; s++)
                 if (step<false>(s)) return true;
         }
