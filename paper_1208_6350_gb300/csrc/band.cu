@@ -130,9 +130,11 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
         typename DirWord<W>::T dw;
         zero<W>(dw);
         int row_hit = -1;
-        // rows whose band cells all lie inside the rectangle (most of them):
-        // no boundary tests per cell; cells past the band width stay -inf
-        const bool interior = i >= 1 && i + dlo >= 1 && i + dlo + wb - 1 <= s.cols;
+        // rows whose band cells all lie inside the rectangle (most of them,
+        // but not the last, which holds the final cell): no boundary tests
+        // per cell.  The callers pass wb == W (a band wider than the
+        // provable one is still exact), so no cell lies past the band.
+        const bool interior = i >= 1 && i < s.rows + (REV ? 1 : 0) && i + dlo >= 1 && i + dlo + wb - 1 <= s.cols;
         if (interior) {
 #pragma unroll
             for (int k = 0; k < W; k++) {
@@ -145,18 +147,12 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
                 if constexpr (DNA) w = (int)(int8_t)(uint8_t)(wpack >> (8 * tw[k]));
                 else w = wrow[tw[k]];
                 const int hdg = Hp[k] + w;
-                int H = max(hdg, max(E, F));
-                if (k >= wb) {
-                    H = kNegB;
-                    E = kNegB;
-                    F = kNegB;
-                }
+                const int H = max(hdg, max(E, F));
                 if constexpr (REV) {
                     if (H == target && row_hit < 0) row_hit = i + dlo + k;
                 } else {
                     const uint32_t src = H == hdg ? 0u : (H == E ? 1u : 2u);
                     put_nib<W>(dw, k, src | (E == eo ? 4u : 0u) | (F == fo ? 8u : 0u));
-                    if (i == s.rows && i + dlo + k == s.cols) fin = H;
                 }
                 Hp[k] = H;
                 Fp[k] = F;
@@ -308,6 +304,7 @@ __device__ void band_trace(const BatchView &b, const Scoring &sc, gsw_result *rp
     using DW = typename DirWord<WT>::T;
     DW *dirs = reinterpret_cast<DW *>(warp_scratch) + lane;
     const int la = s.rows, lb = s.cols;
+    wb = WT;  // the band widened to the template: still exact, no per-cell width test
     int fin = 0, di, dj;
     if (sc.dna4) band_dp<WT, false, true>(s, dlo, wb, sW, sc.A, sc.O, sc.X, 0, dirs, &di, &dj, &fin);
     else band_dp<WT, false, false>(s, dlo, wb, sW, sc.A, sc.O, sc.X, 0, dirs, &di, &dj, &fin);
@@ -346,11 +343,15 @@ __device__ void band_pair(const BandLaunch &L, int p, const int8_t *sW, uint32_t
         // against gaps), Gn below (query letters against gaps)
         const int G = reverse_gap_bound(eq, s1, sc);
         const int Gn = reverse_gap_bound_rows(eq, s1, sc);
+        if (G < 0 || G + Gn + 1 > W) {  // the plan's class holds the reverse band
+            rp->flags |= kResInternal;
+            return;
+        }
         BandSeq s{qp + eq, -1, eq + 1, tp + et, -1, reverse_window(eq, et, s1, sc)};
         int bi, bj, dummy;
-        const bool ok =
-            sc.dna4 ? band_dp<W, true, true>(s, -Gn, G + Gn + 1, sW, sc.A, sc.O, sc.X, s1, nullptr, &bi, &bj, &dummy)
-                    : band_dp<W, true, false>(s, -Gn, G + Gn + 1, sW, sc.A, sc.O, sc.X, s1, nullptr, &bi, &bj, &dummy);
+        // (widened to the template's W diagonals: still exact)
+        const bool ok = sc.dna4 ? band_dp<W, true, true>(s, -Gn, W, sW, sc.A, sc.O, sc.X, s1, nullptr, &bi, &bj, &dummy)
+                                : band_dp<W, true, false>(s, -Gn, W, sW, sc.A, sc.O, sc.X, s1, nullptr, &bi, &bj, &dummy);
         if (!ok) {
             rp->flags |= kResInternal;
             return;
