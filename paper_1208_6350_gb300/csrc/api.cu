@@ -88,6 +88,7 @@ struct gsw_ctx {
     DevBuf prof_qoff, prof_qlen;
     void *host_small = nullptr;  // pinned readback area
     cudaEvent_t ev[GSW_NSTAGES + 1] = {};
+    BandStreams aux = {};  // side streams of the band kernel's classes (created on first use)
     bool timing = false;
     int launches = 0;
     int stage_done[GSW_NSTAGES] = {};
@@ -194,6 +195,19 @@ enum MiscSlot {
     kMiscNeed16 = 11,  // 1 word: 16-bit rectangle traceback (direction words per group)
     kMiscWords = 16
 };
+
+// Side streams and fork/join events of the band classes, created once per
+// context outside any capture (the first call of a shape is never captured).
+int ensure_aux(gsw_ctx *ctx) {
+    if (ctx->aux.s[0]) return GSW_OK;
+    if (ctx->capturing) return GSW_ESTATE;
+    for (int k = 0; k < 2; k++)
+        if (cudaStreamCreateWithFlags(&ctx->aux.s[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->aux.join[k], cudaEventDisableTiming) != cudaSuccess)
+            return GSW_ECUDA;
+    if (cudaEventCreateWithFlags(&ctx->aux.fork, cudaEventDisableTiming) != cudaSuccess) return GSW_ECUDA;
+    return GSW_OK;
+}
 
 // event e[k] marks the end of stage k-1 / start of stage k
 int mark(gsw_ctx *ctx, int k, cudaStream_t st) {
@@ -380,24 +394,14 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
             // thread-per-pair banded reverse and traceback for narrow bands
             GSW_TRY(plan(kPlanBand));
             const int rows_cap = std::min(std::max(maxm, 1), kBandMaxRows);
-            const int64_t words = (int64_t)(rows_cap + 1) * 32 * 4;  // widest class: 4 words per lane and row
-            int bgrid = ctx->sms * 8;
-            const int bwarps_per_block = band_block_threads() / 32;
-            {
-                // a quarter of what is left: the band scratch holds every row of
-                // the pairs in flight
-                size_t have = room(ctx, ctx->band_scr, ctx->misc) + ctx->misc.bytes;  // budget left without band_scr
-                size_t per_warp = (size_t)words * sizeof(uint32_t);
-                size_t max_warps = have / 4 / per_warp;
-                if ((size_t)bgrid * bwarps_per_block > max_warps)
-                    bgrid = (int)std::max<size_t>(1, max_warps / bwarps_per_block);
-            }
-            {
-                const size_t need = (size_t)bgrid * bwarps_per_block * words * sizeof(uint32_t);
-                if (need > ctx->band_scr.bytes) release(ctx, ctx->band_scr);
-                GSW_TRY(ensure(ctx, ctx->band_scr, need));
-            }
-            CUDA_TRY(launch_band(bv, sc, pb, ctx->band_scr.p, words, bgrid, st));
+            // a quarter of what is left: the band scratch holds every row of
+            // the pairs in flight
+            const size_t have = room(ctx, ctx->band_scr, ctx->misc) + ctx->misc.bytes;  // budget left without band_scr
+            const BandGrids bg = band_grids(rows_cap, ctx->sms, have / 4);
+            if (bg.total_bytes > ctx->band_scr.bytes) release(ctx, ctx->band_scr);
+            GSW_TRY(ensure(ctx, ctx->band_scr, bg.total_bytes));
+            GSW_TRY(ensure_aux(ctx));
+            CUDA_TRY(launch_band(bv, sc, pb, ctx->band_scr.p, bg, st, ctx->aux));
             S.launches += 3;
             S.stage_done[4] = 1;
         }
@@ -871,6 +875,11 @@ int gsw_context_destroy(gsw_ctx *c) {
     if (c->host_small) cudaFreeHost(c->host_small);
     for (int k = 0; k <= GSW_NSTAGES; k++)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    for (int k = 0; k < 2; k++) {
+        if (c->aux.s[k]) cudaStreamDestroy(c->aux.s[k]);
+        if (c->aux.join[k]) cudaEventDestroy(c->aux.join[k]);
+    }
+    if (c->aux.fork) cudaEventDestroy(c->aux.fork);
     delete c;
     return GSW_OK;
 }

@@ -23,6 +23,8 @@
 // runs, once to write them in forward order at the reserved offset.
 #include "gsw_impl.cuh"
 
+#include <algorithm>
+
 namespace gsw {
 namespace {
 
@@ -405,20 +407,65 @@ __global__ void __launch_bounds__(kBBlock) k_band(BandLaunch L) {
 
 int band_block_threads() { return kBBlock; }
 
+// Resident blocks per SM of each class's kernel (width 8, 16, 32).
+static void band_occupancy(int occ[3]) {
+    occ[0] = occ[1] = occ[2] = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_band<8, 0>, kBBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_band<16, 1>, kBBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_band<32, 2>, kBBlock, 0);
+    for (int c = 0; c < 3; c++) occ[c] = std::max(1, occ[c]);
+}
+
+BandGrids band_grids(int rows_cap, int sms, size_t budget_bytes) {
+    int occ[3];
+    band_occupancy(occ);
+    BandGrids g;
+    size_t total = 0;
+    for (int c = 0; c < 3; c++) {
+        // a warp's rows: (rows_cap + 1) x 32 lanes x W/8 words
+        g.words[c] = (int64_t)(rows_cap + 1) * 32 * ((8 << c) / 8);
+        g.grid[c] = sms * occ[c];
+        total += (size_t)g.grid[c] * (kBBlock / 32) * (size_t)g.words[c] * sizeof(uint32_t);
+    }
+    const double scale = total > budget_bytes && total > 0 ? (double)budget_bytes / (double)total : 1.0;
+    size_t off = 0;
+    for (int c = 0; c < 3; c++) {
+        g.grid[c] = std::max(1, (int)(g.grid[c] * scale));
+        g.off[c] = off;
+        off += (size_t)g.grid[c] * (kBBlock / 32) * (size_t)g.words[c] * sizeof(uint32_t);
+        off = (off + 255) & ~(size_t)255;
+    }
+    g.total_bytes = off;
+    return g;
+}
+
 cudaError_t launch_band(const BatchView &b, const Scoring &sc, const PlanBuffers &pb, void *scratch,
-                        int64_t scratch_words, int grid, cudaStream_t st) {
+                        const BandGrids &g, cudaStream_t st, const BandStreams &aux) {
     BandLaunch L;
     L.b = b;
     L.sc = sc;
     L.order = pb.order;
     L.var_start = pb.var_start;
     L.head = pb.task_lo;  // reused as per-class counters (zeroed below)
-    L.scratch = scratch;
-    L.scratch_words = scratch_words;
     cudaMemsetAsync(pb.task_lo, 0, sizeof(int32_t) * kNumVariants, st);
-    k_band<8, 0><<<grid, kBBlock, 0, st>>>(L);
-    k_band<16, 1><<<grid, kBBlock, 0, st>>>(L);
-    k_band<32, 2><<<grid, kBBlock, 0, st>>>(L);
+    // the three classes run side by side (each its own scratch): the widest
+    // (slowest per pair) on the calling stream, the others on two auxiliary
+    // streams forked and joined by events, so a class's tail overlaps the others
+    cudaEventRecord(aux.fork, st);
+    cudaStreamWaitEvent(aux.s[0], aux.fork, 0);
+    cudaStreamWaitEvent(aux.s[1], aux.fork, 0);
+    const cudaStream_t on[3] = {aux.s[1], aux.s[0], st};
+    for (int c = 2; c >= 0; c--) {
+        L.scratch = static_cast<uint8_t *>(scratch) + g.off[c];
+        L.scratch_words = g.words[c];
+        if (c == 2) k_band<32, 2><<<g.grid[2], kBBlock, 0, on[2]>>>(L);
+        else if (c == 1) k_band<16, 1><<<g.grid[1], kBBlock, 0, on[1]>>>(L);
+        else k_band<8, 0><<<g.grid[0], kBBlock, 0, on[0]>>>(L);
+    }
+    cudaEventRecord(aux.join[0], aux.s[0]);
+    cudaEventRecord(aux.join[1], aux.s[1]);
+    cudaStreamWaitEvent(st, aux.join[0], 0);
+    cudaStreamWaitEvent(st, aux.join[1], 0);
     return cudaGetLastError();
 }
 

@@ -382,8 +382,21 @@ cudaError_t launch_trace16(const BatchView &b, const Scoring &sc, const T16Scrat
                            cudaStream_t st);
 
 int band_block_threads();
+// Grids and scratch of the three band classes (widths 8, 16, 32), each
+// sized to the blocks that can be resident, scaled down to the budget.
+struct BandGrids {
+    int grid[3];
+    int64_t words[3];  // per warp
+    size_t off[3];     // byte offsets of the classes' scratch
+    size_t total_bytes;
+};
+BandGrids band_grids(int rows_cap, int sms, size_t budget_bytes);
+struct BandStreams {
+    cudaStream_t s[2];
+    cudaEvent_t fork, join[2];
+};
 cudaError_t launch_band(const BatchView &b, const Scoring &sc, const PlanBuffers &pb, void *scratch,
-                        int64_t scratch_words, int grid, cudaStream_t st);
+                        const BandGrids &g, cudaStream_t st, const BandStreams &aux);
 
 // small helpers (misc.cu)
 cudaError_t launch_max_lengths(const int32_t *q_len, const int32_t *t_len, int32_t n, int32_t *out2,
