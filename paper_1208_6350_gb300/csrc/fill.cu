@@ -59,6 +59,12 @@
 #ifndef GSW_FILL_TTRICK
 #define GSW_FILL_TTRICK 0
 #endif
+// 1: 16-bit lanes hold signed values (the clamp at 0 folds into the first
+// add-max: one instruction fewer per word, one DPX more); 0: values biased
+// by 0x8000 in unsigned lanes
+#ifndef GSW_FILL_SIGNED
+#define GSW_FILL_SIGNED 0
+#endif
 // unroll factors of the steady loops: one-strip forward fills (FAST), other strips
 #ifndef GSW_FILL_UNROLL_FAST
 #define GSW_FILL_UNROLL_FAST 4
@@ -82,14 +88,51 @@ struct L16 {
     static constexpr bool FOLD = true;
     using cm_t = uint16_t;
     using bnd_t = uint32_t;
+#if GSW_FILL_SIGNED
+    static constexpr uint32_t Z = 0u;  // zero of one lane
+    static constexpr uint32_t Z2 = 0u;
+    static __device__ __forceinline__ uint32_t vmax(uint32_t a, uint32_t b) { return __vmaxs2(a, b); }
+    static __device__ __forceinline__ uint32_t lane1(int v) { return (uint32_t)v & 0xFFFFu; }
+    // lane value as stored in the max array (biased by 0x8000, read as u16)
+    static __device__ __forceinline__ uint32_t cm16(uint32_t x) { return x ^ 0x8000u; }
+    static __device__ __forceinline__ int value(uint32_t x16) { return (int)(int16_t)(uint16_t)x16; }
+    // max(diag + W, E, 0) in one DPX instruction
+    static __device__ __forceinline__ uint32_t tt_relu(uint32_t d, uint32_t w, uint32_t e) {
+        return __viaddmax_s16x2_relu(d, w, e);
+    }
+    // H - O per lane (kO = -O in both halves); H >= 0, so no lane goes below -O
+    static __device__ __forceinline__ uint32_t ok(int O) { return halves(-O, -O); }
+    static __device__ __forceinline__ uint32_t sub_o(uint32_t h, uint32_t kO) {
+        return __viaddmax_s16x2(h, kO, 0x80008000u);
+    }
+#else
     static constexpr uint32_t Z = 0x8000u;    // bias of one lane
     static constexpr uint32_t Z2 = 0x80008000u;
     static __device__ __forceinline__ uint32_t vmax(uint32_t a, uint32_t b) { return __vmaxu2(a, b); }
     static __device__ __forceinline__ uint32_t lane1(int v) { return (uint32_t)(v + 0x8000) & 0xFFFFu; }
+    static __device__ __forceinline__ uint32_t cm16(uint32_t x) { return x; }
+    static __device__ __forceinline__ int value(uint32_t x16) { return (int)x16 - 0x8000; }
+    static __device__ __forceinline__ uint32_t tt_relu(uint32_t d, uint32_t w, uint32_t e) {
+        return vmax(addmax(d, w, e), Z2);
+    }
+    // H - O per lane: a plain add (every biased lane value is >= O)
+    static __device__ __forceinline__ uint32_t ok(int O) { return addk(-O); }
+    static __device__ __forceinline__ uint32_t sub_o(uint32_t h, uint32_t kO) { return h + kO; }
+#endif
     static __device__ __forceinline__ uint32_t both(int v) { return lane1(v) | (lane1(v) << 16); }
     // integer that adds c to both lanes of a word
     static __device__ __forceinline__ uint32_t addk(int c) { return (uint32_t)(c * 65537); }
-#if GSW_FILL_DPX
+#if GSW_FILL_SIGNED
+    static __device__ __forceinline__ uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) {
+        return __viaddmax_s16x2(a, b, c);
+    }
+    static __device__ __forceinline__ uint32_t halves(int lo, int hi) {
+        return ((uint32_t)lo & 0xFFFFu) | (((uint32_t)hi & 0xFFFFu) << 16);
+    }
+    static __device__ __forceinline__ uint32_t merge(uint32_t a, uint32_t b) {
+        return (a & 0x0000FFFFu) | (b & 0xFFFF0000u);
+    }
+#elif GSW_FILL_DPX
     // per-lane max(a + b, c) in one DPX instruction; b holds two 16-bit
     // two's-complement halves (no borrow between them)
     static __device__ __forceinline__ uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) {
@@ -126,11 +169,22 @@ struct L32 {
     static __device__ __forceinline__ uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) { return vmax(a + b, c); }
     static __device__ __forceinline__ uint32_t halves(int lo, int hi) { return (uint32_t)lo; }
     static __device__ __forceinline__ uint32_t merge(uint32_t a, uint32_t b) { return a; }
+    static __device__ __forceinline__ uint32_t cm16(uint32_t x) { return x; }
+    static __device__ __forceinline__ uint32_t tt_relu(uint32_t d, uint32_t w, uint32_t e) {
+        return vmax(addmax(d, w, e), Z2);
+    }
+    static __device__ __forceinline__ uint32_t ok(int O) { return addk(-O); }
+    static __device__ __forceinline__ uint32_t sub_o(uint32_t h, uint32_t kO) { return h + kO; }
 };
+
+// DNA table layout of a variant with R row words per lane (one for all:
+// the combined table's smaller profile for the tallest variant, 3 -> 4
+// blocks per SM, measured slower all the same)
+__host__ __device__ constexpr int dna_split(int R) { return GSW_FILL_SPLIT; }
 
 // words of one lane's profile (the warp region holds 32 lanes' worth)
 __host__ __device__ constexpr int prof_words(int R, bool fold, bool dna, int A) {
-    return dna ? (fold ? (GSW_FILL_SPLIT == 0 ? 16 * R : GSW_FILL_SPLIT == 1 ? 8 * R : 4 * R) : 4 * R) : A * R;
+    return dna ? (fold ? (dna_split(R) == 0 ? 16 * R : dna_split(R) == 1 ? 8 * R : 4 * R) : 4 * R) : A * R;
 }
 
 // Index of profile word (table c, row r) of lane l inside the warp region:
@@ -202,7 +256,7 @@ __device__ __forceinline__ void build_profile(uint32_t *psm, const Job &job, con
             int rho_hi = st * SP + S + k * R + r - pad_top;
             qhi = rho_hi >= 0 ? min((int)job.q[(long long)rho_hi * job.qs], A - 1) : -1;
         }
-        if constexpr (DNA && GSW_FILL_SPLIT == 0) {
+        if constexpr (DNA && dna_split(R) == 0) {
             if constexpr (L::FOLD) {
 #pragma unroll
                 for (int a = 0; a < 4; a++)
@@ -216,7 +270,7 @@ __device__ __forceinline__ void build_profile(uint32_t *psm, const Job &job, con
 #pragma unroll
                 for (int a = 0; a < 4; a++) psm[pidx<R>(a, r, lane)] = (uint32_t)(qlo >= 0 ? sc_w(sc, qlo, a) : 0);
             }
-        } else if constexpr (DNA && GSW_FILL_SPLIT == 1) {
+        } else if constexpr (DNA && dna_split(R) == 1) {
             for (int a = 0; a < A; a++) {
                 psm[pidx<R>(a, r, lane)] = L::halves(qlo >= 0 ? sc_w(sc, qlo, a) : 0, 0);
                 if constexpr (L::FOLD)
@@ -236,12 +290,12 @@ __device__ __forceinline__ void build_profile(uint32_t *psm, const Job &job, con
 
 template <class L>
 __device__ __forceinline__ int lane_lo(uint32_t w) {
-    if constexpr (L::FOLD) return (int)(w & 0xFFFFu) - 0x8000;
+    if constexpr (L::FOLD) return L::value(w & 0xFFFFu);
     else return (int)w;
 }
 template <class L>
 __device__ __forceinline__ int lane_hi(uint32_t w) {
-    if constexpr (L::FOLD) return (int)(w >> 16) - 0x8000;
+    if constexpr (L::FOLD) return L::value(w >> 16);
     else return (int)w;
 }
 
@@ -282,7 +336,7 @@ struct StripRunner {
         nsteps = job_.ncols + (L::FOLD ? 2 * P - 1 : P - 1);
         pad_top = pad_top_;
         gmask = gmask_;
-        kO = L::addk(-sc.O);
+        kO = L::ok(sc.O);
         kXm = L::halves(-sc.X, -sc.X);
         NEGE = L::both(-sc.O);
         bzh = k_ == 0 ? L::lane1(0) : 0u;
@@ -401,9 +455,9 @@ struct StripRunner {
             }
         }
         uint32_t pw[R];
-        if constexpr (DNA && GSW_FILL_SPLIT == 0) {
+        if constexpr (DNA && dna_split(R) == 0) {
             load_words<R>(psm, L::FOLD ? al * 4 + ah : al, lane, pw);
-        } else if constexpr (DNA && GSW_FILL_SPLIT == 1) {
+        } else if constexpr (DNA && dna_split(R) == 1) {
             load_words<R>(psm, al, lane, pw);
             if constexpr (L::FOLD) {
                 uint32_t ph[R];
@@ -425,16 +479,15 @@ struct StripRunner {
         uint32_t f = fin, m = cmin;
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            uint32_t tt = L::addmax(diag, pw[r], E[r]);
-            tt = L::vmax(tt, Z2);
+            const uint32_t tt = L::tt_relu(diag, pw[r], E[r]);
             const uint32_t h = L::vmax(tt, f);
 #if GSW_FILL_TTRICK
-            f = L::addmax(f, kXm, tt + kO);  // = max(F - X, H - O) since O >= X
-            E[r] = L::addmax(E[r], kXm, h + kO);
+            f = L::addmax(f, kXm, L::sub_o(tt, kO));  // = max(F - X, H - O) since O >= X
+            E[r] = L::addmax(E[r], kXm, L::sub_o(h, kO));
 #else
             // one H - O for both gap states; the F chain then runs through
             // h (3 dependent instructions per row), hidden by the other warps
-            const uint32_t ho = h + kO;
+            const uint32_t ho = L::sub_o(h, kO);
             f = L::addmax(f, kXm, ho);
             E[r] = L::addmax(E[r], kXm, ho);
 #endif
@@ -481,14 +534,15 @@ struct StripRunner {
         // the last lane holds complete columns: column max and strip boundary
         bool found = false;
         if (FAST && k == P - 1) {
-            if constexpr (L::FOLD) cms[jhi] = (uint16_t)(m >> 16);
+            if constexpr (L::FOLD) cms[jhi] = (uint16_t)L::cm16(m >> 16);
             else cms[jhi] = (int)m;
         } else if (!FAST && k == P - 1 && (!CHECKED || (jhi >= 0 && jhi < n))) {
             if constexpr (L::FOLD) {
                 const uint32_t full = m >> 16;
                 if (has_cms) {
-                    if (st == 0) cms[jhi] = (uint16_t)full;
-                    else cms[jhi] = (uint16_t)max((uint32_t)cm_prev, full);
+                    // the array holds biased u16: merged with the strips above as such
+                    if (st == 0) cms[jhi] = (uint16_t)L::cm16(full);
+                    else cms[jhi] = (uint16_t)max((uint32_t)cm_prev, L::cm16(full));
                 }
                 if (!last_strip) bout[jhi] = (H[R - 1] >> 16) | (f & 0xFFFF0000u);
                 found = full == job.stop_u;
