@@ -187,13 +187,12 @@ int make_scoring(const int8_t *matrix, int32_t A, int32_t O, int32_t X, Scoring 
 enum MiscSlot {
     kMiscTraceHead = 0,
     kMiscCursor = 1,
-    kMiscMaxLen = 2,
     kMiscValid = 3,
     kMiscNeed = 4,   // 2 words: anti-diagonal traceback (direction words, op words per pair)
     kMiscRing = 6,   // 3 words: wide-band traceback (total words, max words of a pair, max op words)
-    kMiscExt = 9,    // 2 words: arena extents in letters (packed input)
     kMiscNeed16 = 11,  // 1 word: 16-bit rectangle traceback (direction words per group)
-    kMiscWords = 16
+    kMiscStats = 12,   // 5 words: largest lengths, arena extents, bad lengths or offsets
+    kMiscWords = 17
 };
 
 // Side streams and fork/join events of the band classes, created once per
@@ -593,24 +592,44 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
     bv.cigar_cursor = misc + kMiscCursor;
     int maxm = 0, maxn = 0;
     const bool hio = (flags & GSW_HOST_IO) != 0;
+    unsigned long long *hstat = reinterpret_cast<unsigned long long *>(ctx->host_small);
+    // the batch's sizes and the checks of its lengths and offsets, on the
+    // device in one pass (one 40-byte readback before anything is sized)
+    auto batch_stats = [&](const int64_t *qo, const int32_t *ql, const int64_t *to, const int32_t *tl) -> int {
+        CUDA_TRY(launch_batch_stats(qo, ql, to, tl, npairs, misc + kMiscStats, st));
+        ctx->launches += 1;
+        CUDA_TRY(cudaMemcpyAsync(hstat, misc + kMiscStats, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                 st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return GSW_OK;
+    };
     if (hio) {
-        int64_t qext = 0, text = 0, cmext = 0;
-        for (int32_t p = 0; p < npairs; p++) {
-            if (q_len[p] < 0 || t_len[p] < 0 || q_len[p] >= (1 << 24) || t_len[p] >= (1 << 24))
-                return set_err(GSW_EINVAL, "pair %d: length out of [0, 2^24)", p);
-            if (q_off[p] < 0 || t_off[p] < 0) return set_err(GSW_EINVAL, "pair %d: negative offset", p);
-            maxm = std::max(maxm, q_len[p]);
-            maxn = std::max(maxn, t_len[p]);
-            qext = std::max<int64_t>(qext, q_off[p] + q_len[p]);
-            text = std::max<int64_t>(text, t_off[p] + t_len[p]);
-            if (flags & GSW_COLMAX) cmext = std::max<int64_t>(cmext, colmax_off[p] + t_len[p]);
-        }
-        GSW_TRY(ensure(ctx, ctx->io_q, (size_t)std::max<int64_t>(qext, 1)));
-        GSW_TRY(ensure(ctx, ctx->io_t, (size_t)std::max<int64_t>(text, 1)));
+        // offsets and lengths first; the arenas once their extents are known
         GSW_TRY(ensure(ctx, ctx->io_qoff, sizeof(int64_t) * npairs));
         GSW_TRY(ensure(ctx, ctx->io_toff, sizeof(int64_t) * npairs));
         GSW_TRY(ensure(ctx, ctx->io_qlen, sizeof(int32_t) * npairs));
         GSW_TRY(ensure(ctx, ctx->io_tlen, sizeof(int32_t) * npairs));
+        CUDA_TRY(cudaMemcpyAsync(ctx->io_qoff.p, q_off, sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(ctx->io_toff.p, t_off, sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(ctx->io_qlen.p, q_len, sizeof(int32_t) * npairs, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(ctx->io_tlen.p, t_len, sizeof(int32_t) * npairs, cudaMemcpyHostToDevice, st));
+        GSW_TRY(batch_stats((const int64_t *)ctx->io_qoff.p, (const int32_t *)ctx->io_qlen.p,
+                            (const int64_t *)ctx->io_toff.p, (const int32_t *)ctx->io_tlen.p));
+        if (hstat[4]) {
+            for (int32_t p = 0; p < npairs; p++) {
+                if (q_len[p] < 0 || t_len[p] < 0 || q_len[p] >= (1 << 24) || t_len[p] >= (1 << 24))
+                    return set_err(GSW_EINVAL, "pair %d: length out of [0, 2^24)", p);
+                if (q_off[p] < 0 || t_off[p] < 0) return set_err(GSW_EINVAL, "pair %d: negative offset", p);
+            }
+        }
+        maxm = (int)hstat[0];
+        maxn = (int)hstat[1];
+        const int64_t qext = (int64_t)hstat[2], text = (int64_t)hstat[3];
+        int64_t cmext = 0;
+        if (flags & GSW_COLMAX)
+            for (int32_t p = 0; p < npairs; p++) cmext = std::max<int64_t>(cmext, colmax_off[p] + t_len[p]);
+        GSW_TRY(ensure(ctx, ctx->io_q, (size_t)std::max<int64_t>(qext, 1)));
+        GSW_TRY(ensure(ctx, ctx->io_t, (size_t)std::max<int64_t>(text, 1)));
         GSW_TRY(ensure(ctx, ctx->io_res, sizeof(gsw_result) * npairs));
         if (flags & GSW_CIGAR) GSW_TRY(ensure(ctx, ctx->io_cigar, sizeof(uint32_t) * (size_t)std::max<int64_t>(cigar_capacity, 1)));
         if (flags & GSW_COLMAX) {
@@ -631,10 +650,6 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
             CUDA_TRY(cudaMemcpyAsync(ctx->io_q.p, q, qext, cudaMemcpyHostToDevice, st));
             CUDA_TRY(cudaMemcpyAsync(ctx->io_t.p, t, text, cudaMemcpyHostToDevice, st));
         }
-        CUDA_TRY(cudaMemcpyAsync(ctx->io_qoff.p, q_off, sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, st));
-        CUDA_TRY(cudaMemcpyAsync(ctx->io_toff.p, t_off, sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, st));
-        CUDA_TRY(cudaMemcpyAsync(ctx->io_qlen.p, q_len, sizeof(int32_t) * npairs, cudaMemcpyHostToDevice, st));
-        CUDA_TRY(cudaMemcpyAsync(ctx->io_tlen.p, t_len, sizeof(int32_t) * npairs, cudaMemcpyHostToDevice, st));
         if (flags & GSW_COLMAX)
             CUDA_TRY(cudaMemcpyAsync(ctx->io_cmoff.p, colmax_off, sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, st));
         bv.q = (const uint8_t *)ctx->io_q.p;
@@ -658,26 +673,13 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
         bv.cigar = cigar;
         bv.colmax = colmax;
         bv.colmax_off = colmax_off;
-        int32_t *ml = reinterpret_cast<int32_t *>(misc + kMiscMaxLen);
-        CUDA_TRY(launch_max_lengths(q_len, t_len, npairs, ml, st));
-        ctx->launches += 1;
-        if (flags & GSW_PACKED2) {
-            CUDA_TRY(launch_extents(q_off, q_len, t_off, t_len, npairs, misc + kMiscExt, st));
-            ctx->launches += 1;
-        }
-        int32_t *hs = reinterpret_cast<int32_t *>(ctx->host_small);
-        CUDA_TRY(cudaMemcpyAsync(hs, ml, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        if (flags & GSW_PACKED2)
-            CUDA_TRY(cudaMemcpyAsync(hs + 4, misc + kMiscExt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                                     st));
-        CUDA_TRY(cudaStreamSynchronize(st));
-        maxm = hs[0];
-        maxn = hs[1];
-        if (maxm >= (1 << 24) || maxn >= (1 << 24)) return set_err(GSW_EINVAL, "a length is >= 2^24");
+        GSW_TRY(batch_stats(q_off, q_len, t_off, t_len));
+        if (hstat[4]) return set_err(GSW_EINVAL, "a length is outside [0, 2^24) or an offset is negative");
+        maxm = (int)hstat[0];
+        maxn = (int)hstat[1];
         if (flags & GSW_PACKED2) {
             // expand the caller's packed arenas into context scratch
-            unsigned long long ext[2];
-            std::memcpy(ext, hs + 4, sizeof(ext));
+            const unsigned long long ext[2] = {hstat[2], hstat[3]};
             GSW_TRY(ensure(ctx, ctx->io_q, (size_t)std::max<unsigned long long>(ext[0], 1)));
             GSW_TRY(ensure(ctx, ctx->io_t, (size_t)std::max<unsigned long long>(ext[1], 1)));
             CUDA_TRY(launch_unpack2(q, (uint8_t *)ctx->io_q.p, (long long)ext[0], st));

@@ -404,6 +404,10 @@ cudaError_t launch_max_lengths(const int32_t *q_len, const int32_t *t_len, int32
 // largest offset + length of the query and target arenas (letters)
 cudaError_t launch_extents(const int64_t *q_off, const int32_t *q_len, const int64_t *t_off, const int32_t *t_len,
                            int32_t n, unsigned long long *out2, cudaStream_t st);
+// one pass over the pairs: [0, 1] largest lengths, [2, 3] arena extents,
+// [4] nonzero if a length is outside [0, 2^24) or an offset negative
+cudaError_t launch_batch_stats(const int64_t *q_off, const int32_t *q_len, const int64_t *t_off,
+                               const int32_t *t_len, int32_t n, unsigned long long *out5, cudaStream_t st);
 // 2-bit packed DNA letters to one byte per letter
 cudaError_t launch_unpack2(const uint8_t *in, uint8_t *out, long long nletters, cudaStream_t st);
 cudaError_t launch_validate(const BatchView &b, const Scoring &sc, int32_t *bad, cudaStream_t st);

@@ -41,6 +41,39 @@ __global__ void k_validate(BatchView b, int32_t A, int32_t *bad) {
     if (__any_sync(0xFFFFFFFFu, found) && lane == 0) atomicOr(bad, 1);
 }
 
+// Checks and sizes of a batch in one pass: [0] largest query length, [1]
+// largest target length, [2] query arena extent, [3] target arena extent
+// (offset + length, letters), [4] nonzero if a length is outside [0, 2^24)
+// or an offset is negative.
+__global__ void k_batch_stats(const int64_t *q_off, const int32_t *q_len, const int64_t *t_off,
+                              const int32_t *t_len, int32_t n, unsigned long long *out5) {
+    unsigned long long mq = 0, mt = 0, eq = 0, et = 0, bad = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t ql = q_len[i], tl = t_len[i];
+        const int64_t qo = q_off[i], to = t_off[i];
+        bad |= ((uint32_t)ql >= (1u << 24)) | ((uint32_t)tl >= (1u << 24)) | (qo < 0) | (to < 0);
+        mq = max(mq, (unsigned long long)(uint32_t)ql);
+        mt = max(mt, (unsigned long long)(uint32_t)tl);
+        eq = max(eq, (unsigned long long)(qo + ql));
+        et = max(et, (unsigned long long)(to + tl));
+    }
+    mq = __reduce_max_sync(0xFFFFFFFFu, (unsigned)min(mq, 0xFFFFFFFFull));
+    mt = __reduce_max_sync(0xFFFFFFFFu, (unsigned)min(mt, 0xFFFFFFFFull));
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        eq = max(eq, __shfl_xor_sync(0xFFFFFFFFu, eq, d));
+        et = max(et, __shfl_xor_sync(0xFFFFFFFFu, et, d));
+    }
+    bad = __reduce_or_sync(0xFFFFFFFFu, (unsigned)bad);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&out5[0], mq);
+        atomicMax(&out5[1], mt);
+        atomicMax(&out5[2], eq);
+        atomicMax(&out5[3], et);
+        if (bad) atomicOr(&out5[4], 1ull);
+    }
+}
+
 // largest extent (offset + length) of each arena, in letters
 __global__ void k_extents(const int64_t *q_off, const int32_t *q_len, const int64_t *t_off, const int32_t *t_len,
                           int32_t n, unsigned long long *out2) {
@@ -118,6 +151,17 @@ cudaError_t launch_validate(const BatchView &b, const Scoring &sc, int32_t *bad,
         int blocks = (b.npairs * 32 + 255) / 256;
         blocks = blocks > 4096 ? 4096 : blocks;
         k_validate<<<blocks, 256, 0, st>>>(b, sc.A, bad);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_stats(const int64_t *q_off, const int32_t *q_len, const int64_t *t_off,
+                               const int32_t *t_len, int32_t n, unsigned long long *out5, cudaStream_t st) {
+    cudaMemsetAsync(out5, 0, 5 * sizeof(unsigned long long), st);
+    if (n > 0) {
+        int blocks = (n + 255) / 256;
+        blocks = blocks > 1024 ? 1024 : blocks;
+        k_batch_stats<<<blocks, 256, 0, st>>>(q_off, q_len, t_off, t_len, n, out5);
     }
     return cudaGetLastError();
 }
