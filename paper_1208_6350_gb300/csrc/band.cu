@@ -96,7 +96,7 @@ struct BandSeq {
 // none.  !REV: stores decision nibbles per row and returns H(rows, cols).
 template <int W, bool REV, bool DNA>
 __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int A, int O, int X, int target,
-                        typename DirWord<W>::T *dirs, int *out_i, int *out_j, int *final_h) {
+                        typename DirWord<W>::T *dirs, int *out_i, int *out_j, int *final_h, int rstride = 32) {
     int Hp[W], Fp[W];
     int tw[W];  // target letter of each band cell's column in the current row (sliding window)
 #pragma unroll
@@ -215,7 +215,7 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
             // no later row can reach a column <= best_j inside the band
             if (best_j != INT_MAX && i + 1 + dlo >= best_j) break;
         } else {
-            dirs[(long long)i * 32] = dw;
+            dirs[(long long)i * rstride] = dw;
         }
     }
     if constexpr (REV) {
@@ -230,13 +230,14 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
 
 // Walks the decision nibbles from (la, lb) back to (0, 0).  With WRITE the
 // runs go to out[0..nr) in forward order; returns the run count or -1.
-template <int W, bool WRITE>
+// Rows are STRIDE words of the template apart.
+template <int W, bool WRITE, int STRIDE = 32>
 __device__ int band_walk(const typename DirWord<W>::T *dirs, int la, int lb, int dlo, int wb, uint32_t *out, int nr) {
     int i = la, j = lb, state = 0, cur = -1, len = 0, runs = 0, guard = 2 * (la + lb) + 4;
     // the walk moves up at most one row per step: it holds the current row's
     // word and the one above, loaded when the row before it was entered
-    typename DirWord<W>::T word = dirs[(long long)la * 32], above;
-    if (la > 0) above = dirs[(long long)(la - 1) * 32];
+    typename DirWord<W>::T word = dirs[(long long)la * STRIDE], above;
+    if (la > 0) above = dirs[(long long)(la - 1) * STRIDE];
     else zero<W>(above);
     int row = la;
     while ((i > 0 || j > 0) && guard-- > 0) {
@@ -245,7 +246,7 @@ __device__ int band_walk(const typename DirWord<W>::T *dirs, int la, int lb, int
         if (i != row) {
             word = above;
             row = i;
-            if (i > 0) above = dirs[(long long)(i - 1) * 32];
+            if (i > 0) above = dirs[(long long)(i - 1) * STRIDE];
         }
         const uint32_t nib = get_nib<W>(word, k);
         int op;
@@ -298,23 +299,26 @@ struct BandLaunch {
 };
 
 // Banded global DP, walk and CIGAR output of one pair in the narrowest
-// template that holds its band (WT cells per row); the decision words of
-// the warp's lanes are interleaved row by row.
-template <int WT>
+// template that holds its band (WT cells per row).  The decision words of
+// the warp's lanes are interleaved row by row in the class's layout (W cells
+// per lane and row) whatever template each lane takes, so the rows of lanes
+// with different templates never overlap.
+template <int W, int WT>
 __device__ void band_trace(const BatchView &b, const Scoring &sc, gsw_result *rp, const BandSeq &s, int dlo, int wb,
                            int s1, const int8_t *sW, uint32_t *warp_scratch, int lane) {
     using DW = typename DirWord<WT>::T;
-    DW *dirs = reinterpret_cast<DW *>(warp_scratch) + lane;
+    constexpr int RSTRIDE = 32 * (W / WT);  // a row of 32 lanes of W/8 words, in DW units
+    DW *dirs = reinterpret_cast<DW *>(warp_scratch + (size_t)lane * (W / 8));
     const int la = s.rows, lb = s.cols;
     wb = WT;  // the band widened to the template: still exact, no per-cell width test
     int fin = 0, di, dj;
-    if (sc.dna4) band_dp<WT, false, true>(s, dlo, wb, sW, sc.A, sc.O, sc.X, 0, dirs, &di, &dj, &fin);
-    else band_dp<WT, false, false>(s, dlo, wb, sW, sc.A, sc.O, sc.X, 0, dirs, &di, &dj, &fin);
+    if (sc.dna4) band_dp<WT, false, true>(s, dlo, wb, sW, sc.A, sc.O, sc.X, 0, dirs, &di, &dj, &fin, RSTRIDE);
+    else band_dp<WT, false, false>(s, dlo, wb, sW, sc.A, sc.O, sc.X, 0, dirs, &di, &dj, &fin, RSTRIDE);
     if (fin != s1) {
         rp->flags |= kResInternal;
         return;
     }
-    const int nr = band_walk<WT, false>(dirs, la, lb, dlo, wb, nullptr, 0);
+    const int nr = band_walk<WT, false, RSTRIDE>(dirs, la, lb, dlo, wb, nullptr, 0);
     if (nr < 0) {
         rp->flags |= kResInternal;
         return;
@@ -326,7 +330,7 @@ __device__ void band_trace(const BatchView &b, const Scoring &sc, gsw_result *rp
         rp->cigar_off = -1;
         return;
     }
-    band_walk<WT, true>(dirs, la, lb, dlo, wb, b.cigar + off, nr);
+    band_walk<WT, true, RSTRIDE>(dirs, la, lb, dlo, wb, b.cigar + off, nr);
     rp->cigar_len = nr;
     rp->cigar_off = (int64_t)off;
 }
@@ -376,10 +380,10 @@ __device__ void band_pair(const BandLaunch &L, int p, const int8_t *sW, uint32_t
     // the traceback band is usually much narrower than the reverse band that
     // put the pair in this class
     const BandSeq s{qp + bq, 1, la, tp + bt, 1, lb};
-    if (wb <= 8) band_trace<8>(b, sc, rp, s, dlo, wb, s1, sW, warp_scratch, lane);
+    if (wb <= 8) band_trace<W, 8>(b, sc, rp, s, dlo, wb, s1, sW, warp_scratch, lane);
     else if constexpr (W >= 16) {
-        if (wb <= 16) band_trace<16>(b, sc, rp, s, dlo, wb, s1, sW, warp_scratch, lane);
-        else if constexpr (W >= 32) band_trace<32>(b, sc, rp, s, dlo, wb, s1, sW, warp_scratch, lane);
+        if (wb <= 16) band_trace<W, 16>(b, sc, rp, s, dlo, wb, s1, sW, warp_scratch, lane);
+        else if constexpr (W >= 32) band_trace<W, 32>(b, sc, rp, s, dlo, wb, s1, sW, warp_scratch, lane);
     }
 }
 

@@ -507,3 +507,35 @@ def test_reverse_band_edges_in_the_band_kernel(ctx):
     b = _batch(qs, ts, wl.dna_matrix(2, -2), 3, 1, "edge_indels")
     assert b.npairs >= 1 << 14
     compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
+def test_band_kernels_mixed_widths_general_dna_matrix(ctx):
+    # 17,000 pairs with a non-uniform 4x4 matrix (transitions -1, transversions
+    # -3): the one-pair-per-thread band classes, with traceback bands of
+    # several widths in one warp (reads with 0-8 substitutions and 0-2 indels
+    # of 1-6 letters)
+    rng = np.random.default_rng(93)
+    M = np.full((4, 4), -3, np.int8)
+    np.fill_diagonal(M, 2)
+    for a, b_ in ((0, 2), (1, 3)):
+        M[a, b_] = M[b_, a] = -1
+    qs, ts = [], []
+    for p in range(17000):
+        L = int(rng.integers(80, 200))
+        src = rng.integers(0, 4, L).astype(np.uint8)
+        q = src.copy()
+        for _ in range(int(rng.integers(0, 3))):
+            at = int(rng.integers(5, len(q) - 5))
+            k = int(rng.integers(1, 7))
+            q = np.concatenate([q[:at], rng.integers(0, 4, k).astype(np.uint8), q[at:]]) if rng.random() < 0.5 \
+                else np.concatenate([q[:at], q[at + k:]])
+        nsub = int(rng.integers(0, 9))
+        if nsub:
+            pos = rng.integers(0, len(q), nsub)
+            q[pos] = (q[pos] + rng.integers(1, 4, nsub)) % 4
+        t = np.concatenate([rng.integers(0, 4, int(rng.integers(0, 80))), src,
+                            rng.integers(0, 4, int(rng.integers(0, 80)))]).astype(np.uint8)
+        qs.append(q.astype(np.uint8))
+        ts.append(t)
+    b = _batch(qs, ts, M, 4, 1, "mixed_widths_matrix")
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
