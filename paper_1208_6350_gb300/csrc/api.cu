@@ -190,9 +190,9 @@ enum MiscSlot {
     kMiscValid = 3,
     kMiscNeed = 4,   // 2 words: anti-diagonal traceback (direction words, op words per pair)
     kMiscRing = 6,   // 3 words: wide-band traceback (total words, max words of a pair, max op words)
-    kMiscNeed16 = 11,  // 1 word: 16-bit rectangle traceback (direction words per group)
     kMiscStats = 12,   // 5 words: largest lengths, arena extents, bad lengths or offsets
-    kMiscWords = 17
+    kMiscNeed16 = 17,  // 4 words: 16-bit rectangle traceback (direction words per group, per class)
+    kMiscWords = 21
 };
 
 // Side streams and fork/join events of the band classes, created once per
@@ -420,8 +420,8 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
             CUDA_TRY(launch_ring_needs(bv, sc, pb.order, pb.var_start, S.ring_prefix, misc + kMiscRing, st));
             CUDA_TRY(cudaMemsetAsync(S.ring_group, 0, 3 * sizeof(int), st));
             S.launches += 2;
-            CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                                     st));
+            CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscNeed, (kMiscWords - kMiscNeed) * sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, st));
         }
         return GSW_OK;
     };
@@ -429,10 +429,10 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
 
     if (bv.flags & GSW_CIGAR) {
         CUDA_TRY(cudaStreamSynchronize(st));
-        // [0, 1] anti-diagonal, [2, 4] ring, [7] 16-bit rectangle ([5, 6]: extents, unused here)
-        unsigned long long need[8];
+        // [0, 1] anti-diagonal, [2, 4] ring, [13, 16] 16-bit rectangle classes (others unused here)
+        unsigned long long need[kMiscWords - kMiscNeed];
         std::memcpy(need, hs, sizeof(need));
-        need[5] = need[6] = 0;
+        for (int k = 5; k < kMiscNeed16 - kMiscNeed; k++) need[k] = 0;
         std::vector<uint8_t> key2 = key;
         key_add(key2, need);
         for (const DevBuf *d : {&ctx->fill_bnd, &ctx->trace_dirs, &ctx->trace_ops, &ctx->ring_meta})
@@ -456,16 +456,26 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
                 max_dir = (size_t)warps * (size_t)ad_dir;
                 max_ops = (size_t)warps * (size_t)ad_ops;
             }
-            // 16-bit rectangle kernel: 4 groups per warp, direction and op words per group
-            const long long t16_dir = ((long long)need[7] + 3) & ~3LL;  // 16-byte aligned group areas
-            int t16_warps = 0;
-            if (t16_dir > 0) {
+            // 16-bit rectangle kernel: per class, 4 groups per warp, direction
+            // and op words per group (the classes run one after the other)
+            T16Scratch t16{};
+            bool any16 = false;
+            {
                 const size_t have = room(ctx, ctx->trace_dirs, ctx->trace_ops) / 2;
-                const size_t per_warp = 4 * (size_t)(t16_dir + ad_ops) * sizeof(uint32_t);
-                t16_warps = (int)std::min<size_t>((size_t)t16_max_warps(sc, ctx->sms),
-                                                  std::max<size_t>(1, have / per_warp));
-                max_dir = std::max(max_dir, (size_t)t16_warps * 4 * (size_t)t16_dir);
-                max_ops = std::max(max_ops, (size_t)t16_warps * 4 * (size_t)ad_ops);
+                for (int v = 0; v < kTraceT16Classes; v++) {
+                    // 16-byte aligned group areas
+                    const long long dw = ((long long)need[kMiscNeed16 - kMiscNeed + v] + 3) & ~3LL;
+                    if (dw <= 0) continue;
+                    const size_t per_warp = 4 * (size_t)(dw + ad_ops) * sizeof(uint32_t);
+                    const int w = (int)std::min<size_t>((size_t)t16_max_warps(sc, ctx->sms, v),
+                                                        std::max<size_t>(1, have / per_warp));
+                    if (w <= 0) continue;
+                    t16.dir_words[v] = dw;
+                    t16.warps[v] = w;
+                    max_dir = std::max(max_dir, (size_t)w * 4 * (size_t)dw);
+                    max_ops = std::max(max_ops, (size_t)w * 4 * (size_t)ad_ops);
+                    any16 = true;
+                }
             }
             // wide bands: the pool of direction words, groups of pairs that fit it
             const unsigned long long ring_total = need[2], ring_max = need[3], ring_ops = need[4];
@@ -484,17 +494,15 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
             if (max_dir > 0) {
                 GSW_TRY(ensure2(ctx, ctx->trace_dirs, max_dir * sizeof(uint32_t), ctx->trace_ops,
                                 max_ops * sizeof(uint32_t)));
-                if (t16_warps > 0) {
-                    T16Scratch t;
-                    t.dirs = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
-                    t.dir_words = t16_dir;
-                    t.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
-                    t.op_words = ad_ops;
-                    t.order = pb.order;
-                    t.var_start = pb.var_start;
-                    t.head = pb.head;
-                    CUDA_TRY(launch_trace16(bv, sc, t, t16_warps, ctx->sms, st));
-                    S.launches += sc.dna4 ? 4 : 2;
+                if (any16) {
+                    t16.dirs = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
+                    t16.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
+                    t16.op_words = ad_ops;
+                    t16.order = pb.order;
+                    t16.var_start = pb.var_start;
+                    t16.head = pb.head;
+                    CUDA_TRY(launch_trace16(bv, sc, t16, ctx->sms, st));
+                    for (int v = 0; v < kTraceT16Classes; v++) S.launches += t16.warps[v] > 0 ? 1 : 0;
                 }
                 if (ad_grid > 0) {
                     TraceScratch ts;

@@ -257,6 +257,10 @@ constexpr int kTraceT16Classes = 4;
 constexpr int kT16P = 8;                   // lanes per pair
 constexpr int kT16MaxCols = 4096;          // longest target region of the 16-bit kernel
 constexpr long long kT16MaxWords = 1 << 17;  // scratch words of one pair (512 KB)
+// general alphabets: regions over kT16MaxWords in 64-row strips take the
+// 128-row class with this allowance (its own launch and scratch, so the few
+// large pairs do not shrink the groups of the others)
+constexpr long long kT16MaxWordsBig = 1 << 20;
 __host__ __device__ inline int t16_R(int v) { return 4 * (v + 1); }
 __host__ __device__ inline int t16_strip_rows(int v) { return 2 * kT16P * t16_R(v); }
 __host__ __device__ inline int t16_strips(int la, int v) { return (la + t16_strip_rows(v) - 1) / t16_strip_rows(v); }
@@ -283,7 +287,12 @@ __host__ __device__ inline int trace_class(int la, int lb, int score1, const Sco
         // (128 measured 2.5 % slower on protein search: a third of the warps per SM)
         const int vmax = sc.dna4 ? kTraceT16Classes - 1 : GSW_T16_GEN_VMAX;
         const int v0 = (la - 1) / 64;
-        const int v = v0 < vmax ? v0 : vmax;
+        int v = v0 < vmax ? v0 : vmax;
+        long long cap = kT16MaxWords;
+        if (!sc.dna4 && v == 0 && t16_need_words(la, lb, 0) > kT16MaxWords) {
+            v = 1;
+            cap = kT16MaxWordsBig;
+        }
         const long long rows = (long long)t16_strips(la, v) * t16_strip_rows(v);
         const long long cols = lb + 2 * kT16P;
         // every value of the DP over the padded rectangle lies in
@@ -291,12 +300,14 @@ __host__ __device__ inline int trace_class(int la, int lb, int score1, const Sco
         // it must fit a biased 16-bit lane
         const long long lo = 3LL * sc.O + (long long)sc.X * (rows + cols + 2) - (sc.wmin < 0 ? sc.wmin : 0);
         const long long hi = (long long)sc.wmax * ((cols < rows ? cols : rows) + 1);
-        if (lo <= 30000 && hi <= 30000 && t16_need_words(la, lb, v) <= kT16MaxWords) {
+        if (lo <= 30000 && hi <= 30000 && t16_need_words(la, lb, v) <= cap) {
             // cell updates: the padded rectangle against the band's
             // anti-diagonal slots; a 16-bit pair of cells costs about the
             // instructions of one 32-bit anti-diagonal cell
+            // (bands wider than 512 diagonals: the rectangle always)
             const long long rect = rows * t16_steps(lb);
-            const long long band = ad < kTraceRingClass ? (32LL << ad) * (la + lb + 1) : (1LL << 62);
+            if (ad == kTraceRingClass) return kTraceT16First + v;
+            const long long band = (32LL << ad) * (la + lb + 1);
             if (rect <= (small ? 2 : 3) * band) return kTraceT16First + v;
         }
     }
@@ -363,27 +374,29 @@ struct TraceScratch {
 };
 int trace_block_threads();
 // largest needs of a pair: [0] direction words of the anti-diagonal classes,
-// [1] op words of the warp classes; need16: direction words of the 16-bit classes
+// [1] op words of the warp classes; need16[v]: direction words of 16-bit class v
 cudaError_t launch_trace_need(const BatchView &b, const Scoring &sc, unsigned long long *max_need,
                               unsigned long long *need16, cudaStream_t st);
 cudaError_t launch_trace_ad(const BatchView &b, const Scoring &sc, const TraceScratch &ts, int grid,
                             cudaStream_t st);
 
-// 16-bit full-rectangle traceback (trace16.cu): per group of 8 lanes
-// dir_words direction words and op_words op words
+// 16-bit full-rectangle traceback (trace16.cu): per class v (strips of
+// 64(v+1) rows) and group of 8 lanes, dir_words[v] direction words (0: no
+// pairs) and op_words op words; the classes run one after the other on the
+// stream and share the buffers
 struct T16Scratch {
     uint32_t *dirs;
-    int64_t dir_words;  // per group
+    int64_t dir_words[kTraceT16Classes];  // per group
     uint32_t *ops;
     int64_t op_words;   // per group
     const int32_t *order;
     const int32_t *var_start;
     int32_t *head;      // per-class task counters (zeroed by the plan)
+    int warps[kTraceT16Classes];  // warps of each class's launch (the scratch holds 4 groups each)
 };
-// most warps any of the launches keeps resident (4 groups each)
-int t16_max_warps(const Scoring &sc, int sms);
-cudaError_t launch_trace16(const BatchView &b, const Scoring &sc, const T16Scratch &ts, int max_warps, int sms,
-                           cudaStream_t st);
+// warps of class v's launch that can be resident
+int t16_max_warps(const Scoring &sc, int sms, int v);
+cudaError_t launch_trace16(const BatchView &b, const Scoring &sc, const T16Scratch &ts, int sms, cudaStream_t st);
 
 int band_block_threads();
 // Grids and scratch of the three band classes (widths 8, 16, 32), each

@@ -408,10 +408,11 @@ __global__ void __launch_bounds__(kT16Block) k_trace16(BatchView b, Scoring sc, 
     const int tile_steps = pwords / (R / 4);
     const int gwarp = blockIdx.x * (kT16Block / 32) + warp;
     const size_t gid = (size_t)gwarp * (32 / kP) + g;
-    uint32_t *dirs = ts.dirs + gid * ts.dir_words;
+    const int v = cls - kTraceT16First;
+    const int64_t dir_words = ts.dir_words[v];
+    uint32_t *dirs = ts.dirs + gid * dir_words;
     uint32_t *ops = ts.ops + gid * ts.op_words;
     const int first = ts.var_start[cls], last = ts.var_start[cls + 1];
-    const int v = cls - kTraceT16First;
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(&ts.head[cls], 1);
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(kT16Block) k_trace16(BatchView b, Scoring sc, 
             lb = rr.ref_end1 - tb + 1;
             const bool fits = score1 > 0 && (flags & kResPendingTrace) && !(flags & kResInternal) && qb >= 0 &&
                               tb >= 0 && la >= 1 && lb >= 1 && lb <= kT16MaxCols &&
-                              t16_need_words(la, lb, v) <= ts.dir_words && (long long)la + lb + 2 <= ts.op_words;
+                              t16_need_words(la, lb, v) <= dir_words && (long long)la + lb + 2 <= ts.op_words;
             if (!fits) {
                 if (k == 0 && score1 > 0 && (flags & kResPendingTrace)) b.res[p].flags |= kResInternal;
                 p = -1;
@@ -508,39 +509,45 @@ int t16_blocks(const Scoring &sc) {
 }
 
 template <int R, bool DNA>
-cudaError_t t16_launch(const BatchView &b, const Scoring &sc, const T16Scratch &ts, int max_warps, int sms,
-                       int cls, cudaStream_t st) {
+cudaError_t t16_launch(const BatchView &b, const Scoring &sc, const T16Scratch &ts, int sms, int cls,
+                       cudaStream_t st) {
+    const int v = cls - kTraceT16First;
+    if (ts.dir_words[v] <= 0 || ts.warps[v] <= 0) return cudaSuccess;  // no pairs of the class
     const int per_sm = t16_blocks<R, DNA>(sc);
     if (per_sm <= 0) return cudaErrorInvalidConfiguration;
-    const int grid = std::max(1, std::min(sms * per_sm, max_warps / (kT16Block / 32)));
+    const int grid = std::max(1, std::min(sms * per_sm, ts.warps[v] / (kT16Block / 32)));
     k_trace16<R, DNA><<<grid, kT16Block, t16_smem_bytes<R, DNA>(sc), st>>>(b, sc, ts, cls);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-int t16_max_warps(const Scoring &sc, int sms) {
-    int per_sm;
-    if (sc.dna4)
-        per_sm = std::max(std::max(t16_blocks<4, true>(sc), t16_blocks<8, true>(sc)),
-                          std::max(t16_blocks<12, true>(sc), t16_blocks<16, true>(sc)));
-    else
-        per_sm = std::max(t16_blocks<4, false>(sc), t16_blocks<8, false>(sc));
-    return std::max(1, sms * per_sm) * (kT16Block / 32);
+int t16_max_warps(const Scoring &sc, int sms, int v) {
+    int per_sm = 0;
+    if (sc.dna4) {
+        switch (v) {
+        case 0: per_sm = t16_blocks<4, true>(sc); break;
+        case 1: per_sm = t16_blocks<8, true>(sc); break;
+        case 2: per_sm = t16_blocks<12, true>(sc); break;
+        default: per_sm = t16_blocks<16, true>(sc); break;
+        }
+    } else if (v <= 1) {
+        per_sm = v == 0 ? t16_blocks<4, false>(sc) : t16_blocks<8, false>(sc);
+    }
+    return std::max(0, sms * per_sm) * (kT16Block / 32);
 }
 
-cudaError_t launch_trace16(const BatchView &b, const Scoring &sc, const T16Scratch &ts, int max_warps, int sms,
-                           cudaStream_t st) {
+cudaError_t launch_trace16(const BatchView &b, const Scoring &sc, const T16Scratch &ts, int sms, cudaStream_t st) {
     cudaError_t e;
     const int c0 = kTraceT16First;
     if (sc.dna4) {
-        if ((e = t16_launch<16, true>(b, sc, ts, max_warps, sms, c0 + 3, st))) return e;
-        if ((e = t16_launch<12, true>(b, sc, ts, max_warps, sms, c0 + 2, st))) return e;
-        if ((e = t16_launch<8, true>(b, sc, ts, max_warps, sms, c0 + 1, st))) return e;
-        if ((e = t16_launch<4, true>(b, sc, ts, max_warps, sms, c0, st))) return e;
+        if ((e = t16_launch<16, true>(b, sc, ts, sms, c0 + 3, st))) return e;
+        if ((e = t16_launch<12, true>(b, sc, ts, sms, c0 + 2, st))) return e;
+        if ((e = t16_launch<8, true>(b, sc, ts, sms, c0 + 1, st))) return e;
+        if ((e = t16_launch<4, true>(b, sc, ts, sms, c0, st))) return e;
     } else {
-        if ((e = t16_launch<8, false>(b, sc, ts, max_warps, sms, c0 + 1, st))) return e;
-        if ((e = t16_launch<4, false>(b, sc, ts, max_warps, sms, c0, st))) return e;
+        if ((e = t16_launch<8, false>(b, sc, ts, sms, c0 + 1, st))) return e;
+        if ((e = t16_launch<4, false>(b, sc, ts, sms, c0, st))) return e;
     }
     return cudaSuccess;
 }

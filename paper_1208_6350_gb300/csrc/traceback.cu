@@ -43,10 +43,10 @@ __device__ __forceinline__ bool wants_trace(const gsw_result &r) {
 
 // Largest needs of a pair of the warp classes: [0] direction words of the
 // anti-diagonal classes, [1] op words (anti-diagonal and 16-bit classes);
-// need16: direction words of the 16-bit classes (per group of 8 lanes).
+// need16[v]: direction words of 16-bit class v (per group of 8 lanes).
 __global__ void k_trace_need(BatchView b, Scoring sc, unsigned long long *max_need, unsigned long long *need16) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned v[3] = {0, 0, 0};
+    unsigned v[2 + kTraceT16Classes] = {};
     if (p < b.npairs) {
         const gsw_result r = b.res[p];
         if (wants_trace(r)) {
@@ -57,15 +57,16 @@ __global__ void k_trace_need(BatchView b, Scoring sc, unsigned long long *max_ne
                 v[0] = (unsigned)min(ad_dir_words(la, lb, 1 << cls), (long long)UINT_MAX);
                 v[1] = (unsigned)min((long long)la + lb + 2, (long long)UINT_MAX);
             } else if (cls >= kTraceT16First) {
-                v[2] = (unsigned)min(t16_need_words(la, lb, cls - kTraceT16First), (long long)UINT_MAX);
+                v[2 + cls - kTraceT16First] =
+                    (unsigned)min(t16_need_words(la, lb, cls - kTraceT16First), (long long)UINT_MAX);
                 v[1] = (unsigned)min((long long)la + lb + 2, (long long)UINT_MAX);
             }
         }
     }
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
+    for (int k = 0; k < 2 + kTraceT16Classes; k++) {
         const unsigned m = __reduce_max_sync(0xFFFFFFFFu, v[k]);
-        if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(k < 2 ? &max_need[k] : need16, (unsigned long long)m);
+        if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(k < 2 ? &max_need[k] : &need16[k - 2], (unsigned long long)m);
     }
 }
 
@@ -278,7 +279,7 @@ int trace_block_threads() { return kTBlock; }
 cudaError_t launch_trace_need(const BatchView &b, const Scoring &sc, unsigned long long *max_need,
                               unsigned long long *need16, cudaStream_t st) {
     cudaMemsetAsync(max_need, 0, 2 * sizeof(unsigned long long), st);
-    cudaMemsetAsync(need16, 0, sizeof(unsigned long long), st);
+    cudaMemsetAsync(need16, 0, kTraceT16Classes * sizeof(unsigned long long), st);
     const int nb = (b.npairs + 255) / 256;
     if (nb > 0) k_trace_need<<<nb, 256, 0, st>>>(b, sc, max_need, need16);
     return cudaGetLastError();

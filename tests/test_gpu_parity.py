@@ -539,3 +539,17 @@ def test_band_kernels_mixed_widths_general_dna_matrix(ctx):
         ts.append(t)
     b = _batch(qs, ts, M, 4, 1, "mixed_widths_matrix")
     compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
+def test_rect16_traceback_large_regions_general_alphabet(ctx):
+    # regions over a million cells (here 1,100-1,500 letters a side) exceed the
+    # 64-row classes' per-pair words and take the 128-row class with its
+    # larger allowance, in a launch of their own
+    rng = np.random.default_rng(95)
+    A = 20
+    M = rng.integers(-4, 3, (A, A))
+    M = ((M + M.T) // 2).astype(np.int8)
+    np.fill_diagonal(M, rng.integers(4, 12, A))
+    qs, ts = _weak_pairs(rng, [1100, 1300, 1500, 120, 300], ident=0.6, A=A, flank=(0, 40))
+    b = _batch(qs, ts, M, 11, 1, "weak_protein_large", alphabet="ARNDCQEGHILKMFPSTWYV")
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
