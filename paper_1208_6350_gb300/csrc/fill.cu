@@ -82,6 +82,8 @@ namespace {
 constexpr int kBlock = 128;
 constexpr int kUnrollFast = GSW_FILL_UNROLL_FAST;
 constexpr int kUnrollGen = GSW_FILL_UNROLL_GEN;
+// forms of the strip step (StripRunner::step)
+constexpr int kModeGen = 0, kModeFast = 1, kModeFwdFirst = 2, kModeFwdLater = 3;
 
 // ---------------------------------------------------------------- lanes
 struct L16 {
@@ -397,11 +399,15 @@ struct StripRunner {
     // One step of lane k: low half at column s - k, high half P columns
     // behind.  CHECKED steps handle columns outside [0, n) (start-up and
     // drain of the wavefront); steady steps have every column in range.
-    // FAST steps are those of a forward fill of one strip with a max array
-    // (no boundary rows, no reverse stop).  Returns true when the reverse
-    // fill found its target column.
-    template <bool CHECKED, bool FAST = false>
+    // MODE: kModeGen decides everything at run time; the other modes are the
+    // steady steps of forward fills with a max array (no reverse stop):
+    // kModeFast one strip (no boundary rows), kModeFwdFirst the first of
+    // several strips (boundary row out), kModeFwdLater a later strip
+    // (boundary row in, the max array merged with the strips above).
+    // Returns true when the reverse fill found its target column.
+    template <bool CHECKED, int MODE = kModeGen>
     __device__ __forceinline__ bool step(const int s) {
+        constexpr bool FAST = MODE == kModeFast;
         const int jlo = s - k;
         const int jhi = L::FOLD ? jlo - P : jlo;
         uint32_t hin, fin, cmin;
@@ -412,7 +418,7 @@ struct StripRunner {
         fin = xf * mulh + bzf;
         cmin = xc * mulh + bzc;
         cm_t cm_prev{};
-        if (!FAST && st > 0) {
+        if (MODE == kModeGen ? st > 0 : MODE == kModeFwdLater) {
             const int bi = s & (P - 1);
             if (bi == 0) {
                 b_cur = b_nxt;
@@ -536,7 +542,17 @@ struct StripRunner {
         if (FAST && k == P - 1) {
             if constexpr (L::FOLD) cms[jhi] = (uint16_t)L::cm16(m >> 16);
             else cms[jhi] = (int)m;
-        } else if (!FAST && k == P - 1 && (!CHECKED || (jhi >= 0 && jhi < n))) {
+        } else if ((MODE == kModeFwdFirst || MODE == kModeFwdLater) && k == P - 1) {
+            // (steady: jhi is in range)
+            if constexpr (L::FOLD) {
+                const uint32_t c = L::cm16(m >> 16);
+                cms[jhi] = (uint16_t)(MODE == kModeFwdFirst ? c : max((uint32_t)cm_prev, c));
+                if (MODE == kModeFwdFirst || !last_strip) bout[jhi] = (H[R - 1] >> 16) | (f & 0xFFFF0000u);
+            } else {
+                cms[jhi] = MODE == kModeFwdFirst ? (int)m : max((int)cm_prev, (int)m);
+                if (MODE == kModeFwdFirst || !last_strip) bout[jhi] = make_int2((int)H[R - 1], (int)f);
+            }
+        } else if (MODE == kModeGen && k == P - 1 && (!CHECKED || (jhi >= 0 && jhi < n))) {
             if constexpr (L::FOLD) {
                 const uint32_t full = m >> 16;
                 if (has_cms) {
@@ -559,7 +575,7 @@ struct StripRunner {
         // the target.  Every column up to it is complete in every strip (the
         // earlier strips are ahead), so the first column holding the maximum
         // is at or before it and the strip trackers hold it.
-        if (!FAST && job.stop_u && last_strip && __any_sync(gmask, found)) return true;
+        if (MODE == kModeGen && job.stop_u && last_strip && __any_sync(gmask, found)) return true;
         xh = __shfl_sync(gmask, H[R - 1], src);
         xf = __shfl_sync(gmask, f, src);
         xc = __shfl_sync(gmask, m, src);
@@ -569,8 +585,11 @@ struct StripRunner {
     // Steps [s0, s1) of the current strip: start-up (checked), steady
     // (unchecked), drain (checked).  Returns true on an early stop.  With
     // MAYBE_FAST the steady steps of a one-strip forward fill take the FAST
-    // form (the CTA kernel's strips never do).
-    template <bool MAYBE_FAST = true>
+    // form (the CTA kernel's strips never do).  With MAYBE_MULTI the strips of
+    // a forward fill of several strips take the kModeFwdFirst/Later forms;
+    // the 8-lane variants (one-strip short reads, whose registers the extra
+    // loops would crowd) keep the general step for them.
+    template <bool MAYBE_FAST = true, bool MAYBE_MULTI = (P != 8)>
     __device__ bool run(int s0, int s1) {
         const int s_steady = L::FOLD ? 2 * P - 1 : P - 1;
         const int s_drain = max(s_steady, n - 1);
@@ -579,9 +598,16 @@ struct StripRunner {
 #pragma unroll 1
         for (; s < s1 && s < s_steady; s++)
             if (step<true>(s)) return true;
-        if (MAYBE_FAST && st == 0 && last_strip && !job.stop_u && has_cms && job.ts == 1) {
+        const bool fwd = !job.stop_u && has_cms;
+        if (MAYBE_FAST && st == 0 && last_strip && fwd && job.ts == 1) {
 #pragma unroll kUnrollFast
-            for (; s < s1 && s < s_drain; s++) step<false, true>(s);
+            for (; s < s1 && s < s_drain; s++) step<false, kModeFast>(s);
+        } else if (MAYBE_MULTI && fwd && st == 0 && !last_strip) {
+#pragma unroll kUnrollGen
+            for (; s < s1 && s < s_drain; s++) step<false, kModeFwdFirst>(s);
+        } else if (MAYBE_MULTI && fwd && st > 0) {
+#pragma unroll kUnrollGen
+            for (; s < s1 && s < s_drain; s++) step<false, kModeFwdLater>(s);
         } else {
 #pragma unroll kUnrollGen
             for (; s < s1 && s < s_drain; s++)
