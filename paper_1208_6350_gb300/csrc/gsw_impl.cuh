@@ -416,11 +416,6 @@ cudaError_t launch_band(const BatchView &b, const Scoring &sc, const PlanBuffers
                         const BandGrids &g, cudaStream_t st, const BandStreams &aux);
 
 // small helpers (misc.cu)
-cudaError_t launch_max_lengths(const int32_t *q_len, const int32_t *t_len, int32_t n, int32_t *out2,
-                               cudaStream_t st);
-// largest offset + length of the query and target arenas (letters)
-cudaError_t launch_extents(const int64_t *q_off, const int32_t *q_len, const int64_t *t_off, const int32_t *t_len,
-                           int32_t n, unsigned long long *out2, cudaStream_t st);
 // one pass over the pairs: [0, 1] largest lengths, [2, 3] arena extents,
 // [4] nonzero if a length is outside [0, 2^24) or an offset negative
 cudaError_t launch_batch_stats(const int64_t *q_off, const int32_t *q_len, const int64_t *t_off,

@@ -4,20 +4,6 @@
 namespace gsw {
 namespace {
 
-__global__ void k_max_lengths(const int32_t *q_len, const int32_t *t_len, int32_t n, int32_t *out2) {
-    int mq = 0, mt = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        mq = max(mq, q_len[i]);
-        mt = max(mt, t_len[i]);
-    }
-    mq = __reduce_max_sync(0xFFFFFFFFu, mq);
-    mt = __reduce_max_sync(0xFFFFFFFFu, mt);
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(&out2[0], mq);
-        atomicMax(&out2[1], mt);
-    }
-}
-
 __global__ void k_fill_const(int32_t *dst, int32_t v, int32_t n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = v;
 }
@@ -74,32 +60,6 @@ __global__ void k_batch_stats(const int64_t *q_off, const int32_t *q_len, const 
     }
 }
 
-// largest extent (offset + length) of each arena, in letters
-__global__ void k_extents(const int64_t *q_off, const int32_t *q_len, const int64_t *t_off, const int32_t *t_len,
-                          int32_t n, unsigned long long *out2) {
-    unsigned long long eq = 0, et = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        eq = max(eq, (unsigned long long)(q_off[i] + q_len[i]));
-        et = max(et, (unsigned long long)(t_off[i] + t_len[i]));
-    }
-    eq = max(eq, __shfl_xor_sync(0xFFFFFFFFu, eq, 16));
-    eq = max(eq, __shfl_xor_sync(0xFFFFFFFFu, eq, 8));
-    eq = max(eq, __shfl_xor_sync(0xFFFFFFFFu, eq, 4));
-    eq = max(eq, __shfl_xor_sync(0xFFFFFFFFu, eq, 2));
-    eq = max(eq, __shfl_xor_sync(0xFFFFFFFFu, eq, 1));
-    et = max(et, __shfl_xor_sync(0xFFFFFFFFu, et, 16));
-    et = max(et, __shfl_xor_sync(0xFFFFFFFFu, et, 8));
-    et = max(et, __shfl_xor_sync(0xFFFFFFFFu, et, 4));
-    et = max(et, __shfl_xor_sync(0xFFFFFFFFu, et, 2));
-    et = max(et, __shfl_xor_sync(0xFFFFFFFFu, et, 1));
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(&out2[0], eq);
-        atomicMax(&out2[1], et);
-    }
-}
-
-// 2-bit packed letters to one byte each: a thread expands 16 letters (4 bytes
-// in, one 16-byte store out)
 __global__ void k_unpack2(const uint8_t *in, uint8_t *out, long long nletters) {
     const long long groups = (nletters + 15) / 16;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < groups;
@@ -126,17 +86,6 @@ __global__ void k_unpack2(const uint8_t *in, uint8_t *out, long long nletters) {
 
 }  // namespace
 
-cudaError_t launch_extents(const int64_t *q_off, const int32_t *q_len, const int64_t *t_off, const int32_t *t_len,
-                           int32_t n, unsigned long long *out2, cudaStream_t st) {
-    cudaMemsetAsync(out2, 0, 2 * sizeof(unsigned long long), st);
-    if (n > 0) {
-        int blocks = (n + 255) / 256;
-        blocks = blocks > 1024 ? 1024 : blocks;
-        k_extents<<<blocks, 256, 0, st>>>(q_off, q_len, t_off, t_len, n, out2);
-    }
-    return cudaGetLastError();
-}
-
 cudaError_t launch_unpack2(const uint8_t *in, uint8_t *out, long long nletters, cudaStream_t st) {
     if (nletters > 0) {
         long long blocks = ((nletters + 15) / 16 + 255) / 256;
@@ -162,17 +111,6 @@ cudaError_t launch_batch_stats(const int64_t *q_off, const int32_t *q_len, const
         int blocks = (n + 255) / 256;
         blocks = blocks > 1024 ? 1024 : blocks;
         k_batch_stats<<<blocks, 256, 0, st>>>(q_off, q_len, t_off, t_len, n, out5);
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_max_lengths(const int32_t *q_len, const int32_t *t_len, int32_t n, int32_t *out2,
-                               cudaStream_t st) {
-    cudaMemsetAsync(out2, 0, 2 * sizeof(int32_t), st);
-    if (n > 0) {
-        int blocks = (n + 255) / 256;
-        blocks = blocks > 1024 ? 1024 : blocks;
-        k_max_lengths<<<blocks, 256, 0, st>>>(q_len, t_len, n, out2);
     }
     return cudaGetLastError();
 }
