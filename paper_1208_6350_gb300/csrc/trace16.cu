@@ -1,16 +1,15 @@
-// Traceback of pairs with wide bands and short regions in 16-bit lanes: the
-// global Gotoh DP between begin and end ("Algorithm and implementation", item
-// (1): the banded SW whose band the begin and end define yields the CIGAR),
-// computed over the whole rectangle q[begin..end] x t[begin..end] of at most
-// 256 query rows.
+// Traceback of pairs with wide bands in 16-bit lanes: the global Gotoh DP
+// between begin and end ("Algorithm and implementation", item (1): the banded
+// SW whose band the begin and end define yields the CIGAR), computed over the
+// whole rectangle q[begin..end] x t[begin..end], strip after strip of 64 to
+// 256 query rows, when every value of it fits a biased 16-bit lane.
 //
 // The rectangle contains every band, and the traceback over it is the
 // oracle's own definition (the full-rectangle DP), so the CIGAR is the
-// canonical one.  For random local alignments (bands of 100-500 diagonals
-// over regions of 50-250 rows) the provable band covers most of the
-// rectangle anyway; the rectangle in the folded ring of the fill (fill.cu)
-// costs about a quarter of the instructions per cell of the 32-bit
-// anti-diagonal kernel.
+// canonical one.  For random local alignments (bands of hundreds of
+// diagonals) the provable band covers most of the rectangle anyway; the
+// rectangle in the folded ring of the fill (fill.cu) costs about a quarter of
+// the instructions per cell of the 32-bit anti-diagonal kernel.
 //
 // Layout: a group of 8 lanes per pair; lane k holds R 32-bit words, word r
 // packing row k*R + r (bits 0-15) and row S + k*R + r (bits 16-31), S = 8R,
@@ -19,7 +18,10 @@
 // the ring by a shuffle, lane 7's low half wrapping to lane 0's high half.
 // Boundaries are those of the oracle's recurrences with H(0,0) = 0 and -inf
 // outside: H(0,j) = -(O + (j-1)X), H(i,0) = -(O + (i-1)X), E(i,1) = H(i,0) - O,
-// F(1,j) = H(0,j) - O.
+// F(1,j) = H(0,j) - O.  A region taller than a strip runs strip after strip:
+// lane 7's high half (the strip's last row) leaves H and F(next row) per
+// column in a ping-pong buffer, which the next strip's lane 0 reads in place
+// of the top boundary, one block of 8 columns ahead.
 //
 // Per cell (i, j) 4 bits: bit 0 H != H(i-1,j-1) + W; bit 1 H != E(i,j);
 // bit 2 E(i,j+1) != H(i,j) - O (the horizontal gap through (i,j+1) extends
