@@ -247,7 +247,9 @@ __host__ __device__ inline int band_range(int la, int lb, int score1, const Scor
 // most 64/128/256/512 diagonals), 4 the CTA strip kernel (wider bands), 5-8
 // the 16-bit full-rectangle kernel with strips of 64/128/192/256 query rows
 // (8 lanes x R = 4/8/12/16 words x 2 halves; regions taller than the class's
-// strip run several strips: 256-row strips for DNA, 128 for other alphabets).
+// strip run several strips: 256-row strips for DNA; other alphabets 64-row
+// strips, and 128-row ones with a larger scratch allowance for regions whose
+// decisions exceed kT16MaxWords in 64-row strips).
 #ifndef GSW_T16_GEN_VMAX
 #define GSW_T16_GEN_VMAX 0
 #endif
