@@ -61,7 +61,7 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
         if (r.score1 <= 0 || (r.flags & kResInternal)) { keys[p] = -1; return; }
         rows = r.read_end1 + 1;
         const int wrev = reverse_band_width(r.read_end1, r.score1, sc);
-        if (!small_batch(b) && wrev >= 0 && wrev <= kBandMaxWidth && rows <= kBandMaxRows) {
+        if (!small_batch(b) && wrev >= 0 && wrev <= kBandMaxRevWidth && rows <= kBandMaxRows) {
             keys[p] = -1;
             return;
         }
@@ -103,7 +103,7 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
             const int wrev = reverse_band_width(r.read_end1, r.score1, sc);
             rows = r.read_end1 + 1;
             width = wrev < 0 ? INT_MAX : wrev;
-            if (width > kBandMaxWidth || rows > kBandMaxRows) {
+            if (width > kBandMaxRevWidth || rows > kBandMaxRows) {
                 b.res[p].flags |= kResInternal;  // the ring reverse should have taken it
                 keys[p] = -1;
                 return;
