@@ -1,0 +1,305 @@
+"""CPU checks of the library's host-side geometry rules, compiled from the
+library's own header with g++ (tests/host_rules_shim.cpp):
+
+* the reversed fill's window and its band [-Gn, G] (gap letters bounded by the
+  score; the reversed pass for the begin, "Algorithm and implementation") hold
+  every optimal path the oracle reports, and are exact on closed-form gapped
+  pairs;
+* the traceback band [dlo, dhi] (the banded global alignment between begin and
+  end, same section) holds the oracle's CIGAR path, and is exact on the same
+  pairs;
+* the traceback class routing: widths map to the anti-diagonal classes, bands
+  wider than 512 diagonals go to the 16-bit rectangle whenever its values and
+  scratch fit (never to the ring kernel then), and the rectangle is never
+  chosen for values or regions it cannot hold.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+T16_FIRST, RING = 5, 4
+
+
+def _cuda_include():
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
+    if not os.path.exists(os.path.join(inc, "cuda_runtime.h")):
+        pytest.skip("cuda_runtime.h not found")
+    return inc
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not found")
+    out = str(tmp_path_factory.mktemp("host_rules") / "libhostrules.so")
+    subprocess.run([gxx, "-std=c++17", "-O1", "-shared", "-fPIC", "-w",
+                    "-I", os.path.join(ROOT, "include"),
+                    "-I", os.path.join(ROOT, "paper_1208_6350_gb300", "csrc"),
+                    "-I", _cuda_include(),
+                    os.path.join(HERE, "host_rules_shim.cpp"), "-o", out], check=True)
+    L = ctypes.CDLL(out)
+    P = ctypes.c_void_p
+    i32 = ctypes.c_int
+    ip = ctypes.POINTER(ctypes.c_int)
+    for name, args in (("hr_reverse_window", [i32, P, i32, i32, i32, i32, i32]),
+                       ("hr_reverse_gap_bound", [i32, P, i32, i32, i32, i32]),
+                       ("hr_reverse_gap_bound_rows", [i32, P, i32, i32, i32, i32]),
+                       ("hr_band_range", [i32, P, i32, i32, i32, i32, i32, ip, ip]),
+                       ("hr_trace_class", [i32, P, i32, i32, i32, i32, i32, i32, ip, ip])):
+        getattr(L, name).argtypes = args
+        getattr(L, name).restype = i32
+    L.hr_t16_need_words.argtypes = [i32, i32, i32]
+    L.hr_t16_need_words.restype = ctypes.c_longlong
+    return L
+
+
+class Rules:
+    """The rules for one scoring scheme (W is A x A int8, row = query letter)."""
+
+    def __init__(self, L, W, O, X):
+        self.L, self.O, self.X = L, O, X
+        self.W = np.ascontiguousarray(W, dtype=np.int8)
+        self.A = self.W.shape[0]
+        self.p = self.W.ctypes.data_as(ctypes.c_void_p)
+
+    def window(self, eq, et, s1):
+        return self.L.hr_reverse_window(self.A, self.p, self.O, self.X, eq, et, s1)
+
+    def G(self, eq, s1):
+        return self.L.hr_reverse_gap_bound(self.A, self.p, self.O, self.X, eq, s1)
+
+    def Gn(self, eq, s1):
+        return self.L.hr_reverse_gap_bound_rows(self.A, self.p, self.O, self.X, eq, s1)
+
+    def band(self, la, lb, s1):
+        lo, hi = ctypes.c_int(), ctypes.c_int()
+        self.L.hr_band_range(self.A, self.p, self.O, self.X, la, lb, s1, ctypes.byref(lo), ctypes.byref(hi))
+        return lo.value, hi.value
+
+    def trace_class(self, la, lb, s1, small=False):
+        lo, hi = ctypes.c_int(), ctypes.c_int()
+        c = self.L.hr_trace_class(self.A, self.p, self.O, self.X, la, lb, s1, int(small),
+                                  ctypes.byref(lo), ctypes.byref(hi))
+        return c, hi.value - lo.value + 1
+
+
+def dna(match, mismatch, A=4):
+    W = np.full((A, A), mismatch, dtype=np.int8)
+    np.fill_diagonal(W, match)
+    return W
+
+
+def protein_like(rng, A=20):
+    W = rng.integers(-4, 4, (A, A))
+    W = np.triu(W) + np.triu(W, 1).T
+    np.fill_diagonal(W, rng.integers(4, 12, A))
+    return W.astype(np.int8)
+
+
+def mutate(rng, s, A, sub, indel, max_run=6):
+    out = []
+    i = 0
+    while i < len(s):
+        r = rng.random()
+        if r < indel / 2:
+            out.extend(rng.integers(0, A, int(rng.integers(1, max_run + 1))).tolist())
+        elif r < indel:
+            i += int(rng.integers(1, max_run + 1))
+            continue
+        out.append(int(rng.integers(0, A)) if rng.random() < sub else int(s[i]))
+        i += 1
+    return np.array(out if out else [0], dtype=np.uint8)
+
+
+def path_diagonals(cigar):
+    """Diagonals (target minus query letters consumed) of every cell of a CIGAR
+    path, forward from the begin and backward from the end."""
+    fwd, bwd = [0], [0]
+    i = j = 0
+    for n, op in cigar:
+        for _ in range(n):
+            i += op != 2   # M and I consume a query letter
+            j += op != 1   # M and D consume a target letter
+            fwd.append(j - i)
+    i = j = 0
+    for n, op in reversed(cigar):
+        for _ in range(n):
+            i += op != 2
+            j += op != 1
+            bwd.append(j - i)
+    return fwd, bwd
+
+
+def check_pair(R, q, t):
+    r = oracle.align(q, t, R.W, R.O, R.X)
+    s1 = r["score1"]
+    if s1 <= 0:
+        return False
+    eq, et, bq, bt = r["read_end1"], r["ref_end1"], r["read_begin1"], r["ref_begin1"]
+    cig = r["cigar"]
+    la, lb = eq - bq + 1, et - bt + 1
+    # the reversed fill scans columns [end_t + 1 - window, end_t]
+    assert bt >= et + 1 - R.window(eq, et, s1)
+    # its band [-Gn, G] below/above the reversed main diagonal
+    G, Gn = R.G(eq, s1), R.Gn(eq, s1)
+    gaps_t = sum(n for n, op in cig if op == 2)
+    gaps_q = sum(n for n, op in cig if op == 1)
+    assert gaps_t + gaps_q <= G and gaps_q <= Gn
+    fwd, bwd = path_diagonals(cig)
+    assert min(bwd) >= -Gn and max(bwd) <= G
+    # the traceback band between begin and end
+    dlo, dhi = R.band(la, lb, s1)
+    assert dlo <= min(fwd) and max(fwd) <= dhi
+    assert fwd[-1] == lb - la
+    return True
+
+
+@pytest.mark.parametrize("kind", ["dna", "protein"])
+def test_bounds_hold_the_oracle_paths_on_related_pairs(lib, kind):
+    rng = np.random.default_rng(11 if kind == "dna" else 12)
+    checked = 0
+    for it in range(120):
+        if kind == "dna":
+            A = 4
+            W = dna(int(rng.integers(1, 4)), -int(rng.integers(1, 5)))
+        else:
+            A = 20
+            W = protein_like(rng)
+        X = int(rng.integers(1, 4))
+        O = X + int(rng.integers(0, 10))
+        R = Rules(lib, W, O, X)
+        n = int(rng.integers(5, 300))
+        base = rng.integers(0, A, n).astype(np.uint8)
+        q = mutate(rng, base, A, sub=rng.random() * 0.2, indel=rng.random() * 0.15)
+        t = np.concatenate([rng.integers(0, A, int(rng.integers(0, 40))).astype(np.uint8),
+                            mutate(rng, base, A, sub=0.05, indel=0.05),
+                            rng.integers(0, A, int(rng.integers(0, 40))).astype(np.uint8)])
+        checked += check_pair(R, q, t)
+    assert checked > 100
+
+
+@pytest.mark.parametrize("g", [1, 2, 5, 8])
+def test_bounds_are_exact_on_one_gap_pairs(lib, g):
+    """Query x+y against target x+z+y (z: g letters that match nothing): the
+    optimum is the one-gap path, score (a+b)m - O - (g-1)X; the forward bound
+    on gap letters, the reversed band's upper edge and the traceback band
+    are then exactly g (the gap count follows from the score).
+    Swapping the roles gives the rows bound Gn = g."""
+    rng = np.random.default_rng(100 + g)
+    A, m, O, X = 5, 2, 5, 2
+    W = dna(m, -3, A)
+    W[4, 4] = -3  # letter 4 matches nothing
+    R = Rules(lib, W, O, X)
+    a, b = 40, 50
+    x = rng.integers(0, 4, a).astype(np.uint8)
+    y = rng.integers(0, 4, b).astype(np.uint8)
+    z = np.full(g, 4, dtype=np.uint8)
+    expect = (a + b) * m - O - (g - 1) * X
+
+    r = oracle.align(np.concatenate([x, y]), np.concatenate([x, z, y]), W, O, X)
+    assert r["score1"] == expect
+    assert (r["read_begin1"], r["ref_begin1"], r["read_end1"], r["ref_end1"]) == (0, 0, a + b - 1, a + b + g - 1)
+    assert R.G(a + b - 1, expect) == g
+    assert R.band(a + b, a + b + g, expect) == (0, g)
+    assert check_pair(R, np.concatenate([x, y]), np.concatenate([x, z, y]))
+
+    r = oracle.align(np.concatenate([x, z, y]), np.concatenate([x, y]), W, O, X)
+    assert r["score1"] == expect
+    assert R.Gn(a + b + g - 1, expect) == g
+    assert R.band(a + b + g, a + b, expect) == (-g, 0)
+    assert check_pair(R, np.concatenate([x, z, y]), np.concatenate([x, y]))
+
+
+def test_band_widths_map_to_the_anti_diagonal_classes(lib):
+    R = Rules(lib, dna(2, -3), 5, 2)
+    seen = set()
+    # targets longer than the rectangle's 4096 columns keep the band classes
+    for s1 in range(20000, 200, -97):
+        c, width = R.trace_class(5000, 5000, s1)
+        expect = 0 if width <= 64 else 1 if width <= 128 else 2 if width <= 256 else 3 if width <= 512 else RING
+        assert c == expect, (s1, width, c)
+        seen.add(c)
+    assert seen == {0, 1, 2, 3, RING}
+
+
+def test_wide_bands_go_to_the_rectangle_when_it_fits(lib):
+    rng = np.random.default_rng(5)
+    # DNA: class 5 + min((la - 1) / 64, 3), for narrow bands too while the
+    # rectangle costs at most 3x the band's anti-diagonal slots
+    R = Rules(lib, dna(2, -3), 2, 1)
+    for la in (40, 60, 100, 130, 200, 300, 600):
+        c, width = R.trace_class(la, la + 50, 10)
+        assert c == T16_FIRST + min((la - 1) // 64, 3), (la, width, c)
+    c, width = R.trace_class(600, 650, 10)
+    assert width > 512
+    # DNA regions whose decisions exceed 2^17 words keep the ring kernel
+    c, width = R.trace_class(1000, 1050, 10)
+    assert width > 512 and c == RING
+    assert lib.hr_t16_need_words(1000, 1050, 3) > (1 << 17)
+    # general alphabet: 64-row strips, 128-row ones for regions whose
+    # decisions exceed 2^17 words in 64-row strips (the large pair that the
+    # routing once sent to the ring kernel by an overflow)
+    P = Rules(lib, protein_like(rng), 11, 1)
+    c, width = P.trace_class(1000, 1000, 50)
+    assert width > 512 and c == T16_FIRST + 1
+    assert lib.hr_t16_need_words(1000, 1000, 0) > (1 << 17)
+    c, width = P.trace_class(500, 700, 50)
+    assert width > 512 and c == T16_FIRST
+    for la, lb in ((2000, 2100), (3000, 2500), (1200, 4096)):
+        c, width = P.trace_class(la, lb, 30)
+        assert width > 512 and c in (T16_FIRST, T16_FIRST + 1), (la, lb, c)
+        assert lib.hr_t16_need_words(la, lb, c - T16_FIRST) <= (1 << 20)
+
+
+def test_rectangle_refused_beyond_its_values_and_columns(lib):
+    # a 600 x 650 region in 256-row strips: 768 rows, 666 columns padded
+    la, lb = 600, 650
+    # lowest value 3O + X(rows + cols + 2) + |wmin|: 28789 fits, 31672 does not
+    c, width = Rules(lib, dna(44, -3), 22, 20).trace_class(la, lb, 10)
+    assert width > 512 and c == T16_FIRST + 3
+    c, width = Rules(lib, dna(44, -3), 22, 22).trace_class(la, lb, 10)
+    assert width > 512 and c == RING
+    # highest value wmax (min(rows, cols) + 1): 44 x 667 fits, 46 x 667 does not
+    c, width = Rules(lib, dna(46, -3), 22, 20).trace_class(la, lb, 10)
+    assert width > 512 and c == RING
+    # columns: targets beyond 4096 letters
+    R = Rules(lib, dna(2, -3), 3, 1)
+    c, width = R.trace_class(60, 4096, 10)
+    assert width > 512 and c == T16_FIRST
+    c, width = R.trace_class(60, 4097, 10)
+    assert width > 512 and c == RING
+
+
+def test_routing_is_total_and_consistent_on_random_regions(lib):
+    rng = np.random.default_rng(9)
+    for it in range(3000):
+        if rng.random() < 0.5:
+            W, need_cap = dna(int(rng.integers(1, 6)), -int(rng.integers(1, 6))), 1 << 17
+        else:
+            W, need_cap = protein_like(rng), 1 << 20
+        X = int(rng.integers(1, 5))
+        R = Rules(lib, W, X + int(rng.integers(0, 12)), X)
+        la = int(rng.integers(1, 6000))
+        lb = int(rng.integers(1, 6000))
+        s1 = int(rng.integers(1, 2 * int(W.max()) * min(la, lb) + 2))
+        c, width = R.trace_class(la, lb, s1, small=bool(rng.random() < 0.5))
+        assert 0 <= c <= T16_FIRST + 3
+        if c >= T16_FIRST:
+            assert lb <= 4096
+            assert lib.hr_t16_need_words(la, lb, c - T16_FIRST) <= need_cap
+            if W.shape[0] != 4:
+                assert c in (T16_FIRST, T16_FIRST + 1)
+        else:
+            expect = 0 if width <= 64 else 1 if width <= 128 else 2 if width <= 256 else 3 if width <= 512 else RING
+            assert c == expect
