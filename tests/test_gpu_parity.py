@@ -553,3 +553,49 @@ def test_rect16_traceback_large_regions_general_alphabet(ctx):
     qs, ts = _weak_pairs(rng, [1100, 1300, 1500, 120, 300], ident=0.6, A=A, flank=(0, 40))
     b = _batch(qs, ts, M, 11, 1, "weak_protein_large", alphabet="ARNDCQEGHILKMFPSTWYV")
     compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
+
+def _one_gap_pairs(rng, npairs, A, gmax):
+    """Query x+y against target x+z+y (and the roles swapped for every other
+    pair), z a run of g letters, in random flanks: with z of a letter that
+    matches nothing (A = 5) the optimum is the one-gap path, whose gap count is
+    exactly the reverse band's bound G on its side and whose diagonals fill the
+    traceback band [0, g] (or [-g, 0]) exactly.  Returns the pairs and each
+    pair's (a, b, g)."""
+    qs, ts, abg = [], [], []
+    for p in range(npairs):
+        g = int(rng.integers(1, gmax + 1))
+        a, b = (int(v) for v in rng.integers(max(24, g + 4), 121, 2))
+        x = rng.integers(0, 4, a).astype(np.uint8)
+        y = rng.integers(0, 4, b).astype(np.uint8)
+        z = (np.full(g, 4) if A == 5 else rng.integers(0, 4, g)).astype(np.uint8)
+        gapped = np.concatenate([x, z, y])
+        plain = np.concatenate([x, y])
+        q, core = (plain, gapped) if p % 2 == 0 else (gapped, plain)
+        ts.append(np.concatenate([rng.integers(0, 4, int(rng.integers(0, 50))), core,
+                                  rng.integers(0, 4, int(rng.integers(0, 50)))]).astype(np.uint8))
+        qs.append(q)
+        abg.append((a, b, g))
+    return qs, ts, np.array(abg)
+
+
+@pytest.mark.parametrize("A,npairs", [(5, 17000), (4, 17000), (5, 3000)])
+def test_one_gap_pairs_on_the_exact_band_edges(ctx, A, npairs):
+    # 17,000 pairs take the thread-per-pair band kernel (reverse bands up to
+    # 32 diagonals; wider ones the 16-bit reverse fill); 3,000 pairs the ring
+    # reverse and the warp tracebacks; gaps of up to 40 letters cover every
+    # traceback class of these lengths
+    rng = np.random.default_rng(95 + A + npairs)
+    qs, ts, abg = _one_gap_pairs(rng, npairs, A, 40)
+    W = np.full((A, A), -3, np.int8)
+    np.fill_diagonal(W, 2)
+    b = _batch(qs, ts, W, 5, 2, f"one_gap_A{A}", alphabet="ACGTN"[:A])
+    ora = run_oracle(b)
+    if A == 5:
+        # the construction holds: the one-gap optimum over the whole query
+        res = ora[0]
+        a, bb, g = abg.T
+        assert (res["score1"] == 2 * (a + bb) - 5 - 2 * (g - 1)).all()
+        assert (res["read_begin1"] == 0).all() and (res["read_end1"] == b.q_len - 1).all()
+    compare(b, ora, run_gpu_device(ctx, b))
