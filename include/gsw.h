@@ -159,6 +159,8 @@ int gsw_context_set_tune(gsw_ctx *ctx, const gsw_tune *tune);
  * local alignment of the longest read, so the work is one batch of
  * reads x windows plus two small passes.  Pointers follow gsw_align_batch's
  * rules (GSW_HOST_IO: all host); ref_len < 2^31; the reads' lengths < 2^24.
+ * Work and the read-back of device read lengths are ordered on `stream`, so
+ * inputs written by work queued there before the call are seen.
  * Errors: GSW_EINVAL (arguments, or `window` smaller than 2 x mask + overlap),
  * GSW_ENOMEM, GSW_ECUDA, GSW_ECIGAR_SPACE (records complete, CIGARs that do
  * not fit have cigar_len = -needed).
@@ -202,7 +204,10 @@ int gsw_context_set_sm_limit(gsw_ctx *ctx, int sms);
  * batch (may be NULL with capacity 0 when GSW_CIGAR is not set); pairs that
  * do not fit are marked GSW_RES_CIGAR_SPACE and the call returns
  * GSW_ECIGAR_SPACE after filling everything else.  With GSW_COLMAX, colmax
- * receives t_len[p] int32 values at colmax[colmax_off[p]].
+ * receives t_len[p] int32 values at colmax[colmax_off[p]]; words outside
+ * every pair's range are left unchanged.  With GSW_HOST_IO a negative
+ * colmax_off is rejected (GSW_EINVAL); device offsets are the caller's to keep
+ * inside its buffer.
  *
  * mask_len is the half-width L of the window masked around ref_end1 before
  * the suboptimal score is taken; negative means max(q_len/2, 15).

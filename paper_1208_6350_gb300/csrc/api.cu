@@ -197,14 +197,30 @@ enum MiscSlot {
 
 // Side streams and fork/join events of the band classes, created once per
 // context outside any capture (the first call of a shape is never captured).
+void destroy_aux(BandStreams &a) {
+    for (int k = 0; k < 2; k++) {
+        if (a.s[k]) cudaStreamDestroy(a.s[k]);
+        if (a.join[k]) cudaEventDestroy(a.join[k]);
+    }
+    if (a.fork) cudaEventDestroy(a.fork);
+    a = BandStreams{};
+}
+
 int ensure_aux(gsw_ctx *ctx) {
-    if (ctx->aux.s[0]) return GSW_OK;
+    if (ctx->aux.fork) return GSW_OK;
     if (ctx->capturing) return GSW_ESTATE;
-    for (int k = 0; k < 2; k++)
-        if (cudaStreamCreateWithFlags(&ctx->aux.s[k], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ctx->aux.join[k], cudaEventDisableTiming) != cudaSuccess)
-            return GSW_ECUDA;
-    if (cudaEventCreateWithFlags(&ctx->aux.fork, cudaEventDisableTiming) != cudaSuccess) return GSW_ECUDA;
+    BandStreams a{};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+        e = cudaStreamCreateWithFlags(&a.s[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.join[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        destroy_aux(a);  // all or nothing: a later call tries again
+        return set_err(GSW_ECUDA, "band side streams: %s", cudaGetErrorString(e));
+    }
+    ctx->aux = a;
     return GSW_OK;
 }
 
@@ -599,6 +615,7 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
     bv.cigar_cap = cigar_capacity;
     bv.cigar_cursor = misc + kMiscCursor;
     int maxm = 0, maxn = 0;
+    int64_t cmext = 0;  // host I/O: colmax words from 0 to the end of the last pair's range
     const bool hio = (flags & GSW_HOST_IO) != 0;
     unsigned long long *hstat = reinterpret_cast<unsigned long long *>(ctx->host_small);
     // the batch's sizes and the checks of its lengths and offsets, on the
@@ -633,9 +650,11 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
         maxm = (int)hstat[0];
         maxn = (int)hstat[1];
         const int64_t qext = (int64_t)hstat[2], text = (int64_t)hstat[3];
-        int64_t cmext = 0;
         if (flags & GSW_COLMAX)
-            for (int32_t p = 0; p < npairs; p++) cmext = std::max<int64_t>(cmext, colmax_off[p] + t_len[p]);
+            for (int32_t p = 0; p < npairs; p++) {
+                if (colmax_off[p] < 0) return set_err(GSW_EINVAL, "pair %d: negative colmax offset", p);
+                cmext = std::max<int64_t>(cmext, colmax_off[p] + t_len[p]);
+            }
         GSW_TRY(ensure(ctx, ctx->io_q, (size_t)std::max<int64_t>(qext, 1)));
         GSW_TRY(ensure(ctx, ctx->io_t, (size_t)std::max<int64_t>(text, 1)));
         GSW_TRY(ensure(ctx, ctx->io_res, sizeof(gsw_result) * npairs));
@@ -658,8 +677,12 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
             CUDA_TRY(cudaMemcpyAsync(ctx->io_q.p, q, qext, cudaMemcpyHostToDevice, st));
             CUDA_TRY(cudaMemcpyAsync(ctx->io_t.p, t, text, cudaMemcpyHostToDevice, st));
         }
-        if (flags & GSW_COLMAX)
+        if (flags & GSW_COLMAX) {
             CUDA_TRY(cudaMemcpyAsync(ctx->io_cmoff.p, colmax_off, sizeof(int64_t) * npairs, cudaMemcpyHostToDevice, st));
+            // the staging copy starts as the caller's buffer, so the words
+            // between the pairs' ranges come back unchanged
+            CUDA_TRY(cudaMemcpyAsync(ctx->io_colmax.p, colmax, sizeof(int32_t) * cmext, cudaMemcpyHostToDevice, st));
+        }
         bv.q = (const uint8_t *)ctx->io_q.p;
         bv.t = (const uint8_t *)ctx->io_t.p;
         bv.q_off = (const int64_t *)ctx->io_qoff.p;
@@ -708,11 +731,8 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
     CUDA_TRY(cudaMemcpyAsync(hs + 1, misc + kMiscValid, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     if (hio) {
         CUDA_TRY(cudaMemcpyAsync(results, bv.res, sizeof(gsw_result) * npairs, cudaMemcpyDeviceToHost, st));
-        if (flags & GSW_COLMAX) {
-            int64_t cmext = 0;
-            for (int32_t p = 0; p < npairs; p++) cmext = std::max<int64_t>(cmext, colmax_off[p] + t_len[p]);
+        if (flags & GSW_COLMAX)
             CUDA_TRY(cudaMemcpyAsync(colmax, bv.colmax, sizeof(int32_t) * cmext, cudaMemcpyDeviceToHost, st));
-        }
     }
     CUDA_TRY(cudaStreamSynchronize(st));
     const unsigned long long used_words = hs[0];
@@ -720,7 +740,10 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
     ctx->cigar_words = (flags & GSW_CIGAR) ? (long long)used_words : 0;
     if (hio && (flags & GSW_CIGAR) && cigar_capacity > 0) {
         const size_t n = (size_t)std::min<unsigned long long>(used_words, (unsigned long long)cigar_capacity);
-        if (n) CUDA_TRY(cudaMemcpy(cigar, bv.cigar, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        if (n) {
+            CUDA_TRY(cudaMemcpyAsync(cigar, bv.cigar, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+        }
     }
     if (bad_letters) return set_err(GSW_EINVAL, "a letter code is >= the alphabet size (%d)", sc.A);
     if ((flags & GSW_CIGAR) && used_words > (unsigned long long)cigar_capacity)
@@ -885,11 +908,7 @@ int gsw_context_destroy(gsw_ctx *c) {
     if (c->host_small) cudaFreeHost(c->host_small);
     for (int k = 0; k <= GSW_NSTAGES; k++)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
-    for (int k = 0; k < 2; k++) {
-        if (c->aux.s[k]) cudaStreamDestroy(c->aux.s[k]);
-        if (c->aux.join[k]) cudaEventDestroy(c->aux.join[k]);
-    }
-    if (c->aux.fork) cudaEventDestroy(c->aux.fork);
+    destroy_aux(c->aux);
     delete c;
     return GSW_OK;
 }

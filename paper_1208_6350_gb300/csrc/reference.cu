@@ -260,7 +260,9 @@ extern "C" int gsw_align_to_reference(gsw_ctx *ctx, int32_t nreads, const uint8_
     if (hio) {
         std::copy(q_len, q_len + nreads, hql.begin());
         std::copy(q_off, q_off + nreads, hqo.begin());
-    } else if (cudaMemcpy(hql.data(), q_len, 4 * (size_t)nreads, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    } else if (cudaMemcpyAsync(hql.data(), q_len, 4 * (size_t)nreads, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+               cudaStreamSynchronize(st) != cudaSuccess) {
+        // read on the call's stream: work queued there before the call may write the lengths
         return GSW_ECUDA;
     }
     int maxm = 0;

@@ -599,3 +599,36 @@ def test_one_gap_pairs_on_the_exact_band_edges(ctx, A, npairs):
         assert (res["score1"] == 2 * (a + bb) - 5 - 2 * (g - 1)).all()
         assert (res["read_begin1"] == 0).all() and (res["read_end1"] == b.q_len - 1).all()
     compare(b, ora, run_gpu_device(ctx, b))
+
+
+def test_host_io_colmax_at_callers_offsets(ctx):
+    # host buffers: each pair's column maxima land at its own offset (here in
+    # reverse pair order with gaps of 5 words), the words between the ranges
+    # keep the caller's values, and a negative offset is refused
+    b = mixed_dna(97, 300, 80, 400)
+    ores, _, (ocm, ocmoff) = run_oracle(b)
+    n = b.npairs
+    cmoff = np.zeros(n, np.int64)
+    at = 5
+    for p in reversed(range(n)):
+        cmoff[p] = at
+        at += int(b.t_len[p]) + 5
+    cm = np.full(at, -7, np.int32)
+    res = np.zeros(n, gsw.RESULT_DTYPE)
+    cap = int(b.q_len.sum() + b.t_len.sum() + 16)
+    cig = np.zeros(cap, np.uint32)
+    flags = gsw.GSW_CIGAR | gsw.GSW_COLMAX | gsw.GSW_HOST_IO
+    rc = gsw.gsw_align_batch(ctx.handle, n, b.q, b.q_off, b.q_len, b.t, b.t_off, b.t_len, b.W, b.gap_open,
+                             b.gap_extend, flags, -1, res, cig, cap, cm, cmoff)
+    assert rc == gsw.GSW_OK
+    assert (res["score1"] == ores["score1"]).all() and (res["ref_end2"] == ores["ref_end2"]).all()
+    inside = np.zeros(at, bool)
+    for p in range(n):
+        lo, L = int(cmoff[p]), int(b.t_len[p])
+        assert np.array_equal(cm[lo:lo + L], ocm[ocmoff[p]:ocmoff[p] + L]), p
+        inside[lo:lo + L] = True
+    assert (cm[~inside] == -7).all()
+    cmoff[3] = -1
+    rc = gsw.gsw_align_batch(ctx.handle, n, b.q, b.q_off, b.q_len, b.t, b.t_off, b.t_len, b.W, b.gap_open,
+                             b.gap_extend, flags, -1, res, cig, cap, cm, cmoff, check=False)
+    assert rc == gsw.GSW_EINVAL

@@ -90,3 +90,49 @@ def test_window_smaller_than_mask_and_overlap_rejected():
     finally:
         ctx.close()
     assert rc == gsw.GSW_EINVAL
+
+
+def test_device_inputs_written_on_the_callers_stream():
+    # device arrays and a non-default stream: the read lengths are written by
+    # work queued on that stream just before the call (behind a ~20 ms delay
+    # kernel), so the call must read them on the same stream
+    import torch
+    q, q_off, q_len, ref = _reads_and_reference(73)
+    W = wl.dna_matrix(2, -3)
+    O, X = 5, 2
+    n = len(q_len)
+    dev = torch.device("cuda", 0)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    dq, dqo, dref, ql_src = T(q), T(q_off), T(ref), T(q_len)
+    dql = torch.zeros(n, dtype=torch.int32, device=dev)
+    cap = int(2 * q_len.sum() + 64 * n + 64)
+    dres = torch.zeros(n * gsw.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    dcig = torch.zeros(cap, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    ctx = gsw.Context(0, 4 << 30)
+    try:
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            torch.cuda._sleep(40_000_000)
+            dql.copy_(ql_src)
+            rc = gsw.load().gsw_align_to_reference(
+                ctx.handle, n, dq.data_ptr(), dqo.data_ptr(), dql.data_ptr(), dref.data_ptr(), len(ref),
+                W.ctypes.data, 4, O, X, gsw.GSW_CIGAR, -1, 2048, dres.data_ptr(), dcig.data_ptr(), cap,
+                s.cuda_stream)
+        s.synchronize()
+    finally:
+        ctx.close()
+    assert rc == gsw.GSW_OK
+    res = dres.cpu().numpy().view(gsw.RESULT_DTYPE)
+    cig = dcig.cpu().numpy().view(np.uint32)
+    t_off = np.zeros(n, np.int64)
+    t_len = np.full(n, len(ref), np.int32)
+    ores, ocg, _ = oracle.align_batch(q, q_off, q_len, ref, t_off, t_len, W, O, X,
+                                      cigar_stride=int(q_len.max() + len(ref) + 2))
+    for p in range(n):
+        for f in FIELDS:
+            assert int(res[f][p]) == int(ores[f][p]), (p, f, int(res[f][p]), int(ores[f][p]))
+        want = oracle.decode_cigar(ocg[p, : ores["cigar_len"][p]])
+        got = oracle.decode_cigar(cig[res["cigar_off"][p]: res["cigar_off"][p] + res["cigar_len"][p]]) \
+            if res["cigar_len"][p] > 0 else []
+        assert got == want, p
