@@ -129,6 +129,12 @@ int run_batch(gsw_server *srv, Worker *w, std::vector<Req *> &batch) {
         tl += (int64_t)r->t.size();
     }
     cudaStream_t st = w->st;
+    // on an error, copies from this worker's pinned staging may still be
+    // queued: wait for them before the next batch refills it
+    auto fail = [st](int rc) {
+        cudaStreamSynchronize(st);
+        return rc;
+    };
     cudaError_t e = cudaSuccess;
     if (ql) e = cudaMemcpyAsync(w->d_q, w->h_q, ql, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && tl) e = cudaMemcpyAsync(w->d_t, w->h_t, tl, cudaMemcpyHostToDevice, st);
@@ -136,16 +142,16 @@ int run_batch(gsw_server *srv, Worker *w, std::vector<Req *> &batch) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(w->d_toff, w->h_toff, 8 * (size_t)np, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(w->d_qlen, w->h_qlen, 4 * (size_t)np, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(w->d_tlen, w->h_tlen, 4 * (size_t)np, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return GSW_ECUDA;
+    if (e != cudaSuccess) return fail(GSW_ECUDA);
     const gsw_serve_config &c = srv->cfg;
     int rc = gsw_align_batch(w->ctx, np, w->d_q, w->d_qoff, w->d_qlen, w->d_t, w->d_toff, w->d_tlen,
                              srv->matrix.data(), c.alphabet, c.gap_open, c.gap_extend, c.flags, c.mask_len,
                              w->d_res, (c.flags & GSW_CIGAR) ? w->d_cig : nullptr,
                              (c.flags & GSW_CIGAR) ? w->cap_cigar : 0, nullptr, nullptr, st);
-    if (rc != GSW_OK) return rc;
+    if (rc != GSW_OK) return fail(rc);
     e = cudaMemcpyAsync(w->h_res, w->d_res, sizeof(gsw_result) * (size_t)np, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return GSW_ECUDA;
+    if (e != cudaSuccess) return fail(GSW_ECUDA);
     int64_t cig_words = 0;
     if (c.flags & GSW_CIGAR) {
         for (int32_t p = 0; p < np; p++)
@@ -153,7 +159,7 @@ int run_batch(gsw_server *srv, Worker *w, std::vector<Req *> &batch) {
         if (cig_words) {
             e = cudaMemcpyAsync(w->h_cig, w->d_cig, 4 * (size_t)cig_words, cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return GSW_ECUDA;
+            if (e != cudaSuccess) return fail(GSW_ECUDA);
         }
     }
     int32_t at = 0;
