@@ -303,3 +303,88 @@ def test_routing_is_total_and_consistent_on_random_regions(lib):
         else:
             expect = 0 if width <= 64 else 1 if width <= 128 else 2 if width <= 256 else 3 if width <= 512 else RING
             assert c == expect
+
+
+NEG = -(1 << 30)
+
+
+def first_reversed_max(q, t, W, O, X, eq, et, score1, band=None):
+    """Local Gotoh fill over reverse(q[0..eq]) x reverse(t[0..et]), written
+    out cell by cell; with band = (Gn, G) the cells off the diagonals
+    [-Gn, G] (j - i, reversed) are never computed: H = 0, E = F = -inf there,
+    the fill kernel's boundary values.  Returns the first cell, by column and
+    then row, whose H equals score1, as a begin (begin_q, begin_t)."""
+    m, n = eq + 1, et + 1
+    Hp = [0] * (n + 1)          # row i-1 of H, column 0 is the boundary
+    Fp = [NEG] * (n + 1)
+    Hrows = []
+    for i in range(1, m + 1):
+        a = int(q[eq - (i - 1)])
+        H = [0] * (n + 1)
+        F = [NEG] * (n + 1)
+        E = NEG
+        for j in range(1, n + 1):
+            if band is not None and not (-band[0] <= (j - i) <= band[1]):
+                H[j], F[j], E = 0, NEG, NEG
+                continue
+            E = max(H[j - 1] - O, E - X)
+            F[j] = max(Hp[j] - O, Fp[j] - X)
+            H[j] = max(0, Hp[j - 1] + int(W[a, int(t[et - (j - 1)])]), E, F[j])
+        Hrows.append(H)
+        Hp, Fp = H, F
+    for j in range(1, n + 1):
+        for i in range(1, m + 1):
+            if Hrows[i - 1][j] == score1:
+                return eq - (i - 1), et - (j - 1)
+    return None
+
+
+@pytest.mark.parametrize("kind", ["related", "one_gap"])
+def test_banded_reversed_fill_finds_the_same_begin(lib, kind):
+    """The reversed fill restricted to the reverse band [-Gn, G] reaches
+    score1 first at the same cell as the unrestricted one, the oracle's begin:
+    every path reaching score1 starts at the reversed origin and stays in the
+    band, and a restriction only lowers the other cells."""
+    rng = np.random.default_rng(21 if kind == "related" else 22)
+    checked = narrow = tight = 0
+    for it in range(40):
+        if kind == "related":
+            A = 4
+            W = dna(int(rng.integers(1, 4)), -int(rng.integers(1, 5)))
+            X = int(rng.integers(1, 4))
+            O = X + int(rng.integers(0, 6))
+            base = rng.integers(0, A, int(rng.integers(10, 70))).astype(np.uint8)
+            q = mutate(rng, base, A, sub=0.1, indel=0.1, max_run=4)
+            t = np.concatenate([rng.integers(0, A, int(rng.integers(0, 20))).astype(np.uint8),
+                                mutate(rng, base, A, sub=0.05, indel=0.05, max_run=4),
+                                rng.integers(0, A, int(rng.integers(0, 20))).astype(np.uint8)])
+        else:
+            A, O, X = 5, 5, 2
+            W = dna(2, -3, A)
+            g = int(rng.integers(1, 9))
+            x = rng.integers(0, 4, int(rng.integers(g + 4, 40))).astype(np.uint8)
+            y = rng.integers(0, 4, int(rng.integers(g + 4, 40))).astype(np.uint8)
+            z = np.full(g, 4, np.uint8)
+            q, t = (np.concatenate([x, y]), np.concatenate([x, z, y]))
+            if it % 2:
+                q, t = t, q
+            t = np.concatenate([rng.integers(0, 4, int(rng.integers(0, 15))).astype(np.uint8), t])
+        R = Rules(lib, W, O, X)
+        r = oracle.align(q, t, R.W, O, X)
+        s1 = r["score1"]
+        if s1 <= 0:
+            continue
+        eq, et = r["read_end1"], r["ref_end1"]
+        begin = (r["read_begin1"], r["ref_begin1"])
+        G, Gn = R.G(eq, s1), R.Gn(eq, s1)
+        assert first_reversed_max(q, t, R.W, O, X, eq, et, s1) == begin
+        assert first_reversed_max(q, t, R.W, O, X, eq, et, s1, band=(Gn, G)) == begin
+        checked += 1
+        narrow += (G + Gn + 1) < min(eq + 1, et + 1)
+        if kind == "one_gap" and G > 0 and Gn > 0:
+            # the one-gap path touches an edge: one diagonal less loses the begin
+            tight += (first_reversed_max(q, t, R.W, O, X, eq, et, s1, band=(Gn, G - 1)) != begin) + \
+                (first_reversed_max(q, t, R.W, O, X, eq, et, s1, band=(Gn - 1, G)) != begin)
+    assert checked >= 30 and narrow >= 10
+    if kind == "one_gap":
+        assert tight >= 15
