@@ -388,3 +388,109 @@ def test_banded_reversed_fill_finds_the_same_begin(lib, kind):
     assert checked >= 30 and narrow >= 10
     if kind == "one_gap":
         assert tight >= 15
+
+
+def global_cigar(qs, ts, W, O, X, band=None):
+    """Global Gotoh over qs x ts (a gap of k letters costs O + (k-1)X),
+    written out cell by cell, and its traceback from the end in state H with
+    the fixed preference: diagonal, then the E state (D, target letters),
+    then F (I, query letters); in E and F an open is preferred to an extend.
+    With band = (dlo, dhi) the cells off the diagonals [dlo, dhi] (j - i) are
+    -inf.  Returns the CIGAR as (length, op) runs, op 0/1/2 = M/I/D, and the
+    score; (None, None) when the band leaves out the end cell."""
+    la, lb = len(qs), len(ts)
+    H = [[NEG] * (lb + 1) for _ in range(la + 1)]
+    E = [[NEG] * (lb + 1) for _ in range(la + 1)]
+    F = [[NEG] * (lb + 1) for _ in range(la + 1)]
+    inb = lambda i, j: band is None or band[0] <= j - i <= band[1]
+    H[0][0] = 0
+    for i in range(la + 1):
+        for j in range(lb + 1):
+            if (i == 0 and j == 0) or not inb(i, j):
+                continue
+            if j > 0:
+                E[i][j] = max(H[i][j - 1] - O, E[i][j - 1] - X)
+            if i > 0:
+                F[i][j] = max(H[i - 1][j] - O, F[i - 1][j] - X)
+            d = H[i - 1][j - 1] + int(W[int(qs[i - 1]), int(ts[j - 1])]) if i > 0 and j > 0 else NEG
+            H[i][j] = max(d, E[i][j], F[i][j])
+    if H[la][lb] <= NEG // 2:
+        return None, None
+    ops = []
+    i, j, state = la, lb, 0
+    while i > 0 or j > 0:
+        if state == 0:
+            if i > 0 and j > 0 and H[i][j] == H[i - 1][j - 1] + int(W[int(qs[i - 1]), int(ts[j - 1])]):
+                ops.append(0)
+                i, j = i - 1, j - 1
+                continue
+            state = 1 if H[i][j] == E[i][j] else 2
+        if state == 1:
+            ops.append(2)
+            state = 0 if E[i][j] == H[i][j - 1] - O else 1
+            j -= 1
+        else:
+            ops.append(1)
+            state = 0 if F[i][j] == H[i - 1][j] - O else 2
+            i -= 1
+    runs = []
+    for op in reversed(ops):
+        if runs and runs[-1][1] == op:
+            runs[-1] = (runs[-1][0] + 1, op)
+        else:
+            runs.append((1, op))
+    return runs, H[la][lb]
+
+
+@pytest.mark.parametrize("kind", ["related", "two_gaps"])
+def test_banded_traceback_gives_the_full_rectangle_cigar(lib, kind):
+    """Global alignment between begin and end on the band [dlo, dhi] gives
+    the oracle's canonical CIGAR (full rectangle): optimal paths lie in the
+    band, so their cells keep their values and every preference test decides
+    alike.  Two-gap pairs (x + z1 + y against x + z2 + y, z1 and z2 g letters
+    that mismatch at -20, so both are gapped out) have begin and end on
+    diagonal 0 and a path reaching diagonal g or -g; the score bound gives
+    the band [-g, g] exactly, and one diagonal less on the path's side loses
+    the CIGAR."""
+    rng = np.random.default_rng(31 if kind == "related" else 32)
+    checked = tight = 0
+    for it in range(40):
+        if kind == "related":
+            A = 4
+            W = dna(int(rng.integers(1, 4)), -int(rng.integers(1, 5)))
+            X = int(rng.integers(1, 4))
+            O = X + int(rng.integers(0, 6))
+            base = rng.integers(0, A, int(rng.integers(10, 60))).astype(np.uint8)
+            q = mutate(rng, base, A, sub=0.1, indel=0.1, max_run=4)
+            t = mutate(rng, base, A, sub=0.05, indel=0.05, max_run=4)
+        else:
+            A, O, X = 6, 5, 2
+            W = dna(2, -3, A)
+            W[4, 5] = W[5, 4] = -20
+            g = int(rng.integers(1, 7))
+            x = rng.integers(0, 4, int(rng.integers(2 * g + 8, 40))).astype(np.uint8)
+            y = rng.integers(0, 4, int(rng.integers(2 * g + 8, 40))).astype(np.uint8)
+            q = np.concatenate([x, np.full(g, 4, np.uint8), y])
+            t = np.concatenate([x, np.full(g, 5, np.uint8), y])
+        R = Rules(lib, W, O, X)
+        r = oracle.align(q, t, R.W, O, X)
+        s1 = r["score1"]
+        if s1 <= 0:
+            continue
+        qs = q[r["read_begin1"]: r["read_end1"] + 1]
+        ts = t[r["ref_begin1"]: r["ref_end1"] + 1]
+        dlo, dhi = R.band(len(qs), len(ts), s1)
+        full, sc_full = global_cigar(qs, ts, R.W, O, X)
+        banded, sc_band = global_cigar(qs, ts, R.W, O, X, band=(dlo, dhi))
+        assert sc_full == s1 and sc_band == s1
+        assert full == r["cigar"] and banded == r["cigar"]
+        checked += 1
+        if kind == "two_gaps":
+            assert s1 == 2 * (len(x) + len(y)) - 2 * (O + (g - 1) * X)
+            assert (dlo, dhi) == (-g, g)
+            lost = [global_cigar(qs, ts, R.W, O, X, band=cut)[0] != r["cigar"]
+                    for cut in ((dlo + 1, dhi), (dlo, dhi - 1))]
+            tight += any(lost)
+    assert checked >= 30
+    if kind == "two_gaps":
+        assert tight == checked
