@@ -178,6 +178,28 @@ def fill_traffic_bytes(cells, workload):
         return None
 
 
+def work_summary(r, cells):
+    """Work beside the forward fill, from one step's records (reported apart,
+    not counted in the metric): pairs refilled in 32-bit lanes; the reversed
+    rectangle from the end back to the begin column, (read_end1 + 1) x
+    (ref_end1 - ref_begin1 + 1), that a reversed fill stopping at the begin
+    covers; the region between begin and end, where the CIGAR's global
+    alignment runs.  Pairs with score1 = 0 have neither."""
+    n = len(r)
+    hit = r["score1"] > 0
+    eq = r["read_end1"][hit].astype(np.int64)
+    et = r["ref_end1"][hit].astype(np.int64)
+    bq = r["read_begin1"][hit].astype(np.int64)
+    bt = r["ref_begin1"][hit].astype(np.int64)
+    rev = int(((eq + 1) * (et - bt + 1)).sum())
+    region = int(((eq - bq + 1) * (et - bt + 1)).sum())
+    s32 = int(np.count_nonzero(r["flags"] & 0x1))
+    return {"pairs": n, "aligned_pairs": int(hit.sum()),
+            "s32_refill_pairs": s32, "s32_refill_frac": round(s32 / max(n, 1), 4),
+            "reverse_rect_cells": rev, "reverse_rect_frac": round(rev / max(cells, 1), 4),
+            "region_cells": region, "region_frac": round(region / max(cells, 1), 4)}
+
+
 # ------------------------------------------------------------ GPU arm
 def combine_ranks(ms, cells, dist=None, device="cpu"):
     """Whole-job step time and cells: the slowest rank's time, every rank's
@@ -280,6 +302,7 @@ def run_gsw(args):
     ms = e0.elapsed_time(e1) / args.steps
     ms_max, job_cells = combine_ranks(ms, cells, dist if world > 1 else None, dev)
     value = job_cells / (ms_max / 1e3) / 1e9
+    work = work_summary(res.cpu().numpy().view(gsw.RESULT_DTYPE), cells)
 
     # e2e: the same call on host buffers (pinned), copies inside the timed region
     e2e = None
@@ -308,7 +331,8 @@ def run_gsw(args):
             "gpu_launches": launches,
             "graph_segments_replayed": graph_segments,
             "stage_ms": {k: round(v / args.steps, 3) for k, v in stage_sum.items()},
-            "checked_pairs": checked, "clocks": clocks, "roofline": roof, "autotune": tune}
+            "checked_pairs": checked, "clocks": clocks, "roofline": roof, "autotune": tune,
+            "work_beside_fill": work}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(b, args.cpu_seconds)
     if world == 1 and not args.no_serve:
