@@ -80,3 +80,30 @@ def test_pack2_layout_and_packed_flag_checks_without_gpu():
     rc = lib.gsw_align_batch(None, 1, None, None, None, None, None, None, W.ctypes.data, 20, 3, 1,
                              gsw.GSW_PACKED2, -1, None, None, 0, None, None, None)
     assert rc == gsw.GSW_EINVAL
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # a fresh interpreter whose library path points nowhere: load() raises
+    import subprocess
+    import sys
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_1208_6350_gb300 import _build, gsw\n"
+        "_build.LIB = %r\n"
+        "try:\n"
+        "    gsw.load(build_if_missing=False)\n"
+        "except RuntimeError as e:\n"
+        "    print('raised:', e)\n"
+        "else:\n"
+        "    print('loaded')\n" % (ROOT, str(tmp_path / "absent" / "libgsw.so")))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.startswith("raised: CUDA library not built"), out.stdout
+
+
+def test_context_without_a_gpu_raises():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(gsw.GswError):
+        gsw.Context(0, 1 << 20)
