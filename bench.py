@@ -302,7 +302,8 @@ def run_gsw(args):
     ms = e0.elapsed_time(e1) / args.steps
     ms_max, job_cells = combine_ranks(ms, cells, dist if world > 1 else None, dev)
     value = job_cells / (ms_max / 1e3) / 1e9
-    work = work_summary(res.cpu().numpy().view(gsw.RESULT_DTYPE), cells)
+    rec = res.cpu().numpy().view(gsw.RESULT_DTYPE)
+    work = work_summary(rec, cells)
 
     # e2e: the same call on host buffers (pinned), copies inside the timed region
     e2e = None
@@ -333,6 +334,8 @@ def run_gsw(args):
             "stage_ms": {k: round(v / args.steps, 3) for k, v in stage_sum.items()},
             "checked_pairs": checked, "clocks": clocks, "roofline": roof, "autotune": tune,
             "work_beside_fill": work}
+    if world == 1 and args.plain_pairs > 0:
+        line["plain_per_pair"] = run_plain(gsw, b, ctx, args.plain_pairs, rec)
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(b, args.cpu_seconds)
     if world == 1 and not args.no_serve:
@@ -378,6 +381,33 @@ def run_e2e(args, gsw, b, ctx, stream, dev, torch, packed=False):
     return {"value": round(b.cells / dt / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 3),
             "api": "gsw_align_batch with GSW_HOST_IO (pinned host buffers)"}
+
+
+def run_plain(gsw, b, ctx, n_pairs, batched=None):
+    """The plain per-pair path (GSW_PLAIN: every pair its own launch sequence,
+    waited for before the next, as a caller aligning one pair per call) on
+    the first n_pairs pairs of the workload, host buffers; GCUPS on those
+    pairs, and whether their records equal the batched step's."""
+    s = b.subset(np.arange(min(n_pairs, b.npairs)))
+    flags = gsw.GSW_CIGAR | gsw.GSW_PLAIN
+    w = s.subset(np.arange(min(8, s.npairs)))
+    ctx.align_host(w.q, w.q_off, w.q_len, w.t, w.t_off, w.t_len, b.W, b.gap_open, b.gap_extend, flags, -1,
+                   int(w.q_len.sum() + w.t_len.sum() + 64))
+    t0 = time.perf_counter()
+    res, _, _, rc = ctx.align_host(s.q, s.q_off, s.q_len, s.t, s.t_off, s.t_len, b.W, b.gap_open,
+                                   b.gap_extend, flags, -1, int(s.q_len.sum() + s.t_len.sum() + 64))
+    dt = time.perf_counter() - t0
+    if rc != gsw.GSW_OK:
+        raise SystemExit(f"plain per-pair path failed with {rc}")
+    same = None
+    if batched is not None:
+        fields = ("score1", "score2", "ref_begin1", "ref_end1", "read_begin1", "read_end1", "ref_end2",
+                  "cigar_len")
+        same = all(np.array_equal(res[f], batched[f][:s.npairs]) for f in fields)
+    return {"pairs": s.npairs, "cells": int(s.cells), "seconds": round(dt, 3),
+            "gcups": round(s.cells / dt / 1e9, 3), "ms_per_pair": round(dt / s.npairs * 1e3, 3),
+            "api": "gsw_align_batch with GSW_PLAIN | GSW_HOST_IO (one launch sequence per pair)",
+            "same_records_as_batched": same}
 
 
 def check_sample(b, res, cig, rank, k=300, max_cells=3e9):
@@ -830,6 +860,8 @@ def main():
     ap.add_argument("--head", type=int, default=100,
                     help="serving_stream: leading requests also run by the plain per-pair baseline")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving run of the default line")
+    ap.add_argument("--plain-pairs", type=int, default=0,
+                    help="also time the plain per-pair path (GSW_PLAIN) on this many of the workload's pairs")
     ap.add_argument("--no-tune", action="store_true", help="default fill classes instead of the autotuner's")
     ap.add_argument("--tune-table", default="", help="fill class per 32-row bucket, comma-separated (no tuning)")
     ap.add_argument("--no-pack", action="store_true", help="DNA arenas one byte per letter instead of 2-bit packed")

@@ -41,3 +41,35 @@ def test_invariants_on_oracle_records():
     # decoys (10 %) still align somewhere; true reads align over most of the read
     assert w["aligned_pairs"] == int((ores["score1"] > 0).sum())
     assert 0.05 < w["region_frac"] < 0.5
+
+
+class _OracleContext:
+    """Stands in for gsw.Context.align_host: the oracle's records in the
+    library's record layout (no GPU)."""
+
+    def __init__(self):
+        self.calls = []
+
+    def align_host(self, q, q_off, q_len, t, t_off, t_len, W, O, X, flags, mask_len, cap):
+        self.calls.append((len(q_len), flags))
+        o, _, _ = oracle.align_batch(q, q_off, q_len, t, t_off, t_len, W, O, X, mask_len)
+        r = np.zeros(len(q_len), gsw.RESULT_DTYPE)
+        for f in ("score1", "score2", "ref_begin1", "ref_end1", "read_begin1", "read_end1", "ref_end2"):
+            r[f] = o[f]
+        return r, np.zeros(max(cap, 1), np.uint32), (None, None), gsw.GSW_OK
+
+
+def test_plain_per_pair_leg_reports_and_compares():
+    b, _ = bench.make_workload("dna_short_read_extension_1M", 300, 0)
+    ctx = _OracleContext()
+    batched = ctx.align_host(b.q, b.q_off, b.q_len, b.t, b.t_off, b.t_len, b.W, b.gap_open, b.gap_extend,
+                             gsw.GSW_CIGAR, -1, 0)[0]
+    out = bench.run_plain(gsw, b, ctx, 120, batched)
+    assert out["pairs"] == 120 and out["same_records_as_batched"] is True
+    assert out["cells"] == int((b.q_len[:120].astype(np.int64) * b.t_len[:120]).sum())
+    # a warm-up call, then one call over the pairs, both on the plain path
+    assert [c[0] for c in ctx.calls[1:]] == [8, 120]
+    assert all(c[1] & gsw.GSW_PLAIN for c in ctx.calls[1:])
+    batched = batched.copy()
+    batched["score1"][5] += 1
+    assert bench.run_plain(gsw, b, ctx, 120, batched)["same_records_as_batched"] is False
