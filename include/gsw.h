@@ -79,9 +79,9 @@ extern "C" {
 #define GSW_RES_CIGAR_SPACE 0x2u  /* no room for this pair's CIGAR: cigar_len = -needed */
 
 /*
- * One pair's result (Results, "Usage": the SW score, alignment location and
- * traceback of the optimal alignment, and the score and location of the
- * suboptimal alignment).  Missing values are -1: with score1 = 0 there is no
+ * One pair's result (Results, Usage: the record the paper lists for a call --
+ * the optimum's score, where it lies and how it aligns, and the second-best
+ * score with where it ends).  Missing values are -1: with score1 = 0 there is no
  * alignment and every position is -1; begins are -1 unless GSW_BEGIN or
  * GSW_CIGAR was given; score2 = 0 gives ref_end2 = -1.
  */
@@ -326,8 +326,8 @@ int gsw_fill_static(int32_t npairs, const uint8_t *q, const int64_t *q_off, cons
  * while the other workers' batches are on the GPU, so requests that arrive
  * while others are being aligned are admitted as soon as a slot frees.  Each
  * request's results are those gsw_align_batch gives for it alone.
- * Paper analogue: the library "called in multi-threaded way" by MOSAIK,
- * SCISSORS and TANGRAM (Applications).
+ * Paper analogue: MOSAIK, SCISSORS and TANGRAM calling the library from many
+ * threads at once (Applications).
  */
 typedef struct gsw_server gsw_server;
 typedef struct gsw_serve_config {

@@ -333,8 +333,8 @@ int ora_cigar(const uint8_t *qs, int32_t la, const uint8_t *ts, int32_t lb,
     return ORA_OK;
 }
 
-/* the four steps for one pair (Results, Usage: score, location and traceback of
- * the optimum; score and location of the suboptimal alignment) */
+/* the four steps for one pair (Results, Usage: the optimum's score, position
+ * and alignment; the second-best score and its end column) */
 int ora_align(const uint8_t *q, int32_t m, const uint8_t *t, int32_t n,
               const int8_t *W, int32_t A, int32_t O, int32_t X, int32_t mask_len,
               int32_t *colmax_out, uint32_t *cigar, int32_t cigar_cap, ora_result *res) {

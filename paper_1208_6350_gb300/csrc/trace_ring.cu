@@ -1,7 +1,7 @@
 // Banded global Gotoh with the traceback that emits the CIGAR, for bands too
 // wide for the anti-diagonal warp kernels ("Algorithm and implementation",
-// item (1): the banded SW between the beginning and ending positions
-// generates the detailed alignment).
+// item (1): the detailed alignment comes from a banded SW between the begin
+// and the end).
 //
 // Region.  Rows i in [1, la] (query), columns j in [1, lb] (target), row and
 // column 0 the global boundary.  The provable band is the diagonals

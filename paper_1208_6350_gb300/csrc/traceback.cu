@@ -1,7 +1,7 @@
 // Banded global Gotoh between begin and end, with the traceback that emits the
-// CIGAR on the device ("Algorithm and implementation", item (1): the banded SW
-// whose band is defined by the beginning and ending positions generates the
-// detailed alignment), for bands of at most 512 diagonals (wider bands:
+// CIGAR on the device ("Algorithm and implementation", item (1): the detailed
+// alignment comes from a banded SW whose band the begin and the end fix), for
+// bands of at most 512 diagonals (wider bands:
 // trace_ring.cu; at most 32 diagonals and 4096 rows: band.cu).
 //
 // The band is the provable one (band_range): every diagonal that can carry a
