@@ -36,8 +36,20 @@ def _inputs():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
+STAMP = LIB + ".flags"  # the nvcc flags the library was built with
+
+
+def _flags():
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+                   "-diag-suppress", "177"] + os.environ.get("GSW_NVCC_EXTRA", "").split()
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    """The library exists, is newer than every source and header, and was
+    built with the current flags (GSW_NVCC_EXTRA included)."""
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
+        return False
+    if open(STAMP).read() != " ".join(_flags()):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(f) <= t for f in _inputs())
@@ -48,8 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(OUT, exist_ok=True)
     cc = nvcc()
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-                    "-diag-suppress", "177"] + os.environ.get("GSW_NVCC_EXTRA", "").split()
+    flags = _flags()
 
     def compile_one(src):
         obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
@@ -68,6 +79,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(flags))
     return LIB
 
 

@@ -107,3 +107,12 @@ def test_context_without_a_gpu_raises():
         pytest.skip("a GPU is present")
     with pytest.raises(gsw.GswError):
         gsw.Context(0, 1 << 20)
+
+
+def test_library_is_rebuilt_when_the_nvcc_flags_change(monkeypatch):
+    _build.build()
+    assert _build.up_to_date()
+    monkeypatch.setenv("GSW_NVCC_EXTRA", "-DGSW_FLAG_STAMP_CHECK=1")
+    assert not _build.up_to_date()
+    monkeypatch.delenv("GSW_NVCC_EXTRA")
+    assert _build.up_to_date()
