@@ -274,6 +274,28 @@ def _stream_handle(stream):
     return stream.cuda_stream  # torch.cuda.Stream
 
 
+CIGAR_OPS = "MID"  # op codes 0, 1, 2 of a CIGAR word (len << 4) | op
+
+
+def pair_cigar(record, cigar_words):
+    """One pair's CIGAR as (length, op) runs: the words its record points at in
+    the batch's CIGAR buffer.  Empty when the pair has no CIGAR; raises when the
+    pair's CIGAR did not fit the buffer (GSW_RES_CIGAR_SPACE)."""
+    n = int(record["cigar_len"])
+    if int(record["flags"]) & GSW_RES_CIGAR_SPACE:
+        raise ValueError(f"the pair's CIGAR did not fit the buffer: it needs {-n} words")
+    if n <= 0:
+        return []
+    off = int(record["cigar_off"])
+    w = np.asarray(cigar_words[off: off + n]).view(np.uint32)
+    return [(int(x) >> 4, int(x) & 15) for x in w]
+
+
+def cigar_string(runs) -> str:
+    """SAM-style text of (length, op) runs, e.g. [(3, 0), (1, 2), (2, 0)] -> "3M1D2M"."""
+    return "".join(f"{n}{CIGAR_OPS[op]}" for n, op in runs)
+
+
 def pack2(codes) -> np.ndarray:
     """DNA codes 0..3 packed 4 to a byte (letter x in bits 2(x%4) of byte x/4),
     the GSW_PACKED2 layout; offsets and lengths stay in letters."""

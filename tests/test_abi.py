@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_1208_6350_gb300 import _build, gsw
@@ -116,3 +117,18 @@ def test_library_is_rebuilt_when_the_nvcc_flags_change(monkeypatch):
     assert not _build.up_to_date()
     monkeypatch.delenv("GSW_NVCC_EXTRA")
     assert _build.up_to_date()
+
+
+def test_pair_cigar_and_cigar_string():
+    rec = np.zeros(3, gsw.RESULT_DTYPE)
+    words = np.array([7, 7, (3 << 4) | 0, (1 << 4) | 2, (2 << 4) | 0, (4 << 4) | 1], np.uint32)
+    rec[0]["cigar_off"], rec[0]["cigar_len"] = 2, 4
+    rec[2]["cigar_len"], rec[2]["flags"] = -9, gsw.GSW_RES_CIGAR_SPACE
+    runs = gsw.pair_cigar(rec[0], words)
+    assert runs == [(3, 0), (1, 2), (2, 0), (4, 1)]
+    assert gsw.cigar_string(runs) == "3M1D2M4I"
+    assert gsw.pair_cigar(rec[1], words) == []           # no CIGAR
+    with pytest.raises(ValueError, match="needs 9 words"):
+        gsw.pair_cigar(rec[2], words)
+    # int32 buffers (torch's dtype for the device copy) read the same
+    assert gsw.pair_cigar(rec[0], words.view(np.int32)) == runs
