@@ -44,12 +44,18 @@ def _flags():
                    "-diag-suppress", "177"] + os.environ.get("GSW_NVCC_EXTRA", "").split()
 
 
+def _stamp() -> str:
+    # the flags that shape the code, without the include path (the same tree
+    # may be reached through a symlink)
+    return " ".join(f for f in _flags() if f != INCLUDE)
+
+
 def up_to_date() -> bool:
     """The library exists, is newer than every source and header, and was
     built with the current flags (GSW_NVCC_EXTRA included)."""
     if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return False
-    if open(STAMP).read() != " ".join(_flags()):
+    if open(STAMP).read() != _stamp():
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(f) <= t for f in _inputs())
@@ -80,7 +86,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
     with open(STAMP, "w") as f:
-        f.write(" ".join(flags))
+        f.write(_stamp())
     return LIB
 
 
