@@ -11,7 +11,10 @@ traceback (CIGAR).  GCUPS counts forward-fill cells (sum of m*n) per second.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gsw|reference]
 
 Under torchrun every rank aligns its own batch of the same size (weak
-scaling, no collective on the data path); rank 0 prints one JSON line.
+scaling, no collective on the data path); rank 0 prints one JSON line.  With
+--split the ranks share one job instead: pairs go to ranks by cells (longest
+processing time first), each rank aligns its shard, and rank 0 gathers the
+records in the job's pair order after the timed region (strong scaling).
 """
 from __future__ import annotations
 
@@ -215,6 +218,51 @@ def combine_ranks(ms, cells, dist=None, device="cpu"):
     return float(t.item()), int(round(float(c.item())))
 
 
+def lpt_partition(cells, nparts):
+    """One job split over nparts ranks by work: pairs in decreasing order of
+    cells (m * n), each to the least loaded rank so far (longest processing
+    time first).  Returns each rank's pair indices, ascending."""
+    import heapq
+    cells = np.asarray(cells, np.int64)
+    order = np.argsort(-cells, kind="stable")
+    heap = [(0, k) for k in range(nparts)]
+    parts = [[] for _ in range(nparts)]
+    for p, c in zip(order.tolist(), cells[order].tolist()):
+        load, k = heapq.heappop(heap)
+        parts[k].append(p)
+        heapq.heappush(heap, (load + c, k))
+    return [np.sort(np.asarray(x, np.int64)) for x in parts]
+
+
+def merge_shards(npairs, shards):
+    """The whole job's records from the ranks' shards (pair indices, records,
+    CIGAR words): records go back to their pairs' places and each shard's
+    CIGAR words follow the previous shard's, with cigar_off moved along."""
+    from paper_1208_6350_gb300 import gsw
+    out = np.zeros(npairs, gsw.RESULT_DTYPE)
+    words, base = [], 0
+    for idx, rec, cig in shards:
+        rec = rec.copy()
+        has = rec["cigar_len"] > 0
+        rec["cigar_off"][has] += base
+        out[idx] = rec
+        words.append(np.asarray(cig, np.uint32))
+        base += len(cig)
+    return out, (np.concatenate(words) if words else np.zeros(0, np.uint32))
+
+
+def gather_shards(dist, rank, world, idx, rec, cig, npairs):
+    """Rank 0 receives every rank's shard (no collective on the data path
+    before this: it runs after the timed region) and returns the merged
+    records and CIGAR words; the other ranks return None."""
+    payload = (np.asarray(idx, np.int64), np.asarray(rec), np.asarray(cig, np.uint32))
+    objs = [None] * world if rank == 0 else None
+    dist.gather_object(payload, objs, dst=0)
+    if rank != 0:
+        return None
+    return merge_shards(npairs, objs)
+
+
 def run_gsw(args):
     import torch
     import torch.distributed as dist
@@ -229,7 +277,17 @@ def run_gsw(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    b, wcfg = make_workload(args.workload, args.pairs, rank)
+    split = None
+    if args.split and world > 1:
+        # one job split over the ranks by cells (LPT); every rank builds the
+        # same batch and aligns its shard
+        full, wcfg = make_workload(args.workload, args.pairs, 0)
+        parts = lpt_partition(full.q_len.astype(np.int64) * full.t_len, world)
+        b = full.subset(parts[rank])
+        split = {"full": full, "idx": parts[rank],
+                 "cells_per_rank": [int((full.q_len[x].astype(np.int64) * full.t_len[x]).sum()) for x in parts]}
+    else:
+        b, wcfg = make_workload(args.workload, args.pairs, rank)
     cells = b.cells
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     # DNA arenas stay 2-bit packed (4 letters per byte) in memory; the call
@@ -304,6 +362,20 @@ def run_gsw(args):
     value = job_cells / (ms_max / 1e3) / 1e9
     rec = res.cpu().numpy().view(gsw.RESULT_DTYPE)
     work = work_summary(rec, cells)
+    split_info = None
+    if split is not None:
+        # the ranks' records concatenated on rank 0 in the job's pair order,
+        # then a random sample of the whole job checked against the oracle
+        used = int(max(0, (rec["cigar_off"] + rec["cigar_len"])[rec["cigar_len"] > 0].max(initial=0)))
+        words = cig.cpu().numpy().view(np.uint32)[:used]
+        merged = gather_shards(dist, rank, world, split["idx"], rec, words, split["full"].npairs)
+        if rank == 0:
+            whole, whole_cig = merged
+            k = check_records(split["full"], whole, whole_cig, 0) if not args.no_check else 0
+            cpr = split["cells_per_rank"]
+            split_info = {"ranks": world, "partition": "LPT over pairs sorted by cells (m x n)",
+                          "cells_per_rank": cpr, "imbalance": round(max(cpr) / (sum(cpr) / len(cpr)), 5),
+                          "gathered_pairs": int(len(whole)), "checked_pairs_of_the_whole_job": k}
 
     # e2e: the same call on host buffers (pinned), copies inside the timed region
     e2e = None
@@ -326,7 +398,8 @@ def run_gsw(args):
         return
     line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i16x2 (i32 refill)",
+            "higher_is_better": True, "scaling": "strong" if split is not None else "weak", "vs_baseline": None,
+            "dtype": "i16x2 (i32 refill)",
             "data": "synthetic (seeded; stands in for simulated short reads)",
             "config": workload_config(wcfg, b), "e2e": e2e,
             "gpu_launches": launches,
@@ -334,6 +407,8 @@ def run_gsw(args):
             "stage_ms": {k: round(v / args.steps, 3) for k, v in stage_sum.items()},
             "checked_pairs": checked, "clocks": clocks, "roofline": roof, "autotune": tune,
             "work_beside_fill": work}
+    if split_info is not None:
+        line["split"] = split_info
     if world == 1 and args.plain_pairs > 0:
         line["plain_per_pair"] = run_plain(gsw, b, ctx, args.plain_pairs, rec)
     if world == 1 and not args.no_cpu:
@@ -411,8 +486,16 @@ def run_plain(gsw, b, ctx, n_pairs, batched=None):
 
 
 def check_sample(b, res, cig, rank, k=300, max_cells=3e9):
-    import oracle
     from paper_1208_6350_gb300 import gsw
+    r = res.cpu().numpy().view(gsw.RESULT_DTYPE)
+    c = cig.cpu().numpy().view(np.uint32)
+    return check_records(b, r, c, rank, k, max_cells)
+
+
+def check_records(b, r, c, rank, k=300, max_cells=3e9):
+    """k random pairs of the batch (their cells bounded) against the oracle:
+    every field and the CIGAR; raises SystemExit on a mismatch."""
+    import oracle
     rng = np.random.default_rng(7 + rank)
     idx = rng.permutation(b.npairs)[:k]
     # keep the oracle's share of the check bounded (long pairs)
@@ -422,8 +505,6 @@ def check_sample(b, res, cig, rank, k=300, max_cells=3e9):
     s = b.subset(idx)
     ores, ocg, _ = oracle.align_batch(s.q, s.q_off, s.q_len, s.t, s.t_off, s.t_len, s.W, s.gap_open,
                                       s.gap_extend, cigar_stride=int(s.q_len.max() + s.t_len.max() + 2))
-    r = res.cpu().numpy().view(gsw.RESULT_DTYPE)
-    c = cig.cpu().numpy().view(np.uint32)
     for j, p in enumerate(idx):
         for f in ("score1", "score2", "ref_begin1", "ref_end1", "read_begin1", "read_end1", "ref_end2"):
             if int(r[f][p]) != int(ores[f][j]):
@@ -871,6 +952,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--split", action="store_true",
+                    help="N>1: split one workload over the ranks by cells (LPT) and gather the records on rank 0 "
+                         "(strong scaling) instead of one batch per rank")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
