@@ -49,6 +49,9 @@ extern "C" {
 #define GSW_EOVERFLOW (-6)    /* a score does not fit in int32 arithmetic */
 #define GSW_ENOTFOUND (-7)    /* unknown request id */
 #define GSW_ESTATE (-8)       /* call not valid in the object's current state */
+#define GSW_EINTERNAL (-9)    /* a pair failed one of the library's own consistency
+                                 checks (a bug, never expected): its record carries
+                                 GSW_RES_INTERNAL, every other record is complete */
 
 /* flags for gsw_align_batch / gsw_align_profile */
 #define GSW_BEGIN 0x1u      /* also run the reversed SW: ref_begin1, read_begin1 */
@@ -77,6 +80,13 @@ extern "C" {
 /* per-pair status bits in gsw_result.flags */
 #define GSW_RES_S32 0x1u          /* the fill ran in 32-bit lanes (16-bit overflowed or forced) */
 #define GSW_RES_CIGAR_SPACE 0x2u  /* no room for this pair's CIGAR: cigar_len = -needed */
+#define GSW_RES_INVALID 0x4u      /* gsw_fill_static only: the pair's lengths, offsets or
+                                     letters were rejected; the record is the empty one */
+#define GSW_RES_INTERNAL 0x80u    /* a consistency check of the kernels failed for this
+                                     pair (the reversed maximum differs from score1, the
+                                     traceback left its band, ...); the call returns
+                                     GSW_EINTERNAL and the pair's begins / CIGAR are
+                                     not to be trusted */
 
 /*
  * One pair's result (Results, Usage: the record the paper lists for a call --
@@ -110,6 +120,8 @@ typedef struct gsw_profile gsw_profile;
  * per-slot scratch would exceed it, fewer pairs run at a time.  One context
  * may be used by one host thread at a time.  Errors: GSW_EINVAL (bad
  * device), GSW_ECUDA, GSW_ENOMEM.
+ * Paper: none (a GPU resource holder; the paper's library keeps no state
+ * between calls beyond the query profile).
  */
 int gsw_context_create(int device, size_t mem_budget_bytes, gsw_ctx **out);
 
@@ -126,6 +138,8 @@ int gsw_context_destroy(gsw_ctx *ctx);
  * per strip), -1 = the default rule (the smallest one-strip class of 0..6, the
  * CTA class from 1792 rows).  The choice changes speed only: every class
  * gives the same results.
+ * Paper: none for the tuner itself; it chooses among layouts of the one
+ * fill the paper describes (Algorithm and implementation, item (1)).
  */
 #define GSW_TUNE_BUCKETS 32
 #define GSW_TUNE_ROWS 32
@@ -164,6 +178,8 @@ int gsw_context_set_tune(gsw_ctx *ctx, const gsw_tune *tune);
  * Errors: GSW_EINVAL (arguments, or `window` smaller than 2 x mask + overlap),
  * GSW_ENOMEM, GSW_ECUDA, GSW_ECIGAR_SPACE (records complete, CIGARs that do
  * not fit have cigar_len = -needed).
+ * Paper: Results (Performance: reads aligned against whole viral, bacterial
+ * and chromosome sequences with the library).
  */
 int gsw_align_to_reference(gsw_ctx *ctx, int32_t nreads, const uint8_t *q, const int64_t *q_off,
                            const int32_t *q_len, const uint8_t *ref, int64_t ref_len,
@@ -181,6 +197,7 @@ int gsw_align_to_reference(gsw_ctx *ctx, int32_t nreads, const uint8_t *q, const
  * ends, score2).  The pairs are generated on the device and run in chunks of
  * `chunk` pairs (0: 2^22) through the batched path; CIGAR offsets refer to the
  * whole `cigar` buffer.  Errors as gsw_align_batch.
+ * Paper: Applications (the read-overlap use of the library).
  */
 int gsw_align_all_pairs(gsw_ctx *ctx, int32_t n, const uint8_t *seq, const int64_t *off,
                         const int32_t *len, const int8_t *matrix, int32_t alphabet,
@@ -191,6 +208,7 @@ int gsw_align_all_pairs(gsw_ctx *ctx, int32_t n, const uint8_t *seq, const int64
 /* Sizes the context's persistent launches for at most `sms` SMs (0: all), so
  * that work of other streams finds free SMs while this context's kernels
  * run.  Results do not depend on it.  Errors: GSW_EINVAL (sms < 0). */
+/* Paper: none (GPU scheduling). */
 int gsw_context_set_sm_limit(gsw_ctx *ctx, int sms);
 
 /*
@@ -222,6 +240,14 @@ int gsw_context_set_sm_limit(gsw_ctx *ctx, int sms);
  * large), GSW_ENOMEM, GSW_ECUDA, GSW_ECIGAR_SPACE, GSW_EOVERFLOW (a pair whose
  * score or intermediate value exceeds int32 range cannot happen for lengths
  * below 2^24 and |W| <= 127; longer inputs are rejected with GSW_EINVAL).
+ * GSW_EINTERNAL: a pair failed one of the kernels' own consistency checks
+ * (never expected; its record carries GSW_RES_INTERNAL, the others are
+ * complete).
+ *
+ * Paper: Algorithm and implementation, item (1) (the fill with the max array
+ * and the recorded column, then the reversed SW for the begin and the banded
+ * SW for the alignment) and item (2) (the suboptimal score from the masked
+ * max array); Results, Usage (the record returned per alignment).
  */
 int gsw_align_batch(gsw_ctx *ctx, int32_t npairs,
                     const uint8_t *q, const int64_t *q_off, const int32_t *q_len,
@@ -232,9 +258,52 @@ int gsw_align_batch(gsw_ctx *ctx, int32_t npairs,
                     int32_t *colmax, const int64_t *colmax_off, void *stream);
 
 /*
+ * Library-owned results.  The paper's library returns, for each alignment, a
+ * record it allocates and the caller releases (Results, Usage: the optimum's
+ * score, ends and begins, its traceback, and the second-best score with its
+ * end).  gsw_align_batch_results runs gsw_align_batch on the same arguments
+ * (GSW_HOST_IO decides whether the inputs are host or device memory; flags
+ * and errors as gsw_align_batch, except that a CIGAR buffer is never too
+ * small: the library reserves a sixteenth of each pair's shorter sequence
+ * plus 4 words, and aligns the pairs whose CIGARs did not fit once more on
+ * their own with the room they reported) and returns the records, CIGAR words and
+ * (GSW_COLMAX) max arrays as one handle in host memory.  gsw_results_get
+ * copies record i out as a gsw_record whose pointers point into the handle;
+ * they stay valid until gsw_results_free.  On GSW_EINTERNAL the handle is
+ * still returned (the flagged records carry GSW_RES_INTERNAL); on any other
+ * error *out is NULL.  The call returns when the results are on the host.
+ */
+typedef struct gsw_results gsw_results;
+typedef struct gsw_record {
+    int32_t score1, score2;         /* optimal and suboptimal scores */
+    int32_t ref_begin1, ref_end1;   /* target begin / end of the optimum (-1 if none) */
+    int32_t read_begin1, read_end1; /* query begin / end of the optimum (-1 if none) */
+    int32_t ref_end2;               /* target end of the suboptimal score (-1 if none) */
+    uint8_t lane_bits_used;         /* 16 or 32: width of the fill lanes that gave score1 */
+    const uint32_t *cigar;          /* cigar_len CIGAR words (GSW_CIGAR), else NULL */
+    int32_t cigar_len;
+    const int32_t *colmax;          /* n max-array values (GSW_COLMAX), else NULL */
+    int32_t n;                      /* target length */
+    int32_t flags;                  /* GSW_RES_* bits */
+} gsw_record;
+
+int gsw_align_batch_results(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_off,
+                            const int32_t *q_len, const uint8_t *t, const int64_t *t_off, const int32_t *t_len,
+                            const int8_t *matrix, int32_t alphabet, int32_t gap_open, int32_t gap_extend,
+                            uint32_t flags, int32_t mask_len, void *stream, gsw_results **out);
+/* Records in the handle (0 for NULL). */
+int32_t gsw_results_count(const gsw_results *res);
+/* Copies record i (0 <= i < count) to *rec.  Errors: GSW_EINVAL. */
+int gsw_results_get(const gsw_results *res, int32_t i, gsw_record *rec);
+/* Releases the handle and everything its records point to (NULL is ignored). */
+void gsw_results_free(gsw_results *res);
+
+/*
  * ssw_init-style query profile: copies one query and its scoring onto the
  * device, where it stays until gsw_profile_destroy.  query is host memory.
  * Errors: as gsw_align_batch for the scoring arguments; GSW_ENOMEM.
+ * Paper: Algorithm and implementation (the query profile is built once per
+ * query and reused for every target, after Farrar).
  */
 int gsw_profile_create(gsw_ctx *ctx, const uint8_t *query, int32_t qlen,
                        const int8_t *matrix, int32_t alphabet, int32_t gap_open,
@@ -244,6 +313,8 @@ int gsw_profile_destroy(gsw_profile *prof);
 /*
  * Aligns the profile's query against ntargets targets (layout and memory
  * rules of gsw_align_batch's t, t_off, t_len, results, cigar, colmax).
+ * Paper: Results, Usage (one query aligned against many targets with one
+ * profile).
  */
 int gsw_align_profile(gsw_ctx *ctx, const gsw_profile *prof, int32_t ntargets,
                       const uint8_t *t, const int64_t *t_off, const int32_t *t_len,
@@ -269,6 +340,7 @@ int gsw_align_profile(gsw_ctx *ctx, const gsw_profile *prof, int32_t ntargets,
  * of a captured CUDA graph: a call repeated with the same buffers, sizes,
  * flags and scoring on a non-default stream is captured on its second run and
  * replayed from the third.  Errors: GSW_EINVAL (NULL).
+ * Paper: none (measurement).
  */
 #define GSW_NSTAGES 7
 typedef struct gsw_stats {
@@ -277,20 +349,28 @@ typedef struct gsw_stats {
     float stage_ms[8];
     int32_t graph_segments;
     int64_t cigar_words;  /* CIGAR words the call needed (all pairs) */
+    /* wide-band traceback (bands over 512 diagonals): direction words of all
+     * its pairs, the pool they are written to, and the groups of pairs the
+     * pool was used in one after the other (ring_words > ring_pool_words
+     * means at least two groups held pairs) */
+    int64_t ring_words, ring_pool_words;
+    int32_t ring_groups;
+    int32_t internal_pairs;  /* records flagged GSW_RES_INTERNAL */
 } gsw_stats;
 int gsw_last_stats(const gsw_ctx *ctx, gsw_stats *out);
 
 /*
  * Allocation-free forward fill.  The paper has no counterpart: this entry
  * exists for callers that cannot allocate device memory -- code running where
- * cudaMalloc is forbidden or unsafe (inside a host callback or a memory-pool
- * / arena owned by someone else, a hard real-time loop that must not block on
- * the allocator, or a process whose device memory was reserved up front by a
- * framework).  It needs no context and allocates nothing: the caller passes
- * inputs and outputs, and the scratch of the pairs in flight (their column
- * maxima and strip boundaries) lives in one file-scope device array of the
- * library, GSW_STATIC_SCRATCH_BYTES (about 24 MiB) per GPU that loads the
- * library, held until the process exits.
+ * cudaMalloc is forbidden or unsafe (a memory pool or arena owned by another
+ * framework, a hard real-time loop that must not block on the allocator, or a
+ * process whose device memory was reserved up front by a framework).  It must
+ * not be called from a CUDA stream callback (cudaLaunchHostFunc): it issues
+ * CUDA calls and waits for its stream.  It needs no context and allocates
+ * nothing: the caller passes inputs and outputs, and the scratch of the pairs
+ * in flight (their column maxima and strip boundaries) lives in one
+ * file-scope device array of the library, GSW_STATIC_SCRATCH_BYTES (about
+ * 24 MiB) per GPU that loads the library, held until the process exits.
  *
  * It computes what gsw_align_batch computes without GSW_BEGIN / GSW_CIGAR:
  * score1, ref_end1, read_end1, score2, ref_end2 (begins -1, no CIGAR), and
@@ -298,8 +378,12 @@ int gsw_last_stats(const gsw_ctx *ctx, gsw_stats *out);
  * gsw_align_batch, device pointers only (no GSW_HOST_IO); flags may be 0 or
  * GSW_COLMAX.  max_target_len must be at least the longest t_len of the batch
  * and at most GSW_STATIC_MAX_TARGET (1024); larger values are rejected with
- * GSW_EINVAL before any work, and a pair whose target is nevertheless longer
- * is not aligned (its record has score1 = 0) and the call returns GSW_EINVAL.
+ * GSW_EINVAL before any work.  The kernel checks every pair before touching
+ * its data, as gsw_align_batch does: a pair with a length outside [0, 2^24),
+ * a negative offset (colmax_off too, with GSW_COLMAX), a target longer than
+ * GSW_STATIC_MAX_TARGET or a letter code >= alphabet is not aligned; its
+ * record is the empty one (score1 = 0, positions -1) flagged GSW_RES_INVALID,
+ * and the call returns GSW_EINVAL after every other pair is done.
  *
  * The first call on a device looks up the device address of the array (and
  * sets the kernel's shared-memory limit); make that first call before any
@@ -374,6 +458,12 @@ int gsw_serve_submit(gsw_server *srv, int32_t npairs, const uint8_t *q, const in
  * is kept).  Thread-safe with submit. */
 int gsw_serve_poll(gsw_server *srv, uint64_t req_id, int32_t timeout_us, gsw_result *results,
                    uint32_t *cigar, int64_t cigar_capacity, int64_t *cigar_words);
+
+/* gsw_serve_poll returning the request's records as a library-owned handle
+ * (see gsw_align_batch_results; no max arrays); *out is set on GSW_OK and
+ * GSW_EINTERNAL, and the request is forgotten.  Other returns as
+ * gsw_serve_poll (GSW_ETIMEDOUT: poll again). */
+int gsw_serve_poll_results(gsw_server *srv, uint64_t req_id, int32_t timeout_us, gsw_results **out);
 
 /* Times of one request on the server's monotonic clock (seconds since
  * gsw_serve_create): queued by submit, taken into a batch by a worker, and

@@ -54,14 +54,14 @@ extern "C" int gsw_align_all_pairs(gsw_ctx *ctx, int32_t n, const uint8_t *seq, 
                                    int32_t gap_extend, uint32_t flags, int32_t mask_len, int64_t chunk,
                                    gsw_result *results, uint32_t *cigar, int64_t cigar_capacity, void *stream) {
     using namespace gsw;
-    if (!ctx || n < 0 || chunk < 0 || n > 65536) return GSW_EINVAL;
-    if (flags & ~(GSW_BEGIN | GSW_CIGAR | GSW_HOST_IO | GSW_PACKED2)) return GSW_EINVAL;
+    if (!ctx || n < 0 || chunk < 0 || n > 65536) return set_err(GSW_EINVAL, "context, n (<= 65,536) or chunk");
+    if (flags & ~(GSW_BEGIN | GSW_CIGAR | GSW_HOST_IO | GSW_PACKED2)) return set_err(GSW_EINVAL, "unknown flag bits 0x%x", flags);
     const long long total = (long long)n * (n - 1) / 2;
     if (total == 0) return GSW_OK;
-    if (!seq || !off || !len || !results) return GSW_EINVAL;
-    if ((flags & GSW_CIGAR) && !cigar && cigar_capacity > 0) return GSW_EINVAL;
+    if (!seq || !off || !len || !results) return set_err(GSW_EINVAL, "NULL input or result pointer");
+    if ((flags & GSW_CIGAR) && !cigar && cigar_capacity > 0) return set_err(GSW_EINVAL, "cigar is NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaSetDevice(context_device(ctx)) != cudaSuccess) return GSW_ECUDA;
+    if (cudaSetDevice(context_device(ctx)) != cudaSuccess) return set_err(GSW_ECUDA, "cudaSetDevice");
     const bool hio = (flags & GSW_HOST_IO) != 0;
     const long long C = chunk > 0 ? std::min<long long>(chunk, 1LL << 30) : (1LL << 22);
     const uint32_t f = flags & (GSW_BEGIN | GSW_CIGAR | GSW_PACKED2);
@@ -81,7 +81,7 @@ extern "C" int gsw_align_all_pairs(gsw_ctx *ctx, int32_t n, const uint8_t *seq, 
         // the sequences once on the device; the chunks' results go back to the host
         int64_t ext = 0;
         for (int r = 0; r < n; r++) {
-            if (len[r] < 0 || off[r] < 0) return GSW_EINVAL;
+            if (len[r] < 0 || off[r] < 0) return set_err(GSW_EINVAL, "sequence %d: negative length or offset", r);
             ext = std::max<int64_t>(ext, off[r] + len[r]);
         }
         const size_t bytes = (f & GSW_PACKED2) ? (size_t)(ext + 3) / 4 : (size_t)ext;
@@ -115,8 +115,8 @@ extern "C" int gsw_align_all_pairs(gsw_ctx *ctx, int32_t n, const uint8_t *seq, 
         const int64_t gcap = (f & GSW_CIGAR) ? std::max<int64_t>(cigar_capacity - cig_used, 0) : 0;
         int r = gsw_align_batch(ctx, (int32_t)cnt, S, qo, ql, S, to, tl, matrix, alphabet, gap_open, gap_extend, f,
                                 mask_len, R, G, gcap, nullptr, nullptr, stream);
-        if (r == GSW_ECIGAR_SPACE) {
-            rc_cigar = r;
+        if (r == GSW_ECIGAR_SPACE || r == GSW_EINTERNAL) {  // records complete: carry on
+            if (rc_cigar != GSW_EINTERNAL) rc_cigar = r;
             r = GSW_OK;
         }
         if (r != GSW_OK) {

@@ -15,9 +15,10 @@
 using namespace gsw;
 
 namespace {
-
 thread_local char g_err[512] = "";
+}  // namespace
 
+namespace gsw {
 int set_err(int code, const char *fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
@@ -25,6 +26,31 @@ int set_err(int code, const char *fmt, ...) {
     va_end(ap);
     return code;
 }
+
+int make_scoring(const int8_t *matrix, int32_t A, int32_t O, int32_t X, Scoring *sc) {
+    if (!matrix) return set_err(GSW_EINVAL, "matrix is NULL");
+    if (A < 1 || A > kMaxAlpha) return set_err(GSW_EINVAL, "alphabet %d not in [1, %d]", A, kMaxAlpha);
+    if (X < 0 || O < X || O > 255) return set_err(GSW_EINVAL, "need 0 <= gap_extend <= gap_open <= 255 (got %d, %d)", O, X);
+    std::memset(sc, 0, sizeof(*sc));
+    sc->A = A;
+    sc->O = O;
+    sc->X = X;
+    int wmax = -128, wmin = 127;
+    for (int i = 0; i < A * A; i++) {
+        if (matrix[i] < -127) return set_err(GSW_EINVAL, "matrix entry %d out of [-127, 127]", matrix[i]);
+        sc->W[i] = matrix[i];
+        wmax = std::max<int>(wmax, matrix[i]);
+        wmin = std::min<int>(wmin, matrix[i]);
+    }
+    sc->wmax = wmax;
+    sc->wmin = wmin;
+    sc->dna4 = A == 4;
+    std::memset(sc->fill_class, -1, sizeof(sc->fill_class));
+    return GSW_OK;
+}
+}  // namespace gsw
+
+namespace {
 
 #define CUDA_TRY(x)                                                                            \
     do {                                                                                       \
@@ -54,6 +80,8 @@ struct PipeState {
     int max_blocks = 0;
     long long *ring_prefix = nullptr;
     int *ring_final = nullptr, *ring_group = nullptr;
+    long long ring_words = 0, ring_pool = 0;  // wide-band traceback sizes (stats)
+    int ring_groups = 0;
     int launches = 0;
     int stage_done[GSW_NSTAGES] = {};
 };
@@ -94,6 +122,9 @@ struct gsw_ctx {
     int stage_done[GSW_NSTAGES] = {};
     int graph_segments = 0;  // segments of the last call replayed from a graph
     long long cigar_words = 0;  // CIGAR words the last call needed
+    long long internal = 0;     // records of the last call flagged kResInternal
+    long long ring_words = 0, ring_pool = 0;  // wide-band traceback of the last call
+    int ring_groups = 0;
 };
 
 struct gsw_profile {
@@ -113,9 +144,6 @@ int ensure(gsw_ctx *ctx, DevBuf &b, size_t need) {
     if (need <= b.bytes) return GSW_OK;
     if (ctx->capturing) return GSW_ESTATE;  // the segment runs without a graph
     need = std::max<size_t>(need, 256);
-    if (std::getenv("GSW_DEBUG_GRAPHS"))
-        std::fprintf(stderr, "gsw: buffer at +%td grows %zu -> %zu\n",
-                     reinterpret_cast<const char *>(&b) - reinterpret_cast<const char *>(ctx), b.bytes, need);
     if (b.p) {
         CUDA_TRY(cudaFreeAsync(b.p, ctx->st));
         ctx->used -= b.bytes;
@@ -161,32 +189,12 @@ int ensure2(gsw_ctx *ctx, DevBuf &a, size_t na, DevBuf &b, size_t nb) {
     return rc != GSW_OK ? rc : ensure(ctx, b, nb);
 }
 
-int make_scoring(const int8_t *matrix, int32_t A, int32_t O, int32_t X, Scoring *sc) {
-    if (!matrix) return set_err(GSW_EINVAL, "matrix is NULL");
-    if (A < 1 || A > kMaxAlpha) return set_err(GSW_EINVAL, "alphabet %d not in [1, %d]", A, kMaxAlpha);
-    if (X < 0 || O < X || O > 255) return set_err(GSW_EINVAL, "need 0 <= gap_extend <= gap_open <= 255 (got %d, %d)", O, X);
-    std::memset(sc, 0, sizeof(*sc));
-    sc->A = A;
-    sc->O = O;
-    sc->X = X;
-    int wmax = -128, wmin = 127;
-    for (int i = 0; i < A * A; i++) {
-        if (matrix[i] < -127) return set_err(GSW_EINVAL, "matrix entry %d out of [-127, 127]", matrix[i]);
-        sc->W[i] = matrix[i];
-        wmax = std::max<int>(wmax, matrix[i]);
-        wmin = std::min<int>(wmin, matrix[i]);
-    }
-    sc->wmax = wmax;
-    sc->wmin = wmin;
-    sc->dna4 = A == 4;
-    std::memset(sc->fill_class, -1, sizeof(sc->fill_class));
-    return GSW_OK;
-}
 
 // device scratch layout of ctx->misc (64-bit words)
 enum MiscSlot {
     kMiscTraceHead = 0,
     kMiscCursor = 1,
+    kMiscInternal = 2,  // records flagged kResInternal (counted after the pipeline)
     kMiscValid = 3,
     kMiscNeed = 4,   // 2 words: anti-diagonal traceback (direction words, op words per pair)
     kMiscRing = 6,   // 3 words: wide-band traceback (total words, max words of a pair, max op words)
@@ -259,11 +267,6 @@ int run_segment(gsw_ctx *ctx, GraphSeg &g, const std::vector<uint8_t> &key, cuda
         return GSW_OK;
     }
     const bool capture = st != nullptr && g.seen && g.key == key;
-    if (!capture && g.seen && std::getenv("GSW_DEBUG_GRAPHS")) {
-        size_t at = 0;
-        while (at < key.size() && at < g.key.size() && key[at] == g.key[at]) at++;
-        std::fprintf(stderr, "gsw: segment key changed at byte %zu of %zu\n", at, key.size());
-    }
     if (g.exec) {
         cudaGraphExecDestroy(g.exec);
         g.exec = nullptr;
@@ -290,10 +293,7 @@ int run_segment(gsw_ctx *ctx, GraphSeg &g, const std::vector<uint8_t> &key, cuda
         return GSW_OK;
     }
     if (gr) cudaGraphDestroy(gr);
-    const cudaError_t le = cudaGetLastError();
-    if (std::getenv("GSW_DEBUG_GRAPHS"))
-        std::fprintf(stderr, "gsw: segment not captured (body %d, end capture %s, last %s)\n", rc,
-                     cudaGetErrorString(e), cudaGetErrorString(le));
+    cudaGetLastError();  // a failed capture leaves no error for the eager run
     g.seen = false;
     state = before;
     return body();
@@ -556,6 +556,9 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
                         CUDA_TRY(launch_ring_group(ra, ctx->sms, st));
                         S.launches += 4;
                     }
+                    S.ring_words = (long long)ring_total;
+                    S.ring_pool = (long long)ring_pool;
+                    S.ring_groups = (int)groups;
                 }
             }
             S.stage_done[5] = 1;
@@ -567,6 +570,9 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
         GSW_TRY(mark(ctx, 6, st));
     }
     ctx->launches += S.launches;
+    ctx->ring_words = S.ring_words;
+    ctx->ring_pool = S.ring_pool;
+    ctx->ring_groups = S.ring_groups;
     for (int k = 0; k < GSW_NSTAGES; k++) ctx->stage_done[k] |= S.stage_done[k];
     return GSW_OK;
 }
@@ -602,6 +608,9 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
     ctx->launches = 0;
     ctx->graph_segments = 0;
     ctx->cigar_words = 0;
+    ctx->internal = 0;
+    ctx->ring_words = ctx->ring_pool = 0;
+    ctx->ring_groups = 0;
     for (int k = 0; k < GSW_NSTAGES; k++) ctx->stage_done[k] = 0;
     ctx->timing = (flags & GSW_TIMING) != 0;
     if (ctx->timing && !ctx->ev[0])
@@ -720,15 +729,17 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
             bv.t = (const uint8_t *)ctx->io_t.p;
         }
     }
-    CUDA_TRY(cudaMemsetAsync(misc + kMiscCursor, 0, sizeof(unsigned long long), st));
+    CUDA_TRY(cudaMemsetAsync(misc + kMiscCursor, 0, 2 * sizeof(unsigned long long), st));  // cursor, internal
     CUDA_TRY(launch_validate(bv, sc, reinterpret_cast<int32_t *>(misc + kMiscValid), st));
     ctx->launches += 1;
     GSW_TRY(run_pipeline(ctx, bv, sc, st, maxm, maxn));
 
-    // completion: invalid letters, CIGAR space
+    // completion: invalid letters, internal checks, CIGAR space
+    CUDA_TRY(launch_count_flag(bv.res, npairs, kResInternal, misc + kMiscInternal, st));
+    ctx->launches += 1;
     unsigned long long *hs = reinterpret_cast<unsigned long long *>(ctx->host_small);
-    CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscCursor, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemcpyAsync(hs + 1, misc + kMiscValid, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hs, misc + kMiscCursor, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hs + 2, misc + kMiscValid, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     if (hio) {
         CUDA_TRY(cudaMemcpyAsync(results, bv.res, sizeof(gsw_result) * npairs, cudaMemcpyDeviceToHost, st));
         if (flags & GSW_COLMAX)
@@ -736,7 +747,8 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
     }
     CUDA_TRY(cudaStreamSynchronize(st));
     const unsigned long long used_words = hs[0];
-    const int bad_letters = (int)(hs[1] & 0xFFFFFFFFu);
+    const unsigned long long internal = hs[1];
+    const int bad_letters = (int)(hs[2] & 0xFFFFFFFFu);
     ctx->cigar_words = (flags & GSW_CIGAR) ? (long long)used_words : 0;
     if (hio && (flags & GSW_CIGAR) && cigar_capacity > 0) {
         const size_t n = (size_t)std::min<unsigned long long>(used_words, (unsigned long long)cigar_capacity);
@@ -745,11 +757,17 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
             CUDA_TRY(cudaStreamSynchronize(st));
         }
     }
-    if (bad_letters) return set_err(GSW_EINVAL, "a letter code is >= the alphabet size (%d)", sc.A);
-    if ((flags & GSW_CIGAR) && used_words > (unsigned long long)cigar_capacity)
+    ctx->internal = (long long)internal;
+    switch (batch_status(bad_letters, internal, (flags & GSW_CIGAR) != 0, used_words, cigar_capacity)) {
+    case GSW_EINVAL: return set_err(GSW_EINVAL, "a letter code is >= the alphabet size (%d)", sc.A);
+    case GSW_EINTERNAL:
+        return set_err(GSW_EINTERNAL, "%llu pairs failed a consistency check of the kernels (GSW_RES_INTERNAL)",
+                       internal);
+    case GSW_ECIGAR_SPACE:
         return set_err(GSW_ECIGAR_SPACE, "CIGAR words needed %llu > capacity %lld", used_words,
                        (long long)cigar_capacity);
-    return GSW_OK;
+    default: return GSW_OK;
+    }
 }
 
 // Baseline without batching: every pair goes through its own launch
@@ -764,18 +782,24 @@ int plain_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
     if ((flags & GSW_CIGAR) && (flags & GSW_HOST_IO) == 0)
         return set_err(GSW_EINVAL, "GSW_PLAIN with GSW_CIGAR needs GSW_HOST_IO (per-pair CIGAR offsets)");
     int64_t cig_used = 0;
+    int rc_internal = GSW_OK;
     for (int32_t p = 0; p < npairs; p++) {
         uint32_t *cg = cigar ? cigar + cig_used : nullptr;
         const int64_t cap = cigar ? cigar_capacity - cig_used : 0;
         int rc = batch_impl(ctx, 1, q, q_off + p, q_len + p, t, t_off + p, t_len + p, sc, flags, mask_len,
                             results + p, cg, cap, colmax, colmax_off ? colmax_off + p : nullptr, st);
+        if (rc == GSW_EINTERNAL) {  // the record is complete apart from its flagged parts
+            rc_internal = rc;
+            rc = GSW_OK;
+        }
         if (rc != GSW_OK) return rc;
         if ((flags & GSW_CIGAR) && results[p].cigar_len > 0) {
             results[p].cigar_off += cig_used;
             cig_used += results[p].cigar_len;
         }
     }
-    return GSW_OK;
+    return rc_internal != GSW_OK ? set_err(rc_internal, "pairs failed a consistency check (GSW_RES_INTERNAL)")
+                                 : GSW_OK;
 }
 
 }  // namespace
@@ -795,6 +819,7 @@ const char *gsw_strerror(int code) {
     case GSW_EOVERFLOW: return "score overflow";
     case GSW_ENOTFOUND: return "not found";
     case GSW_ESTATE: return "invalid state";
+    case GSW_EINTERNAL: return "internal consistency check failed";
     default: return "unknown error";
     }
 }
@@ -807,6 +832,10 @@ int gsw_last_stats(const gsw_ctx *ctx, gsw_stats *out) {
     out->kernel_launches = ctx->launches;
     out->graph_segments = ctx->graph_segments;
     out->cigar_words = ctx->cigar_words;
+    out->ring_words = ctx->ring_words;
+    out->ring_pool_words = ctx->ring_pool;
+    out->ring_groups = ctx->ring_groups;
+    out->internal_pairs = (int32_t)ctx->internal;
     if (!ctx->timing || !ctx->ev[0]) return GSW_OK;
     out->timed = 1;
     // stage k spans events k..k+1, except: [0] = e0..e1, [1] = e1..e2, [2] = e2..e3,

@@ -1269,17 +1269,33 @@ __global__ void __launch_bounds__(kBlock) k_fill_static(BatchView b, Scoring sc,
     for (int base = gwarp * 2; base < b.npairs; base += nwarps * 2) {
         const int pair = base + g;
         const bool has = pair < b.npairs;
-        const int m = has ? b.q_len[pair] : 0, n = has ? b.t_len[pair] : 0;
-        const bool too_long = has && n > kStaticMaxTarget;
-        const bool empty = has && !too_long && (m <= 0 || n <= 0);
-        const bool run = has && !too_long && !empty;
-        if (has && k == 0 && (too_long || empty)) {
+        // the checks gsw_align_batch makes before any fill, made here by
+        // each group before its pair's first access: lengths in [0, 2^24),
+        // offsets >= 0 and targets within the slot; then the letter codes
+        int m = 0, n = 0;
+        bool bad = false;
+        if (has) {
+            m = b.q_len[pair];
+            n = b.t_len[pair];
+            bad = (uint32_t)m >= (1u << 24) || (uint32_t)n >= (1u << 24) || b.q_off[pair] < 0 || b.t_off[pair] < 0 ||
+                  ((b.flags & GSW_COLMAX) && b.colmax_off[pair] < 0) || n > kStaticMaxTarget;
+        }
+        if (has && !bad) {
+            const uint8_t *qp = b.q + b.q_off[pair], *tp = b.t + b.t_off[pair];
+            int found = 0;
+            for (int i = k; i < m; i += 16) found |= qp[i] >= sc.A;
+            for (int j = k; j < n; j += 16) found |= tp[j] >= sc.A;
+            bad = __any_sync(gmask, found) != 0;
+        }
+        const bool empty = has && !bad && (m == 0 || n == 0);
+        const bool run = has && !bad && !empty;
+        if (has && k == 0 && (bad || empty)) {
             gsw_result *rp = b.res + pair;
             rp->score1 = 0; rp->score2 = 0; rp->ref_begin1 = -1; rp->ref_end1 = -1; rp->read_begin1 = -1;
             rp->read_end1 = -1; rp->ref_end2 = -1; rp->cigar_len = 0; rp->cigar_off = -1;
-            rp->flags = too_long ? kResInternal : 0;
+            rp->flags = bad ? kResInvalid : 0;
             rp->reserved = 0;
-            if (too_long) atomicOr(err, 1);
+            if (bad) atomicOr(err, 1);
         }
         if (empty && (b.flags & GSW_COLMAX))
             for (int j = k; j < n; j += 16) b.colmax[b.colmax_off[pair] + j] = 0;
@@ -1314,30 +1330,22 @@ extern "C" int gsw_fill_static(int32_t npairs, const uint8_t *q, const int64_t *
                                int32_t gap_extend, uint32_t flags, int32_t mask_len, gsw_result *results,
                                int32_t *colmax, const int64_t *colmax_off, void *stream) {
     using namespace gsw;
-    if (npairs < 0 || (flags & ~(uint32_t)GSW_COLMAX)) return GSW_EINVAL;
-    if (max_target_len < 0 || max_target_len > kStaticMaxTarget) return GSW_EINVAL;
-    if (!matrix || alphabet < 1 || alphabet > kMaxAlpha || gap_extend < 0 || gap_open < gap_extend || gap_open > 255)
-        return GSW_EINVAL;
-    if (npairs == 0) return GSW_OK;
-    if (!q || !q_off || !q_len || !t || !t_off || !t_len || !results) return GSW_EINVAL;
-    if ((flags & GSW_COLMAX) && (!colmax || !colmax_off)) return GSW_EINVAL;
+    if (npairs < 0) return set_err(GSW_EINVAL, "npairs < 0");
+    if (flags & ~(uint32_t)GSW_COLMAX) return set_err(GSW_EINVAL, "flags other than GSW_COLMAX (0x%x)", flags);
+    if (max_target_len < 0 || max_target_len > kStaticMaxTarget)
+        return set_err(GSW_EINVAL, "max_target_len %d not in [0, %d]", max_target_len, kStaticMaxTarget);
+    if (mask_len > (1 << 30)) return set_err(GSW_EINVAL, "mask_len too large");
     Scoring sc;
-    memset(&sc, 0, sizeof(sc));
-    sc.A = alphabet;
-    sc.O = gap_open;
-    sc.X = gap_extend;
-    int wmax = -128, wmin = 127;
-    for (int i = 0; i < alphabet * alphabet; i++) {
-        if (matrix[i] < -127) return GSW_EINVAL;
-        sc.W[i] = matrix[i];
-        wmax = matrix[i] > wmax ? matrix[i] : wmax;
-        wmin = matrix[i] < wmin ? matrix[i] : wmin;
+    {
+        const int e = make_scoring(matrix, alphabet, gap_open, gap_extend, &sc);
+        if (e != GSW_OK) return e;
     }
-    sc.wmax = wmax;
-    sc.wmin = wmin;
-    sc.dna4 = alphabet == 4;
+    if (npairs == 0) return GSW_OK;
+    if (!q || !q_off || !q_len || !t || !t_off || !t_len || !results)
+        return set_err(GSW_EINVAL, "NULL input or result pointer");
+    if ((flags & GSW_COLMAX) && (!colmax || !colmax_off)) return set_err(GSW_EINVAL, "colmax output missing");
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GSW_ECUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return set_err(GSW_ECUDA, "no current device");
     const size_t per_warp = (size_t)prof_words(8, true, sc.dna4 != 0, alphabet) * 32 * sizeof(uint32_t);
     int wpb = (int)((200u << 10) / per_warp);
     wpb = wpb > 4 ? 4 : (wpb < 1 ? 1 : wpb);
@@ -1350,12 +1358,13 @@ extern "C" int gsw_fill_static(int32_t npairs, const uint8_t *q, const int64_t *
         StaticSetup &su = g_static_setup[dev];
         if (!su.done) {
             void *ptr = nullptr;
-            if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess) return GSW_ECUDA;
+            const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+            if (e != cudaSuccess) return set_err(GSW_ECUDA, "scratch address: %s", cudaGetErrorString(e));
             if (cudaFuncSetAttribute(k_fill_static<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10) !=
                     cudaSuccess ||
                 cudaFuncSetAttribute(k_fill_static<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10) !=
                     cudaSuccess)
-                return GSW_ECUDA;
+                return set_err(GSW_ECUDA, "kernel shared-memory limit");
             su.ptr = static_cast<uint8_t *>(ptr);
             su.done = true;
         }
@@ -1373,16 +1382,24 @@ extern "C" int gsw_fill_static(int32_t npairs, const uint8_t *q, const int64_t *
     bv.colmax_off = colmax_off;
     cudaStream_t st = (cudaStream_t)stream;
     // the error word must start at zero; the slots need no clearing
-    if (cudaMemsetAsync(scratch + kStaticErrOff, 0, sizeof(int32_t), st) != cudaSuccess) return GSW_ECUDA;
+    if (cudaMemsetAsync(scratch + kStaticErrOff, 0, sizeof(int32_t), st) != cudaSuccess)
+        return set_err(GSW_ECUDA, "clearing the error word");
     const int grid = kStaticWarps / wpb;
     if (sc.dna4) k_fill_static<true><<<grid, wpb * 32, smem, st>>>(bv, sc, scratch, (int)(per_warp / 4));
     else k_fill_static<false><<<grid, wpb * 32, smem, st>>>(bv, sc, scratch, (int)(per_warp / 4));
-    if (cudaGetLastError() != cudaSuccess) return GSW_ECUDA;
+    {
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return set_err(GSW_ECUDA, "fill launch: %s", cudaGetErrorString(e));
+    }
     int32_t err = 0;
     if (cudaMemcpyAsync(&err, scratch + kStaticErrOff, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
-        return GSW_ECUDA;
-    return err ? GSW_EINVAL : GSW_OK;
+        return set_err(GSW_ECUDA, "error-word readback");
+    if (err)
+        return set_err(GSW_EINVAL, "pairs with a length outside [0, 2^24), a target over %d letters, a negative "
+                                   "offset or a letter code >= %d (records flagged GSW_RES_INVALID)",
+                       kStaticMaxTarget, alphabet);
+    return GSW_OK;
 }
 
 namespace gsw {

@@ -5,8 +5,20 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <vector>
 
 #include "gsw.h"
+
+// Results owned by the library (gsw_align_batch_results, gsw_serve_poll_results):
+// host copies of the records, the CIGAR words they index and, with GSW_COLMAX,
+// the max arrays; released by gsw_results_free.
+struct gsw_results {
+    std::vector<gsw_result> res;
+    std::vector<uint32_t> cigar;
+    std::vector<int32_t> colmax;
+    std::vector<int64_t> colmax_off;  // per pair, into colmax (empty without GSW_COLMAX)
+    std::vector<int32_t> t_len;       // per pair
+};
 
 namespace gsw {
 
@@ -141,7 +153,8 @@ struct FillLaunch {
 
 // internal per-pair bits (besides the public GSW_RES_*)
 constexpr int32_t kResPendingS32 = 0x40;  // 16-bit fill overflowed: refill in 32-bit lanes
-constexpr int32_t kResInternal = 0x80;    // a consistency check failed (should never happen)
+constexpr int32_t kResInternal = GSW_RES_INTERNAL;  // a consistency check failed (should never happen)
+constexpr int32_t kResInvalid = GSW_RES_INVALID;    // gsw_fill_static: the pair's inputs were rejected
 constexpr int32_t kResPendingTrace = 0x100;  // band too wide for one thread: warp traceback
 
 // The thread-per-pair band kernel handles bands up to this many diagonals and
@@ -325,6 +338,26 @@ __host__ __device__ inline int trace_class(int la, int lb, int score1, const Sco
 }
 
 // stage launchers (host side, enqueue on `st`)
+// Status of a completed batch from what its kernels counted, in order of
+// precedence: letter codes outside the alphabet (GSW_EINVAL), records that
+// failed a consistency check (GSW_EINTERNAL), CIGAR words beyond the
+// caller's capacity (GSW_ECIGAR_SPACE, only with GSW_CIGAR).
+__host__ __device__ inline int batch_status(int bad_letters, unsigned long long internal, bool cigar,
+                                            unsigned long long cigar_words, long long cigar_capacity) {
+    if (bad_letters) return GSW_EINVAL;
+    if (internal) return GSW_EINTERNAL;
+    if (cigar && cigar_words > (unsigned long long)(cigar_capacity < 0 ? 0 : cigar_capacity)) return GSW_ECIGAR_SPACE;
+    return GSW_OK;
+}
+
+// Host helpers of the runtime (api.cu): the calling thread's error detail,
+// the scoring checks shared by every entry point, and the count of records
+// flagged kResInternal (one small kernel and a readback on `st`).
+int set_err(int code, const char *fmt, ...);
+int make_scoring(const int8_t *matrix, int32_t A, int32_t O, int32_t X, Scoring *sc);
+cudaError_t launch_count_flag(const gsw_result *res, int32_t n, int32_t flag, unsigned long long *count,
+                              cudaStream_t st);
+
 int fill_block_threads();
 // largest number of slots (pairs in flight) of any variant's launch
 int fill_slots(const Scoring &sc, int sms);

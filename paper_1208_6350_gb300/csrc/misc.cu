@@ -60,6 +60,15 @@ __global__ void k_batch_stats(const int64_t *q_off, const int32_t *q_len, const 
     }
 }
 
+// number of records whose flags have `flag` set
+__global__ void k_count_flag(const gsw_result *res, int32_t n, int32_t flag, unsigned long long *count) {
+    unsigned c = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        c += (res[i].flags & flag) ? 1u : 0u;
+    c = __reduce_add_sync(0xFFFFFFFFu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+}
+
 __global__ void k_unpack2(const uint8_t *in, uint8_t *out, long long nletters) {
     const long long groups = (nletters + 15) / 16;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < groups;
@@ -111,6 +120,16 @@ cudaError_t launch_batch_stats(const int64_t *q_off, const int32_t *q_len, const
         int blocks = (n + 255) / 256;
         blocks = blocks > 1024 ? 1024 : blocks;
         k_batch_stats<<<blocks, 256, 0, st>>>(q_off, q_len, t_off, t_len, n, out5);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_flag(const gsw_result *res, int32_t n, int32_t flag, unsigned long long *count,
+                              cudaStream_t st) {
+    if (n > 0) {
+        int blocks = (n + 255) / 256;
+        blocks = blocks > 1024 ? 1024 : blocks;
+        k_count_flag<<<blocks, 256, 0, st>>>(res, n, flag, count);
     }
     return cudaGetLastError();
 }

@@ -242,17 +242,21 @@ extern "C" int gsw_align_to_reference(gsw_ctx *ctx, int32_t nreads, const uint8_
                                       uint32_t flags, int32_t mask_len, int64_t window, gsw_result *results,
                                       uint32_t *cigar, int64_t cigar_capacity, void *stream) {
     using namespace gsw;
-    if (!ctx || nreads < 0 || ref_len < 0 || ref_len >= (1LL << 31) || !matrix || window < 0) return GSW_EINVAL;
-    if (flags & ~(GSW_BEGIN | GSW_CIGAR | GSW_HOST_IO)) return GSW_EINVAL;
+    if (!ctx || nreads < 0 || ref_len < 0 || ref_len >= (1LL << 31) || !matrix || window < 0)
+        return set_err(GSW_EINVAL, "context, read count, reference length (< 2^31), matrix or window");
+    if (flags & ~(GSW_BEGIN | GSW_CIGAR | GSW_HOST_IO)) return set_err(GSW_EINVAL, "unknown flag bits 0x%x", flags);
     if (nreads == 0) return GSW_OK;
-    if (!q || !q_off || !q_len || !results || (ref_len > 0 && !ref)) return GSW_EINVAL;
-    if ((flags & GSW_CIGAR) && !cigar && cigar_capacity > 0) return GSW_EINVAL;
-    if (alphabet < 1 || alphabet > kMaxAlpha || gap_extend < 0 || gap_open < gap_extend || gap_open > 255)
-        return GSW_EINVAL;
+    if (!q || !q_off || !q_len || !results || (ref_len > 0 && !ref)) return set_err(GSW_EINVAL, "NULL input or result pointer");
+    if ((flags & GSW_CIGAR) && !cigar && cigar_capacity > 0) return set_err(GSW_EINVAL, "cigar is NULL");
+    {
+        Scoring chk;
+        const int e = make_scoring(matrix, alphabet, gap_open, gap_extend, &chk);
+        if (e != GSW_OK) return e;
+    }
     int wmax = -128;
     for (int i = 0; i < alphabet * alphabet; i++) wmax = std::max<int>(wmax, matrix[i]);
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaSetDevice(context_device(ctx)) != cudaSuccess) return GSW_ECUDA;
+    if (cudaSetDevice(context_device(ctx)) != cudaSuccess) return set_err(GSW_ECUDA, "cudaSetDevice");
     const bool hio = (flags & GSW_HOST_IO) != 0;
     // read lengths on the host (the window geometry depends on the longest)
     std::vector<int32_t> hql(nreads);
@@ -263,12 +267,12 @@ extern "C" int gsw_align_to_reference(gsw_ctx *ctx, int32_t nreads, const uint8_
     } else if (cudaMemcpyAsync(hql.data(), q_len, 4 * (size_t)nreads, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                cudaStreamSynchronize(st) != cudaSuccess) {
         // read on the call's stream: work queued there before the call may write the lengths
-        return GSW_ECUDA;
+        return set_err(GSW_ECUDA, "read-length readback");
     }
     int maxm = 0;
     int64_t qext = 0;
     for (int r = 0; r < nreads; r++) {
-        if (hql[r] < 0 || hql[r] >= (1 << 24)) return GSW_EINVAL;
+        if (hql[r] < 0 || hql[r] >= (1 << 24)) return set_err(GSW_EINVAL, "read %d: length out of [0, 2^24)", r);
         maxm = std::max(maxm, hql[r]);
         if (hio) qext = std::max<int64_t>(qext, hqo[r] + hql[r]);
     }
@@ -279,10 +283,11 @@ extern "C" int gsw_align_to_reference(gsw_ctx *ctx, int32_t nreads, const uint8_
     // the mask around an end meets at most 2 windows when S > 2L + V
     const long long Lmax = mask_len >= 0 ? mask_len : std::max(maxm / 2, 15);
     const long long Smin = 2 * Lmax + g.V + 1;
-    if (window > 0 && window < Smin) return GSW_EINVAL;
+    if (window > 0 && window < Smin) return set_err(GSW_EINVAL, "window %lld < 2 x mask + overlap + 1 = %lld", (long long)window, Smin);
     g.S = window > 0 ? window : std::max({65536LL, 4 * g.V, Smin});
     g.K = (int)std::max(1LL, (ref_len + g.S - 1) / g.S);
-    if ((long long)nreads * g.K >= (1LL << 31) || g.S + g.V >= (1LL << 24)) return GSW_EINVAL;
+    if ((long long)nreads * g.K >= (1LL << 31) || g.S + g.V >= (1LL << 24))
+        return set_err(GSW_EINVAL, "reads x windows >= 2^31 or window + overlap >= 2^24");
     const long long np = (long long)nreads * g.K;
 
     // device buffers (plain allocations for this call)
@@ -294,6 +299,7 @@ extern "C" int gsw_align_to_reference(gsw_ctx *ctx, int32_t nreads, const uint8_
     int *sec = nullptr;
     long long *sec_col = nullptr;
     uint32_t *dcig = nullptr;
+    unsigned long long *nflag = nullptr, hflag = 0;
     const long long cm_stride = (g.S + g.V + 3) / 4 * 4;
     const long long nm = (long long)nreads * kRefMaskSlots;
     int rc = GSW_OK;
@@ -325,6 +331,7 @@ extern "C" int gsw_align_to_reference(gsw_ctx *ctx, int32_t nreads, const uint8_
     alloc((void **)&eql, 4 * (size_t)nreads);
     alloc((void **)&etl, 4 * (size_t)nreads);
     alloc((void **)&eres, sizeof(gsw_result) * (size_t)nreads);
+    alloc((void **)&nflag, sizeof(unsigned long long));
     const uint8_t *Q = q, *R = ref;
     const int64_t *RQO = q_off;
     const int32_t *RQL = q_len;
@@ -365,13 +372,18 @@ extern "C" int gsw_align_to_reference(gsw_ctx *ctx, int32_t nreads, const uint8_
                              nullptr, nullptr, stream);
     }
     int rc_cigar = GSW_OK;
-    if (rc == GSW_ECIGAR_SPACE) {  // records are complete; the caller learns the space needed
-        rc_cigar = rc;
+    if (rc == GSW_ECIGAR_SPACE || rc == GSW_EINTERNAL) {
+        // records are complete; the caller learns the space needed (the
+        // internal flags are counted again below, after the merge)
+        if (rc == GSW_ECIGAR_SPACE) rc_cigar = rc;
         rc = GSW_OK;
     }
     if (rc == GSW_OK) {
         k_ref_finish<<<grid_for(nreads), 256, 0, st>>>(nreads, best, sec, sec_col, eto, RES);
-        if (cudaGetLastError() != cudaSuccess) rc = GSW_ECUDA;
+        if (cudaMemsetAsync(nflag, 0, sizeof(unsigned long long), st) != cudaSuccess ||
+            launch_count_flag(RES, nreads, kResInternal, nflag, st) != cudaSuccess ||
+            cudaMemcpyAsync(&hflag, nflag, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            rc = GSW_ECUDA;
     }
     if (rc == GSW_OK && hio) {
         bool ok = cudaMemcpyAsync(results, eres, sizeof(gsw_result) * (size_t)nreads, cudaMemcpyDeviceToHost, st) ==
@@ -382,8 +394,10 @@ extern "C" int gsw_align_to_reference(gsw_ctx *ctx, int32_t nreads, const uint8_
     }
     if (cudaStreamSynchronize(st) != cudaSuccess && rc == GSW_OK) rc = GSW_ECUDA;
     void *bufs[] = {dq, dref, drqo, drql, dcig, wqo, wto, wql, wtl, wres, best, cmoff, colmax, mres,
-                    sec, sec_col, eqo, eto, eql, etl, eres};
+                    sec, sec_col, eqo, eto, eql, etl, eres, nflag};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    if (rc == GSW_OK && hflag)
+        return set_err(GSW_EINTERNAL, "%llu reads failed a consistency check (GSW_RES_INTERNAL)", hflag);
     return rc != GSW_OK ? rc : rc_cigar;
 }

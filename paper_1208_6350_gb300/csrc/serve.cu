@@ -148,7 +148,9 @@ int run_batch(gsw_server *srv, Worker *w, std::vector<Req *> &batch) {
                              srv->matrix.data(), c.alphabet, c.gap_open, c.gap_extend, c.flags, c.mask_len,
                              w->d_res, (c.flags & GSW_CIGAR) ? w->d_cig : nullptr,
                              (c.flags & GSW_CIGAR) ? w->cap_cigar : 0, nullptr, nullptr, st);
-    if (rc != GSW_OK) return fail(rc);
+    // GSW_EINTERNAL: every record is complete, the flagged pairs' requests
+    // report it (the worker sets each request's status from its records)
+    if (rc != GSW_OK && rc != GSW_EINTERNAL) return fail(rc);
     e = cudaMemcpyAsync(w->h_res, w->d_res, sizeof(gsw_result) * (size_t)np, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(GSW_ECUDA);
@@ -175,7 +177,7 @@ int run_batch(gsw_server *srv, Worker *w, std::vector<Req *> &batch) {
         }
         at += r->npairs;
     }
-    return GSW_OK;
+    return rc;
 }
 
 // Takes as many whole requests from the head of `q` as fit one batch.
@@ -218,6 +220,11 @@ void worker_loop(gsw_server *srv, Worker *w) {
             const double td = srv->now();
             for (Req *r : batch) {
                 r->status = rc;
+                if (rc == GSW_EINTERNAL) {
+                    r->status = GSW_OK;
+                    for (const gsw_result &x : r->res)
+                        if (x.flags & GSW_RES_INTERNAL) r->status = GSW_EINTERNAL;
+                }
                 r->done = true;
                 r->t_done = td;
                 srv->stats.completed++;
@@ -237,7 +244,7 @@ void worker_loop(gsw_server *srv, Worker *w) {
 extern "C" {
 
 int gsw_serve_create(const gsw_serve_config *cfg_in, gsw_server **out) {
-    if (!cfg_in || !out) return GSW_EINVAL;
+    if (!cfg_in || !out) return gsw::set_err(GSW_EINVAL, "NULL argument");
     *out = nullptr;
     gsw_serve_config c = *cfg_in;
     if (c.workers <= 0) c.workers = 4;
@@ -249,11 +256,14 @@ int gsw_serve_create(const gsw_serve_config *cfg_in, gsw_server **out) {
     if (c.heavy_workers < 0) c.heavy_workers = 0;
     if (c.heavy_workers > c.workers) c.heavy_workers = c.workers;
     if (c.heavy_cells <= 0) c.heavy_cells = (int64_t)1 << 25;
-    if (c.flags & ~(uint32_t)(GSW_BEGIN | GSW_CIGAR)) return GSW_EINVAL;
-    if (!c.matrix || c.alphabet < 1 || c.alphabet > gsw::kMaxAlpha || c.gap_extend < 0 || c.gap_open < c.gap_extend ||
-        c.gap_open > 255 || c.workers > 64)
-        return GSW_EINVAL;
-    if (cudaSetDevice(c.device) != cudaSuccess) return GSW_ECUDA;
+    if (c.flags & ~(uint32_t)(GSW_BEGIN | GSW_CIGAR)) return gsw::set_err(GSW_EINVAL, "flags other than GSW_BEGIN | GSW_CIGAR");
+    if (c.workers > 64) return gsw::set_err(GSW_EINVAL, "more than 64 workers");
+    {
+        gsw::Scoring chk;
+        const int e = gsw::make_scoring(c.matrix, c.alphabet, c.gap_open, c.gap_extend, &chk);
+        if (e != GSW_OK) return e;
+    }
+    if (cudaSetDevice(c.device) != cudaSuccess) return gsw::set_err(GSW_ECUDA, "device %d", c.device);
     std::unique_ptr<gsw_server> srv(new (std::nothrow) gsw_server());
     if (!srv) return GSW_ENOMEM;
     srv->matrix.assign(c.matrix, c.matrix + c.alphabet * c.alphabet);
@@ -300,8 +310,9 @@ int gsw_serve_destroy(gsw_server *srv) {
 
 int gsw_serve_submit(gsw_server *srv, int32_t npairs, const uint8_t *q, const int64_t *q_off, const int32_t *q_len,
                      const uint8_t *t, const int64_t *t_off, const int32_t *t_len, uint64_t *req_id) {
-    if (!srv || !req_id || npairs < 1 || !q_off || !q_len || !t_off || !t_len) return GSW_EINVAL;
-    if (npairs > srv->cfg.max_batch_pairs) return GSW_EINVAL;
+    if (!srv || !req_id || npairs < 1 || !q_off || !q_len || !t_off || !t_len)
+        return gsw::set_err(GSW_EINVAL, "NULL argument or npairs < 1");
+    if (npairs > srv->cfg.max_batch_pairs) return gsw::set_err(GSW_EINVAL, "request larger than max_batch_pairs");
     std::unique_ptr<Req> r(new (std::nothrow) Req());
     if (!r) return GSW_ENOMEM;
     r->npairs = npairs;
@@ -309,11 +320,12 @@ int gsw_serve_submit(gsw_server *srv, int32_t npairs, const uint8_t *q, const in
     for (int32_t p = 0; p < npairs; p++) {
         if (q_len[p] < 0 || t_len[p] < 0 || q_len[p] >= (1 << 24) || t_len[p] >= (1 << 24) || q_off[p] < 0 ||
             t_off[p] < 0)
-            return GSW_EINVAL;
+            return gsw::set_err(GSW_EINVAL, "pair %d: length out of [0, 2^24) or negative offset", p);
         qn += q_len[p];
         tn += t_len[p];
     }
-    if (qn + tn > srv->cfg.max_batch_letters || (qn && !q) || (tn && !t)) return GSW_EINVAL;
+    if (qn + tn > srv->cfg.max_batch_letters || (qn && !q) || (tn && !t))
+        return gsw::set_err(GSW_EINVAL, "request larger than max_batch_letters, or NULL sequences");
     r->q.resize((size_t)qn);
     r->t.resize((size_t)tn);
     r->qoff.resize(npairs);
@@ -332,13 +344,14 @@ int gsw_serve_submit(gsw_server *srv, int32_t npairs, const uint8_t *q, const in
         r->cells += (int64_t)q_len[p] * t_len[p];
     }
     for (uint8_t x : r->q)
-        if (x >= A) return GSW_EINVAL;
+        if (x >= A) return gsw::set_err(GSW_EINVAL, "a query letter code is >= the alphabet size (%d)", A);
     for (uint8_t x : r->t)
-        if (x >= A) return GSW_EINVAL;
+        if (x >= A) return gsw::set_err(GSW_EINVAL, "a target letter code is >= the alphabet size (%d)", A);
     r->letters = qn + tn;
     {
         std::lock_guard<std::mutex> lk(srv->mu);
-        if ((int32_t)(srv->queue.size() + srv->heavy_queue.size()) >= srv->cfg.max_queue_requests) return GSW_ENOMEM;
+        if ((int32_t)(srv->queue.size() + srv->heavy_queue.size()) >= srv->cfg.max_queue_requests)
+            return gsw::set_err(GSW_ENOMEM, "queue full (%d requests)", srv->cfg.max_queue_requests);
         r->id = srv->next_id++;
         r->t_submit = srv->now();
         *req_id = r->id;
@@ -373,7 +386,7 @@ int gsw_serve_poll_timed(gsw_server *srv, uint64_t req_id, int32_t timeout_us, g
         times->started = r->t_start;
         times->done = r->t_done;
     }
-    if (status == GSW_OK) {
+    if (status == GSW_OK || status == GSW_EINTERNAL) {  // records complete (flagged ones included)
         std::memcpy(results, r->res.data(), sizeof(gsw_result) * (size_t)r->npairs);
         if (!r->cigar.empty()) std::memcpy(cigar, r->cigar.data(), 4 * r->cigar.size());
     }
@@ -385,6 +398,29 @@ int gsw_serve_poll_timed(gsw_server *srv, uint64_t req_id, int32_t timeout_us, g
 int gsw_serve_poll(gsw_server *srv, uint64_t req_id, int32_t timeout_us, gsw_result *results, uint32_t *cigar,
                    int64_t cigar_capacity, int64_t *cigar_words) {
     return gsw_serve_poll_timed(srv, req_id, timeout_us, results, cigar, cigar_capacity, cigar_words, nullptr);
+}
+
+int gsw_serve_poll_results(gsw_server *srv, uint64_t req_id, int32_t timeout_us, gsw_results **out) {
+    if (!srv || !out) return gsw::set_err(GSW_EINVAL, "NULL argument");
+    *out = nullptr;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(req_id);
+    if (it == srv->reqs.end()) return gsw::set_err(GSW_ENOTFOUND, "request %llu", (unsigned long long)req_id);
+    Req *r = it->second.get();
+    auto ready = [&] { return r->done; };
+    if (timeout_us < 0) srv->cv_done.wait(lk, ready);
+    else if (!srv->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) return GSW_ETIMEDOUT;
+    const int status = r->status;
+    if (status == GSW_OK || status == GSW_EINTERNAL) {
+        gsw_results *h = new (std::nothrow) gsw_results();
+        if (!h) return gsw::set_err(GSW_ENOMEM, "host allocation");  // the request is kept
+        h->res.swap(r->res);
+        h->cigar.swap(r->cigar);
+        h->t_len = r->tlen;
+        *out = h;
+    }
+    srv->reqs.erase(it);
+    return status;
 }
 
 double gsw_serve_now(gsw_server *srv) { return srv ? srv->now() : -1.0; }

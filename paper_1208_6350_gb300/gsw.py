@@ -23,6 +23,7 @@ GSW_ECIGAR_SPACE = -5
 GSW_EOVERFLOW = -6
 GSW_ENOTFOUND = -7
 GSW_ESTATE = -8
+GSW_EINTERNAL = -9
 
 GSW_BEGIN = 0x1
 GSW_CIGAR = 0x2
@@ -37,6 +38,8 @@ STAGE_NAMES = ("plan_fwd", "fill_fwd", "refill_s32", "reverse_wide", "band", "tr
 
 GSW_RES_S32 = 0x1
 GSW_RES_CIGAR_SPACE = 0x2
+GSW_RES_INVALID = 0x4
+GSW_RES_INTERNAL = 0x80
 
 RESULT_DTYPE = np.dtype([
     ("score1", np.int32), ("score2", np.int32), ("ref_begin1", np.int32), ("ref_end1", np.int32),
@@ -51,7 +54,18 @@ _lib = None
 class GswStats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int32), ("timed", ctypes.c_int32),
                 ("stage_ms", ctypes.c_float * 8), ("graph_segments", ctypes.c_int32),
-                ("cigar_words", ctypes.c_int64)]
+                ("cigar_words", ctypes.c_int64), ("ring_words", ctypes.c_int64),
+                ("ring_pool_words", ctypes.c_int64), ("ring_groups", ctypes.c_int32),
+                ("internal_pairs", ctypes.c_int32)]
+
+
+class GswRecord(ctypes.Structure):
+    """One record of a library-owned results handle (gsw_results_get)."""
+    _fields_ = [("score1", ctypes.c_int32), ("score2", ctypes.c_int32), ("ref_begin1", ctypes.c_int32),
+                ("ref_end1", ctypes.c_int32), ("read_begin1", ctypes.c_int32), ("read_end1", ctypes.c_int32),
+                ("ref_end2", ctypes.c_int32), ("lane_bits_used", ctypes.c_uint8),
+                ("cigar", ctypes.POINTER(ctypes.c_uint32)), ("cigar_len", ctypes.c_int32),
+                ("colmax", ctypes.POINTER(ctypes.c_int32)), ("n", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 TUNE_BUCKETS = 32
@@ -123,6 +137,17 @@ def load(build_if_missing: bool = True):
     for f in (lib.gsw_context_create, lib.gsw_context_destroy, lib.gsw_align_batch,
               lib.gsw_profile_create, lib.gsw_profile_destroy, lib.gsw_align_profile):
         f.restype = ctypes.c_int
+    lib.gsw_align_batch_results.argtypes = [P, i32, P, P, P, P, P, P, P, i32, i32, i32, u32, i32, P,
+                                            ctypes.POINTER(P)]
+    lib.gsw_align_batch_results.restype = ctypes.c_int
+    lib.gsw_results_count.argtypes = [P]
+    lib.gsw_results_count.restype = i32
+    lib.gsw_results_get.argtypes = [P, i32, ctypes.POINTER(GswRecord)]
+    lib.gsw_results_get.restype = ctypes.c_int
+    lib.gsw_results_free.argtypes = [P]
+    lib.gsw_results_free.restype = None
+    lib.gsw_serve_poll_results.argtypes = [P, ctypes.c_uint64, i32, ctypes.POINTER(P)]
+    lib.gsw_serve_poll_results.restype = ctypes.c_int
     lib.gsw_fill_static.argtypes = [i32, P, P, P, P, P, P, i32, P, i32, i32, i32, u32, i32, P, P, P, P]
     lib.gsw_fill_static.restype = ctypes.c_int
     lib.gsw_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(P)]
@@ -222,10 +247,43 @@ def gsw_last_stats(ctx) -> dict:
     st = GswStats()
     _check(load().gsw_last_stats(ctx, ctypes.byref(st)), "gsw_last_stats")
     out = {"kernel_launches": st.kernel_launches, "timed": bool(st.timed), "graph_segments": st.graph_segments,
-           "cigar_words": st.cigar_words}
+           "cigar_words": st.cigar_words, "ring_words": st.ring_words, "ring_pool_words": st.ring_pool_words,
+           "ring_groups": st.ring_groups, "internal_pairs": st.internal_pairs}
     if st.timed:
         out["stage_ms"] = {n: float(st.stage_ms[k]) for k, n in enumerate(STAGE_NAMES)}
     return out
+
+
+def gsw_align_batch_results(ctx, npairs, q, q_off, q_len, t, t_off, t_len, matrix, gap_open, gap_extend,
+                            flags=0, mask_len=-1, stream=None):
+    """gsw_align_batch_results; returns (status, handle) -- the handle (an int)
+    is set on GSW_OK and GSW_EINTERNAL and must go to gsw_results_free."""
+    m = np.ascontiguousarray(matrix, dtype=np.int8)
+    out = ctypes.c_void_p()
+    rc = load().gsw_align_batch_results(ctx, npairs, _ptr(q), _ptr(q_off), _ptr(q_len), _ptr(t), _ptr(t_off),
+                                        _ptr(t_len), m.ctypes.data, m.shape[0], gap_open, gap_extend, flags,
+                                        mask_len, _stream_handle(stream), ctypes.byref(out))
+    return rc, out.value
+
+
+def gsw_results_count(handle) -> int:
+    return load().gsw_results_count(handle)
+
+
+def gsw_results_get(handle, i) -> dict:
+    """Record i of a results handle as a dict (CIGAR as (length, op) runs,
+    the max array as a numpy copy, or None)."""
+    r = GswRecord()
+    _check(load().gsw_results_get(handle, i, ctypes.byref(r)), "gsw_results_get")
+    out = {k: getattr(r, k) for k, _ in GswRecord._fields_ if k not in ("cigar", "colmax")}
+    out["cigar"] = [(int(r.cigar[k]) >> 4, int(r.cigar[k]) & 15) for k in range(max(r.cigar_len, 0))] \
+        if r.cigar else []
+    out["colmax"] = np.ctypeslib.as_array(r.colmax, shape=(r.n,)).copy() if r.colmax and r.n > 0 else None
+    return out
+
+
+def gsw_results_free(handle) -> None:
+    load().gsw_results_free(handle)
 
 
 GSW_STATIC_MAX_TARGET = 1024
@@ -454,6 +512,13 @@ class Server:
             return (rc, None, None, None) if times else (rc, None, None)
         out = (rc, res, cig[: used.value])
         return out + ((tm.submitted, tm.started, tm.done),) if times else out
+
+    def poll_results(self, req_id, timeout_us=-1):
+        """gsw_serve_poll_results: (status, handle or None); free the handle
+        with gsw_results_free."""
+        out = ctypes.c_void_p()
+        rc = load().gsw_serve_poll_results(self.handle, req_id, timeout_us, ctypes.byref(out))
+        return rc, out.value
 
     def now(self) -> float:
         """The server clock (seconds since creation)."""

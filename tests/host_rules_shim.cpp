@@ -1,6 +1,7 @@
 // C entry points over the library's host-side geometry rules (gsw_impl.cuh),
 // compiled by g++ for the CPU tests of those rules: the reverse fill's window
-// and band, the traceback band, and the traceback class routing.
+// and band, the traceback band, the traceback class routing, and the status a
+// batch returns from its kernels' counts.
 #include "gsw_impl.cuh"
 
 namespace {
@@ -46,5 +47,10 @@ int hr_trace_class(int A, const signed char *W, int O, int X, int la, int lb, in
 }
 
 long long hr_t16_need_words(int la, int lb, int v) { return gsw::t16_need_words(la, lb, v); }
+
+int hr_batch_status(int bad_letters, unsigned long long internal, int cigar, unsigned long long words,
+                    long long capacity) {
+    return gsw::batch_status(bad_letters, internal, cigar != 0, words, capacity);
+}
 
 }  // extern "C"

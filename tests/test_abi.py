@@ -132,3 +132,88 @@ def test_pair_cigar_and_cigar_string():
         gsw.pair_cigar(rec[2], words)
     # int32 buffers (torch's dtype for the device copy) read the same
     assert gsw.pair_cigar(rec[0], words.view(np.int32)) == runs
+
+
+def _header_defines():
+    src = open(os.path.join(ROOT, "include", "gsw.h")).read()
+    out = {}
+    for name, val in re.findall(r"#define\s+(GSW_\w+)\s+\(?(-?(?:0x)?[0-9a-fA-F]+)u?\)?", src):
+        out[name] = int(val, 0)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    d = _header_defines()
+    for name in ("GSW_OK", "GSW_EINVAL", "GSW_ENOMEM", "GSW_ECUDA", "GSW_ETIMEDOUT", "GSW_ECIGAR_SPACE",
+                 "GSW_EOVERFLOW", "GSW_ENOTFOUND", "GSW_ESTATE", "GSW_EINTERNAL", "GSW_BEGIN", "GSW_CIGAR",
+                 "GSW_COLMAX", "GSW_HOST_IO", "GSW_FORCE_S32", "GSW_PLAIN", "GSW_TIMING", "GSW_PACKED2",
+                 "GSW_RES_S32", "GSW_RES_CIGAR_SPACE", "GSW_RES_INVALID", "GSW_RES_INTERNAL",
+                 "GSW_STATIC_MAX_TARGET"):
+        assert getattr(gsw, name) == d[name], name
+
+
+def test_every_error_code_has_a_name():
+    names = {gsw.strerror(c) for c in range(0, -10, -1)}
+    assert len(names) == 10 and "unknown error" not in names
+    assert gsw.strerror(gsw.GSW_EINTERNAL) == "internal consistency check failed"
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """ctypes mirrors of gsw_stats and gsw_record against gcc's layout of
+    include/gsw.h."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    src = tmp_path / "lay.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "gsw.h"\n'
+        'int main(void) {\n'
+        ' printf("%zu %zu %zu %zu %zu\\n", sizeof(gsw_stats), offsetof(gsw_stats, ring_words),'
+        ' offsetof(gsw_stats, internal_pairs), sizeof(gsw_record), offsetof(gsw_record, colmax));\n'
+        ' printf("%zu %zu\\n", sizeof(gsw_result), sizeof(gsw_serve_config));\n return 0; }\n')
+    exe = tmp_path / "lay"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    a = [int(x) for x in a.split()]
+    b = [int(x) for x in b.split()]
+    assert a == [ctypes.sizeof(gsw.GswStats), gsw.GswStats.ring_words.offset, gsw.GswStats.internal_pairs.offset,
+                 ctypes.sizeof(gsw.GswRecord), gsw.GswRecord.colmax.offset]
+    assert b == [gsw.RESULT_DTYPE.itemsize, ctypes.sizeof(gsw.ServeConfig)]
+
+
+def test_results_handle_calls_check_arguments_without_gpu():
+    lib = gsw.load()
+    assert lib.gsw_results_count(None) == 0
+    rec = gsw.GswRecord()
+    assert lib.gsw_results_get(None, 0, ctypes.byref(rec)) == gsw.GSW_EINVAL
+    lib.gsw_results_free(None)  # ignored
+    W = np.eye(4, dtype=np.int8)
+    out = ctypes.c_void_p()
+    rc = lib.gsw_align_batch_results(None, 1, None, None, None, None, None, None, W.ctypes.data, 4, 3, 1, 0, -1,
+                                     None, ctypes.byref(out))
+    assert rc == gsw.GSW_EINVAL and out.value is None
+    assert lib.gsw_align_batch_results(None, 1, None, None, None, None, None, None, W.ctypes.data, 4, 3, 1, 0,
+                                       -1, None, None) == gsw.GSW_EINVAL
+    assert lib.gsw_serve_poll_results(None, 1, 0, ctypes.byref(out)) == gsw.GSW_EINVAL
+
+
+def test_static_fill_checks_arguments_before_any_device_work():
+    W = np.eye(4, dtype=np.int8)
+    lib = gsw.load()
+    # flags other than GSW_COLMAX, a too-large mask, O < X, a NULL pointer
+    assert lib.gsw_fill_static(1, None, None, None, None, None, None, 10, W.ctypes.data, 4, 3, 1,
+                               gsw.GSW_CIGAR, -1, None, None, None, None) == gsw.GSW_EINVAL
+    assert lib.gsw_fill_static(1, None, None, None, None, None, None, 10, W.ctypes.data, 4, 3, 1, 0,
+                               (1 << 30) + 1, None, None, None, None) == gsw.GSW_EINVAL
+    assert lib.gsw_fill_static(1, None, None, None, None, None, None, 10, W.ctypes.data, 4, 1, 3, 0, -1,
+                               None, None, None, None) == gsw.GSW_EINVAL
+    assert "gap" in gsw.last_error()
+    assert lib.gsw_fill_static(1, None, None, None, None, None, None, 10, W.ctypes.data, 4, 3, 1, 0, -1,
+                               None, None, None, None) == gsw.GSW_EINVAL
+    assert "NULL" in gsw.last_error()
+    # a maximum target length beyond the static slot's
+    assert lib.gsw_fill_static(1, 1, 1, 1, 1, 1, 1, gsw.GSW_STATIC_MAX_TARGET + 1, W.ctypes.data, 4, 3, 1, 0, -1,
+                               1, None, None, None) == gsw.GSW_EINVAL
+    assert "max_target_len" in gsw.last_error()

@@ -61,6 +61,8 @@ def lib(tmp_path_factory):
         getattr(L, name).restype = i32
     L.hr_t16_need_words.argtypes = [i32, i32, i32]
     L.hr_t16_need_words.restype = ctypes.c_longlong
+    L.hr_batch_status.argtypes = [i32, ctypes.c_ulonglong, i32, ctypes.c_ulonglong, ctypes.c_longlong]
+    L.hr_batch_status.restype = i32
     return L
 
 
@@ -494,3 +496,19 @@ def test_banded_traceback_gives_the_full_rectangle_cigar(lib, kind):
     assert checked >= 30
     if kind == "two_gaps":
         assert tight == checked
+
+
+def test_batch_status_precedence(lib):
+    """A batch's return code from its kernels' counts: bad letters, then
+    records flagged by a consistency check, then CIGAR space (with GSW_CIGAR
+    only); otherwise GSW_OK."""
+    from paper_1208_6350_gb300 import gsw
+    st = lib.hr_batch_status
+    assert st(0, 0, 1, 10, 10) == gsw.GSW_OK
+    assert st(0, 0, 1, 11, 10) == gsw.GSW_ECIGAR_SPACE
+    assert st(0, 0, 0, 11, 10) == gsw.GSW_OK          # no CIGAR asked: words never counted
+    assert st(0, 0, 1, 1, 0) == gsw.GSW_ECIGAR_SPACE
+    assert st(0, 1, 1, 11, 10) == gsw.GSW_EINTERNAL   # one flagged record is loud
+    assert st(0, 5, 0, 0, 0) == gsw.GSW_EINTERNAL
+    assert st(1, 5, 1, 11, 10) == gsw.GSW_EINVAL      # bad input first
+    assert st(1, 0, 0, 0, 0) == gsw.GSW_EINVAL
