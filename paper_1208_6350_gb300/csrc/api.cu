@@ -45,6 +45,7 @@ int make_scoring(const int8_t *matrix, int32_t A, int32_t O, int32_t X, Scoring 
     sc->wmax = wmax;
     sc->wmin = wmin;
     sc->dna4 = A == 4;
+    sc->one = 1;
     std::memset(sc->fill_class, -1, sizeof(sc->fill_class));
     return GSW_OK;
 }
@@ -341,7 +342,10 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
 
         // fill launch geometry and per-slot scratch
         const int warps_per_block = fill_block_threads() / 32;
-        S.ncap = (size_t)std::max(maxn, 1);
+        // columns per slot, a multiple of 4: every slot's max array starts on
+        // a 16-byte boundary (the fill stores four 16-bit column maxima at a
+        // time with one 8-byte store)
+        S.ncap = ((size_t)std::max(maxn, 1) + 3) & ~(size_t)3;
         const size_t per_slot = S.ncap * sizeof(int32_t) + 2 * S.ncap * sizeof(int2);
         S.slots = (size_t)fill_slots(sc, ctx->sms);
         if (S.slots == 0) return set_err(GSW_ECUDA, "fill kernels cannot be resident");
@@ -362,6 +366,7 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
         FillLaunch &fl = S.fl;
         fl.b = bv;
         fl.sc = sc;
+        fl.bad_letters = reinterpret_cast<const int32_t *>(misc + kMiscValid);
         fl.plan.order = pb.order;
         fl.plan.var_start = pb.var_start;
         fl.plan.task_lo = pb.task_lo;

@@ -42,36 +42,6 @@
 
 #include <climits>
 
-#ifndef GSW_FILL_DPX
-#define GSW_FILL_DPX 1
-#endif
-// DNA score tables per lane: 0 = one per (low letter, high letter) pair;
-// 1 = a low-letter and a high-letter table, added; 2 = one table holding both
-// halves' scores, merged by a mask (the general-alphabet layout: half the
-// shared memory of 1, but 4 % slower on the short-read fill: the merge's
-// logic op issues at a lower rate than the add)
-#ifndef GSW_FILL_SPLIT
-#define GSW_FILL_SPLIT 1
-#endif
-// 1: F' = max(F - X, T - O) with T = max(H(i-1,j-1) + W, E, 0), off the F
-// chain but an extra add per cell; 0: F' = max(F - X, H - O) sharing H - O
-// with E (one add fewer, longer chain)
-#ifndef GSW_FILL_TTRICK
-#define GSW_FILL_TTRICK 0
-#endif
-// 1: 16-bit lanes hold signed values (the clamp at 0 folds into the first
-// add-max: one instruction fewer per word, one DPX more); 0: values biased
-// by 0x8000 in unsigned lanes
-#ifndef GSW_FILL_SIGNED
-#define GSW_FILL_SIGNED 0
-#endif
-// unroll factors of the steady loops: one-strip forward fills (FAST), other strips
-#ifndef GSW_FILL_UNROLL_FAST
-#define GSW_FILL_UNROLL_FAST 4
-#endif
-#ifndef GSW_FILL_UNROLL_GEN
-#define GSW_FILL_UNROLL_GEN 2
-#endif
 #include <type_traits>
 #include <cstring>
 #include <mutex>
@@ -80,8 +50,8 @@ namespace gsw {
 namespace {
 
 constexpr int kBlock = 128;
-constexpr int kUnrollFast = GSW_FILL_UNROLL_FAST;
-constexpr int kUnrollGen = GSW_FILL_UNROLL_GEN;
+constexpr int kUnrollFast = 4;  // steady loop of one-strip forward fills
+constexpr int kUnrollGen = 2;   // other steady loops
 // forms of the strip step (StripRunner::step)
 constexpr int kModeGen = 0, kModeFast = 1, kModeFwdFirst = 2, kModeFwdLater = 3;
 
@@ -90,24 +60,9 @@ struct L16 {
     static constexpr bool FOLD = true;
     using cm_t = uint16_t;
     using bnd_t = uint32_t;
-#if GSW_FILL_SIGNED
-    static constexpr uint32_t Z = 0u;  // zero of one lane
-    static constexpr uint32_t Z2 = 0u;
-    static __device__ __forceinline__ uint32_t vmax(uint32_t a, uint32_t b) { return __vmaxs2(a, b); }
-    static __device__ __forceinline__ uint32_t lane1(int v) { return (uint32_t)v & 0xFFFFu; }
-    // lane value as stored in the max array (biased by 0x8000, read as u16)
-    static __device__ __forceinline__ uint32_t cm16(uint32_t x) { return x ^ 0x8000u; }
-    static __device__ __forceinline__ int value(uint32_t x16) { return (int)(int16_t)(uint16_t)x16; }
-    // max(diag + W, E, 0) in one DPX instruction
-    static __device__ __forceinline__ uint32_t tt_relu(uint32_t d, uint32_t w, uint32_t e) {
-        return __viaddmax_s16x2_relu(d, w, e);
-    }
-    // H - O per lane (kO = -O in both halves); H >= 0, so no lane goes below -O
-    static __device__ __forceinline__ uint32_t ok(int O) { return halves(-O, -O); }
-    static __device__ __forceinline__ uint32_t sub_o(uint32_t h, uint32_t kO) {
-        return __viaddmax_s16x2(h, kO, 0x80008000u);
-    }
-#else
+    // lane values are biased by 0x8000 in unsigned 16-bit halves (measured
+    // against signed halves with the zero clamp folded into a DPX add-max:
+    // one instruction fewer per word but one DPX more, slower)
     static constexpr uint32_t Z = 0x8000u;    // bias of one lane
     static constexpr uint32_t Z2 = 0x80008000u;
     static __device__ __forceinline__ uint32_t vmax(uint32_t a, uint32_t b) { return __vmaxu2(a, b); }
@@ -120,21 +75,9 @@ struct L16 {
     // H - O per lane: a plain add (every biased lane value is >= O)
     static __device__ __forceinline__ uint32_t ok(int O) { return addk(-O); }
     static __device__ __forceinline__ uint32_t sub_o(uint32_t h, uint32_t kO) { return h + kO; }
-#endif
     static __device__ __forceinline__ uint32_t both(int v) { return lane1(v) | (lane1(v) << 16); }
     // integer that adds c to both lanes of a word
     static __device__ __forceinline__ uint32_t addk(int c) { return (uint32_t)(c * 65537); }
-#if GSW_FILL_SIGNED
-    static __device__ __forceinline__ uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) {
-        return __viaddmax_s16x2(a, b, c);
-    }
-    static __device__ __forceinline__ uint32_t halves(int lo, int hi) {
-        return ((uint32_t)lo & 0xFFFFu) | (((uint32_t)hi & 0xFFFFu) << 16);
-    }
-    static __device__ __forceinline__ uint32_t merge(uint32_t a, uint32_t b) {
-        return (a & 0x0000FFFFu) | (b & 0xFFFF0000u);
-    }
-#elif GSW_FILL_DPX
     // per-lane max(a + b, c) in one DPX instruction; b holds two 16-bit
     // two's-complement halves (no borrow between them)
     static __device__ __forceinline__ uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) {
@@ -147,13 +90,6 @@ struct L16 {
     static __device__ __forceinline__ uint32_t merge(uint32_t a, uint32_t b) {
         return (a & 0x0000FFFFu) | (b & 0xFFFF0000u);
     }
-#else
-    static __device__ __forceinline__ uint32_t addmax(uint32_t a, uint32_t b, uint32_t c) { return vmax(a + b, c); }
-    static __device__ __forceinline__ uint32_t halves(int lo, int hi) { return (uint32_t)(lo + hi * 65536); }
-    static __device__ __forceinline__ uint32_t merge(uint32_t a, uint32_t b) {
-        return b - (uint32_t)(int)(int16_t)(b & 0xFFFFu) + (uint32_t)(int)(int16_t)(a & 0xFFFFu);
-    }
-#endif
 };
 
 struct L32 {
@@ -179,14 +115,14 @@ struct L32 {
     static __device__ __forceinline__ uint32_t sub_o(uint32_t h, uint32_t kO) { return h + kO; }
 };
 
-// DNA table layout of a variant with R row words per lane (one for all:
-// the combined table's smaller profile for the tallest variant, 3 -> 4
-// blocks per SM, measured slower all the same)
-__host__ __device__ constexpr int dna_split(int R) { return GSW_FILL_SPLIT; }
-
-// words of one lane's profile (the warp region holds 32 lanes' worth)
+// Words of one lane's profile (the warp region holds 32 lanes' worth).  DNA
+// in 16-bit lanes: a low-letter table and a high-letter table (8 R words),
+// added per step (measured against one word per letter pair, 16 R words,
+// whose larger profile costs occupancy, and one table holding both halves,
+// 4 R words, merged by a logic op that issues at a lower rate than the add:
+// both slower); other alphabets: one table with both halves per letter.
 __host__ __device__ constexpr int prof_words(int R, bool fold, bool dna, int A) {
-    return dna ? (fold ? (dna_split(R) == 0 ? 16 * R : dna_split(R) == 1 ? 8 * R : 4 * R) : 4 * R) : A * R;
+    return dna ? (fold ? 8 * R : 4 * R) : A * R;
 }
 
 // Index of profile word (table c, row r) of lane l inside the warp region:
@@ -258,21 +194,7 @@ __device__ __forceinline__ void build_profile(uint32_t *psm, const Job &job, con
             int rho_hi = st * SP + S + k * R + r - pad_top;
             qhi = rho_hi >= 0 ? min((int)job.q[(long long)rho_hi * job.qs], A - 1) : -1;
         }
-        if constexpr (DNA && dna_split(R) == 0) {
-            if constexpr (L::FOLD) {
-#pragma unroll
-                for (int a = 0; a < 4; a++)
-#pragma unroll
-                    for (int b = 0; b < 4; b++) {
-                        int wl = qlo >= 0 ? sc_w(sc, qlo, a) : 0;
-                        int wh = qhi >= 0 ? sc_w(sc, qhi, b) : 0;
-                        psm[pidx<R>(a * 4 + b, r, lane)] = L::halves(wl, wh);
-                    }
-            } else {
-#pragma unroll
-                for (int a = 0; a < 4; a++) psm[pidx<R>(a, r, lane)] = (uint32_t)(qlo >= 0 ? sc_w(sc, qlo, a) : 0);
-            }
-        } else if constexpr (DNA && dna_split(R) == 1) {
+        if constexpr (DNA) {
             for (int a = 0; a < A; a++) {
                 psm[pidx<R>(a, r, lane)] = L::halves(qlo >= 0 ? sc_w(sc, qlo, a) : 0, 0);
                 if constexpr (L::FOLD)
@@ -358,6 +280,7 @@ struct StripRunner {
     int c_lo, c_hi, nal, nah;
     bnd_t b_cur, b_nxt;
     cm_t c_cur, c_nxt;
+    uint32_t cmpk, cmw0;  // max-array values of the packed 4-step store
 
 
     // Strips after the first read the previous strip's boundary (lane 0,
@@ -405,7 +328,7 @@ struct StripRunner {
     // several strips (boundary row out), kModeFwdLater a later strip
     // (boundary row in, the max array merged with the strips above).
     // Returns true when the reverse fill found its target column.
-    template <bool CHECKED, int MODE = kModeGen>
+    template <bool CHECKED, int MODE = kModeGen, int PK = -1>
     __device__ __forceinline__ bool step(const int s) {
         constexpr bool FAST = MODE == kModeFast;
         const int jlo = s - k;
@@ -455,15 +378,18 @@ struct StripRunner {
                     const int j2 = j1 - P;
                     nah = (j2 >= 0 && j2 < n) ? min((int)job.t[(long long)j2 * job.ts], A - 1) : 0;
                 }
+            } else if constexpr (FAST) {
+                // letters were checked before the fill (bad_letters, or the
+                // static entry's per-pair check): no clamp
+                nal = job.t[j1];
+                if constexpr (L::FOLD) nah = job.t[j1 - P];
             } else {
                 nal = min((int)job.t[(long long)j1 * job.ts], A - 1);
                 if constexpr (L::FOLD) nah = min((int)job.t[(long long)(j1 - P) * job.ts], A - 1);
             }
         }
         uint32_t pw[R];
-        if constexpr (DNA && dna_split(R) == 0) {
-            load_words<R>(psm, L::FOLD ? al * 4 + ah : al, lane, pw);
-        } else if constexpr (DNA && dna_split(R) == 1) {
+        if constexpr (DNA) {
             load_words<R>(psm, al, lane, pw);
             if constexpr (L::FOLD) {
                 uint32_t ph[R];
@@ -487,16 +413,11 @@ struct StripRunner {
         for (int r = 0; r < R; r++) {
             const uint32_t tt = L::tt_relu(diag, pw[r], E[r]);
             const uint32_t h = L::vmax(tt, f);
-#if GSW_FILL_TTRICK
-            f = L::addmax(f, kXm, L::sub_o(tt, kO));  // = max(F - X, H - O) since O >= X
-            E[r] = L::addmax(E[r], kXm, L::sub_o(h, kO));
-#else
             // one H - O for both gap states; the F chain then runs through
             // h (3 dependent instructions per row), hidden by the other warps
             const uint32_t ho = L::sub_o(h, kO);
             f = L::addmax(f, kXm, ho);
             E[r] = L::addmax(E[r], kXm, ho);
-#endif
             diag = H[r];
             H[r] = h;
             m = L::vmax(m, h);
@@ -520,26 +441,40 @@ struct StripRunner {
         }
         // tracker: first column where the running column max strictly improved
         {
+            // branch-free: a mask of the halves that improved selects this
+            // column's rows into the saved copy (no branch splits the step,
+            // so the steps of the unrolled loop interleave)
             const uint32_t nb = L::vmax(cme, best);
-            if (nb != best) {
-                const uint32_t diff = nb ^ best;
-                uint32_t mk;
-                if constexpr (L::FOLD) {
-                    mk = ((diff & 0xFFFFu) ? 0x0000FFFFu : 0u) | ((diff >> 16) ? 0xFFFF0000u : 0u);
-                    if (diff & 0xFFFFu) c_lo = jlo;
-                    if (diff >> 16) c_hi = jhi;
-                } else {
-                    mk = 0xFFFFFFFFu;
-                    c_lo = jlo;
-                }
-                best = nb;
-#pragma unroll
-                for (int r = 0; r < R; r++) SV[r] = (H[r] & mk) | (SV[r] & ~mk);
+            const uint32_t diff = nb ^ best;
+            uint32_t mk;
+            if constexpr (L::FOLD) {
+                const uint32_t t = __vminu2(diff, 0x00010001u);  // 1 in each half that changed
+                mk = t * 0xFFFFu;
+                c_lo = (t & 1u) ? jlo : c_lo;
+                c_hi = (t >> 16) ? jhi : c_hi;
+            } else {
+                mk = diff ? 0xFFFFFFFFu : 0u;
+                c_lo = diff ? jlo : c_lo;
             }
+            best = nb;
+#pragma unroll
+            for (int r = 0; r < R; r++) SV[r] = (H[r] & mk) | (SV[r] & ~mk);
         }
+
         // the last lane holds complete columns: column max and strip boundary
         bool found = false;
-        if (FAST && k == P - 1) {
+        if (FAST && PK >= 0) {
+            // four columns' maxima in one 8-byte store: two 16-bit values per
+            // word, packed on the way (jhi of the block's first step is a
+            // multiple of 4)
+            if constexpr ((PK & 1) == 0) {
+                cmpk = m >> 16;
+            } else {
+                const uint32_t w = cmpk | (m & 0xFFFF0000u);
+                if constexpr (PK == 1) cmw0 = w;
+                else if (k == P - 1) *reinterpret_cast<uint2 *>(cms + (jhi - 3)) = make_uint2(cmw0, w);
+            }
+        } else if (FAST && k == P - 1) {
             if constexpr (L::FOLD) cms[jhi] = (uint16_t)L::cm16(m >> 16);
             else cms[jhi] = (int)m;
         } else if ((MODE == kModeFwdFirst || MODE == kModeFwdLater) && k == P - 1) {
@@ -600,8 +535,24 @@ struct StripRunner {
             if (step<true>(s)) return true;
         const bool fwd = !job.stop_u && has_cms;
         if (MAYBE_FAST && st == 0 && last_strip && fwd && job.ts == 1) {
+            if constexpr (L::FOLD) {
+                // blocks of 4 steps whose max-array values go out in one
+                // store (the first steady step's column is 0, so the blocks
+                // stay aligned); the last few steady steps run as drain steps
+                if ((s - s_steady) % 4 == 0) {
+                    const int se = min(s1, s_drain);
+#pragma unroll 1
+                    for (; s + 4 <= se; s += 4) {
+                        step<false, kModeFast, 0>(s);
+                        step<false, kModeFast, 1>(s + 1);
+                        step<false, kModeFast, 2>(s + 2);
+                        step<false, kModeFast, 3>(s + 3);
+                    }
+                }
+            } else {
 #pragma unroll kUnrollFast
-            for (; s < s1 && s < s_drain; s++) step<false, kModeFast>(s);
+                for (; s < s1 && s < s_drain; s++) step<false, kModeFast>(s);
+            }
         } else if (MAYBE_MULTI && fwd && st == 0 && !last_strip) {
 #pragma unroll kUnrollGen
             for (; s < s1 && s < s_drain; s++) step<false, kModeFwdFirst>(s);
@@ -797,6 +748,16 @@ __device__ void run_task(const FillLaunch &fl, int first, int last, uint32_t *ws
     const int pair = fl.plan.order[idx];
     gsw_result *rp = b.res + pair;
     uint32_t *psm = wsm;  // the warp's profile region (lane-interleaved)
+    if (*fl.bad_letters) {
+        // a letter outside the alphabet somewhere in the batch: no letter
+        // is read (the steady steps index the profile unclamped)
+        if (k == 0 && fl.mode != kFillReverse) {
+            rp->score1 = 0; rp->score2 = 0; rp->ref_begin1 = -1; rp->ref_end1 = -1;
+            rp->read_begin1 = -1; rp->read_end1 = -1; rp->ref_end2 = -1; rp->cigar_len = 0;
+            rp->cigar_off = -1; rp->flags = 0; rp->reserved = 0;
+        }
+        return;
+    }
     Job job;
     slot_scratch(fl.scr, slot_base + g, &job);
     if (fl.mode == kFillReverse) {
@@ -836,8 +797,15 @@ GSW_FILL_VARIANTS(GSW_VARC)
 
 // Persistent fill kernel of one variant: warps take tasks (32/P pairs) from
 // the variant's counter; the plan sorted them by cost, descending.
+// Blocks per SM the compiler keeps each variant's registers for (0: its own
+// choice).  Measured on the short-read workload: the 8-lane variants of up
+// to 14 row words run best capped at 128 registers (4 blocks of 4 warps);
+// the 16-word one keeps its own choice (about 160 registers, 3 blocks).
+__host__ __device__ constexpr int fill_min_blocks(int v) {
+    return v >= kVarP8First && v < kNumVariants - 1 ? 4 : 0;
+}
 template <bool DNA, int VID>
-__global__ void __launch_bounds__(kBlock) k_fill(FillLaunch fl, int warp_words) {
+__global__ void __launch_bounds__(kBlock, fill_min_blocks(VID)) k_fill(FillLaunch fl, int warp_words) {
     using V = VarC<VID>;
     extern __shared__ __align__(16) uint32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1207,6 +1175,8 @@ namespace {
 
 constexpr int kStaticMaxTarget = GSW_STATIC_MAX_TARGET;
 constexpr size_t kStaticSlotBytes = (size_t)kStaticMaxTarget * sizeof(int32_t) + 2 * (size_t)kStaticMaxTarget * sizeof(int2);
+static_assert(kStaticMaxTarget % 4 == 0 && kStaticSlotBytes % 16 == 0,
+              "slots start on 16-byte boundaries (the fill's 8-byte max-array stores)");
 constexpr int kStaticWarps = 152 * 4;                 // warps of one launch
 constexpr int kStaticSlots = kStaticWarps * 2;        // two pairs in flight per warp
 constexpr size_t kStaticErrOff = kStaticSlotBytes * kStaticSlots;

@@ -31,6 +31,7 @@ struct Scoring {
     int32_t wmax;   // max matrix entry
     int32_t wmin;   // min matrix entry
     int32_t dna4;   // 1 when A == 4: the fill uses the letter-pair profile
+    int32_t one;    // 1, unknown to the compiler: x * one + y issues as an integer multiply-add on the FMA pipe
     int8_t W[kMaxAlpha * kMaxAlpha];  // W[a * A + b]: query letter a vs target letter b
     int8_t fill_class[GSW_TUNE_BUCKETS];  // tuned 16-bit fill class per query-row bucket, -1: default rule
 };
@@ -139,7 +140,7 @@ struct FillPlan {
 struct FillScratch {
     void *colmax;    // slots x ncap elements (uint16 biased for 16-bit, int32 for 32-bit)
     void *boundary;  // slots x 2 x ncap boundary words (uint32 for 16-bit, int2 for 32-bit)
-    int32_t ncap;    // columns per slot
+    int32_t ncap;    // columns per slot (a multiple of 4: 8-byte stores of four 16-bit maxima)
     int32_t nslots;  // slots allocated
 };
 
@@ -149,6 +150,11 @@ struct FillLaunch {
     FillPlan plan;
     FillScratch scr;
     int32_t mode;
+    // nonzero once the batch's letter check found a code >= the alphabet
+    // (written by the check, which runs first on the stream): the fill then
+    // writes empty records and touches no letter, so its steady steps need
+    // no clamp (the call returns GSW_EINVAL)
+    const int32_t *bad_letters;
 };
 
 // internal per-pair bits (besides the public GSW_RES_*)
