@@ -410,19 +410,93 @@ def run_gsw(args):
     if split_info is not None:
         line["split"] = split_info
     if world == 1 and args.plain_pairs > 0:
-        line["plain_per_pair"] = run_plain(gsw, b, ctx, args.plain_pairs, rec)
+        pp = run_plain(gsw, b, ctx, args.plain_pairs, rec)
+        # the batched step's rate over the same pairs, for comparison
+        sub = int(min(args.plain_pairs, b.npairs))
+        pp["batched_gcups_same_workload"] = round(value, 1)
+        pp["batched_over_plain"] = round(value / max(pp["gcups"], 1e-9), 1)
+        pp["pairs_are_the_first_of_the_workload"] = sub
+        line["plain_per_pair"] = pp
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(b, args.cpu_seconds)
-    if world == 1 and not args.no_serve:
+    if world == 1 and args.workload == WORKLOAD and not args.no_long:
+        # the long-read workload (10,000 reads of 1-20 kb) through the same
+        # call, reported beside the metric's workload
         ctx.close()
         ctx = None
+        del q, t, qo, to, ql, tl, res, cig
         torch.cuda.empty_cache()
-        line["serving"] = run_serving([10000.0], 300, 40, gsw)[0]
+        line["long_reads"] = run_long_reads(args, gsw, torch, dev)
+    if world == 1 and not args.no_serve:
+        if ctx is not None:
+            ctx.close()
+            ctx = None
+        torch.cuda.empty_cache()
+        rates = [float(x) for x in args.serve_rates.split(",") if x]
+        line["serving"] = run_serving(rates, args.serve_requests, args.serve_head, gsw)
     print(json.dumps(line), flush=True)
     if ctx is not None:
         ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_long_reads(args, gsw, torch, dev):
+    """The long-read workload (10,000 DNA reads, lengths log-uniform 1-20 kb at
+    10 % error, targets 1.2x; +2/-4, open 4, extend 2): whole pipeline on
+    device buffers (CUDA events on the launching stream), the same call from
+    pinned host buffers (e2e), and a sample of the timed batch checked
+    against the oracle."""
+    b, wcfg = make_workload("dna_long_reads_10k", args.long_pairs, 0)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    q, t = T(gsw.pack2(b.q)), T(gsw.pack2(b.t))
+    qo, to = T(b.q_off.astype(np.int64)), T(b.t_off.astype(np.int64))
+    ql, tl = T(b.q_len.astype(np.int32)), T(b.t_len.astype(np.int32))
+    n = b.npairs
+    res = torch.zeros(n * 12, dtype=torch.int32, device=dev)
+    cap = int(min(64 * n + (b.q_len.sum() + b.t_len.sum()) // 4, 1 << 30))
+    cig = torch.zeros(cap, dtype=torch.int32, device=dev)
+    ctx = gsw.Context(dev.index or 0, args.budget_gb << 30)
+    try:
+        t0 = time.perf_counter()
+        tune = ctx.autotune(b.W, b.gap_open, b.gap_extend, target_len=max(1, int(b.t_len.mean())))
+        tune_s = round(time.perf_counter() - t0, 2)
+        stream = torch.cuda.Stream(dev)
+        flags = gsw.GSW_CIGAR | gsw.GSW_TIMING | gsw.GSW_PACKED2
+
+        def step():
+            gsw.gsw_align_batch(ctx.handle, n, q, qo, ql, t, to, tl, b.W, b.gap_open, b.gap_extend, flags, -1,
+                                res, cig, cap, stream=stream)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize(dev)
+        checked = check_sample(b, res, cig, 0, k=300, max_cells=2e9) if not args.no_check else 0
+        steps = max(1, args.long_steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stage_sum = {}
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+            for k, v in gsw.gsw_last_stats(ctx.handle)["stage_ms"].items():
+                stage_sum[k] = stage_sum.get(k, 0.0) + v
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        out = {"workload": "dna_long_reads_10k", "pairs": n, "cells": b.cells,
+               "value": round(b.cells / (ms / 1e3) / 1e9, 2), "unit": UNIT, "ms_per_step": round(ms, 3),
+               "steps": steps, "warmup": 3,
+               "stage_ms": {k: round(v / steps, 3) for k, v in stage_sum.items()},
+               "checked_pairs": checked, "config": workload_config(dict(wcfg, input="2-bit packed DNA arenas"), b),
+               "autotune_seconds": tune_s}
+        if not args.no_e2e:
+            import types
+            out["e2e"] = run_e2e(types.SimpleNamespace(warmup=1, steps=steps), gsw, b, ctx, stream, dev, torch,
+                                 packed=True)
+        out["work_beside_fill"] = work_summary(res.cpu().numpy().view(gsw.RESULT_DTYPE), b.cells)
+        return out
+    finally:
+        ctx.close()
 
 
 def run_e2e(args, gsw, b, ctx, stream, dev, torch, packed=False):
@@ -940,9 +1014,18 @@ def main():
     ap.add_argument("--requests", type=int, default=2000, help="serving_stream: requests per rate")
     ap.add_argument("--head", type=int, default=100,
                     help="serving_stream: leading requests also run by the plain per-pair baseline")
-    ap.add_argument("--no-serve", action="store_true", help="skip the short serving run of the default line")
-    ap.add_argument("--plain-pairs", type=int, default=0,
-                    help="also time the plain per-pair path (GSW_PLAIN) on this many of the workload's pairs")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving runs of the default line")
+    ap.add_argument("--serve-rates", default="1000,10000",
+                    help="default line: arrival rates of the served stream (one within capacity, one in overload)")
+    ap.add_argument("--serve-requests", type=int, default=20000, help="default line: requests per served rate")
+    ap.add_argument("--serve-head", type=int, default=60,
+                    help="default line: leading requests of each rate also run by the plain per-pair baseline")
+    ap.add_argument("--no-long", action="store_true", help="skip the long-read sub-record of the default line")
+    ap.add_argument("--long-pairs", type=int, default=0, help="long-read sub-record: pairs (default 10,000)")
+    ap.add_argument("--long-steps", type=int, default=3, help="long-read sub-record: timed steps")
+    ap.add_argument("--plain-pairs", type=int, default=2000,
+                    help="also time the plain per-pair path (GSW_PLAIN) on this many of the workload's pairs "
+                         "(0: skip)")
     ap.add_argument("--no-tune", action="store_true", help="default fill classes instead of the autotuner's")
     ap.add_argument("--tune-table", default="", help="fill class per 32-row bucket, comma-separated (no tuning)")
     ap.add_argument("--no-pack", action="store_true", help="DNA arenas one byte per letter instead of 2-bit packed")
