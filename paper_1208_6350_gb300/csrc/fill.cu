@@ -854,6 +854,18 @@ __host__ __device__ constexpr int long_lag() {
     return 1 + (2 * P - 1 + dw + kLongChunk - 1) / kLongChunk;
 }
 
+// Lag of a banded reversed fill, whose strip x+1 starts up to SP columns
+// right of strip x: strip x+1 reads absolute column c0(x+1) + s + 2P - 1 at
+// its step s, which strip x writes at its step c0(x+1) - c0(x) + s + 2P - 1
+// + dw, so (lag - 1) * C >= SP + 2P - 1 + dw (16-bit lanes: 11 phases).  The
+// same lag keeps strip x+2's writes after strip x+1's reads of the ping-pong
+// buffer (lag * C + dw > SP).
+template <class L, int SP>
+__host__ __device__ constexpr int long_lag_band() {
+    constexpr int P = 32, dw = L::FOLD ? 2 * P - 1 : P - 1;
+    return 1 + (SP + 2 * P - 1 + dw + kLongChunk - 1) / kLongChunk;
+}
+
 struct LongSlot {
     Job job;
     int pair;  // -1: free
@@ -865,7 +877,32 @@ struct LongSlot {
     int stopped;     // the last strip found the reverse target
     int fin;         // finalisation handed out
     int bv, bc, br;  // merged maximum, its column and (padded) row
+    int band;        // reversed fill restricted to the reverse band (below)
+    int G, Gn;       // reverse band [-Gn, G] around the main diagonal
+    int lag;         // phases between the starts of consecutive strips
 };
+
+// Columns [c0, c1] of strip x of a banded reversed fill: every path reaching
+// score1 starts at the reversed origin and keeps j - i within [-Gn, G] (the
+// band kernel's argument), so the strip's rows [r0, r1] need only the
+// columns [r0 - Gn, r1 + G] of the window, plus the column left of them: the
+// first row's band cell (r0, r0 - Gn) takes its diagonal predecessor from the
+// boundary row at column r0 - Gn - 1, and the strip reads its boundary row
+// one column behind the cell it computes.  Cells outside the band are never
+// on such a path; what a strip reads from outside its neighbour's columns
+// (the top boundary right of the strip above) is H = 0 and F = -inf, a lower
+// bound like any restriction of the local DP, so the band's values on those
+// paths are the full DP's.  c1 < c0: the band misses the window.
+__device__ __forceinline__ void band_cols(const LongSlot &S, int strip, int SP, int *c0, int *c1) {
+    if (!S.band) {
+        *c0 = 0;
+        *c1 = S.job.ncols - 1;
+        return;
+    }
+    const int r0 = max(0, strip * SP - S.pad_top), r1 = (strip + 1) * SP - 1 - S.pad_top;
+    *c0 = max(0, r0 - S.Gn - 1);
+    *c1 = min(S.job.ncols - 1, r1 + S.G);
+}
 
 struct LongCmd {
     int slot;   // -1: idle
@@ -895,12 +932,24 @@ __device__ bool long_open(const FillLaunch &fl, int cls, LongSlot &S, int s, int
     const int pair = fl.plan.order[fl.plan.var_start[cls] + t];
     Job job;
     slot_scratch(fl.scr, blockIdx.x * kLongSlots + s, &job);
+    S.band = 0;
+    S.G = S.Gn = 0;
     if (fl.mode == kFillReverse) {
         reverse_job(fl.b, fl.sc, pair, &job);
-        job.stop_u = L::lane1(fl.b.res[pair].score1);
+        const gsw_result r = fl.b.res[pair];
+        job.stop_u = L::lane1(r.score1);
+        // the band pays when it takes at least a quarter off every strip
+        const int G = reverse_gap_bound(r.read_end1, r.score1, fl.sc);
+        const int Gn = reverse_gap_bound_rows(r.read_end1, r.score1, fl.sc);
+        if (G >= 0 && ((long long)SP + G + Gn + 1) * 4 <= 3LL * job.ncols) {
+            S.band = 1;
+            S.G = G;
+            S.Gn = Gn;
+        }
     } else {
         forward_job(fl.b, pair, &job);
     }
+    S.lag = S.band ? long_lag_band<L, SP>() : long_lag<L>();
     S.job = job;
     S.pair = pair;
     S.seq = seq;
@@ -919,7 +968,6 @@ __device__ bool long_open(const FillLaunch &fl, int cls, LongSlot &S, int s, int
 
 template <class L, int NW, int SP>
 __device__ void long_schedule(const FillLaunch &fl, int cls, LongShared<NW> &sh, int ph) {
-    constexpr int LAG = long_lag<L>();
     // results of strips that ended, finished finalisations
     for (int w = 0; w < NW; w++) {
         if (!sh.rep[w].ended) continue;
@@ -958,7 +1006,7 @@ __device__ void long_schedule(const FillLaunch &fl, int cls, LongShared<NW> &sh,
         int best_seq = INT_MAX;
         for (int s = 0; s < kLongSlots; s++) {
             const LongSlot &S = sh.slot[s];
-            if (S.pair >= 0 && !S.stopped && S.next < S.nstrips && (S.next == 0 || ph >= S.last_start + LAG) &&
+            if (S.pair >= 0 && !S.stopped && S.next < S.nstrips && (S.next == 0 || ph >= S.last_start + S.lag) &&
                 S.seq < best_seq) {
                 best_seq = S.seq;
                 pick = s;
@@ -994,12 +1042,15 @@ struct LongCfg {
     using L = std::conditional_t<S32, L32, L16>;
     static constexpr int P = 32, R = 8;
     static constexpr int NW = DNA ? 8 : 4;
+    // blocks per SM the registers are kept for: 128 registers a thread
+    // (the shared-memory profile allows 3 DNA blocks, 2 fit the registers)
+    static constexpr int MINB = DNA ? 2 : 4;
     static constexpr int SP = S32 ? P * R : 2 * P * R;
     static constexpr int CLS = S32 ? kClassLong32 : kClassLong16;
 };
 
 template <bool DNA, bool S32>
-__global__ void __launch_bounds__(LongCfg<DNA, S32>::NW * 32, 1)
+__global__ void __launch_bounds__(LongCfg<DNA, S32>::NW * 32, LongCfg<DNA, S32>::MINB)
     k_fill_long(FillLaunch fl, int warp_words) {
     using C = LongCfg<DNA, S32>;
     using L = typename C::L;
@@ -1019,6 +1070,7 @@ __global__ void __launch_bounds__(LongCfg<DNA, S32>::NW * 32, 1)
         sh.done = 0;
     }
     StripRunner<C::P, C::R, L, DNA> sr;
+    int strip_c0 = 0;  // first window column of the warp's strip
 #pragma unroll 1
     for (int ph = 0;; ph++) {
         __syncthreads();
@@ -1043,10 +1095,29 @@ __global__ void __launch_bounds__(LongCfg<DNA, S32>::NW * 32, 1)
             continue;
         }
         if (ph == cmd.start) {
-            sr.init(S.job, fl.sc, psm, lane, 0xFFFFFFFFu, 0, lane, S.pad_top);
-            typename L::bnd_t *bnd = reinterpret_cast<typename L::bnd_t *>(S.job.bnd);
+            using bnd_t = typename L::bnd_t;
+            bnd_t *bnd = reinterpret_cast<bnd_t *>(S.job.bnd);
             const size_t n = (size_t)S.job.ncols;
-            sr.begin(fl.sc, cmd.strip, bnd + ((cmd.strip + 1) & 1) * n, bnd + (cmd.strip & 1) * n,
+            // the strip's columns (all of the window unless banded): its
+            // letters, boundary reads and writes start at column c0
+            int c1;
+            band_cols(S, cmd.strip, SP, &strip_c0, &c1);
+            Job jb = S.job;
+            jb.t = S.job.t + (long long)strip_c0 * S.job.ts;
+            jb.ncols = max(0, c1 - strip_c0 + 1);
+            bnd_t *bout = bnd + (cmd.strip & 1) * n;
+            if (S.band && cmd.strip + 1 < S.nstrips) {
+                // the next strip's columns right of this strip's last one
+                // read the outside value: H = 0, F = -inf (biased -O)
+                int n0, n1;
+                band_cols(S, cmd.strip + 1, SP, &n0, &n1);
+                bnd_t out;
+                if constexpr (L::FOLD) out = L::lane1(0) | (L::lane1(-fl.sc.O) << 16);
+                else out = make_int2(0, -fl.sc.O);
+                for (int c = max(n0, jb.ncols > 0 ? c1 + 1 : n0) + lane; c <= n1; c += 32) bout[c] = out;
+            }
+            sr.init(jb, fl.sc, psm, lane, 0xFFFFFFFFu, 0, lane, S.pad_top);
+            sr.begin(fl.sc, cmd.strip, bnd + ((cmd.strip + 1) & 1) * n + strip_c0, bout + strip_c0,
                      cmd.strip == S.nstrips - 1);
         }
         bool stop = false, fin = S.stopped != 0;
@@ -1061,7 +1132,7 @@ __global__ void __launch_bounds__(LongCfg<DNA, S32>::NW * 32, 1)
             if (lane == 0) {
                 LongRep &r = sh.rep[warp];
                 r.v = v;
-                r.c = c;
+                r.c = v > 0 ? c + strip_c0 : c;  // the window's column
                 r.row = cmd.strip * SP + row;
                 r.stop = stop ? 1 : 0;
                 r.ended = 1;

@@ -601,6 +601,34 @@ def test_one_gap_pairs_on_the_exact_band_edges(ctx, A, npairs):
     compare(b, ora, run_gpu_device(ctx, b))
 
 
+def test_banded_cta_reverse_on_the_band_edges(ctx):
+    # long one-gap pairs (queries of 1,800-3,000 letters: the reversed fill
+    # runs in the CTA kernel, each strip restricted to the reverse band's
+    # columns): the one-gap optimum's gap count equals the band's bound on its
+    # side, so the path touches the band's edge, and strips of 512 rows start
+    # right of each other; plus exact self-alignments (a band of one diagonal)
+    rng = np.random.default_rng(131)
+    qs, ts = [], []
+    for p, g in enumerate((1, 2, 17, 40, 200, 333, 1, 64)):
+        a, b = (int(v) for v in rng.integers(900, 1501, 2))
+        x = rng.integers(0, 4, a).astype(np.uint8)
+        y = rng.integers(0, 4, b).astype(np.uint8)
+        z = rng.integers(0, 4, g).astype(np.uint8)
+        gapped, plain = np.concatenate([x, z, y]), np.concatenate([x, y])
+        q, core = (plain, gapped) if p % 2 == 0 else (gapped, plain)
+        qs.append(q)
+        ts.append(np.concatenate([rng.integers(0, 4, int(rng.integers(0, 60))), core,
+                                  rng.integers(0, 4, int(rng.integers(0, 60)))]).astype(np.uint8))
+    for L in (1900, 2600):
+        q = rng.integers(0, 4, L).astype(np.uint8)
+        qs.append(q)
+        ts.append(np.concatenate([rng.integers(0, 4, 40), q, rng.integers(0, 4, 25)]).astype(np.uint8))
+    W = wl.dna_matrix(2, -3)
+    b = _batch(qs, ts, W, 5, 2, "long_one_gap")
+    assert (b.q_len > 1792).all()
+    compare(b, run_oracle(b), run_gpu_device(ctx, b))
+
+
 def test_host_io_colmax_at_callers_offsets(ctx):
     # host buffers: each pair's column maxima land at its own offset (here in
     # reverse pair order with gaps of 5 words), the words between the ranges
