@@ -302,7 +302,8 @@ def run_gsw(args):
     res = torch.zeros(n * 12, dtype=torch.int32, device=dev)
     cap = int(min(32 * n + 1024 + (b.q_len.sum() + b.t_len.sum()) // 4, 1 << 30))
     cig = torch.zeros(cap, dtype=torch.int32, device=dev)
-    ctx = gsw.Context(local, args.budget_gb << 30)
+    budget = args.long_budget_gb if args.workload == "dna_long_reads_10k" else args.budget_gb
+    ctx = gsw.Context(local, budget << 30)
     tune = None
     if args.tune_table:
         # a saved table instead of measuring (e.g. to profile one variant)
@@ -433,7 +434,8 @@ def run_gsw(args):
             ctx = None
         torch.cuda.empty_cache()
         rates = [float(x) for x in args.serve_rates.split(",") if x]
-        line["serving"] = run_serving(rates, args.serve_requests, args.serve_head, gsw)
+        line["serving"] = run_serving(rates, args.serve_requests, args.serve_head, gsw,
+                                      eager_rates=tuple(rates[-1:]))
     print(json.dumps(line), flush=True)
     if ctx is not None:
         ctx.close()
@@ -456,7 +458,10 @@ def run_long_reads(args, gsw, torch, dev):
     res = torch.zeros(n * 12, dtype=torch.int32, device=dev)
     cap = int(min(64 * n + (b.q_len.sum() + b.t_len.sum()) // 4, 1 << 30))
     cig = torch.zeros(cap, dtype=torch.int32, device=dev)
-    ctx = gsw.Context(dev.index or 0, args.budget_gb << 30)
+    # a large device-memory budget: the wide-band traceback keeps 4 bits per
+    # region cell for every pair at once (about 69 GB of direction words per
+    # step of this workload), so it runs as one group instead of several
+    ctx = gsw.Context(dev.index or 0, args.long_budget_gb << 30)
     try:
         t0 = time.perf_counter()
         tune = ctx.autotune(b.W, b.gap_open, b.gap_extend, target_len=max(1, int(b.t_len.mean())))
@@ -483,7 +488,9 @@ def run_long_reads(args, gsw, torch, dev):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / steps
+        st_last = gsw.gsw_last_stats(ctx.handle)
         out = {"workload": "dna_long_reads_10k", "pairs": n, "cells": b.cells,
+               "context_budget_gb": args.long_budget_gb, "traceback_pool_groups": st_last["ring_groups"],
                "value": round(b.cells / (ms / 1e3) / 1e9, 2), "unit": UNIT, "ms_per_step": round(ms, 3),
                "steps": steps, "warmup": 3,
                "stage_ms": {k: round(v / steps, 3) for k, v in stage_sum.items()},
@@ -611,13 +618,13 @@ def _latency_summary(lat_s, queue_s=None):
     return out
 
 
-def serve_trace(gsw, reqs, W, O, X, workers=4, check=None):
+def serve_trace(gsw, reqs, W, O, X, workers=4, check=None, light_graphs=0):
     """Submits each request at its arrival time (one client thread) and
     collects results with the server's timestamps (another thread).  Latency
     = completion on the host - scheduled arrival."""
     import threading
     srv = gsw.Server(W, O, X, gsw.GSW_CIGAR, workers=workers, max_batch_pairs=8192,
-                     max_batch_letters=24 << 20, mem_budget_bytes=48 << 30)
+                     max_batch_letters=24 << 20, mem_budget_bytes=48 << 30, light_graphs=light_graphs)
     # warm-up: one request of each kind, not timed
     seen = set()
     for a, k, b in reqs:
@@ -707,7 +714,7 @@ def _same_results(gsw, srv_out, plain_out):
     return True
 
 
-def run_serving(rates, n_requests, head, gsw, dev_name=""):
+def run_serving(rates, n_requests, head, gsw, dev_name="", eager_rates=()):
     """Per arrival rate: the server over the whole stream, and server vs the
     plain per-pair baseline over the stream's first `head` requests."""
     from paper_1208_6350_gb300 import workloads as wl
@@ -726,7 +733,18 @@ def run_serving(rates, n_requests, head, gsw, dev_name=""):
         row = {"rate_req_s": rate, "requests": len(reqs),
                "offered_gcups": round(cells / max(arr_span, 1e-9) / 1e9, 1),
                "achieved_gcups": round(cells / span / 1e9, 1), "server": _latency_summary(lat, qd),
-               "server_by_kind": by_kind, "batches": int(st["batches"])}
+               "server_by_kind": by_kind, "batches": int(st["batches"]),
+               "graph_batches": int(st["graph_batches"])}
+        if rate in eager_rates:
+            # the same stream with every light batch launched eagerly (no
+            # captured graphs), for the short requests' latency
+            elat, eqd, espan, _, _, est = serve_trace(gsw, reqs, W, O, X, light_graphs=-1)
+            elat_a, eqd_a = np.asarray(elat), np.asarray(eqd)
+            row["eager_light_batches"] = {
+                "server_by_kind": {name: _latency_summary(elat_a[kinds == k], eqd_a[kinds == k])
+                                   for k, name in ((1, "short_100x1000"), (2, "short_read_extension"),
+                                                   (3, "long_reads")) if (kinds == k).any()},
+                "achieved_gcups": round(cells / espan / 1e9, 1), "graph_batches": int(est["graph_batches"])}
         if head:
             hr = reqs[:head]
             hlat, _, _, _, hout, _ = serve_trace(gsw, hr, W, O, X)
@@ -1023,6 +1041,8 @@ def main():
     ap.add_argument("--no-long", action="store_true", help="skip the long-read sub-record of the default line")
     ap.add_argument("--long-pairs", type=int, default=0, help="long-read sub-record: pairs (default 10,000)")
     ap.add_argument("--long-steps", type=int, default=3, help="long-read sub-record: timed steps")
+    ap.add_argument("--long-budget-gb", type=int, default=160,
+                    help="long-read sub-record: context device-memory budget (GB)")
     ap.add_argument("--plain-pairs", type=int, default=2000,
                     help="also time the plain per-pair path (GSW_PLAIN) on this many of the workload's pairs "
                          "(0: skip)")

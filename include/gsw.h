@@ -434,6 +434,15 @@ typedef struct gsw_serve_config {
     int32_t heavy_workers;
     int64_t heavy_cells;
     int32_t heavy_sm_limit;
+    /* When the light queue is keeping up (empty once a batch is formed), a
+     * light worker pads a batch of at most 1024 pairs of at most 1024
+     * letters a sequence to 64, 256 or 1024
+     * pairs (with empty pairs) and rounds its largest lengths and traceback
+     * scratch up to powers of four, so that batches of the same bucket
+     * replay one captured CUDA graph of the pipeline instead of launching
+     * each kernel; larger batches and batches formed under a backlog launch
+     * eagerly.  0 -> on (default), < 0 -> off.  Results do not depend on it. */
+    int32_t light_graphs;
 } gsw_serve_config;
 
 /* Starts the workers.  Errors: GSW_EINVAL (scoring, flags), GSW_ENOMEM, GSW_ECUDA. */
@@ -485,6 +494,7 @@ typedef struct gsw_serve_stats {
     uint64_t submitted, completed, batches, pairs, cells;
     double busy_seconds;         /* sum over workers of time with a batch in flight */
     int32_t queued, running;
+    uint64_t graph_batches;      /* batches whose pipeline replayed captured graphs */
 } gsw_serve_stats;
 int gsw_serve_get_stats(gsw_server *srv, gsw_serve_stats *out);
 

@@ -87,14 +87,24 @@ struct PipeState {
     int stage_done[GSW_NSTAGES] = {};
 };
 
-// One captured segment of the pipeline: replayed while the call repeats with
-// the same key (pointers, sizes, flags, scoring, scratch), captured on the
-// second identical call.
+// One captured segment of the pipeline: replayed whenever the call repeats
+// with the same key (pointers, sizes, flags, scoring, scratch), captured on
+// the second call with that key.
 struct GraphSeg {
     std::vector<uint8_t> key;
     bool seen = false;
     cudaGraphExec_t exec = nullptr;
     PipeState state;
+    uint64_t used_at = 0;
+};
+
+// The segments of the keys seen last (least recently used ones make room),
+// so calls whose shapes alternate (a server's length buckets) each replay
+// their own graph.
+constexpr size_t kGraphCacheEntries = 24;
+struct GraphCache {
+    std::vector<GraphSeg> e;
+    uint64_t clock = 0;
 };
 
 struct gsw_ctx {
@@ -105,7 +115,8 @@ struct gsw_ctx {
     int sms_all = 0;  // SMs of the device
     cudaMemPool_t pool = nullptr;  // stream-ordered scratch allocations
     int8_t tune[GSW_TUNE_BUCKETS];  // fill class per query-row bucket (gsw_autotune), -1: default rule
-    GraphSeg seg[2];                // before and after the traceback readback
+    GraphCache seg[2];              // before and after the traceback readback
+    bool graph_buckets = false;     // round shapes up to buckets so graphs repeat (serving)
     bool capturing = false;         // a segment is being captured: no allocation
     cudaStream_t st = nullptr;     // stream of the call in progress
     DevBuf plan_keys, plan_order, plan_small;
@@ -259,22 +270,39 @@ void key_buf(std::vector<uint8_t> &k, const DevBuf &b) {
 // buffer, so the capture allocates nothing) and replayed while the key repeats.
 // A segment that would have to grow a buffer while captured runs eagerly.
 template <class F>
-int run_segment(gsw_ctx *ctx, GraphSeg &g, const std::vector<uint8_t> &key, cudaStream_t st, PipeState &state,
+int run_segment(gsw_ctx *ctx, GraphCache &gc, const std::vector<uint8_t> &key, cudaStream_t st, PipeState &state,
                 F body) {
-    if (g.exec && g.key == key) {
-        CUDA_TRY(cudaGraphLaunch(g.exec, st));
-        state = g.state;
+    GraphSeg *g = nullptr;
+    for (GraphSeg &x : gc.e)
+        if (x.key == key) {
+            g = &x;
+            break;
+        }
+    if (g && g->exec) {
+        CUDA_TRY(cudaGraphLaunch(g->exec, st));
+        state = g->state;
+        g->used_at = ++gc.clock;
         ctx->graph_segments++;
         return GSW_OK;
     }
-    const bool capture = st != nullptr && g.seen && g.key == key;
-    if (g.exec) {
-        cudaGraphExecDestroy(g.exec);
-        g.exec = nullptr;
+    if (!g) {
+        // first sighting: remember the key, run eagerly
+        if (gc.e.size() >= kGraphCacheEntries) {
+            size_t old = 0;
+            for (size_t i = 1; i < gc.e.size(); i++)
+                if (gc.e[i].used_at < gc.e[old].used_at) old = i;
+            if (gc.e[old].exec) cudaGraphExecDestroy(gc.e[old].exec);
+            gc.e.erase(gc.e.begin() + (long)old);
+        }
+        gc.e.emplace_back();
+        g = &gc.e.back();
+        g->key = key;
+        g->seen = true;
+        g->used_at = ++gc.clock;
+        return body();
     }
-    g.key = key;
-    g.seen = true;
-    if (!capture) return body();
+    g->used_at = ++gc.clock;
+    if (st == nullptr) return body();  // the legacy stream cannot be captured
     const PipeState before = state;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
@@ -288,16 +316,26 @@ int run_segment(gsw_ctx *ctx, GraphSeg &g, const std::vector<uint8_t> &key, cuda
     cudaGraphExec_t ex = nullptr;
     if (rc == GSW_OK && e == cudaSuccess && gr && cudaGraphInstantiate(&ex, gr, 0) == cudaSuccess) {
         cudaGraphDestroy(gr);
-        g.exec = ex;
-        g.state = state;
+        g->exec = ex;
+        g->state = state;
         CUDA_TRY(cudaGraphLaunch(ex, st));
         return GSW_OK;
     }
     if (gr) cudaGraphDestroy(gr);
     cudaGetLastError();  // a failed capture leaves no error for the eager run
-    g.seen = false;
     state = before;
     return body();
+}
+
+// Shapes of a call rounded up to powers of four (at least 64) when the
+// context replays graphs across calls of similar shape: the pipeline then
+// sizes its scratch and launches from the bucket, which changes no result,
+// and few buckets mean few captures.
+uint64_t bucket_up(uint64_t x) {
+    if (x == 0) return 0;
+    uint64_t b = 64;
+    while (b < x) b <<= 2;
+    return b;
 }
 
 int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st, int maxm, int maxn) {
@@ -454,6 +492,8 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
         unsigned long long need[kMiscWords - kMiscNeed];
         std::memcpy(need, hs, sizeof(need));
         for (int k = 5; k < kMiscNeed16 - kMiscNeed; k++) need[k] = 0;
+        if (ctx->graph_buckets)
+            for (unsigned long long &x : need) x = bucket_up(x);
         std::vector<uint8_t> key2 = key;
         key_add(key2, need);
         for (const DevBuf *d : {&ctx->fill_bnd, &ctx->trace_dirs, &ctx->trace_ops, &ctx->ring_meta})
@@ -734,6 +774,10 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
             bv.t = (const uint8_t *)ctx->io_t.p;
         }
     }
+    if (ctx->graph_buckets) {
+        maxm = (int)bucket_up((uint64_t)maxm);
+        maxn = (int)bucket_up((uint64_t)maxn);
+    }
     CUDA_TRY(cudaMemsetAsync(misc + kMiscCursor, 0, 2 * sizeof(unsigned long long), st));  // cursor, internal
     CUDA_TRY(launch_validate(bv, sc, reinterpret_cast<int32_t *>(misc + kMiscValid), st));
     ctx->launches += 1;
@@ -901,6 +945,7 @@ int gsw_context_create(int device, size_t mem_budget_bytes, gsw_ctx **out) {
 
 namespace gsw {
 int context_device(const gsw_ctx *ctx) { return ctx->device; }
+void context_set_graph_buckets(gsw_ctx *ctx, bool on) { ctx->graph_buckets = on; }
 }  // namespace gsw
 
 extern "C" {
@@ -934,8 +979,9 @@ int gsw_context_destroy(gsw_ctx *c) {
                      &c->prof_qlen, &c->ring_meta, &c->io_qp, &c->io_tp};
     c->st = nullptr;
     c->capturing = false;
-    for (GraphSeg &g : c->seg)
-        if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (GraphCache &gc : c->seg)
+        for (GraphSeg &g : gc.e)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
     for (DevBuf *b : all) release(c, *b);
     cudaDeviceSynchronize();
     if (c->pool) cudaMemPoolDestroy(c->pool);

@@ -407,6 +407,9 @@ struct RingLaunchArgs {
 };
 int ring_trace_class();
 int context_device(const gsw_ctx *ctx);
+// Rounds a call's shapes (largest lengths, traceback scratch) up to powers of
+// two, so that calls of similar shape repeat a captured pipeline (serving).
+void context_set_graph_buckets(gsw_ctx *ctx, bool on);
 int ring_slots_per_cta();
 // prefix sums of the class's direction words; out[0] total, [1] max words of a pair, [2] max op words
 cudaError_t launch_ring_needs(const BatchView &b, const Scoring &sc, const int32_t *order, const int32_t *var_start,

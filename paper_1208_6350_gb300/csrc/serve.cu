@@ -17,6 +17,7 @@
 #include "gsw_impl.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -58,6 +59,9 @@ struct Worker {
     int32_t *h_qlen = nullptr, *h_tlen = nullptr, *d_qlen = nullptr, *d_tlen = nullptr;
     gsw_result *h_res = nullptr, *d_res = nullptr;
     uint32_t *h_cig = nullptr, *d_cig = nullptr;
+    bool graphs = false;  // light worker replaying captured pipelines (padded batches)
+    double eager_until = 0;  // server clock: no graph replay before (set by a backlog)
+    std::atomic<uint64_t> graph_batches{0};  // written by the worker, read by get_stats
     std::thread th;
 };
 
@@ -108,11 +112,33 @@ int alloc_worker(Worker *w, const gsw_serve_config &c, size_t budget) {
     if (!ok) return GSW_ENOMEM;
     const size_t staging = 2 * L + P * (16 + 8 + sizeof(gsw_result)) + G * 4;
     if (budget <= staging) return GSW_ENOMEM;
-    return gsw_context_create(c.device, budget - staging, &w->ctx);
+    const int rc = gsw_context_create(c.device, budget - staging, &w->ctx);
+    if (rc == GSW_OK && !w->heavy && c.light_graphs >= 0) {
+        w->graphs = true;
+        gsw::context_set_graph_buckets(w->ctx, true);
+    }
+    return rc;
+}
+
+// Light batches of at most this many pairs replay captured graphs: there the
+// launch sequence costs as much as the work; larger batches (a queue that
+// built up) launch eagerly, since each new shape would pay a capture.
+constexpr int32_t kGraphMaxPairs = 1024;
+// ... whose sequences are short reads: a light request may hold a few reads
+// of several kb, whose rounded-up scratch would be large for a replay to pay
+constexpr int32_t kGraphMaxLen = 1024;
+constexpr double kGraphHoldSeconds = 1.0;
+
+// Pair count a light batch is padded to: the next power of four from 64
+// (64, 256, 1024) for batches that replay graphs, else the batch's own count.
+int32_t padded_pairs(const Worker *w, int32_t np) {
+    int64_t b = 64;
+    while (b < np) b <<= 2;
+    return (int32_t)std::min<int64_t>(b, w->cap_pairs);
 }
 
 // One batch: pack, copy in, align, copy out, scatter to the requests.
-int run_batch(gsw_server *srv, Worker *w, std::vector<Req *> &batch) {
+int run_batch(gsw_server *srv, Worker *w, std::vector<Req *> &batch, bool backlog) {
     int32_t np = 0;
     int64_t ql = 0, tl = 0;
     for (Req *r : batch) {
@@ -127,6 +153,29 @@ int run_batch(gsw_server *srv, Worker *w, std::vector<Req *> &batch) {
         std::memcpy(w->h_t + tl, r->t.data(), r->t.size());
         ql += (int64_t)r->q.size();
         tl += (int64_t)r->t.size();
+    }
+    // padding to the batch's bucket: empty pairs (records ignored)
+    // a light batch replays a captured graph when the queue is keeping up
+    // (nothing left behind it) and the batch is small; under a backlog the
+    // batches grow and vary, and launching them eagerly costs no captures
+    const int32_t nreal = np;
+    int32_t maxq = 0, maxt = 0;
+    for (int32_t p = 0; p < np; p++) {
+        maxq = std::max(maxq, w->h_qlen[p]);
+        maxt = std::max(maxt, w->h_tlen[p]);
+    }
+    // a backlog keeps the worker eager for a while (an overloaded queue comes
+    // and goes between batches; captures there only add to the wait)
+    const double tnow = srv->now();
+    if (backlog) w->eager_until = tnow + kGraphHoldSeconds;
+    const bool graph = w->graphs && !backlog && tnow >= w->eager_until && np <= kGraphMaxPairs &&
+                       maxq <= kGraphMaxLen && maxt <= kGraphMaxLen;
+    if (w->graphs) gsw::context_set_graph_buckets(w->ctx, graph);
+    for (const int32_t npad = graph ? padded_pairs(w, np) : np; np < npad; np++) {
+        w->h_qoff[np] = 0;
+        w->h_toff[np] = 0;
+        w->h_qlen[np] = 0;
+        w->h_tlen[np] = 0;
     }
     cudaStream_t st = w->st;
     // on an error, copies from this worker's pinned staging may still be
@@ -151,6 +200,11 @@ int run_batch(gsw_server *srv, Worker *w, std::vector<Req *> &batch) {
     // GSW_EINTERNAL: every record is complete, the flagged pairs' requests
     // report it (the worker sets each request's status from its records)
     if (rc != GSW_OK && rc != GSW_EINTERNAL) return fail(rc);
+    {
+        gsw_stats sts;
+        if (gsw_last_stats(w->ctx, &sts) == GSW_OK && sts.graph_segments > 0) w->graph_batches++;
+    }
+    np = nreal;
     e = cudaMemcpyAsync(w->h_res, w->d_res, sizeof(gsw_result) * (size_t)np, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(GSW_ECUDA);
@@ -198,6 +252,7 @@ void worker_loop(gsw_server *srv, Worker *w) {
     cudaSetDevice(srv->cfg.device);
     for (;;) {
         std::vector<Req *> batch;
+        bool backlog = false;
         {
             std::unique_lock<std::mutex> lk(srv->mu);
             // a heavy worker takes heavy requests, else light ones; a light
@@ -207,13 +262,14 @@ void worker_loop(gsw_server *srv, Worker *w) {
             if (!has_work()) return;  // stopping and drained
             if (w->heavy && !srv->heavy_queue.empty()) take(srv->heavy_queue, w, batch);
             else take(srv->queue, w, batch);
+            backlog = !srv->queue.empty();
             srv->stats.queued = (int32_t)(srv->queue.size() + srv->heavy_queue.size());
             srv->stats.running++;
             const double ts = srv->now();
             for (Req *r : batch) r->t_start = ts;
         }
         const auto t0 = Clock::now();
-        const int rc = run_batch(srv, w, batch);
+        const int rc = run_batch(srv, w, batch, backlog);
         const double secs = std::chrono::duration<double>(Clock::now() - t0).count();
         {
             std::lock_guard<std::mutex> lk(srv->mu);
@@ -430,6 +486,8 @@ int gsw_serve_get_stats(gsw_server *srv, gsw_serve_stats *out) {
     std::lock_guard<std::mutex> lk(srv->mu);
     *out = srv->stats;
     out->queued = (int32_t)(srv->queue.size() + srv->heavy_queue.size());
+    out->graph_batches = 0;
+    for (const auto &w : srv->workers) out->graph_batches += w->graph_batches.load();
     return GSW_OK;
 }
 

@@ -83,7 +83,7 @@ class ServeConfig(ctypes.Structure):
                 ("max_queue_requests", ctypes.c_int32), ("flags", ctypes.c_uint32), ("mask_len", ctypes.c_int32),
                 ("matrix", ctypes.c_void_p), ("alphabet", ctypes.c_int32), ("gap_open", ctypes.c_int32),
                 ("gap_extend", ctypes.c_int32), ("heavy_workers", ctypes.c_int32), ("heavy_cells", ctypes.c_int64),
-                ("heavy_sm_limit", ctypes.c_int32)]
+                ("heavy_sm_limit", ctypes.c_int32), ("light_graphs", ctypes.c_int32)]
 
 
 class ServeTimes(ctypes.Structure):
@@ -93,7 +93,7 @@ class ServeTimes(ctypes.Structure):
 class ServeStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
                 ("pairs", ctypes.c_uint64), ("cells", ctypes.c_uint64), ("busy_seconds", ctypes.c_double),
-                ("queued", ctypes.c_int32), ("running", ctypes.c_int32)]
+                ("queued", ctypes.c_int32), ("running", ctypes.c_int32), ("graph_batches", ctypes.c_uint64)]
 
 
 class GswError(RuntimeError):
@@ -474,11 +474,11 @@ class Server:
 
     def __init__(self, matrix, gap_open, gap_extend, flags=GSW_CIGAR, mask_len=-1, device=0, workers=4,
                  max_batch_pairs=8192, max_batch_letters=16 << 20, mem_budget_bytes=8 << 30, heavy_workers=0,
-                 heavy_cells=0, heavy_sm_limit=0):
+                 heavy_cells=0, heavy_sm_limit=0, light_graphs=0):
         self._m = np.ascontiguousarray(matrix, dtype=np.int8)
         cfg = ServeConfig(device, workers, max_batch_pairs, max_batch_letters, mem_budget_bytes, 0, flags,
                           mask_len, self._m.ctypes.data, self._m.shape[0], gap_open, gap_extend, heavy_workers,
-                          heavy_cells, heavy_sm_limit)
+                          heavy_cells, heavy_sm_limit, light_graphs)
         out = ctypes.c_void_p()
         _check(load().gsw_serve_create(ctypes.byref(cfg), ctypes.byref(out)), "gsw_serve_create")
         self.handle = out.value

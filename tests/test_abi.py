@@ -172,7 +172,8 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         'int main(void) {\n'
         ' printf("%zu %zu %zu %zu %zu\\n", sizeof(gsw_stats), offsetof(gsw_stats, ring_words),'
         ' offsetof(gsw_stats, internal_pairs), sizeof(gsw_record), offsetof(gsw_record, colmax));\n'
-        ' printf("%zu %zu\\n", sizeof(gsw_result), sizeof(gsw_serve_config));\n return 0; }\n')
+        ' printf("%zu %zu %zu %zu\\n", sizeof(gsw_result), sizeof(gsw_serve_config), sizeof(gsw_serve_stats),'
+        ' offsetof(gsw_serve_stats, graph_batches));\n return 0; }\n')
     exe = tmp_path / "lay"
     subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
@@ -180,7 +181,8 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
     b = [int(x) for x in b.split()]
     assert a == [ctypes.sizeof(gsw.GswStats), gsw.GswStats.ring_words.offset, gsw.GswStats.internal_pairs.offset,
                  ctypes.sizeof(gsw.GswRecord), gsw.GswRecord.colmax.offset]
-    assert b == [gsw.RESULT_DTYPE.itemsize, ctypes.sizeof(gsw.ServeConfig)]
+    assert b == [gsw.RESULT_DTYPE.itemsize, ctypes.sizeof(gsw.ServeConfig), ctypes.sizeof(gsw.ServeStats),
+                 gsw.ServeStats.graph_batches.offset]
 
 
 def test_results_handle_calls_check_arguments_without_gpu():

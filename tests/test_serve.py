@@ -110,3 +110,39 @@ def test_poll_timeout_unknown_id_and_bad_letters():
         assert ei.value.code == gsw.GSW_EINVAL
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("light_graphs", [0, -1])
+def test_light_batches_replay_captured_graphs(light_graphs):
+    # one worker, requests of similar shape served one after the other: with
+    # graphs on, batches padded to 64 pairs and bucketed lengths repeat one
+    # captured pipeline (replayed from the third batch on); with graphs off
+    # every batch launches eagerly.  Records and CIGARs equal the oracle's
+    # either way.
+    W = wl.dna_matrix(2, -2)
+    srv = gsw.Server(W, 3, 1, gsw.GSW_CIGAR, workers=1, max_batch_pairs=256, max_batch_letters=1 << 20,
+                     mem_budget_bytes=2 << 30, heavy_workers=-1, light_graphs=light_graphs)
+    try:
+        reqs = [wl.dna_short_reads(int(n), (200, 250), (900, 1000), 0.01, 0.001, 3, 0.10, seed=40 + k)
+                for k, n in enumerate([5, 9, 17, 3, 30, 12, 8, 21, 2, 16])]
+        got = []
+        for b in reqs:
+            rid = srv.submit(b.q, b.q_off, b.q_len, b.t, b.t_off, b.t_len)
+            rc, res, cig = srv.poll(rid, b.npairs, timeout_us=30_000_000)
+            assert rc == gsw.GSW_OK
+            got.append((res, cig))
+        st = srv.stats()
+    finally:
+        srv.close()
+    assert st["batches"] == len(reqs)
+    if light_graphs >= 0:
+        assert st["graph_batches"] >= 3
+    else:
+        assert st["graph_batches"] == 0
+    for b, (res, cig) in zip(reqs, got):
+        ores, ocg, _ = oracle.align_batch(b.q, b.q_off, b.q_len, b.t, b.t_off, b.t_len, W, 3, 1,
+                                          cigar_stride=int(b.q_len.max() + b.t_len.max() + 2))
+        for p in range(b.npairs):
+            for f in FIELDS:
+                assert int(res[f][p]) == int(ores[f][p]), (p, f)
+            assert _decode(res, cig, p) == oracle.decode_cigar(ocg[p, : ores["cigar_len"][p]])
