@@ -21,9 +21,10 @@
 // CTA in phases separated by a barrier, each strip far enough behind the one
 // above (ring_lag) that every boundary word it reads was written in a
 // completed phase; several pairs are in flight per CTA.  Per cell 4 bits go
-// to global memory: the source of H (0 diagonal, 1 E, 2 F), whether E opened
-// here and whether F opened here; lane k's 8 rows of one step form one word,
-// so a warp writes 128 contiguous bytes per step.
+// to global memory: H differs from the diagonal term (bit 0), H differs from E
+// (bit 1), E extends rather than opens here (bit 2), F extends rather than
+// opens here (bit 3); lane k's 8 rows of one step form one word, so a warp
+// writes 128 contiguous bytes per step.
 //
 // Walk.  One warp per pair stages 64 steps x 32 lanes of direction words in
 // shared memory and lane 0 walks from (la, lb) in state H with the fixed
@@ -198,12 +199,18 @@ struct BandStrip {
             for (int r = 0; r < kRR; r++) {
                 const int hleft = H[r];
                 const int e = E[r];
-                const bool eo = e == hleft - O;
-                const bool fo = f == hup - O;
                 const int dw = diag + w[r];
                 const int h = max(max(dw, e), f);
-                const uint32_t src = h == dw ? 0u : (h == e ? 1u : 2u);
-                bits |= (src | (eo ? 4u : 0u) | (fo ? 8u : 0u)) << (4 * r);
+                // each compared pair is ordered by the recurrence (h >= dw,
+                // h >= e, e >= H(i,j-1) - O, f >= H(i-1,j) - O), so "differs"
+                // is min(difference, 1): one add and one min per bit, and the
+                // nibble is put together by multiply-adds on the FMA pipe
+                const int nd = min(h - dw, 1);         // 1: H not from the diagonal
+                const int ne = min(h - e, 1);          // 1: H not from E
+                const int eno = min(e - hleft + O, 1);  // 1: E(i,j) extends, not opened
+                const int fno = min(f - hup + O, 1);    // 1: F(i,j) extends, not opened
+                const int nib = fno * 8 + eno * 4 + ne * 2 + nd;
+                bits += (uint32_t)nib << (4 * r);
                 const int ho = h - O;
                 E[r] = max(ho, e - X);
                 f = max(ho, f - X);
@@ -498,13 +505,13 @@ __global__ void __launch_bounds__(128) k_ring_walk(RingLaunch rl) {
                     const uint32_t wd = stage[(kRTile - 1 - (ts_hi - s2)) * kRP + k2] >> (4 * r2);
                     int op;
                     if (st == 0) {
-                        const int src = wd & 3;
-                        if (src == 0) { op = GSW_CIGAR_M; i--; j--; }
-                        else { st = src; continue; }
+                        // preference: the diagonal, then E, then F
+                        if (!(wd & 1)) { op = GSW_CIGAR_M; i--; j--; }
+                        else { st = (wd & 2) ? 2 : 1; continue; }
                     } else if (st == 1) {
-                        op = GSW_CIGAR_D; st = (wd & 4) ? 0 : 1; j--;
+                        op = GSW_CIGAR_D; st = (wd & 4) ? 1 : 0; j--;
                     } else {
-                        op = GSW_CIGAR_I; st = (wd & 8) ? 0 : 2; i--;
+                        op = GSW_CIGAR_I; st = (wd & 8) ? 2 : 0; i--;
                     }
                     if (op == cur) {
                         len++;
