@@ -86,6 +86,13 @@ struct RingJob {
     int *final_h;          // H(la, lb)
 };
 
+// bits |= m when a != b: a compare into a predicate and a predicated or
+__device__ __forceinline__ void or_if_ne(uint32_t &bits, int a, int b, uint32_t m) {
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.s32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+        : "+r"(bits)
+        : "r"(a), "r"(b), "r"(m));
+}
+
 // One strip of the banded fill for lane k of a warp.
 struct BandStrip {
     RingJob job;
@@ -93,14 +100,16 @@ struct BandStrip {
     int A, O, X;
     uint32_t *psm;
     int k, x, c0, c1, c1a, nsteps, i0;
-    bool first, last;
+    int fin_j;     // column of H(la, lb) when one of this lane's rows is la, else -1
+    bool first, last, bo;  // bo: this lane writes the strip's bottom row
     const int2 *bin;
     int2 *bout;
     uint32_t *dout;
-    int H[kRR], E[kRR];
-    int hdiag, xh, xf;
-    int2 b_cur, b_nxt;
-    int nt;  // target letter of the next step
+    int HO[kRR], E[kRR];  // H(i, j) - O and E(i, j + 1) of the lane's rows
+    int hdiag, xh, xf;     // H values are all kept as H - O
+    int2 b_cur, b_nxt;  // boundary words of the current and next 32 columns
+    int l_cur, l_nxt;   // target letters of the same columns
+    int a_prev;         // target letter this lane used at the previous step
 
     __device__ void begin(const RingJob &jb, const Scoring &sc, const int8_t *sW, uint32_t *psm_, int lane, int x_) {
         job = jb;
@@ -119,59 +128,68 @@ struct BandStrip {
         i0 = 1 + x * kRS + k * kRR;
         first = x == 0;
         last = x == g.nstrips - 1;
+        bo = k == kRP - 1 && !last;
+        fin_j = (i0 <= g.la && g.la < i0 + kRR) ? g.lb : -1;
         // boundary word of column j at [j - 1]
         bin = job.bnd + (size_t)((x + 1) & 1) * g.lb;
         bout = job.bnd + (size_t)(x & 1) * g.lb;
         dout = job.dirs + (size_t)x * g.stride * kRP;
-        // profile: W(q_i, a) of this lane's rows (0 below the last row)
+        // profile: W(q_i, a) + O of this lane's rows (W = 0 below the last
+        // row); with H kept as H - O the diagonal term is one add
         for (int r = 0; r < kRR; r++) {
             const int i = i0 + r;
             const int qa = i <= g.la ? min((int)job.q[i - 1], A - 1) : -1;
-            for (int a = 0; a < A; a++) psm[ridx(a, r, k)] = (uint32_t)(qa >= 0 ? (int)W[qa * A + a] : 0);
+            for (int a = 0; a < A; a++) psm[ridx(a, r, k)] = (uint32_t)((qa >= 0 ? (int)W[qa * A + a] : 0) + O);
         }
         __syncwarp();
         // left boundary: column c0 - 1 is column 0 (H = -O - (i-1)X) or outside (-inf)
 #pragma unroll
         for (int r = 0; r < kRR; r++) {
-            H[r] = c0 == 1 ? -O - (i0 + r - 1) * X : kRNeg;
-            E[r] = c0 == 1 ? H[r] - O : kRNeg;  // E(i, c0)
+            HO[r] = (c0 == 1 ? -O - (i0 + r - 1) * X : kRNeg) - O;
+            E[r] = c0 == 1 ? HO[r] : kRNeg;  // E(i, c0) = H(i, 0) - O
         }
         // H(i0 - 1, c0 - 1), the first diagonal input of lane 0
         const int ia = i0 - 1, ja = c0 - 1;
-        if (ja == 0) hdiag = ia == 0 ? 0 : -O - (ia - 1) * X;
-        else if (first) hdiag = -O - (ja - 1) * X;
-        else hdiag = ja <= c1a ? bin[ja - 1].x : kRNeg;
+        if (ja == 0) hdiag = (ia == 0 ? 0 : -O - (ia - 1) * X) - O;
+        else if (first) hdiag = -O - (ja - 1) * X - O;
+        else hdiag = ja <= c1a ? bin[ja - 1].x : kRNeg - O;
         // H of the row above this lane's first row, at column c0 - 1: lane k
         // takes it as the diagonal input of its first column
-        xh = c0 == 1 ? (i0 == 1 ? 0 : -O - (i0 - 2) * X) : kRNeg;
+        xh = (c0 == 1 ? (i0 == 1 ? 0 : -O - (i0 - 2) * X) : kRNeg) - O;
         xf = kRNeg;
-        b_cur = make_int2(kRNeg, kRNeg);
+        b_cur = make_int2(kRNeg - O, kRNeg);
         b_nxt = b_cur;
-        if (!first) prefetch(0);
-        nt = (c0 - k >= 1 && c0 - k <= c1) ? min((int)job.t[c0 - k - 1], A - 1) : 0;
+        l_cur = l_nxt = a_prev = 0;
+        prefetch(0);
     }
 
-    // lane k loads the boundary word of column c0 + s0 + k (columns the strip
-    // above did not reach are -inf)
+    // lane k loads the boundary word (H - O, F of the row below) of column
+    // c0 + s0 + k (columns the strip above did not reach are -inf) and the
+    // target letter of that column (lane 0 takes it at step s0 + k; the other
+    // lanes get their letters from the lane before, one step later)
     __device__ __forceinline__ void prefetch(int s0) {
         const int j = c0 + s0 + k;
-        b_nxt = (j <= c1a) ? bin[j - 1] : make_int2(kRNeg, kRNeg);
+        b_nxt = (j <= c1a) ? bin[j - 1] : make_int2(kRNeg - O, kRNeg);
+        l_nxt = j <= c1 ? min((int)job.t[j - 1], A - 1) : 0;
     }
 
-    __device__ __forceinline__ void step(int s) {
+    __device__ __forceinline__ void step(int s, uint32_t *dp) {
         const int j = c0 + s - k;
+        const int bi = s & (kRP - 1);
+        if (bi == 0) {
+            b_cur = b_nxt;
+            l_cur = l_nxt;
+            prefetch(s + kRP);
+        }
+        int a = __shfl_up_sync(0xFFFFFFFFu, a_prev, 1);
+        const int a0 = __shfl_sync(0xFFFFFFFFu, l_cur, bi);
         int hin = xh, fin = xf;
         if (first) {
             if (k == 0) {
-                hin = -O - (j - 1) * X;  // H(0, j)
-                fin = hin - O;           // F(1, j): F(0, j) = -inf
+                hin = -O - (j - 1) * X - O;  // H(0, j) - O
+                fin = hin;                   // F(1, j) = H(0, j) - O: F(0, j) = -inf
             }
         } else {
-            const int bi = s & (kRP - 1);
-            if (bi == 0) {
-                b_cur = b_nxt;
-                prefetch(s + kRP);
-            }
             const int hb = __shfl_sync(0xFFFFFFFFu, b_cur.x, bi);
             const int fb = __shfl_sync(0xFFFFFFFFu, b_cur.y, bi);
             if (k == 0) {
@@ -179,16 +197,13 @@ struct BandStrip {
                 fin = fb;
             }
         }
-        const int a = nt;
-        {
-            const int j1 = j + 1;
-            nt = (j1 >= 1 && j1 <= c1) ? min((int)job.t[j1 - 1], A - 1) : 0;
-        }
+        if (k == 0) a = a0;
+        a_prev = a;
         int diag = hdiag;
         hdiag = hin;
-        int hup = hin, f = fin;
+        int houp = hin, f = fin;
         uint32_t bits = 0;
-        if (j >= c0 && j <= c1) {
+        if ((unsigned)(j - c0) <= (unsigned)(c1 - c0)) {
             int w[kRR];
 #pragma unroll
             for (int r = 0; r < kRR; r += 4) {
@@ -197,44 +212,40 @@ struct BandStrip {
             }
 #pragma unroll
             for (int r = 0; r < kRR; r++) {
-                const int hleft = H[r];
+                const int holeft = HO[r];  // H(i, j-1) - O: where E(i, j) opens
                 const int e = E[r];
-                const int dw = diag + w[r];
+                const int dw = diag + w[r];  // H(i-1, j-1) + W(q_i, t_j)
                 const int h = max(max(dw, e), f);
-                // each compared pair is ordered by the recurrence (h >= dw,
-                // h >= e, e >= H(i,j-1) - O, f >= H(i-1,j) - O), so "differs"
-                // is min(difference, 1): one add and one min per bit, and the
-                // nibble is put together by multiply-adds on the FMA pipe
-                const int nd = min(h - dw, 1);         // 1: H not from the diagonal
-                const int ne = min(h - e, 1);          // 1: H not from E
-                const int eno = min(e - hleft + O, 1);  // 1: E(i,j) extends, not opened
-                const int fno = min(f - hup + O, 1);    // 1: F(i,j) extends, not opened
-                const int nib = fno * 8 + eno * 4 + ne * 2 + nd;
-                bits += (uint32_t)nib << (4 * r);
+                // one compare and one predicated or per bit
+                or_if_ne(bits, h, dw, 1u << (4 * r));      // H not from the diagonal
+                or_if_ne(bits, h, e, 2u << (4 * r));       // H not from E
+                or_if_ne(bits, e, holeft, 4u << (4 * r));  // E(i, j) extends, not opened
+                or_if_ne(bits, f, houp, 8u << (4 * r));    // F(i, j) extends, not opened
                 const int ho = h - O;
                 E[r] = max(ho, e - X);
                 f = max(ho, f - X);
-                diag = hleft;
-                hup = h;
-                H[r] = h;
+                diag = holeft;
+                houp = ho;
+                HO[r] = ho;
             }
-            if (i0 <= job.g.la && job.g.la < i0 + kRR && j == job.g.lb) {
+            if (j == fin_j) {
 #pragma unroll
                 for (int r = 0; r < kRR; r++)
-                    if (i0 + r == job.g.la) *job.final_h = H[r];
+                    if (i0 + r == job.g.la) *job.final_h = HO[r] + O;
             }
-            if (k == kRP - 1 && !last) bout[j - 1] = make_int2(H[kRR - 1], f);
+            if (bo) bout[j - 1] = make_int2(HO[kRR - 1], f);
         }
-        dout[(size_t)s * kRP + k] = bits;
-        xh = __shfl_up_sync(0xFFFFFFFFu, H[kRR - 1], 1);
+        *dp = bits;
+        xh = __shfl_up_sync(0xFFFFFFFFu, HO[kRR - 1], 1);
         xf = __shfl_up_sync(0xFFFFFFFFu, f, 1);
     }
 
     // steps [s0, s1); true when the strip is complete
     __device__ bool run(int s0, int s1) {
         s1 = min(s1, nsteps);
+        uint32_t *dp = dout + (size_t)s0 * kRP + k;
 #pragma unroll 1
-        for (int s = s0; s < s1; s++) step(s);
+        for (int s = s0; s < s1; s++, dp += kRP) step(s, dp);
         return s1 >= nsteps;
     }
 };
