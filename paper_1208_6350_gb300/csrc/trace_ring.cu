@@ -26,10 +26,12 @@
 // opens here (bit 3); lane k's 8 rows of one step form one word, so a warp
 // writes 128 contiguous bytes per step.
 //
-// Walk.  One warp per pair stages 64 steps x 32 lanes of direction words in
-// shared memory and lane 0 walks from (la, lb) in state H with the fixed
-// preference (diagonal, then E, then F; open before extend), emitting runs
-// (len << 4) | op in reverse, then the warp writes them forward.
+// Walk.  One warp per pair stages tiles of 32 steps x 32 lanes of direction
+// words in shared memory and lane 0 walks from (la, lb) in state H with the
+// fixed preference (diagonal, then E, then F; open before extend), emitting
+// runs (len << 4) | op in reverse, then the warp writes them forward.  While
+// lane 0 walks one tile the other lanes copy the 32 steps below it (where the
+// path goes next unless it leaves the strip) into a second buffer.
 #include "gsw_impl.cuh"
 
 #include <climits>
@@ -47,7 +49,7 @@ constexpr int kRW = 8;           // warps per CTA
 constexpr int kRC = 64;          // steps per phase
 constexpr int kRSlots = 4;       // pairs in flight per CTA
 constexpr int kRNeg = -(1 << 28);
-constexpr int kRTile = 64;       // steps of direction words the walk stages
+constexpr int kRTile = 32;       // steps of direction words in each of the walk's two tiles
 
 // Geometry of one pair's banded DP.
 struct RingGeom {
@@ -467,11 +469,23 @@ __global__ void __launch_bounds__(1024) k_ring_needs(BatchView b, Scoring sc, co
 }
 
 // Walk of one pair by one warp (see the file comment).
+// A warp copies `steps` rows of 32 direction words (128 bytes each, 16-byte
+// aligned: every pair's words start at a multiple of 32 words) into shared
+// memory without waiting; walk_copy_wait waits for this lane's copies.
+__device__ __forceinline__ void walk_copy(uint32_t *dst, const uint32_t *src, int steps, int lane) {
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(dst);
+    for (int c = lane; c < steps * (kRP / 4); c += 32)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + 16u * c), "l"(src + 4 * c) : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void walk_copy_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __global__ void __launch_bounds__(128) k_ring_walk(RingLaunch rl) {
-    __shared__ uint32_t tile[4][kRTile * kRP];
+    __shared__ __align__(16) uint32_t tile[4][2][kRTile * kRP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gwarp = blockIdx.x * 4 + warp, nwarps = gridDim.x * 4;
-    uint32_t *stage = tile[warp];
+    uint32_t (*stage)[kRTile * kRP] = tile[warp];
     uint32_t *ops = rl.ops + (size_t)gwarp * rl.op_words;
     const int g0 = rl.group[0], g1 = rl.group[1];
     for (int t = g0 + gwarp; t < g1; t += nwarps) {
@@ -486,43 +500,81 @@ __global__ void __launch_bounds__(128) k_ring_walk(RingLaunch rl) {
         }
         const uint32_t *dirs = rl.pool + (rl.prefix[t] - rl.prefix[g0]);
         int i = g.la, j = g.lb, st = 0, cur = -1, len = 0, runs = 0;
-        int tx = -1, ts_hi = -1;  // staged tile: strip, top step
+        // staged tiles: strip and step range [lo, hi] of the current buffer
+        // and of the one being filled ahead of it (the steps just below, in
+        // the same strip, where the walk goes next unless it leaves the strip)
+        int cx = -1, clo = 0, chi = -1, px = -1, plo = 0, phi = -1, buf = 0;
         while (ok && i > 0 && j > 0) {
             const int x = (i - 1) / kRS;
             const int k = ((i - 1) % kRS) / kRR;
-            if (j < g.c0(x) || j > g.c1(x)) {  // left the region (never for an optimal path)
+            const int c0 = g.c0(x);
+            if (j < c0 || j > g.c1(x)) {  // left the region (never for an optimal path)
                 ok = false;
                 break;
             }
-            const int s = j - g.c0(x) + k;
-            if (x != tx || s > ts_hi || s <= ts_hi - kRTile) {
-                tx = x;
-                ts_hi = s;
-                const int lo = max(0, s - kRTile + 1);
-                const uint32_t *src = dirs + ((size_t)x * g.stride + lo) * kRP;
-                for (int w = lane; w < (s - lo + 1) * kRP; w += 32) stage[w + (kRTile - 1 - (s - lo)) * kRP] = src[w];
+            const int s = j - c0 + k;
+            if (x != cx || s < clo || s > chi) {
+                walk_copy_wait();
                 __syncwarp();
+                if (x == px && s >= plo && s <= phi) {
+                    buf ^= 1;
+                    cx = px, clo = plo, chi = phi;
+                } else {
+                    cx = x, chi = s, clo = max(0, s - kRTile + 1);
+                    walk_copy(stage[buf], dirs + ((size_t)x * g.stride + clo) * kRP, chi - clo + 1, lane);
+                    walk_copy_wait();
+                    __syncwarp();
+                }
+                px = -1;
+                if (clo > 0) {
+                    px = cx, phi = clo - 1, plo = max(0, clo - kRTile);
+                    walk_copy(stage[buf ^ 1], dirs + ((size_t)px * g.stride + plo) * kRP, phi - plo + 1, lane);
+                }
             }
             if (lane == 0) {
-                // walk inside the staged tile
-                for (;;) {
-                    if (i <= 0 || j <= 0) break;
-                    const int x2 = (i - 1) / kRS;
-                    if (x2 != tx) break;
-                    if (j < g.c0(x2) || j > g.c1(x2)) { ok = false; break; }  // left the region
-                    const int k2 = ((i - 1) % kRS) / kRR, r2 = (i - 1) % kRR;
-                    const int s2 = j - g.c0(x2) + k2;
-                    if (s2 > ts_hi || s2 <= ts_hi - kRTile) break;
-                    const uint32_t wd = stage[(kRTile - 1 - (ts_hi - s2)) * kRP + k2] >> (4 * r2);
+                // walk inside the tile: idx = (s - clo) * 32 + k, the word of
+                // row i at column j; d = j - c0 (the region's left edge)
+                const uint32_t *tl = stage[buf];
+                int kk = k, sh = 4 * ((i - 1) % kRR), d = j - c0, idx = (s - clo) * kRP + k;
+                while (i > 0 && j > 0 && idx >= 0 && kk >= 0) {
+                    if (d < 0) {  // left the region
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t wd = tl[idx] >> sh;
                     int op;
-                    if (st == 0) {
-                        // preference: the diagonal, then E, then F
-                        if (!(wd & 1)) { op = GSW_CIGAR_M; i--; j--; }
-                        else { st = (wd & 2) ? 2 : 1; continue; }
-                    } else if (st == 1) {
-                        op = GSW_CIGAR_D; st = (wd & 4) ? 1 : 0; j--;
+                    bool up, left;
+                    if (st == 0 && !(wd & 1)) {
+                        op = GSW_CIGAR_M;  // preference: the diagonal, then E, then F
+                        up = left = true;
                     } else {
-                        op = GSW_CIGAR_I; st = (wd & 8) ? 2 : 0; i--;
+                        if (st == 0) st = (wd & 2) ? 2 : 1;
+                        if (st == 1) {
+                            op = GSW_CIGAR_D;
+                            st = (wd & 4) ? 1 : 0;
+                            up = false;
+                            left = true;
+                        } else {
+                            op = GSW_CIGAR_I;
+                            st = (wd & 8) ? 2 : 0;
+                            up = true;
+                            left = false;
+                        }
+                    }
+                    if (left) {
+                        j--;
+                        d--;
+                        idx -= kRP;
+                    }
+                    if (up) {
+                        i--;
+                        if (sh > 0) {
+                            sh -= 4;
+                        } else {  // the lane above: one step earlier
+                            sh = 4 * (kRR - 1);
+                            kk--;
+                            idx -= kRP + 1;
+                        }
                     }
                     if (op == cur) {
                         len++;
@@ -536,8 +588,9 @@ __global__ void __launch_bounds__(128) k_ring_walk(RingLaunch rl) {
             ok = __shfl_sync(0xFFFFFFFFu, (int)ok, 0);
             i = __shfl_sync(0xFFFFFFFFu, i, 0);
             j = __shfl_sync(0xFFFFFFFFu, j, 0);
-            __syncwarp();
         }
+        walk_copy_wait();
+        __syncwarp();
         if (lane == 0 && ok) {
             // row 0 or column 0: the rest is one gap (D along row 0, I along column 0)
             const int rest_op = i == 0 ? GSW_CIGAR_D : GSW_CIGAR_I;
