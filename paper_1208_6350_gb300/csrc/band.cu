@@ -13,7 +13,10 @@
 //
 // Banded SW between begin and end (item (1)): global Gotoh restricted to the
 // provable band (band_halfwidth), with 4 decision bits per cell and the same
-// traceback preferences as the oracle.  The traceback band is never wider than
+// traceback preferences as the oracle.  The bits of a cell: H differs from the
+// diagonal term (bit 0), H differs from E (bit 1), E extends rather than opens
+// (bit 2), F extends rather than opens (bit 3).  The DP keeps H as H - O, so
+// the opening candidates of E and F are stored values.  The traceback band is never wider than
 // the reverse band (it bounds the same gap letters with fewer aligned pairs).
 //
 // Lanes of a warp take consecutive pairs of a list sorted by rows, so their
@@ -63,6 +66,21 @@ __device__ __forceinline__ void put_nib(typename DirWord<W>::T &w, int k, uint32
     }
 }
 
+// The 32-bit word of w that holds nibble k.
+template <int W>
+__device__ __forceinline__ uint32_t &nib_word(typename DirWord<W>::T &w, int k) {
+    if constexpr (W == 8) return w;
+    else if constexpr (W == 16) return k < 8 ? w.x : w.y;
+    else return k < 8 ? w.x : k < 16 ? w.y : k < 24 ? w.z : w.w;
+}
+
+// bits |= m when a != b: a compare into a predicate and a predicated or
+__device__ __forceinline__ void or_if_ne(uint32_t &bits, int a, int b, uint32_t m) {
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.s32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+        : "+r"(bits)
+        : "r"(a), "r"(b), "r"(m));
+}
+
 template <int W>
 __device__ __forceinline__ uint32_t get_nib(const typename DirWord<W>::T &w, int k) {
     if constexpr (W == 8) {
@@ -97,14 +115,16 @@ struct BandSeq {
 template <int W, bool REV, bool DNA>
 __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int A, int O, int X, int target,
                         typename DirWord<W>::T *dirs, int *out_i, int *out_j, int *final_h, int rstride = 32) {
-    int Hp[W], Fp[W];
-    int tw[W];  // target letter of each band cell's column in the current row (sliding window)
+    int Hp[W], Fp[W];  // H - O and F of the previous row's band cells
+    int tw[W];  // target letter (DNA: 8 x letter, a byte shift) of each band cell's column in the current row
+    constexpr int TM = DNA ? 8 : 1;
+    const int negho = kNegB - O;  // H - O of a cell outside
 #pragma unroll
     for (int k = 0; k < W; k++) {
-        Hp[k] = kNegB;
+        Hp[k] = negho;
         Fp[k] = kNegB;
         const int jj = dlo + k - 1;  // row 0: letter index j - 1 = dlo + k - 1 (shifted in before use)
-        tw[k] = (jj >= 0 && jj < s.cols) ? min((int)s.t[(long long)jj * s.ts], A - 1) : 0;
+        tw[k] = (jj >= 0 && jj < s.cols) ? TM * min((int)s.t[(long long)jj * s.ts], A - 1) : 0;
     }
     int best_j = INT_MAX, best_i = -1;
     int fin = kNegB;
@@ -112,9 +132,10 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
     auto qletter = [&](int i) { return i >= 1 && i <= s.rows ? min((int)s.q[(long long)(i - 1) * s.qs], A - 1) : 0; };
     auto tletter = [&](int i) {
         const int jj = i + dlo + W - 2;
-        return (jj >= 0 && jj < s.cols) ? min((int)s.t[(long long)jj * s.ts], A - 1) : 0;
+        return (jj >= 0 && jj < s.cols) ? TM * min((int)s.t[(long long)jj * s.ts], A - 1) : 0;
     };
     int qa_next = qletter(1), tn_next = tletter(1);
+    typename DirWord<W>::T *drow = dirs;
     for (int i = 0; i <= s.rows; i++) {
         const int qa = i >= 1 ? qa_next : 0;
         uint32_t wpack = 0;  // DNA: the 4 scores of the query letter, one byte each
@@ -128,7 +149,7 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
             qa_next = qletter(i + 1);
             tn_next = tletter(i + 1);
         }
-        int hleft = kNegB, eleft = kNegB;
+        int holeft = negho, eleft = kNegB;
         typename DirWord<W>::T dw;
         zero<W>(dw);
         int row_hit = -1;
@@ -140,25 +161,29 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
         if (interior) {
 #pragma unroll
             for (int k = 0; k < W; k++) {
-                const int hup = k + 1 < W ? Hp[k + 1] : kNegB;
+                const int houp = k + 1 < W ? Hp[k + 1] : negho;  // H(i-1, j) - O: where F opens
                 const int fup = k + 1 < W ? Fp[k + 1] : kNegB;
-                const int fo = hup - O, eo = hleft - O;
-                int F = max(fo, fup - X);
-                int E = max(eo, eleft - X);
+                const int F = max(houp, fup - X);
+                const int E = max(holeft, eleft - X);
                 int w;
-                if constexpr (DNA) w = (int)(int8_t)(uint8_t)(wpack >> (8 * tw[k]));
+                if constexpr (DNA) w = (int)(int8_t)(uint8_t)(wpack >> tw[k]);
                 else w = wrow[tw[k]];
-                const int hdg = Hp[k] + w;
+                const int hdg = Hp[k] + w + O;  // H(i-1, j-1) + W
                 const int H = max(hdg, max(E, F));
                 if constexpr (REV) {
                     if (H == target && row_hit < 0) row_hit = i + dlo + k;
                 } else {
-                    const uint32_t src = H == hdg ? 0u : (H == E ? 1u : 2u);
-                    put_nib<W>(dw, k, src | (E == eo ? 4u : 0u) | (F == fo ? 8u : 0u));
+                    uint32_t &bw = nib_word<W>(dw, k);
+                    const int sh = 4 * (k & 7);
+                    or_if_ne(bw, H, hdg, 1u << sh);
+                    or_if_ne(bw, H, E, 2u << sh);
+                    or_if_ne(bw, E, holeft, 4u << sh);
+                    or_if_ne(bw, F, houp, 8u << sh);
                 }
-                Hp[k] = H;
+                const int ho = H - O;
+                Hp[k] = ho;
                 Fp[k] = F;
-                hleft = H;
+                holeft = ho;
                 eleft = E;
             }
         } else {
@@ -166,25 +191,23 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
         for (int k = 0; k < W; k++) {
             const int j = i + dlo + k;
             const bool valid = k < wb && j >= 0 && j <= s.cols;
-            const int hup = k + 1 < W ? Hp[k + 1] : kNegB;
+            const int houp = k + 1 < W ? Hp[k + 1] : negho;
             const int fup = k + 1 < W ? Fp[k + 1] : kNegB;
             int F = kNegB, hdg = kNegB, E = kNegB, H;
             bool fopen = false, eopen = false;
             if (i >= 1) {
-                const int fo = hup - O;
-                F = max(fo, fup - X);
-                fopen = F == fo;
+                F = max(houp, fup - X);
+                fopen = F == houp;
             }
             if (i >= 1 && j >= 1 && valid) {
                 int w;
-                if constexpr (DNA) w = (int)(int8_t)(uint8_t)(wpack >> (8 * tw[k]));
+                if constexpr (DNA) w = (int)(int8_t)(uint8_t)(wpack >> tw[k]);
                 else w = wrow[tw[k]];
-                hdg = Hp[k] + w;
+                hdg = Hp[k] + w + O;
             }
             if (j >= 1) {
-                const int eo = hleft - O;
-                E = max(eo, eleft - X);
-                eopen = E == eo;
+                E = max(holeft, eleft - X);
+                eopen = E == holeft;
             }
             H = max(hdg, max(E, F));
             if (i == 0 && j == 0) H = 0;
@@ -196,14 +219,14 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
             if constexpr (REV) {
                 if (i >= 1 && j >= 1 && H == target && row_hit < 0) row_hit = j;
             } else {
-                const uint32_t src = (i >= 1 && j >= 1 && hdg > kNegBHalf && H == hdg) ? 0u : (H == E ? 1u : 2u);
-                put_nib<W>(dw, k, src | (eopen ? 4u : 0u) | (fopen ? 8u : 0u));
+                const bool diag = i >= 1 && j >= 1 && hdg > kNegBHalf && H == hdg;
+                put_nib<W>(dw, k, (diag ? 0u : 1u) | (H != E ? 2u : 0u) | (eopen ? 0u : 4u) | (fopen ? 0u : 8u));
                 if (i == s.rows && j == s.cols) fin = H;
             }
             // this row's value becomes the next row's "previous row"
-            Hp[k] = H;
+            Hp[k] = H - O;
             Fp[k] = F;
-            hleft = H;
+            holeft = H - O;
             eleft = E;
         }
         }
@@ -215,7 +238,8 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
             // no later row can reach a column <= best_j inside the band
             if (best_j != INT_MAX && i + 1 + dlo >= best_j) break;
         } else {
-            dirs[(long long)i * rstride] = dw;
+            *drow = dw;
+            drow += rstride;
         }
     }
     if constexpr (REV) {
@@ -250,24 +274,21 @@ __device__ int band_walk(const typename DirWord<W>::T *dirs, int la, int lb, int
         }
         const uint32_t nib = get_nib<W>(word, k);
         int op;
-        if (state == 0) {
-            const int src = nib & 3;
-            if (src == 0) {
-                op = GSW_CIGAR_M;
-                i--;
-                j--;
-            } else {
-                state = src;
-                continue;
-            }
-        } else if (state == 1) {
-            op = GSW_CIGAR_D;
-            state = (nib & 4) ? 0 : 1;
+        if (state == 0 && !(nib & 1)) {
+            op = GSW_CIGAR_M;  // preference: the diagonal, then E, then F
+            i--;
             j--;
         } else {
-            op = GSW_CIGAR_I;
-            state = (nib & 8) ? 0 : 2;
-            i--;
+            if (state == 0) state = (nib & 2) ? 2 : 1;
+            if (state == 1) {
+                op = GSW_CIGAR_D;
+                state = (nib & 4) ? 1 : 0;
+                j--;
+            } else {
+                op = GSW_CIGAR_I;
+                state = (nib & 8) ? 2 : 0;
+                i--;
+            }
         }
         if (op == cur) {
             len++;
