@@ -830,8 +830,9 @@ __global__ void __launch_bounds__(kBlock, fill_min_blocks(VID)) k_fill(FillLaunc
 // bottom row (H, F) and the running column maxima that strip x-1 leaves in
 // global scratch, one column at a time, so several strips of a pair can run
 // at once when each stays far enough behind the one above it.  The warps of
-// the CTA (one 32-lane folded ring each, 512 rows per strip in 16-bit lanes)
-// advance in phases of kLongChunk steps separated by a CTA barrier, which
+// the CTA (one 32-lane folded ring each; in 16-bit lanes 1,024 rows per strip
+// for DNA, 512 for general alphabets) advance in phases of kLongChunk steps
+// separated by a CTA barrier, which
 // also makes the previous phases' global writes visible.  Strip x+1 starts
 // long_lag() phases after strip x, so every boundary word and column maximum
 // it reads (one block of 32 columns ahead) was written in a completed phase,
@@ -843,7 +844,7 @@ __global__ void __launch_bounds__(kBlock, fill_min_blocks(VID)) k_fill(FillLaunc
 // strip of a pair no earlier than long_lag() phases after the previous one),
 // and opens the next pair of the class in a free scratch slot, so the end of
 // one pair overlaps the start of the next.
-constexpr int kLongChunk = 64;
+constexpr int kLongChunk = 128;
 constexpr int kLongSlots = 4;  // pairs in flight per CTA
 
 template <class L>
@@ -857,7 +858,7 @@ __host__ __device__ constexpr int long_lag() {
 // Lag of a banded reversed fill, whose strip x+1 starts up to SP columns
 // right of strip x: strip x+1 reads absolute column c0(x+1) + s + 2P - 1 at
 // its step s, which strip x writes at its step c0(x+1) - c0(x) + s + 2P - 1
-// + dw, so (lag - 1) * C >= SP + 2P - 1 + dw (16-bit lanes: 11 phases).  The
+// + dw, so (lag - 1) * C >= SP + 2P - 1 + dw (16-bit DNA lanes: 10 phases).  The
 // same lag keeps strip x+2's writes after strip x+1's reads of the ping-pong
 // buffer (lag * C + dw > SP).
 template <class L, int SP>
@@ -1040,11 +1041,16 @@ __device__ void long_schedule(const FillLaunch &fl, int cls, LongShared<NW> &sh,
 template <bool DNA, bool S32>
 struct LongCfg {
     using L = std::conditional_t<S32, L32, L16>;
-    static constexpr int P = 32, R = 8;
-    static constexpr int NW = DNA ? 8 : 4;
-    // blocks per SM the registers are kept for: 128 registers a thread
-    // (the shared-memory profile allows 3 DNA blocks, 2 fit the registers)
-    static constexpr int MINB = DNA ? 2 : 4;
+    // DNA in 16-bit lanes: 16 row words per lane (1,024 rows per strip), so
+    // the per-step work of a lane (letters, profile loads, shuffles, tracker
+    // bookkeeping, boundary and max-array traffic) is spread over 32 cells;
+    // 4 warps per CTA and 3 CTAs per SM (168 registers a thread, 64 KB of
+    // profile per CTA).  Measured on 10,000 long reads against 8 row words and
+    // 8 warps (2 CTAs per SM): forward fill 265 -> 218 ms, reverse 105 -> 91
+    // ms; 12 or 20-24 row words, 2 or 8 warps per CTA were slower.
+    static constexpr int P = 32, R = (DNA && !S32) ? 16 : 8;
+    static constexpr int NW = 4;
+    static constexpr int MINB = DNA ? 3 : 4;
     static constexpr int SP = S32 ? P * R : 2 * P * R;
     static constexpr int CLS = S32 ? kClassLong32 : kClassLong16;
 };

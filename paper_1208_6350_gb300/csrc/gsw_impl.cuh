@@ -94,8 +94,9 @@ constexpr int kVarMaxS16 = 6;  // the default rule picks among 0..6
 constexpr int kVarP8First = 8;
 // Two more fill classes: pairs whose query spans many strips run on a whole
 // CTA (k_fill_long), one 32-lane warp per strip, strips pipelined across the
-// CTA's warps; 16-bit lanes (2*32*8 = 512 rows per strip) or 32-bit lanes
-// (256 rows per strip).  One pair per task.
+// CTA's warps; 16-bit lanes (2*32*16 = 1,024 rows per strip for DNA, 2*32*8 =
+// 512 for general alphabets) or 32-bit lanes (256 rows per strip).  One pair
+// per task.
 constexpr int kClassLong16 = kNumVariants;
 constexpr int kClassLong32 = kNumVariants + 1;
 constexpr int kNumFillClasses = kNumVariants + 2;
@@ -105,16 +106,13 @@ __host__ __device__ inline Variant variant_at(int v) {
     case id: return Variant{P, R, S32};
         GSW_FILL_VARIANTS(GSW_VARIANT_CASE)
 #undef GSW_VARIANT_CASE
-    case kClassLong16: return Variant{32, 8, 0};
+    case kClassLong16: return Variant{32, 16, 0};  // (DNA; general alphabets 8 row words)
     default: return Variant{32, 8, 1};
     }
 }
-// Warps of a k_fill_long CTA: 8 for the 4-letter DNA profile, 4 for general
-// alphabets (whose 32-lane profiles take 6x the shared memory).
-__host__ __device__ inline int long_warps(bool dna) { return dna ? 8 : 4; }
-// A query goes to the CTA kernel when it spans at least 3.5 strips of 4-letter
-// DNA (a few such pairs in flight keep every warp busy), or more than 8
-// strips of a general alphabet (whose CTA holds fewer warps per SM).
+// A query goes to the CTA kernel when it spans more than 3.5 x 512 rows of
+// 4-letter DNA (a few such pairs in flight keep every warp busy), or more than
+// 8 x 512 rows of a general alphabet (whose CTA holds fewer warps per SM).
 __host__ __device__ inline bool long_pair(int rows, bool s32, bool dna) {
     const int sp = s32 ? 256 : 512;
     return dna ? 2 * rows > 7 * sp : rows > 8 * sp;

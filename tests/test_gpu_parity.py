@@ -214,9 +214,10 @@ def _implanted(rng, A, qlens, flank, p_sub):
 
 
 def test_cta_kernel_many_strips(ctx):
-    # queries of 3.5-18 strips of 512 rows: the CTA kernel, with more strips
-    # than warps and several pairs in flight per CTA, mixed in one batch with
-    # short pairs of the per-group variants
+    # queries of 1,800-9,000 rows (up to 9 strips of 1,024 rows, ragged last
+    # strips): the CTA kernel, with more strips than its 4 warps and several
+    # pairs in flight per CTA, mixed in one batch with short pairs of the
+    # per-group variants
     lb = wl.dna_long_reads(10, 1800, 9000, seed=21)
     sb = mixed_dna(22, 60, 300, 900)
     b = wl.concat([lb, wl.Batch(sb.name, sb.q, sb.q_off, sb.q_len, sb.t, sb.t_off, sb.t_len, lb.W,
@@ -605,7 +606,7 @@ def test_banded_cta_reverse_on_the_band_edges(ctx):
     # long one-gap pairs (queries of 1,800-3,000 letters: the reversed fill
     # runs in the CTA kernel, each strip restricted to the reverse band's
     # columns): the one-gap optimum's gap count equals the band's bound on its
-    # side, so the path touches the band's edge, and strips of 512 rows start
+    # side, so the path touches the band's edge, and strips of 1,024 rows start
     # right of each other; plus exact self-alignments (a band of one diagonal)
     rng = np.random.default_rng(131)
     qs, ts = [], []
