@@ -153,6 +153,7 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
         typename DirWord<W>::T dw;
         zero<W>(dw);
         int row_hit = -1;
+        int rmax = kNegB;  // REV: the row's maximum (no anchored path scores above target)
         // rows whose band cells all lie inside the rectangle (most of them,
         // but not the last, which holds the final cell): no boundary tests
         // per cell.  The callers pass wb == W (a band wider than the
@@ -171,7 +172,7 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
                 const int hdg = Hp[k] + w + O;  // H(i-1, j-1) + W
                 const int H = max(hdg, max(E, F));
                 if constexpr (REV) {
-                    if (H == target && row_hit < 0) row_hit = i + dlo + k;
+                    rmax = max(rmax, H);
                 } else {
                     uint32_t &bw = nib_word<W>(dw, k);
                     const int sh = 4 * (k & 7);
@@ -185,6 +186,14 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
                 Fp[k] = F;
                 holeft = ho;
                 eleft = E;
+            }
+            if constexpr (REV) {
+                if (rmax == target) {
+                    // the row reaches target: its first cell that does
+#pragma unroll
+                    for (int k = W - 1; k >= 0; k--)
+                        if (Hp[k] == target - O) row_hit = i + dlo + k;
+                }
             }
         } else {
 #pragma unroll
