@@ -6,14 +6,14 @@
 // Region.  Rows i in [1, la] (query), columns j in [1, lb] (target), row and
 // column 0 the global boundary.  The provable band is the diagonals
 // dlo <= j - i <= dhi (band_range).  Strip x holds rows
-// [1 + 256x, 256(x+1)] and the columns [c0(x), c1(x)] that the band reaches
+// [1 + 512x, 512(x+1)] and the columns [c0(x), c1(x)] that the band reaches
 // in those rows, so the region computed is a staircase that contains the
 // band.  Any region between the band and the full rectangle gives the
 // canonical traceback: an optimal path lies in the band, so its cells keep
 // their full-rectangle values, and a predecessor that ties on the full
 // rectangle is itself on an optimal path; cells outside the region are -inf.
 //
-// Fill.  One warp per strip, 32 lanes x 8 rows, 32-bit lanes, one target
+// Fill.  One warp per strip, 32 lanes x 16 rows, 32-bit lanes, one target
 // column per lane and step as in the local fill (lane k at step s works on
 // column c0 + s - k, receives H and F of the row above from lane k-1 by
 // shuffle; lane 0 reads the previous strip's bottom row from global memory,
@@ -23,10 +23,10 @@
 // completed phase; several pairs are in flight per CTA.  Per cell 4 bits go
 // to global memory: H differs from the diagonal term (bit 0), H differs from E
 // (bit 1), E extends rather than opens here (bit 2), F extends rather than
-// opens here (bit 3); lane k's 8 rows of one step form one word, so a warp
-// writes 128 contiguous bytes per step.
+// opens here (bit 3); lane k's 16 rows of one step form two words (rows 0-7,
+// rows 8-15), so a warp writes 256 contiguous bytes per step.
 //
-// Walk.  One warp per pair stages tiles of 32 steps x 32 lanes of direction
+// Walk.  One warp per pair stages tiles of 32 steps x 32 lanes x 2 direction
 // words in shared memory and lane 0 walks from (la, lb) in state H with the
 // fixed preference (diagonal, then E, then F; open before extend), emitting
 // runs (len << 4) | op in reverse, then the warp writes them forward.  While
@@ -43,8 +43,10 @@ int ring_trace_class() { return 4; }
 namespace {
 
 constexpr int kRP = 32;          // lanes per strip
-constexpr int kRR = 8;           // rows per lane
+constexpr int kRR = 16;          // rows per lane
 constexpr int kRS = kRP * kRR;   // rows per strip
+constexpr int kRWords = kRR / 8; // direction words per lane and step (8 rows of 4 bits each)
+constexpr int kRStep = kRP * kRWords;  // direction words of one step of a strip
 constexpr int kRW = 8;           // warps per CTA
 constexpr int kRC = 64;          // steps per phase
 constexpr int kRSlots = 4;       // pairs in flight per CTA
@@ -56,7 +58,7 @@ struct RingGeom {
     int la, lb, dlo, dhi, nstrips, stride;
     __device__ int c0(int x) const { return max(1, 1 + x * kRS + dlo); }
     __device__ int c1(int x) const { return min(lb, min((x + 1) * kRS, la) + dhi); }
-    __device__ long long words() const { return (long long)nstrips * stride * kRP; }
+    __device__ long long words() const { return (long long)nstrips * stride * kRStep; }
 };
 
 __device__ __forceinline__ bool ring_geom(const gsw_result &r, const Scoring &sc, RingGeom *g) {
@@ -74,7 +76,7 @@ __device__ __forceinline__ bool ring_geom(const gsw_result &r, const Scoring &sc
 
 // Phases strip x+1 trails strip x: strip x writes column j at its step
 // j - c0(x) + 31, strip x+1 reads columns up to c0(x+1) + s + 63 at its step
-// s, and c0(x+1) - c0(x) <= 256, so (lag - 1) * 64 >= 256 + 63 + 31.
+// s, and c0(x+1) - c0(x) <= 512, so (lag - 1) * 64 >= 512 + 63 + 31.
 constexpr int kRingLag = 1 + (kRS + 2 * kRP - 1 + kRP - 1 + kRC - 1) / kRC;
 
 // Profile index of (letter a, row r, lane l): lane-minor groups of 4 rows.
@@ -135,7 +137,7 @@ struct BandStrip {
         // boundary word of column j at [j - 1]
         bin = job.bnd + (size_t)((x + 1) & 1) * g.lb;
         bout = job.bnd + (size_t)(x & 1) * g.lb;
-        dout = job.dirs + (size_t)x * g.stride * kRP;
+        dout = job.dirs + (size_t)x * g.stride * kRStep;
         // profile: W(q_i, a) + O of this lane's rows (W = 0 below the last
         // row); with H kept as H - O the diagonal term is one add
         for (int r = 0; r < kRR; r++) {
@@ -204,7 +206,7 @@ struct BandStrip {
         int diag = hdiag;
         hdiag = hin;
         int houp = hin, f = fin;
-        uint32_t bits = 0;
+        uint32_t bits[kRWords] = {};
         if ((unsigned)(j - c0) <= (unsigned)(c1 - c0)) {
             int w[kRR];
 #pragma unroll
@@ -219,10 +221,12 @@ struct BandStrip {
                 const int dw = diag + w[r];  // H(i-1, j-1) + W(q_i, t_j)
                 const int h = max(max(dw, e), f);
                 // one compare and one predicated or per bit
-                or_if_ne(bits, h, dw, 1u << (4 * r));      // H not from the diagonal
-                or_if_ne(bits, h, e, 2u << (4 * r));       // H not from E
-                or_if_ne(bits, e, holeft, 4u << (4 * r));  // E(i, j) extends, not opened
-                or_if_ne(bits, f, houp, 8u << (4 * r));    // F(i, j) extends, not opened
+                uint32_t &bw = bits[r / 8];
+                const int sh = 4 * (r % 8);
+                or_if_ne(bw, h, dw, 1u << sh);      // H not from the diagonal
+                or_if_ne(bw, h, e, 2u << sh);       // H not from E
+                or_if_ne(bw, e, holeft, 4u << sh);  // E(i, j) extends, not opened
+                or_if_ne(bw, f, houp, 8u << sh);    // F(i, j) extends, not opened
                 const int ho = h - O;
                 E[r] = max(ho, e - X);
                 f = max(ho, f - X);
@@ -237,7 +241,8 @@ struct BandStrip {
             }
             if (bo) bout[j - 1] = make_int2(HO[kRR - 1], f);
         }
-        *dp = bits;
+        static_assert(kRWords == 2, "one 8-byte store per lane and step");
+        *reinterpret_cast<uint2 *>(dp) = make_uint2(bits[0], bits[1]);
         xh = __shfl_up_sync(0xFFFFFFFFu, HO[kRR - 1], 1);
         xf = __shfl_up_sync(0xFFFFFFFFu, f, 1);
     }
@@ -245,9 +250,9 @@ struct BandStrip {
     // steps [s0, s1); true when the strip is complete
     __device__ bool run(int s0, int s1) {
         s1 = min(s1, nsteps);
-        uint32_t *dp = dout + (size_t)s0 * kRP + k;
+        uint32_t *dp = dout + (size_t)s0 * kRStep + k * kRWords;
 #pragma unroll 1
-        for (int s = s0; s < s1; s++, dp += kRP) step(s, dp);
+        for (int s = s0; s < s1; s++, dp += kRStep) step(s, dp);
         return s1 >= nsteps;
     }
 };
@@ -469,23 +474,26 @@ __global__ void __launch_bounds__(1024) k_ring_needs(BatchView b, Scoring sc, co
 }
 
 // Walk of one pair by one warp (see the file comment).
-// A warp copies `steps` rows of 32 direction words (128 bytes each, 16-byte
-// aligned: every pair's words start at a multiple of 32 words) into shared
-// memory without waiting; walk_copy_wait waits for this lane's copies.
+// A warp copies `steps` steps of direction words (kRStep words, 256 bytes
+// each, 16-byte aligned: every pair's words start at a multiple of kRStep
+// words) into shared memory without waiting; walk_copy_wait waits for this
+// lane's copies.
 __device__ __forceinline__ void walk_copy(uint32_t *dst, const uint32_t *src, int steps, int lane) {
     const uint32_t base = (uint32_t)__cvta_generic_to_shared(dst);
-    for (int c = lane; c < steps * (kRP / 4); c += 32)
+    for (int c = lane; c < steps * (kRStep / 4); c += 32)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + 16u * c), "l"(src + 4 * c) : "memory");
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
 __device__ __forceinline__ void walk_copy_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-__global__ void __launch_bounds__(128) k_ring_walk(RingLaunch rl) {
-    __shared__ __align__(16) uint32_t tile[4][2][kRTile * kRP];
+constexpr int kWalkWarps = 2;  // warps per block: two 16 KB tile pairs
+
+__global__ void __launch_bounds__(kWalkWarps * 32) k_ring_walk(RingLaunch rl) {
+    __shared__ __align__(16) uint32_t tile[kWalkWarps][2][kRTile * kRStep];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gwarp = blockIdx.x * 4 + warp, nwarps = gridDim.x * 4;
-    uint32_t (*stage)[kRTile * kRP] = tile[warp];
+    const int gwarp = blockIdx.x * kWalkWarps + warp, nwarps = gridDim.x * kWalkWarps;
+    uint32_t (*stage)[kRTile * kRStep] = tile[warp];
     uint32_t *ops = rl.ops + (size_t)gwarp * rl.op_words;
     const int g0 = rl.group[0], g1 = rl.group[1];
     for (int t = g0 + gwarp; t < g1; t += nwarps) {
@@ -521,21 +529,23 @@ __global__ void __launch_bounds__(128) k_ring_walk(RingLaunch rl) {
                     cx = px, clo = plo, chi = phi;
                 } else {
                     cx = x, chi = s, clo = max(0, s - kRTile + 1);
-                    walk_copy(stage[buf], dirs + ((size_t)x * g.stride + clo) * kRP, chi - clo + 1, lane);
+                    walk_copy(stage[buf], dirs + ((size_t)x * g.stride + clo) * kRStep, chi - clo + 1, lane);
                     walk_copy_wait();
                     __syncwarp();
                 }
                 px = -1;
                 if (clo > 0) {
                     px = cx, phi = clo - 1, plo = max(0, clo - kRTile);
-                    walk_copy(stage[buf ^ 1], dirs + ((size_t)px * g.stride + plo) * kRP, phi - plo + 1, lane);
+                    walk_copy(stage[buf ^ 1], dirs + ((size_t)px * g.stride + plo) * kRStep, phi - plo + 1, lane);
                 }
             }
             if (lane == 0) {
-                // walk inside the tile: idx = (s - clo) * 32 + k, the word of
-                // row i at column j; d = j - c0 (the region's left edge)
+                // walk inside the tile: idx = (s - clo) * kRStep + 2k + r / 8,
+                // the word of row i (lane k, row r of the lane) at column j;
+                // d = j - c0 (the region's left edge)
                 const uint32_t *tl = stage[buf];
-                int kk = k, sh = 4 * ((i - 1) % kRR), d = j - c0, idx = (s - clo) * kRP + k;
+                int kk = k, r = (i - 1) % kRR, sh = 4 * (r % 8), d = j - c0;
+                int idx = (s - clo) * kRStep + kRWords * k + r / 8;
                 while (i > 0 && j > 0 && idx >= 0 && kk >= 0) {
                     if (d < 0) {  // left the region
                         ok = false;
@@ -564,16 +574,20 @@ __global__ void __launch_bounds__(128) k_ring_walk(RingLaunch rl) {
                     if (left) {
                         j--;
                         d--;
-                        idx -= kRP;
+                        idx -= kRStep;
                     }
                     if (up) {
                         i--;
-                        if (sh > 0) {
-                            sh -= 4;
-                        } else {  // the lane above: one step earlier
-                            sh = 4 * (kRR - 1);
+                        if (--r < 0) {  // the lane above, one step earlier: its row 15
+                            r = kRR - 1;
                             kk--;
-                            idx -= kRP + 1;
+                            idx -= kRStep + 1;
+                            sh = 28;
+                        } else if (r == 7) {  // row 7: the lane's first word
+                            idx -= 1;
+                            sh = 28;
+                        } else {
+                            sh -= 4;
                         }
                     }
                     if (op == cur) {
@@ -681,8 +695,8 @@ cudaError_t launch_ring_group(const RingLaunchArgs &a, int sms, cudaStream_t st)
     if (grid < 1) return cudaErrorInvalidConfiguration;
     if (dna) k_trace_ring<true><<<grid, nw * 32, smem, st>>>(rl);
     else k_trace_ring<false><<<grid, nw * 32, smem, st>>>(rl);
-    const int wgrid = std::max(1, a.walk_warps / 4);
-    k_ring_walk<<<wgrid, 128, 0, st>>>(rl);
+    const int wgrid = std::max(1, a.walk_warps / kWalkWarps);
+    k_ring_walk<<<wgrid, kWalkWarps * 32, 0, st>>>(rl);
     k_ring_advance<<<1, 1, 0, st>>>(a.group);
     return cudaGetLastError();
 }
