@@ -518,37 +518,25 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
                 max_ops = (size_t)warps * (size_t)ad_ops;
             }
             // 16-bit rectangle kernel: per class, 4 groups per warp, direction
-            // and op words per group.  The classes run side by side with the
-            // anti-diagonal kernel, so each takes its own region of the
-            // scratch after the anti-diagonal kernel's, and an equal share of
-            // the room
+            // and op words per group (the classes run one after the other)
             T16Scratch t16{};
             bool any16 = false;
             {
                 const size_t have = room(ctx, ctx->trace_dirs, ctx->trace_ops) / 2;
-                int nclasses = 0;
-                for (int v = 0; v < kTraceT16Classes; v++) nclasses += need[kMiscNeed16 - kMiscNeed + v] > 0 ? 1 : 0;
-                const size_t share = have / (size_t)std::max(1, nclasses);
-                // after the anti-diagonal kernel's regions, 16-byte aligned
-                size_t dir_at = (max_dir + 3) & ~(size_t)3, ops_at = (max_ops + 3) & ~(size_t)3;
                 for (int v = 0; v < kTraceT16Classes; v++) {
                     // 16-byte aligned group areas
                     const long long dw = ((long long)need[kMiscNeed16 - kMiscNeed + v] + 3) & ~3LL;
                     if (dw <= 0) continue;
                     const size_t per_warp = 4 * (size_t)(dw + ad_ops) * sizeof(uint32_t);
                     const int w = (int)std::min<size_t>((size_t)t16_max_warps(sc, ctx->sms, v),
-                                                        std::max<size_t>(1, share / per_warp));
+                                                        std::max<size_t>(1, have / per_warp));
                     if (w <= 0) continue;
                     t16.dir_words[v] = dw;
                     t16.warps[v] = w;
-                    t16.dir_off[v] = (int64_t)dir_at;
-                    t16.op_off[v] = (int64_t)ops_at;
-                    dir_at += (size_t)w * 4 * (size_t)dw;
-                    ops_at = (ops_at + (size_t)w * 4 * (size_t)ad_ops + 3) & ~(size_t)3;
+                    max_dir = std::max(max_dir, (size_t)w * 4 * (size_t)dw);
+                    max_ops = std::max(max_ops, (size_t)w * 4 * (size_t)ad_ops);
                     any16 = true;
                 }
-                max_dir = dir_at;
-                max_ops = ops_at;
             }
             // wide bands: the pool of direction words, groups of pairs that fit it
             const unsigned long long ring_total = need[2], ring_max = need[3], ring_ops = need[4];
@@ -567,7 +555,6 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
             if (max_dir > 0) {
                 GSW_TRY(ensure2(ctx, ctx->trace_dirs, max_dir * sizeof(uint32_t), ctx->trace_ops,
                                 max_ops * sizeof(uint32_t)));
-                if (any16) GSW_TRY(ensure_aux(ctx));
                 if (any16) {
                     t16.dirs = reinterpret_cast<uint32_t *>(ctx->trace_dirs.p);
                     t16.ops = reinterpret_cast<uint32_t *>(ctx->trace_ops.p);
@@ -575,7 +562,7 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
                     t16.order = pb.order;
                     t16.var_start = pb.var_start;
                     t16.head = pb.head;
-                    CUDA_TRY(launch_trace16(bv, sc, t16, ctx->sms, st, ctx->aux));
+                    CUDA_TRY(launch_trace16(bv, sc, t16, ctx->sms, st));
                     for (int v = 0; v < kTraceT16Classes; v++) S.launches += t16.warps[v] > 0 ? 1 : 0;
                 }
                 if (ad_grid > 0) {
@@ -589,8 +576,6 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
                     CUDA_TRY(launch_trace_ad(bv, sc, ts, ad_grid, st));
                     S.launches += 4;
                 }
-                // the ring kernel below reuses the scratch from its start
-                if (any16) CUDA_TRY(join_side_streams(st, ctx->aux));
                 if (ring_total > 0) {
                     RingLaunchArgs ra;
                     ra.b = bv;

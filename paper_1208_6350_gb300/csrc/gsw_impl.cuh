@@ -437,10 +437,8 @@ cudaError_t launch_trace_ad(const BatchView &b, const Scoring &sc, const TraceSc
 struct T16Scratch {
     uint32_t *dirs;
     int64_t dir_words[kTraceT16Classes];  // per group
-    int64_t dir_off[kTraceT16Classes];    // each class's region of dirs (words)
     uint32_t *ops;
     int64_t op_words;   // per group
-    int64_t op_off[kTraceT16Classes];     // each class's region of ops (words)
     const int32_t *order;
     const int32_t *var_start;
     int32_t *head;      // per-class task counters (zeroed by the plan)
@@ -448,13 +446,7 @@ struct T16Scratch {
 };
 // warps of class v's launch that can be resident
 int t16_max_warps(const Scoring &sc, int sms, int v);
-struct BandStreams;
-// The classes run side by side (each in its own scratch region): the two
-// tallest on the side streams (forked from st), the others on st; the caller
-// joins the side streams into st (join_side_streams).
-cudaError_t launch_trace16(const BatchView &b, const Scoring &sc, const T16Scratch &ts, int sms, cudaStream_t st,
-                           const BandStreams &aux);
-cudaError_t join_side_streams(cudaStream_t st, const BandStreams &aux);
+cudaError_t launch_trace16(const BatchView &b, const Scoring &sc, const T16Scratch &ts, int sms, cudaStream_t st);
 
 int band_block_threads();
 // Grids and scratch of the three band classes (widths 8, 16, 32), each

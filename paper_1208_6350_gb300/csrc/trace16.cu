@@ -412,8 +412,8 @@ __global__ void __launch_bounds__(kT16Block) k_trace16(BatchView b, Scoring sc, 
     const size_t gid = (size_t)gwarp * (32 / kP) + g;
     const int v = cls - kTraceT16First;
     const int64_t dir_words = ts.dir_words[v];
-    uint32_t *dirs = ts.dirs + ts.dir_off[v] + gid * dir_words;
-    uint32_t *ops = ts.ops + ts.op_off[v] + gid * ts.op_words;
+    uint32_t *dirs = ts.dirs + gid * dir_words;
+    uint32_t *ops = ts.ops + gid * ts.op_words;
     const int first = ts.var_start[cls], last = ts.var_start[cls + 1];
     for (;;) {
         int t = 0;
@@ -539,33 +539,17 @@ int t16_max_warps(const Scoring &sc, int sms, int v) {
     return std::max(0, sms * per_sm) * (kT16Block / 32);
 }
 
-cudaError_t launch_trace16(const BatchView &b, const Scoring &sc, const T16Scratch &ts, int sms, cudaStream_t st,
-                           const BandStreams &aux) {
-    // a class holds few pairs next to the fill's million (the pairs whose
-    // band the band kernel cannot take), so one launch is bounded by its
-    // longest pairs, not by the GPU's throughput: the classes overlap
+cudaError_t launch_trace16(const BatchView &b, const Scoring &sc, const T16Scratch &ts, int sms, cudaStream_t st) {
     cudaError_t e;
     const int c0 = kTraceT16First;
-    if ((e = cudaEventRecord(aux.fork, st))) return e;
-    for (int k = 0; k < 2; k++)
-        if ((e = cudaStreamWaitEvent(aux.s[k], aux.fork, 0))) return e;
     if (sc.dna4) {
-        if ((e = t16_launch<16, true>(b, sc, ts, sms, c0 + 3, aux.s[0]))) return e;
-        if ((e = t16_launch<12, true>(b, sc, ts, sms, c0 + 2, aux.s[1]))) return e;
+        if ((e = t16_launch<16, true>(b, sc, ts, sms, c0 + 3, st))) return e;
+        if ((e = t16_launch<12, true>(b, sc, ts, sms, c0 + 2, st))) return e;
         if ((e = t16_launch<8, true>(b, sc, ts, sms, c0 + 1, st))) return e;
         if ((e = t16_launch<4, true>(b, sc, ts, sms, c0, st))) return e;
     } else {
-        if ((e = t16_launch<8, false>(b, sc, ts, sms, c0 + 1, aux.s[0]))) return e;
+        if ((e = t16_launch<8, false>(b, sc, ts, sms, c0 + 1, st))) return e;
         if ((e = t16_launch<4, false>(b, sc, ts, sms, c0, st))) return e;
-    }
-    return cudaSuccess;
-}
-
-cudaError_t join_side_streams(cudaStream_t st, const BandStreams &aux) {
-    cudaError_t e;
-    for (int k = 0; k < 2; k++) {
-        if ((e = cudaEventRecord(aux.join[k], aux.s[k]))) return e;
-        if ((e = cudaStreamWaitEvent(st, aux.join[k], 0))) return e;
     }
     return cudaSuccess;
 }
