@@ -22,8 +22,10 @@
 // Lanes of a warp take consecutive pairs of a list sorted by rows, so their
 // loops have similar lengths.  Each lane keeps its band row in registers
 // (W cells) and stores each row's decision nibbles into a per-warp scratch
-// interleaved by lane (coalesced).  The CIGAR is walked twice: once to count
-// runs, once to write them in forward order at the reserved offset.
+// interleaved by lane (coalesced).  The walk keeps the first 16 runs it finds
+// (the CIGAR's last ones) and counts the rest; a CIGAR of at most 16 runs is
+// then written from them in forward order at the reserved offset, a longer
+// one is walked a second time into its reserved words.
 #include "gsw_impl.cuh"
 
 #include <algorithm>
@@ -262,10 +264,12 @@ __device__ bool band_dp(const BandSeq &s, int dlo, int wb, const int8_t *sW, int
 }
 
 // Walks the decision nibbles from (la, lb) back to (0, 0).  With WRITE the
-// runs go to out[0..nr) in forward order; returns the run count or -1.
-// Rows are STRIDE words of the template apart.
+// runs go to out[0..nr) in forward order; otherwise the first `keep` runs
+// found (the CIGAR's last ones) go to out[0..keep) in the order found.
+// Returns the run count or -1.  Rows are STRIDE words of the template apart.
 template <int W, bool WRITE, int STRIDE = 32>
-__device__ int band_walk(const typename DirWord<W>::T *dirs, int la, int lb, int dlo, int wb, uint32_t *out, int nr) {
+__device__ int band_walk(const typename DirWord<W>::T *dirs, int la, int lb, int dlo, int wb, uint32_t *out, int nr,
+                         int keep = 0) {
     int i = la, j = lb, state = 0, cur = -1, len = 0, runs = 0, guard = 2 * (la + lb) + 4;
     // the walk moves up at most one row per step: it holds the current row's
     // word and the one above, loaded when the row before it was entered
@@ -304,6 +308,7 @@ __device__ int band_walk(const typename DirWord<W>::T *dirs, int la, int lb, int
         } else {
             if (len) {
                 if (WRITE) out[nr - 1 - runs] = ((uint32_t)len << 4) | (uint32_t)cur;
+                else if (runs < keep) out[runs] = ((uint32_t)len << 4) | (uint32_t)cur;
                 runs++;
             }
             cur = op;
@@ -313,6 +318,7 @@ __device__ int band_walk(const typename DirWord<W>::T *dirs, int la, int lb, int
     if (i != 0 || j != 0) return -1;
     if (len) {
         if (WRITE) out[nr - 1 - runs] = ((uint32_t)len << 4) | (uint32_t)cur;
+        else if (runs < keep) out[runs] = ((uint32_t)len << 4) | (uint32_t)cur;
         runs++;
     }
     return runs;
@@ -348,7 +354,11 @@ __device__ void band_trace(const BatchView &b, const Scoring &sc, gsw_result *rp
         rp->flags |= kResInternal;
         return;
     }
-    const int nr = band_walk<WT, false, RSTRIDE>(dirs, la, lb, dlo, wb, nullptr, 0);
+    // one walk keeps up to kKeep runs (true reads have a few); a CIGAR with
+    // more is walked a second time, into its reserved words
+    constexpr int kKeep = 16;
+    uint32_t kept[kKeep];
+    const int nr = band_walk<WT, false, RSTRIDE>(dirs, la, lb, dlo, wb, kept, 0, kKeep);
     if (nr < 0) {
         rp->flags |= kResInternal;
         return;
@@ -360,7 +370,11 @@ __device__ void band_trace(const BatchView &b, const Scoring &sc, gsw_result *rp
         rp->cigar_off = -1;
         return;
     }
-    band_walk<WT, true, RSTRIDE>(dirs, la, lb, dlo, wb, b.cigar + off, nr);
+    if (nr <= kKeep) {
+        for (int q = 0; q < nr; q++) b.cigar[off + q] = kept[nr - 1 - q];
+    } else {
+        band_walk<WT, true, RSTRIDE>(dirs, la, lb, dlo, wb, b.cigar + off, nr);
+    }
     rp->cigar_len = nr;
     rp->cigar_off = (int64_t)off;
 }

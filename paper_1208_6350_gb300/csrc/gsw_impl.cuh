@@ -168,12 +168,9 @@ constexpr int kBandMaxWidth = 32;
 constexpr int kBandMaxRows = 4096;
 // Reverse bands the thread-per-pair kernel takes; wider ones reverse in the
 // 16-bit ring fill (the begin), the CIGAR still comes from the band kernel
-// when the traceback band is narrow.  (16 on the short-read workload: band
-// 8.26 -> 6.69 ms but ring reverse 1.89 -> 3.99 ms, so 32.)
-#ifndef GSW_BAND_REV_MAX
-#define GSW_BAND_REV_MAX 32
-#endif
-constexpr int kBandMaxRevWidth = GSW_BAND_REV_MAX;
+// when the traceback band is narrow.  (Measured with 16 on the short-read
+// workload: band 8.26 -> 6.69 ms but ring reverse 1.89 -> 3.99 ms, so 32.)
+constexpr int kBandMaxRevWidth = 32;
 
 // Below this many pairs the thread-per-pair band kernel would occupy a few
 // percent of the GPU's threads: the begins then come from the ring reverse

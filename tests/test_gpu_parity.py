@@ -542,6 +542,40 @@ def test_band_kernels_mixed_widths_general_dna_matrix(ctx):
     compare(b, run_oracle(b), run_gpu_device(ctx, b))
 
 
+def test_band_kernel_cigars_of_many_runs(ctx):
+    # 16,500 reads with 6-12 single-letter indels (alternately inserted and
+    # deleted, at least 8 letters apart) under gap costs of 6 per letter:
+    # narrow bands (the band kernel's traceback), CIGARs of 13-25 runs.  The
+    # band kernel's walk keeps 16 runs and walks a longer CIGAR a second time
+    # into its reserved words, so both kinds are here.
+    rng = np.random.default_rng(151)
+    qs, ts = [], []
+    for p in range(16500):
+        L = int(rng.integers(150, 221))
+        src = rng.integers(0, 4, L).astype(np.uint8)
+        k = int(rng.integers(6, 13))
+        at = np.sort(rng.choice(np.arange(10, L - 10, 9), size=k, replace=False))
+        q, last = [], 0
+        for n, a in enumerate(at):
+            q.append(src[last:a])
+            if n % 2 == 0:
+                q.append(rng.integers(0, 4, 1).astype(np.uint8))  # inserted letter
+                last = a
+            else:
+                last = a + 1                                     # deleted letter
+        q.append(src[last:])
+        t = np.concatenate([rng.integers(0, 4, int(rng.integers(0, 50))), src,
+                            rng.integers(0, 4, int(rng.integers(0, 50)))]).astype(np.uint8)
+        qs.append(np.concatenate(q).astype(np.uint8))
+        ts.append(t)
+    b = _batch(qs, ts, wl.dna_matrix(2, -6), 6, 6, "many_runs")
+    assert b.npairs >= 1 << 14
+    ora = run_oracle(b)
+    runs = ora[0]["cigar_len"]
+    assert (runs > 16).sum() >= 1000 and ((runs > 1) & (runs <= 16)).sum() >= 1000
+    compare(b, ora, run_gpu_device(ctx, b))
+
+
 def test_rect16_traceback_large_regions_general_alphabet(ctx):
     # regions over a million cells (here 1,100-1,500 letters a side) exceed the
     # 64-row classes' per-pair words and take the 128-row class with its
