@@ -779,8 +779,13 @@ int batch_impl(gsw_ctx *ctx, int32_t npairs, const uint8_t *q, const int64_t *q_
         maxn = (int)bucket_up((uint64_t)maxn);
     }
     CUDA_TRY(cudaMemsetAsync(misc + kMiscCursor, 0, 2 * sizeof(unsigned long long), st));  // cursor, internal
-    CUDA_TRY(launch_validate(bv, sc, reinterpret_cast<int32_t *>(misc + kMiscValid), st));
-    ctx->launches += 1;
+    if ((flags & GSW_PACKED2) && sc.A >= 4) {
+        // 2-bit letters are 0..3: valid under any matrix of 4 or more letters
+        CUDA_TRY(cudaMemsetAsync(misc + kMiscValid, 0, sizeof(int32_t), st));
+    } else {
+        CUDA_TRY(launch_validate(bv, sc, reinterpret_cast<int32_t *>(misc + kMiscValid), st));
+        ctx->launches += 1;
+    }
     GSW_TRY(run_pipeline(ctx, bv, sc, st, maxm, maxn));
 
     // completion: invalid letters, internal checks, CIGAR space
