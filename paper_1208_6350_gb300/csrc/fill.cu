@@ -51,6 +51,9 @@ namespace {
 
 constexpr int kBlock = 128;
 constexpr int kUnrollFast = 4;  // steady loop of one-strip forward fills
+// FAST steps of 16-bit lanes keep the tracker's two columns as the signed
+// 16-bit halves of one word: targets up to this many columns take them
+constexpr int kFastMaxCols = 32768;
 constexpr int kUnrollGen = 2;   // other steady loops
 // forms of the strip step (StripRunner::step)
 constexpr int kModeGen = 0, kModeFast = 1, kModeFwdFirst = 2, kModeFwdLater = 3;
@@ -278,6 +281,7 @@ struct StripRunner {
     uint32_t H[R], E[R], SV[R];
     uint32_t hdiag, best, xh, xf, xc;
     int c_lo, c_hi, nal, nah;
+    uint32_t cpk;  // FAST steps (16-bit lanes): c_lo and c_hi as the halves of one word
     bnd_t b_cur, b_nxt;
     cm_t c_cur, c_nxt;
     uint32_t cmpk, cmw0;  // max-array values of the packed 4-step store
@@ -450,8 +454,16 @@ struct StripRunner {
             if constexpr (L::FOLD) {
                 const uint32_t t = __vminu2(diff, 0x00010001u);  // 1 in each half that changed
                 mk = t * 0xFFFFu;
-                c_lo = (t & 1u) ? jlo : c_lo;
-                c_hi = (t >> 16) ? jhi : c_hi;
+                if constexpr (FAST) {
+                    // both columns in one word (columns < 2^15 in FAST
+                    // steps): one multiply-add makes (jhi, jlo), one logic
+                    // op takes the halves that improved
+                    const uint32_t jpk = (uint32_t)jlo * 0x10001u - ((uint32_t)P << 16);
+                    cpk = (jpk & mk) | (cpk & ~mk);
+                } else {
+                    c_lo = (t & 1u) ? jlo : c_lo;
+                    c_hi = (t >> 16) ? jhi : c_hi;
+                }
             } else {
                 mk = diff ? 0xFFFFFFFFu : 0u;
                 c_lo = diff ? jlo : c_lo;
@@ -534,13 +546,14 @@ struct StripRunner {
         for (; s < s1 && s < s_steady; s++)
             if (step<true>(s)) return true;
         const bool fwd = !job.stop_u && has_cms;
-        if (MAYBE_FAST && st == 0 && last_strip && fwd && job.ts == 1) {
+        if (MAYBE_FAST && st == 0 && last_strip && fwd && job.ts == 1 && (!L::FOLD || n <= kFastMaxCols)) {
             if constexpr (L::FOLD) {
                 // blocks of 4 steps whose max-array values go out in one
                 // store (the first steady step's column is 0, so the blocks
                 // stay aligned); the last few steady steps run as drain steps
                 if ((s - s_steady) % 4 == 0) {
                     const int se = min(s1, s_drain);
+                    cpk = ((uint32_t)c_hi << 16) | ((uint32_t)c_lo & 0xFFFFu);
 #pragma unroll 1
                     for (; s + 4 <= se; s += 4) {
                         step<false, kModeFast, 0>(s);
@@ -548,6 +561,8 @@ struct StripRunner {
                         step<false, kModeFast, 2>(s + 2);
                         step<false, kModeFast, 3>(s + 3);
                     }
+                    c_lo = (int)(int16_t)(cpk & 0xFFFFu);  // (-1: none yet)
+                    c_hi = (int)(int16_t)(cpk >> 16);
                 }
             } else {
 #pragma unroll kUnrollFast
