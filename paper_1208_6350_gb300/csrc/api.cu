@@ -393,9 +393,10 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
             size_t have = room(ctx, ctx->fill_cm, ctx->fill_bnd);
             size_t cap_slots = have / 2 / per_slot;
             if (S.slots > cap_slots) {
-                // every variant has at most 2 slots per warp
-                S.max_blocks = (int)std::max<size_t>(1, cap_slots / (2 * warps_per_block));
-                S.slots = (size_t)S.max_blocks * warps_per_block * 2;
+                // a warp holds at most fill_max_pairs_per_warp() pairs
+                const size_t per_warp = (size_t)fill_max_pairs_per_warp();
+                S.max_blocks = (int)std::max<size_t>(1, cap_slots / (per_warp * warps_per_block));
+                S.slots = (size_t)S.max_blocks * warps_per_block * per_warp;
             }
         }
         GSW_TRY(ensure2(ctx, ctx->fill_cm, S.slots * S.ncap * sizeof(int32_t), ctx->fill_bnd,

@@ -1214,6 +1214,9 @@ cudaError_t launch_one(const FillLaunch &fl, int sms, int max_blocks, cudaStream
     if (nb < 1) return cudaErrorInvalidConfiguration;
     int grid = sms * nb;
     if (grid > max_blocks) grid = max_blocks;
+    // every pair in flight has a slot: never more warps than the slots hold
+    grid = std::min(grid, fl.scr.nslots / ((kBlock / 32) * (32 / VarC<VID>::P)));
+    if (grid < 1) return cudaErrorInvalidConfiguration;
     k_fill<DNA, VID><<<grid, kBlock, sm, st>>>(fl, (int)(sm / sizeof(uint32_t) / (kBlock / 32)));
     return cudaGetLastError();
 }
@@ -1248,6 +1251,14 @@ int max_slots(int A, int sms) {
 }  // namespace
 
 int fill_block_threads() { return kBlock; }
+
+int fill_max_pairs_per_warp() {
+    int most = 1;
+#define GSW_PER_WARP(id, P_, R_, S_) most = 32 / P_ > most ? 32 / P_ : most;
+    GSW_FILL_VARIANTS(GSW_PER_WARP)
+#undef GSW_PER_WARP
+    return most;
+}
 
 // Slots (pairs in flight) the largest variant launch can hold, at full
 // occupancy on `sms` SMs; a launch is never given more blocks than

@@ -362,6 +362,9 @@ cudaError_t launch_count_flag(const gsw_result *res, int32_t n, int32_t flag, un
 int fill_block_threads();
 // largest number of slots (pairs in flight) of any variant's launch
 int fill_slots(const Scoring &sc, int sms);
+// Largest number of pairs a warp of a fill variant holds at once (32 / P for
+// the narrowest group): the slots a capped launch needs per warp.
+int fill_max_pairs_per_warp();
 // one persistent launch per variant, heaviest first; each grid capped at max_blocks
 cudaError_t launch_fill(const FillLaunch &fl, int sms, int max_blocks, cudaStream_t st);
 

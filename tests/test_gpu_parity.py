@@ -542,6 +542,33 @@ def test_band_kernels_mixed_widths_general_dna_matrix(ctx):
     compare(b, run_oracle(b), run_gpu_device(ctx, b))
 
 
+def test_capped_fill_scratch_with_four_pairs_per_warp():
+    # targets of 20,000 columns take 400 KB of column maxima and boundaries
+    # per pair in flight, so a 512 MB budget caps the fill's scratch far below
+    # the slots of a full launch; the 8-lane variants hold 4 pairs per warp,
+    # and every launch stays within the slots the cap left (1,200 pairs, more
+    # than the slots, so warps reuse theirs)
+    rng = np.random.default_rng(161)
+    qs, ts = [], []
+    for L in rng.integers(120, 201, 1200):
+        q = rng.integers(0, 4, int(L)).astype(np.uint8)
+        c = q.copy()
+        mut = rng.random(len(c)) < 0.03
+        c[mut] = rng.integers(0, 4, int(mut.sum()))
+        t = rng.integers(0, 4, 20000).astype(np.uint8)
+        o = int(rng.integers(0, len(t) - len(c) + 1))
+        t[o:o + len(c)] = c
+        qs.append(q)
+        ts.append(t)
+    b = _batch(qs, ts, wl.dna_matrix(2, -3), 5, 2, "capped_scratch")
+    small = gsw.Context(0, 512 << 20)
+    try:
+        got = run_gpu_device(small, b)
+    finally:
+        small.close()
+    compare(b, run_oracle(b), got)
+
+
 def test_band_kernel_cigars_of_many_runs(ctx):
     # 16,500 reads with 6-12 single-letter indels (alternately inserted and
     # deleted, at least 8 letters apart) under gap costs of 6 per letter:
