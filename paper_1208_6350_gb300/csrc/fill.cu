@@ -51,8 +51,9 @@ namespace {
 
 constexpr int kBlock = 128;
 constexpr int kUnrollFast = 4;  // steady loop of one-strip forward fills
-// FAST steps of 16-bit lanes keep the tracker's two columns as the signed
-// 16-bit halves of one word: targets up to this many columns take them
+// The steady forward steps (FAST, FwdFirst, FwdLater) of 16-bit lanes keep
+// the tracker's two columns as the signed 16-bit halves of one word: targets
+// up to this many columns take them
 constexpr int kFastMaxCols = 32768;
 constexpr int kUnrollGen = 2;   // other steady loops
 // forms of the strip step (StripRunner::step)
@@ -454,10 +455,10 @@ struct StripRunner {
             if constexpr (L::FOLD) {
                 const uint32_t t = __vminu2(diff, 0x00010001u);  // 1 in each half that changed
                 mk = t * 0xFFFFu;
-                if constexpr (FAST) {
-                    // both columns in one word (columns < 2^15 in FAST
-                    // steps): one multiply-add makes (jhi, jlo), one logic
-                    // op takes the halves that improved
+                if constexpr (MODE != kModeGen) {
+                    // both columns in one word (columns < 2^15 in the
+                    // steady forward steps): one multiply-add makes
+                    // (jhi, jlo), one logic op takes the halves that improved
                     const uint32_t jpk = (uint32_t)jlo * 0x10001u - ((uint32_t)P << 16);
                     cpk = (jpk & mk) | (cpk & ~mk);
                 } else {
@@ -568,12 +569,22 @@ struct StripRunner {
 #pragma unroll kUnrollFast
                 for (; s < s1 && s < s_drain; s++) step<false, kModeFast>(s);
             }
-        } else if (MAYBE_MULTI && fwd && st == 0 && !last_strip) {
+        } else if (MAYBE_MULTI && fwd && st == 0 && !last_strip && (!L::FOLD || n <= kFastMaxCols)) {
+            if constexpr (L::FOLD) cpk = ((uint32_t)c_hi << 16) | ((uint32_t)c_lo & 0xFFFFu);
 #pragma unroll kUnrollGen
             for (; s < s1 && s < s_drain; s++) step<false, kModeFwdFirst>(s);
-        } else if (MAYBE_MULTI && fwd && st > 0) {
+            if constexpr (L::FOLD) {
+                c_lo = (int)(int16_t)(cpk & 0xFFFFu);
+                c_hi = (int)(int16_t)(cpk >> 16);
+            }
+        } else if (MAYBE_MULTI && fwd && st > 0 && (!L::FOLD || n <= kFastMaxCols)) {
+            if constexpr (L::FOLD) cpk = ((uint32_t)c_hi << 16) | ((uint32_t)c_lo & 0xFFFFu);
 #pragma unroll kUnrollGen
             for (; s < s1 && s < s_drain; s++) step<false, kModeFwdLater>(s);
+            if constexpr (L::FOLD) {
+                c_lo = (int)(int16_t)(cpk & 0xFFFFu);
+                c_hi = (int)(int16_t)(cpk >> 16);
+            }
         } else {
 #pragma unroll kUnrollGen
             for (; s < s1 && s < s_drain; s++)
