@@ -57,7 +57,7 @@ constexpr int kUnrollFast = 4;  // steady loop of one-strip forward fills
 constexpr int kFastMaxCols = 32768;
 constexpr int kUnrollGen = 2;   // other steady loops
 // forms of the strip step (StripRunner::step)
-constexpr int kModeGen = 0, kModeFast = 1, kModeFwdFirst = 2, kModeFwdLater = 3;
+constexpr int kModeGen = 0, kModeFast = 1, kModeFwdFirst = 2, kModeFwdLater = 3, kModeRev = 4;
 
 // ---------------------------------------------------------------- lanes
 struct L16 {
@@ -345,8 +345,9 @@ struct StripRunner {
         hin = xh * mulh + bzh;
         fin = xf * mulh + bzf;
         cmin = xc * mulh + bzc;
+        constexpr bool REV = MODE == kModeRev;
         cm_t cm_prev{};
-        if (MODE == kModeGen ? st > 0 : MODE == kModeFwdLater) {
+        if ((MODE == kModeGen || REV) ? st > 0 : MODE == kModeFwdLater) {
             const int bi = s & (P - 1);
             if (bi == 0) {
                 b_cur = b_nxt;
@@ -354,8 +355,13 @@ struct StripRunner {
                 prefetch(s + P);
             }
             const int srcl = gbase + bi;
-            if constexpr (L::FOLD) cm_prev = (cm_t)__shfl_sync(gmask, (uint32_t)c_cur, srcl);
-            else cm_prev = __shfl_sync(gmask, c_cur, srcl);
+            if constexpr (REV) {
+                // (no max array)
+            } else if constexpr (L::FOLD) {
+                cm_prev = (cm_t)__shfl_sync(gmask, (uint32_t)c_cur, srcl);
+            } else {
+                cm_prev = __shfl_sync(gmask, c_cur, srcl);
+            }
             bnd_t w;
             if constexpr (L::FOLD) {
                 w = __shfl_sync(gmask, b_cur, srcl);
@@ -500,6 +506,12 @@ struct StripRunner {
                 cms[jhi] = MODE == kModeFwdFirst ? (int)m : max((int)cm_prev, (int)m);
                 if (MODE == kModeFwdFirst || !last_strip) bout[jhi] = make_int2((int)H[R - 1], (int)f);
             }
+        } else if (REV && k == P - 1) {
+            // steady reversed step (16-bit lanes): boundary row out, the stop test
+            if constexpr (L::FOLD) {
+                if (!last_strip) bout[jhi] = (H[R - 1] >> 16) | (f & 0xFFFF0000u);
+                found = (m >> 16) == job.stop_u;
+            }
         } else if (MODE == kModeGen && k == P - 1 && (!CHECKED || (jhi >= 0 && jhi < n))) {
             if constexpr (L::FOLD) {
                 const uint32_t full = m >> 16;
@@ -523,7 +535,7 @@ struct StripRunner {
         // the target.  Every column up to it is complete in every strip (the
         // earlier strips are ahead), so the first column holding the maximum
         // is at or before it and the strip trackers hold it.
-        if (MODE == kModeGen && job.stop_u && last_strip && __any_sync(gmask, found)) return true;
+        if ((MODE == kModeGen || REV) && job.stop_u && last_strip && __any_sync(gmask, found)) return true;
         xh = __shfl_sync(gmask, H[R - 1], src);
         xf = __shfl_sync(gmask, f, src);
         xc = __shfl_sync(gmask, m, src);
@@ -576,6 +588,21 @@ struct StripRunner {
             if constexpr (L::FOLD) {
                 c_lo = (int)(int16_t)(cpk & 0xFFFFu);
                 c_hi = (int)(int16_t)(cpk >> 16);
+            }
+        } else if (MAYBE_MULTI && L::FOLD && job.stop_u && n <= kFastMaxCols) {
+            // steady reversed steps: no max array, the tracker's columns packed
+            if constexpr (L::FOLD) {
+                cpk = ((uint32_t)c_hi << 16) | ((uint32_t)c_lo & 0xFFFFu);
+                bool stop = false;
+#pragma unroll kUnrollGen
+                for (; s < s1 && s < s_drain; s++)
+                    if (step<false, kModeRev>(s)) {
+                        stop = true;
+                        break;
+                    }
+                c_lo = (int)(int16_t)(cpk & 0xFFFFu);
+                c_hi = (int)(int16_t)(cpk >> 16);
+                if (stop) return true;
             }
         } else if (MAYBE_MULTI && fwd && st > 0 && (!L::FOLD || n <= kFastMaxCols)) {
             if constexpr (L::FOLD) cpk = ((uint32_t)c_hi << 16) | ((uint32_t)c_lo & 0xFFFFu);
