@@ -219,7 +219,7 @@ struct BandStrip {
                 const int holeft = HO[r];  // H(i, j-1) - O: where E(i, j) opens
                 const int e = E[r];
                 const int dw = diag + w[r];  // H(i-1, j-1) + W(q_i, t_j)
-                const int h = max(max(dw, e), f);
+                const int h = __vimax3_s32(dw, e, f);  // three-input max, one instruction
                 // one compare and one predicated or per bit
                 uint32_t &bw = bits[r / 8];
                 const int sh = 4 * (r % 8);
@@ -228,8 +228,8 @@ struct BandStrip {
                 or_if_ne(bw, e, holeft, 4u << sh);  // E(i, j) extends, not opened
                 or_if_ne(bw, f, houp, 8u << sh);    // F(i, j) extends, not opened
                 const int ho = h - O;
-                E[r] = max(ho, e - X);
-                f = max(ho, f - X);
+                E[r] = __viaddmax_s32(e, -X, ho);  // max(e - X, ho), one instruction
+                f = __viaddmax_s32(f, -X, ho);
                 diag = holeft;
                 houp = ho;
                 HO[r] = ho;
