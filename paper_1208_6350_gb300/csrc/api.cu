@@ -436,7 +436,12 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
         GSW_TRY(fill(kFillForward));
         GSW_TRY(mark(ctx, 2, st));
         S.stage_done[0] = S.stage_done[1] = 1;
-        if (!(bv.flags & GSW_FORCE_S32)) {
+        // a local score is at most min(m, n) x the largest matrix entry (gaps
+        // never add), so when that stays within the 16-bit lanes' bound no
+        // pair was flagged for the 32-bit refill and its plan and launches
+        // are left out
+        const bool may_overflow = (long long)std::min(maxm, maxn) * std::max(sc.wmax, 0) > 32767 - sc.wmax;
+        if (!(bv.flags & GSW_FORCE_S32) && may_overflow) {
             GSW_TRY(plan(kFillRerun));
             GSW_TRY(fill(kFillRerun));
             S.stage_done[2] = 1;
