@@ -456,17 +456,20 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
         GSW_TRY(mark(ctx, 4, st));
         if (bv.flags & (GSW_BEGIN | GSW_CIGAR)) {
             // thread-per-pair banded reverse and traceback for narrow bands
+            // (the plan also hands a small batch's pairs to the warp tracebacks)
             GSW_TRY(plan(kPlanBand));
-            const int rows_cap = std::min(std::max(maxm, 1), kBandMaxRows);
-            // a quarter of what is left: the band scratch holds every row of
-            // the pairs in flight
-            const size_t have = room(ctx, ctx->band_scr, ctx->misc) + ctx->misc.bytes;  // budget left without band_scr
-            const BandGrids bg = band_grids(rows_cap, ctx->sms, have / 4);
-            if (bg.total_bytes > ctx->band_scr.bytes) release(ctx, ctx->band_scr);
-            GSW_TRY(ensure(ctx, ctx->band_scr, bg.total_bytes));
-            GSW_TRY(ensure_aux(ctx));
-            CUDA_TRY(launch_band(bv, sc, pb, ctx->band_scr.p, bg, st, ctx->aux));
-            S.launches += 3;
+            if (!small_batch(bv)) {  // a small batch's band classes are empty
+                const int rows_cap = std::min(std::max(maxm, 1), kBandMaxRows);
+                // a quarter of what is left: the band scratch holds every row of
+                // the pairs in flight
+                const size_t have = room(ctx, ctx->band_scr, ctx->misc) + ctx->misc.bytes;  // budget left without band_scr
+                const BandGrids bg = band_grids(rows_cap, ctx->sms, have / 4);
+                if (bg.total_bytes > ctx->band_scr.bytes) release(ctx, ctx->band_scr);
+                GSW_TRY(ensure(ctx, ctx->band_scr, bg.total_bytes));
+                GSW_TRY(ensure_aux(ctx));
+                CUDA_TRY(launch_band(bv, sc, pb, ctx->band_scr.p, bg, st, ctx->aux));
+                S.launches += 3;
+            }
             S.stage_done[4] = 1;
         }
         GSW_TRY(mark(ctx, 5, st));
