@@ -423,11 +423,18 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
             S.launches += 3;
             return GSW_OK;
         };
+        // a local score is at most min(m, n) x the largest matrix entry (gaps
+        // never add), so when that stays within the 16-bit lanes' bound no
+        // pair is flagged for the 32-bit refill
+        const bool force_s32 = (bv.flags & GSW_FORCE_S32) != 0;
+        const bool may_overflow = (long long)std::min(maxm, maxn) * std::max(sc.wmax, 0) > 32767 - sc.wmax;
         auto fill = [&](int32_t mode) -> int {
             fl.mode = mode;
+            // the classes the plan can have used, from the longest query
+            fl.class_mask = fill_class_mask(mode, maxm, sc, force_s32, force_s32 || may_overflow);
             cudaError_t e = launch_fill(fl, ctx->sms, S.max_blocks, st);
             if (e != cudaSuccess) return set_err(GSW_ECUDA, "fill: %s", cudaGetErrorString(e));
-            S.launches += kNumFillClasses;
+            S.launches += __builtin_popcount(fl.class_mask);
             return GSW_OK;
         };
         GSW_TRY(mark(ctx, 0, st));
@@ -436,12 +443,8 @@ int run_pipeline(gsw_ctx *ctx, BatchView bv, const Scoring &sc, cudaStream_t st,
         GSW_TRY(fill(kFillForward));
         GSW_TRY(mark(ctx, 2, st));
         S.stage_done[0] = S.stage_done[1] = 1;
-        // a local score is at most min(m, n) x the largest matrix entry (gaps
-        // never add), so when that stays within the 16-bit lanes' bound no
-        // pair was flagged for the 32-bit refill and its plan and launches
-        // are left out
-        const bool may_overflow = (long long)std::min(maxm, maxn) * std::max(sc.wmax, 0) > 32767 - sc.wmax;
-        if (!(bv.flags & GSW_FORCE_S32) && may_overflow) {
+        // no pair flagged for the refill: its plan and launches are left out
+        if (!force_s32 && may_overflow) {
             GSW_TRY(plan(kFillRerun));
             GSW_TRY(fill(kFillRerun));
             S.stage_done[2] = 1;

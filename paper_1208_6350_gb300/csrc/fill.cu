@@ -1219,6 +1219,7 @@ int long_occupancy(int A) {
 template <bool DNA, bool S32>
 cudaError_t launch_long(const FillLaunch &fl, int sms, int max_blocks, cudaStream_t st) {
     using C = LongCfg<DNA, S32>;
+    if (!((fl.class_mask >> C::CLS) & 1u)) return cudaSuccess;  // no pair of the class
     const size_t sm = long_smem_bytes<DNA, S32>(fl.sc.A);
     const int nb = long_occupancy<DNA, S32>(fl.sc.A);
     if (nb < 1) return cudaErrorInvalidConfiguration;
@@ -1247,6 +1248,7 @@ int occupancy(int A) {
 
 template <bool DNA, int VID>
 cudaError_t launch_one(const FillLaunch &fl, int sms, int max_blocks, cudaStream_t st) {
+    if (!((fl.class_mask >> VID) & 1u)) return cudaSuccess;  // no pair of the class
     const size_t sm = smem_bytes<DNA, VID>(fl.sc.A);
     int nb = occupancy<DNA, VID>(fl.sc.A);
     if (nb < 1) return cudaErrorInvalidConfiguration;

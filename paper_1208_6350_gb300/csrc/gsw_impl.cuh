@@ -122,6 +122,61 @@ __host__ __device__ inline int variant_rows(int v) {
     return x.s32 ? x.P * x.R : 2 * x.P * x.R;
 }
 
+// The smallest one-strip 16-lane variant holding a query of `rows`, or the
+// tallest (several strips).
+__host__ __device__ inline int pick_s16(int rows) {
+    for (int v = 0; v <= kVarMaxS16; v++)
+        if (variant_rows(v) >= rows) return v;
+    return kVarMaxS16;
+}
+
+// 16-bit fill class of a query of `rows` (>= 1): the tuned class of its
+// bucket, else the smallest one-strip variant, or the CTA class for queries
+// of many strips.
+__host__ __device__ inline int pick_class16(int rows, const Scoring &sc) {
+    const int b = (rows - 1) / GSW_TUNE_ROWS;
+    if (rows >= 1 && b < GSW_TUNE_BUCKETS && sc.fill_class[b] >= 0) {
+        const int c = sc.fill_class[b];  // public codes: 0..6, 8 CTA, 9..13 8-lane variants
+        return c == 8 ? kClassLong16 : (c >= 9 ? kVarP8First + (c - 9) : c);
+    }
+    return long_pair(rows, false, sc.dna4) ? kClassLong16 : pick_s16(rows);
+}
+
+// Class of the reversed fill of a query whose end row is rows - 1 (plan.cu):
+// the forward rule, or the 32-bit classes for a pair in 32-bit lanes; a DNA
+// query of several strips reverses in the CTA kernel.
+__host__ __device__ inline int pick_class_reverse(int rows, bool s32, const Scoring &sc) {
+    int v = s32 ? (long_pair(rows, true, sc.dna4) ? kClassLong32 : kVarS32) : pick_class16(rows, sc);
+    if (sc.dna4 && v != kClassLong16 && v != kClassLong32 && rows > variant_rows(v))
+        v = v == kVarS32 ? kClassLong32 : kClassLong16;
+    return v;
+}
+
+// The fill classes a launch of `mode` can meet when no query has more than
+// maxm rows (a superset; each fill launch leaves the other classes out).
+// force_s32: the batch runs in 32-bit lanes; s32: some pair may have been
+// refilled in 32-bit lanes.  Empty pairs of the forward fill take class 0.
+inline uint32_t fill_class_mask(int mode, int maxm, const Scoring &sc, bool force_s32, bool s32) {
+    uint32_t m = 0;
+    const int upto = maxm < GSW_TUNE_BUCKETS * GSW_TUNE_ROWS ? maxm : GSW_TUNE_BUCKETS * GSW_TUNE_ROWS;
+    if (mode == kFillForward && force_s32) return (1u << kVarS32) | (1u << kClassLong32);
+    if (mode == kFillRerun) return (1u << kVarS32) | (1u << kClassLong32);
+    if (mode == kFillForward) m |= 1u << 0;
+    for (int r = 1; r <= upto; r++) {
+        if (mode == kFillForward) {
+            m |= 1u << pick_class16(r, sc);
+        } else {
+            m |= 1u << pick_class_reverse(r, false, sc);
+            if (s32) m |= 1u << pick_class_reverse(r, true, sc);
+        }
+    }
+    if (maxm > upto) {  // past the tuned buckets: the tallest variant or the CTA classes
+        m |= (1u << kVarMaxS16) | (1u << kClassLong16);
+        if (s32 && mode != kFillForward) m |= (1u << kVarS32) | (1u << kClassLong32);
+    }
+    return m;
+}
+
 // Work plan of one fill launch: pairs sorted by (variant, cost descending),
 // cut into warp tasks of 32/P pairs of one variant.  Task indices are handed
 // out heaviest variant first (variant index descending).
@@ -148,6 +203,7 @@ struct FillLaunch {
     FillPlan plan;
     FillScratch scr;
     int32_t mode;
+    uint32_t class_mask;  // classes launched (bit c: class c); the others hold no pair
     // nonzero once the batch's letter check found a code >= the alphabet
     // (written by the check, which runs first on the stream): the fill then
     // writes empty records and touches no letter, so its steady steps need

@@ -14,23 +14,6 @@ namespace {
 
 constexpr int kScanThreads = 1024;
 
-__device__ __forceinline__ int pick_s16(int rows) {
-    for (int v = 0; v <= kVarMaxS16; v++)
-        if (variant_rows(v) >= rows) return v;
-    return kVarMaxS16;  // several strips
-}
-
-// 16-bit fill class of a query of `rows`: the tuned class of its bucket, else
-// the smallest one-strip variant, or the CTA class for queries of many strips.
-__device__ __forceinline__ int pick_class16(int rows, const Scoring &sc) {
-    const int b = (rows - 1) / GSW_TUNE_ROWS;
-    if (rows >= 1 && b < GSW_TUNE_BUCKETS && sc.fill_class[b] >= 0) {
-        const int c = sc.fill_class[b];  // public codes: 0..6, 8 CTA, 9..13 8-lane variants
-        return c == 8 ? kClassLong16 : (c >= 9 ? kVarP8First + (c - 9) : c);
-    }
-    return long_pair(rows, false, sc.dna4) ? kClassLong16 : pick_s16(rows);
-}
-
 
 __device__ __forceinline__ int cost_bin(long long cost) {
     // 32 bins per doubling of cost, descending order inside a variant
@@ -48,7 +31,7 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
         rows = b.q_len[p];
         cols = b.t_len[p];
         if (b.flags & GSW_FORCE_S32) v = (cols > 0 && long_pair(rows, true, sc.dna4)) ? kClassLong32 : kVarS32;
-        else v = cols > 0 ? pick_class16(rows, sc) : pick_s16(rows);
+        else v = (cols > 0 && rows > 0) ? pick_class16(rows, sc) : 0;  // (any class writes an empty pair's record)
     } else if (mode == kFillRerun) {
         if (!(b.res[p].flags & kResPendingS32)) { keys[p] = -1; return; }
         rows = b.q_len[p];
@@ -66,16 +49,13 @@ __global__ void k_plan_keys(BatchView b, Scoring sc, int32_t mode, int32_t *keys
             return;
         }
         cols = reverse_window(r.read_end1, r.ref_end1, r.score1, sc);
-        if (r.flags & GSW_RES_S32) v = long_pair(rows, true, sc.dna4) ? kClassLong32 : kVarS32;
-        else v = pick_class16(rows, sc);
         // a query of several strips reverses in the CTA kernel: its strips run
         // concurrently, so the stop at the first column reaching score1 (often
         // a few dozen columns into a window of thousands) ends every strip,
         // where a group would finish the upper strips over the whole window
-        // before the last one starts
-        // (4-letter DNA: a general alphabet's CTA holds 4 warps per SM)
-        if (sc.dna4 && v != kClassLong16 && v != kClassLong32 && rows > variant_rows(v))
-            v = v == kVarS32 ? kClassLong32 : kClassLong16;
+        // before the last one starts (4-letter DNA: a general alphabet's CTA
+        // holds 4 warps per SM)
+        v = pick_class_reverse(rows, (r.flags & GSW_RES_S32) != 0, sc);
     } else if (mode == kPlanTrace) {
         const gsw_result r = b.res[p];
         if (r.score1 <= 0 || !(r.flags & kResPendingTrace) || (r.flags & kResInternal) || r.read_begin1 < 0) {

@@ -1,7 +1,7 @@
 // C entry points over the library's host-side geometry rules (gsw_impl.cuh),
 // compiled by g++ for the CPU tests of those rules: the reverse fill's window
-// and band, the traceback band, the traceback class routing, and the status a
-// batch returns from its kernels' counts.
+// and band, the traceback band, the traceback class routing, the fill classes
+// and the launch mask, and the status a batch returns from its kernels' counts.
 #include "gsw_impl.cuh"
 
 namespace {
@@ -24,6 +24,21 @@ gsw::Scoring scoring(int A, const signed char *W, int O, int X) {
 }  // namespace
 
 extern "C" {
+
+// fill class of a pair (mode 0 forward, 2 reverse) under a tune table
+// (GSW_TUNE_BUCKETS codes, -1: default rule)
+int hr_pick_class(int A, const signed char *W, int O, int X, const signed char *table, int mode, int rows, int s32) {
+    gsw::Scoring sc = scoring(A, W, O, X);
+    for (int b = 0; b < GSW_TUNE_BUCKETS; ++b) sc.fill_class[b] = table[b];
+    return mode == gsw::kFillForward ? gsw::pick_class16(rows, sc) : gsw::pick_class_reverse(rows, s32 != 0, sc);
+}
+
+unsigned hr_fill_class_mask(int A, const signed char *W, int O, int X, const signed char *table, int mode, int maxm,
+                            int force_s32, int s32) {
+    gsw::Scoring sc = scoring(A, W, O, X);
+    for (int b = 0; b < GSW_TUNE_BUCKETS; ++b) sc.fill_class[b] = table[b];
+    return gsw::fill_class_mask(mode, maxm, sc, force_s32 != 0, s32 != 0);
+}
 
 int hr_reverse_window(int A, const signed char *W, int O, int X, int end_q, int end_t, int score1) {
     return gsw::reverse_window(end_q, end_t, score1, scoring(A, W, O, X));

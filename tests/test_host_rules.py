@@ -61,6 +61,10 @@ def lib(tmp_path_factory):
         getattr(L, name).restype = i32
     L.hr_t16_need_words.argtypes = [i32, i32, i32]
     L.hr_t16_need_words.restype = ctypes.c_longlong
+    L.hr_pick_class.argtypes = [i32, P, i32, i32, P, i32, i32, i32]
+    L.hr_pick_class.restype = i32
+    L.hr_fill_class_mask.argtypes = [i32, P, i32, i32, P, i32, i32, i32, i32]
+    L.hr_fill_class_mask.restype = ctypes.c_uint
     L.hr_batch_status.argtypes = [i32, ctypes.c_ulonglong, i32, ctypes.c_ulonglong, ctypes.c_longlong]
     L.hr_batch_status.restype = i32
     return L
@@ -512,3 +516,42 @@ def test_batch_status_precedence(lib):
     assert st(0, 5, 0, 0, 0) == gsw.GSW_EINTERNAL
     assert st(1, 5, 1, 11, 10) == gsw.GSW_EINVAL      # bad input first
     assert st(1, 0, 0, 0, 0) == gsw.GSW_EINVAL
+
+
+def test_fill_launch_mask_holds_every_class_the_plan_can_pick(lib):
+    """Each fill launch leaves out the classes outside a mask computed on the
+    host from the longest query: every class the plan picks for a query of at
+    most that many rows (forward; reverse with and without 32-bit pairs; any
+    tune table, including the CTA class for short buckets) is in the mask, and
+    a short-read batch under a one-class table launches few classes."""
+    rng = np.random.default_rng(77)
+    codes = [-1, 0, 1, 2, 3, 4, 5, 6, 8, 9, 10, 11, 12, 13]
+    for A, W in ((4, dna(2, -3)), (20, protein_like(rng))):
+        Wc = np.ascontiguousarray(W.astype(np.int8))
+        Wp = Wc.ctypes.data_as(ctypes.c_void_p)
+        for trial in range(40):
+            table = np.full(32, -1, np.int8)
+            if trial % 4:
+                table[:] = rng.choice(codes, 32)
+            tp = table.ctypes.data_as(ctypes.c_void_p)
+            maxm = int(rng.choice([1, 31, 100, 250, 1024, 1025, 1800, 5000, 30000]))
+            for mode in (0, 2):
+                for s32 in (0, 1):
+                    if mode == 0 and s32:
+                        continue
+                    mask = lib.hr_fill_class_mask(A, Wp, 5, 2, tp, mode, maxm, 0, s32)
+                    rows = set(rng.integers(1, maxm + 1, 300).tolist()) | {1, maxm}
+                    for r in rows:
+                        for s in ((0, 1) if s32 else (0,)):
+                            c = lib.hr_pick_class(A, Wp, 5, 2, tp, mode, int(r), s)
+                            assert (mask >> c) & 1, (A, mode, maxm, r, s, c, bin(mask))
+                    if mode == 0:
+                        assert mask & 1  # empty pairs take class 0
+    # the short-read case: every bucket of up to 250 rows tuned to the 8-lane
+    # variants (public codes 9..13): the forward launch holds those and class 0
+    W = np.ascontiguousarray(dna(2, -2).astype(np.int8))
+    table = np.full(32, -1, np.int8)
+    table[:8] = [9, 9, 9, 9, 10, 11, 12, 13]
+    m = lib.hr_fill_class_mask(4, W.ctypes.data_as(ctypes.c_void_p), 3, 1, table.ctypes.data_as(ctypes.c_void_p),
+                               0, 250, 0, 0)
+    assert bin(m).count("1") == 6
