@@ -130,14 +130,30 @@ __global__ void __launch_bounds__(kScanThreads) k_plan_scan(const int32_t *hist,
         loc[i] = sum;
         sum += hist[tid * PER + i];
     }
-    part[tid] = sum;
-    __syncthreads();
-    for (int d = 1; d < kScanThreads; d <<= 1) {
-        int32_t v = tid >= d ? part[tid - d] : 0;
-        __syncthreads();
-        part[tid] += v;
-        __syncthreads();
+    // inclusive scan of the threads' sums: within each warp by shuffles,
+    // then over the warp totals by the first warp
+    static_assert(kScanThreads == 32 * 32, "one warp scans the warp totals");
+    __shared__ int32_t wsum[32];
+    const int lane = tid & 31, warp = tid >> 5;
+    int32_t incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += v;
     }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = wsum[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t v = __shfl_up_sync(0xFFFFFFFFu, w, d);
+            if (lane >= d) w += v;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    part[tid] = incl + (warp > 0 ? wsum[warp - 1] : 0);
     const int32_t base = part[tid] - sum;
 #pragma unroll
     for (int i = 0; i < PER; i++) binoff[tid * PER + i] = base + loc[i];
