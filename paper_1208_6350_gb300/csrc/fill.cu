@@ -55,7 +55,7 @@ constexpr int kUnrollFast = 4;  // steady loop of one-strip forward fills
 // the tracker's two columns as the signed 16-bit halves of one word: targets
 // up to this many columns take them
 constexpr int kFastMaxCols = 32768;
-constexpr int kUnrollGen = 2;   // other steady loops
+constexpr int kUnrollGen = 4;   // other steady loops
 // forms of the strip step (StripRunner::step)
 constexpr int kModeGen = 0, kModeFast = 1, kModeFwdFirst = 2, kModeFwdLater = 3, kModeRev = 4;
 
