@@ -421,7 +421,8 @@ int fill_slots(const Scoring &sc, int sms);
 // Largest number of pairs a warp of a fill variant holds at once (32 / P for
 // the narrowest group): the slots a capped launch needs per warp.
 int fill_max_pairs_per_warp();
-// one persistent launch per variant, heaviest first; each grid capped at max_blocks
+// one persistent launch per class in fl.class_mask, heaviest first; each grid
+// capped at max_blocks and at the slots the scratch holds
 cudaError_t launch_fill(const FillLaunch &fl, int sms, int max_blocks, cudaStream_t st);
 
 struct PlanBuffers {
